@@ -1,0 +1,151 @@
+/*
+ * s2dw.h -- C ABI of the GB300 directional scale-discretized wavelet transform.
+ *
+ * The transform is the one of McEwen, Vandergheynst & Wiaux, "On the
+ * computation of directional scale-discretized wavelet transforms on the
+ * sphere" (2013):
+ *   analysis  W^j(alpha,beta,gamma) = sum_{l<L,m,n} f_lm Psi^j*_ln D^l*_mn
+ *             (Sec. 3.2, Eq. (20)), scaling coefficients W^Phi (Eqs. (3), (31));
+ *   synthesis f_lm from W^j and W^Phi (Sec. 3.3, Eqs. (32)-(41)),
+ * both exact on the Driscoll-Healy SO(3) grid of Sec. 3.1 and computed by the
+ * factoring of rotations (Eq. (25)) and a separation of variables.
+ *
+ * Conventions shared by every entry point:
+ *   - Signals are real on the sphere: f_{l,-m} = (-1)^m conj(f_lm).  Analysis
+ *     reads only m >= 0; synthesis writes every m (m < 0 by that symmetry).
+ *   - f_lm: flat array indexed l*l + l + m, |m| <= l < L.
+ *   - W:  real array [J+1][N][2L][2L-1] = [scale j][gamma_g][beta_b][alpha_a],
+ *         alpha_a = 2 pi a/(2L-1), beta_b = pi (2b+1)/(4L), gamma_g = pi g/N
+ *         (Sec. 3.1).  Scale j = 0 is the finest.
+ *   - Wphi: real array [2L][2L-1] = [theta_t][phi_p] on the same grid.
+ *   - Precision: S2DW_FP64 plans take complex128 f and double W / Wphi;
+ *     S2DW_MIXED plans take complex64 f and float W / Wphi (FP32 arithmetic,
+ *     Wigner Delta generated in FP64 and stored in FP32).
+ *   - Ownership: the caller owns every f / W / Wphi buffer; the plan owns its
+ *     device workspace; the process owns the shared Delta table (reference
+ *     counted, freed with the last plan).
+ *   - Device buffers must be 16-byte aligned (cudaMalloc / torch give 256).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream); they never synchronise the device except where noted.
+ *   - Every entry point returns S2DW_OK (0) or a negative status; nothing
+ *     throws or exits across the ABI.  s2dw_strerror gives static text.
+ *   - A plan must not run two calls concurrently (its workspace is shared
+ *     between calls); use one plan per stream for concurrency.
+ */
+#ifndef S2DW_H
+#define S2DW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  S2DW_OK = 0,
+  S2DW_EINVAL = -1,   /* invalid argument (sizes, flags, NULL pointers)   */
+  S2DW_ENOMEM = -2,   /* device allocation failed                          */
+  S2DW_ECUDA = -3,    /* a CUDA call or kernel launch failed               */
+  S2DW_ETIMEOUT = -4, /* a bounded device wait ran out                     */
+  S2DW_EBUSY = -5,    /* resource in use                                   */
+  S2DW_ENOTSUP = -6   /* valid request outside what this build supports    */
+};
+
+enum {
+  S2DW_FP64 = 1,        /* plain float64 path                              */
+  S2DW_MIXED = 2,       /* float32 arithmetic, FP64-generated Delta        */
+  S2DW_REAL_SIGNAL = 4  /* real signals (required; set implicitly)         */
+};
+
+typedef struct s2dw_plan_s* s2dw_plan_t;
+
+/*
+ * s2dw_plan: create a plan for band-limit L, azimuthal band-limit N,
+ * dilation lambda and J0.
+ *   Scales: J_max = ceil(log_lambda L) (Sec. 2.2), J = J_max - J0, wavelet
+ *   scales j = 0..J; the scaling function Phi covers the rest (Eq. (16)).
+ *   Kernels: Psi^j_ln = kappa^j(l) s_ln (Eqs. (7), (11)-(15)).
+ * Valid ranges: 2 <= L <= 2048, 1 <= N <= min(8, L), lambda > 1 (at most 64
+ * scales), 0 <= J0 <= J_max; flags = exactly one of S2DW_FP64 / S2DW_MIXED,
+ * optionally | S2DW_REAL_SIGNAL.  Otherwise S2DW_EINVAL.
+ * Work: evaluates the kernels, the DH weights (Eq. (18)) and the Delta table
+ * on the device (FP64 recursion, grown to cover l < L on first need) and
+ * allocates the workspace.  Synchronises the device before returning.
+ * *out receives the plan; on failure *out is NULL and nothing leaks.
+ */
+int s2dw_plan(s2dw_plan_t* out, int L, int N, double lambda, int J0, unsigned flags);
+
+/* Release a plan (NULL is accepted).  Synchronises the device first. */
+int s2dw_plan_destroy(s2dw_plan_t plan);
+
+/*
+ * s2dw_query: sizes of a plan, any pointer may be NULL.
+ *   J: largest scale index (scales 0..J);
+ *   w_elems_per_scale: N * 2L * (2L-1);  wphi_elems: 2L * (2L-1);
+ *   workspace_bytes: device bytes owned by the plan (intermediates, tables);
+ *   total_device_bytes: workspace_bytes + the caller's f, W, Wphi bytes for
+ *   one transform (used for admission by HBM footprint).
+ */
+int s2dw_query(s2dw_plan_t plan, int* J, int64_t* w_elems_per_scale, int64_t* wphi_elems,
+               int64_t* workspace_bytes, int64_t* total_device_bytes);
+
+/*
+ * s2dw_kernels: copy the plan's kernels to HOST memory (synchronous).
+ *   psi: complex128 as interleaved doubles [J+1][L][N][2]: Psi^j_{l,n_k},
+ *        n_k = -(N-1) + 2k  (Eq. (7));  phi: double [L]: Phi_l0 (Eq. (16)).
+ * Either pointer may be NULL.
+ */
+int s2dw_kernels(s2dw_plan_t plan, double* psi, double* phi);
+
+/*
+ * s2dw_analysis: wavelet and scaling coefficients of f (device pointers).
+ *   f: [L*L] complex (m >= 0 read);  W: [J+1][N][2L][2L-1] real;
+ *   Wphi: [2L][2L-1] real.  Sec. 3.2: the l-contraction into the Fourier
+ *   cube (Eq. (27)), then the gamma, beta and alpha sums (Eqs. (28)-(30)).
+ */
+int s2dw_analysis(s2dw_plan_t plan, const void* flm, void* W, void* Wphi, void* stream);
+
+/*
+ * s2dw_synthesis: f_lm from W and Wphi (device pointers; same layouts).
+ *   Sec. 3.3: alpha (Eq. (37)), gamma (Eq. (39)), beta (Eq. (40))
+ *   quadratures, then the Delta contraction (Eqs. (34), (32)) and the
+ *   scaling term (Eq. (41)).  Writes every (l, m).
+ */
+int s2dw_synthesis(s2dw_plan_t plan, const void* W, const void* Wphi, void* flm, void* stream);
+
+/*
+ * Batched forms: njobs transforms, each with its own plan (plans may differ
+ * in L, N, lambda and precision, but must all be distinct objects), run as
+ * one set of launches per stage (grouped by N and precision).  Arrays are
+ * HOST arrays of njobs device pointers.  Same layouts as the single calls.
+ */
+int s2dw_analysis_batch(const s2dw_plan_t* plans, const void* const* flm, void* const* W,
+                        void* const* Wphi, int njobs, void* stream);
+int s2dw_synthesis_batch(const s2dw_plan_t* plans, const void* const* W, const void* const* Wphi,
+                         void* const* flm, int njobs, void* stream);
+
+/* Static text for a status code. */
+const char* s2dw_strerror(int status);
+
+/*
+ * Introspection used by the tests (synchronous, host outputs).
+ *   s2dw_scale_support: l-range [lo, hi] on which kappa^j(l) > 0 (j = J+1
+ *     gives Phi's range, lo = 0).
+ *   s2dw_delta_slab: Delta^l_{m'm} = d^l_{m'm}(pi/2) (below Eq. (25)) for
+ *     0 <= m', m <= l from the FP64 table, into a host [l+1][l+1] array;
+ *     requires l < L of the plan.
+ *   s2dw_stage: copy intermediate `stage` of scale j from the last call on
+ *     this plan into host memory: 0 = analysis Fourier cube after the gamma
+ *     step, complex [N][Lj][Lj] (m' rows, m >= 0 columns); 1 = after the beta
+ *     step, complex [N][2L][Lj]; *nbytes gets the size; host may be NULL to
+ *     query only.  Scale j = J+1 is the scaling part (N = 1).
+ */
+int s2dw_scale_support(s2dw_plan_t plan, int j, int* lo, int* hi);
+int s2dw_delta_slab(s2dw_plan_t plan, int l, double* host_out);
+int s2dw_stage(s2dw_plan_t plan, int stage, int j, void* host_out, int64_t* nbytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* S2DW_H */

@@ -1,0 +1,105 @@
+"""Planted mistakes in the CPU oracle must make at least one pin fail.
+
+Each case replaces one oracle function by a plausible wrong variant (a
+transposed operand, a dropped term, a wrong sign or grid) and runs a set of
+the pins of test_oracle_pins.py; the mistake must be caught.  CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.s2dw_oracle as OS
+import tests.test_oracle_pins as P
+
+_orig_wigner_d = OS.wigner_d
+_orig_kernels = OS.kernels
+_orig_dh = OS.dh_weights
+_orig_grids = OS.grids
+_orig_k = OS.k_lambda
+
+
+def _wigner_transposed(beta, L, m, n):
+    return _orig_wigner_d(beta, L, n, m)
+
+
+_orig_rows = OS.analysis_rows
+_orig_synth = OS.synthesis
+
+
+def _analysis_noconj(flm, L, N, lam, J0, b_list, kern=None):
+    psi, phi = kern if kern is not None else _orig_kernels(L, N, lam, J0)
+    return _orig_rows(flm, L, N, lam, J0, b_list, (np.conj(psi), phi))
+
+
+def _synthesis_conj(W, Wphi, L, N, lam, J0, kern=None):
+    psi, phi = kern if kern is not None else _orig_kernels(L, N, lam, J0)
+    return _orig_synth(W, Wphi, L, N, lam, J0, (np.conj(psi), phi))
+
+
+def _dh_no_sin(L):
+    _, theta, _ = _orig_grids(L, 1)
+    k = np.arange(L)
+    s = np.sin(np.outer(theta, 2 * k + 1)) / (2 * k + 1)
+    return 2.0 / L * s.sum(axis=1)
+
+
+def _grids_gamma_2pi(L, N):
+    a, b, g = _orig_grids(L, N)
+    return a, b, 2.0 * g
+
+
+def _grids_alpha_2L(L, N):
+    a, b, g = _orig_grids(L, N)
+    return 2.0 * np.pi * np.arange(2 * L - 1) / (2 * L), b, g
+
+
+def _k_bad_norm(t, lam):
+    t = float(t)
+    if t <= 1.0 / lam:
+        return 1.0
+    if t >= 1.0:
+        return 0.0
+    return OS._I(t, lam) / OS._I(1.0 / lam, lam) * 0.9
+
+
+def _wigner_sign(beta, L, m, n):
+    return _orig_wigner_d(beta, L, m, -np.asarray(n))
+
+
+PINS = [
+    lambda: P.test_single_mode_analysis_closed_form(3, 2.0, 0),
+    lambda: P.test_single_mode_analysis_closed_form(2, 2.0, 1),
+    lambda: P.test_single_mode_synthesis_closed_form(3),
+    lambda: P.test_single_mode_synthesis_closed_form(4),
+    lambda: P.test_round_trip_exact(8, 3, 2.0, 0, "unit"),
+    lambda: P.test_round_trip_exact(16, 2, 2.0, 1, "uniform"),
+    lambda: P.test_wigner_closed_forms(),
+    lambda: P.test_dh_weights(5),
+    lambda: P.test_k_lambda_limits_and_derivative(),
+    lambda: P.test_realness_and_steerability(),
+]
+
+
+@pytest.mark.parametrize("name,attr,bad", [
+    ("transposed d operand", "wigner_d", _wigner_transposed),
+    ("analysis without conj(Psi)", "analysis_rows", _analysis_noconj),
+    ("synthesis with conj(Psi)", "synthesis", _synthesis_conj),
+    ("DH weights without sin(theta)", "dh_weights", _dh_no_sin),
+    ("gamma grid on [0, 2pi)", "grids", _grids_gamma_2pi),
+    ("alpha grid 2L points", "grids", _grids_alpha_2L),
+    ("k_lambda normalisation", "k_lambda", _k_bad_norm),
+    ("sign of n in d", "wigner_d", _wigner_sign),
+])
+def test_planted_mistake_is_caught(monkeypatch, name, attr, bad):
+    monkeypatch.setattr(OS, attr, bad)
+    monkeypatch.setattr(O, attr, bad)
+    OS._I.cache_clear()
+    caught = 0
+    for pin in PINS:
+        try:
+            pin()
+        except (AssertionError, KeyError, ValueError, IndexError):
+            caught += 1
+    assert caught > 0, f"planted mistake '{name}' passed every pin"

@@ -1,0 +1,338 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by textbook closed
+forms (independent of the oracle's own code paths).  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1308_5706_gb300.inputs import flm_gaussian, flm_uniform
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --- closed-form Wigner d (textbook, Varshalovich et al. 1989 Table 4.3) ----
+
+def d_closed(l, m, n, b):
+    """d^l_mn(beta) for l <= 2 from the tabulated closed forms; negative
+    indices by d_mn = (-1)^(m-n) d_nm = d_{-n,-m}."""
+    c, s = math.cos(b), math.sin(b)
+    base = {
+        (0, 0, 0): 1.0,
+        (1, 1, 1): (1 + c) / 2, (1, 1, 0): -s / math.sqrt(2), (1, 1, -1): (1 - c) / 2,
+        (1, 0, 0): c,
+        (2, 2, 2): ((1 + c) / 2) ** 2, (2, 2, 1): -(1 + c) * s / 2,
+        (2, 2, 0): math.sqrt(3.0 / 8.0) * s * s, (2, 2, -1): -(1 - c) * s / 2,
+        (2, 2, -2): ((1 - c) / 2) ** 2,
+        (2, 1, 1): (1 + c) * (2 * c - 1) / 2, (2, 1, 0): -math.sqrt(1.5) * s * c,
+        (2, 1, -1): (1 - c) * (2 * c + 1) / 2, (2, 0, 0): (3 * c * c - 1) / 2,
+    }
+    for key, sign in (((l, m, n), 1.0), ((l, n, m), (-1.0) ** (m - n)),
+                      ((l, -n, -m), 1.0), ((l, -m, -n), (-1.0) ** (m - n))):
+        if key in base:
+            return sign * base[key]
+    raise KeyError((l, m, n))
+
+
+def D_closed(l, m, n, a, b, g):
+    """D^l_mn(alpha, beta, gamma) = e^{-im alpha} d^l_mn(beta) e^{-in gamma} (Eq. (24))."""
+    return np.exp(-1j * m * a) * d_closed(l, m, n, b) * np.exp(-1j * n * g)
+
+
+# --- scales and kernels (Sec. 2.2) -------------------------------------------
+
+def test_jmax_values():
+    assert O.j_max(1024, 2.0) == 10
+    assert O.j_max(32, 2.0) == 5
+    assert O.j_max(128, 2.0) == 7
+    assert O.j_max(1000, 3.0) == 7          # 3^6 = 729 < 1000 <= 2187
+    assert O.j_max(2, 2.0) == 1
+
+
+def test_support_golden_and_kernel_zeros():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "supports_L1024_lam2.txt"))
+            if not ln.startswith("#")]
+    assert rows[0] == ["Jmax", "10"]
+    L, lam = 1024, 2.0
+    for j, lo, hi in ((int(a), int(b), int(c)) for a, b, c in rows[1:]):
+        assert O.support(j, L, lam) == (lo, hi)
+        # kappa^j vanishes at and outside the support ends, is positive inside
+        for l in (lo, min(hi, L - 1) if hi < L else None):
+            if l is not None and l < L:
+                assert O.kappa(j, l, L, lam) == 0.0
+        mid = int(round(lam ** (-j) * L))
+        if 0 < mid < L:
+            assert abs(O.kappa(j, mid, L, lam) - 1.0) < 1e-14     # peak of unity at lam^-j L
+        # strictly inside the support kappa^j > 0 (checked a tenth of the way in;
+        # right at the ends exp(-1/(1-x^2)) underflows in float64)
+        inner = lo + max(1, (min(hi, L - 1) - lo) // 10)
+        if inner < min(hi, L):
+            assert O.kappa(j, inner, L, lam) > 0.0
+
+
+def test_k_lambda_limits_and_derivative():
+    for lam in (2.0, 3.0, 1.5):
+        assert O.k_lambda(0.5 / lam, lam) == 1.0
+        assert O.k_lambda(1.0 / lam, lam) == 1.0
+        assert O.k_lambda(1.0, lam) == 0.0
+        assert O.k_lambda(1.3, lam) == 0.0
+        # I(1/lam) by an independent rule: composite Simpson on 200001 points
+        u = np.linspace(1.0 / lam, 1.0, 200001)
+        f = O.s_lambda(u, lam) ** 2 / u
+        h = u[1] - u[0]
+        I0 = h / 3 * (f[0] + f[-1] + 4 * f[1:-1:2].sum() + 2 * f[2:-1:2].sum())
+        for t in np.linspace(1.0 / lam, 1.0, 9)[1:-1]:
+            eps = 1e-5
+            dk = (O.k_lambda(t + eps, lam) - O.k_lambda(t - eps, lam)) / (2 * eps)
+            expect = -float(O.s_lambda(t, lam)) ** 2 / t / I0
+            assert abs(dk - expect) < 1e-7 * max(1.0, abs(expect))
+            # monotone decrease
+            assert O.k_lambda(t, lam) > O.k_lambda(t + 0.01, lam)
+
+
+def test_directionality_coefficients():
+    for N in range(1, 9):
+        ns = O.n_orders(N)
+        for l in range(0, 20):
+            vals = np.array([O.s_dir(l, int(n), N) for n in range(-l - 2, l + 3)])
+            tot = float(np.sum(np.abs(vals) ** 2))
+            if l == 0:
+                assert tot == 0.0
+            else:
+                assert abs(tot - 1.0) < 1e-15
+            for n in range(-l - 2, l + 3):
+                if n not in ns:
+                    assert O.s_dir(l, n, N) == 0.0
+    # explicit values: N = 3 (eta = 1), l >= 2: gamma = 2
+    assert O.s_dir(5, 2, 3) == pytest.approx(0.5, abs=1e-16)
+    assert O.s_dir(5, 0, 3) == pytest.approx(math.sqrt(0.5), abs=1e-16)
+    # N = 2 (eta = i), l >= 1: gamma = 1, n = +-1: i/sqrt(2)
+    assert abs(O.s_dir(4, 1, 2) - 1j / math.sqrt(2)) < 1e-15
+    # N = 3 at l = 1: gamma = min(2, 1 - 1) = 0 -> only n = 0, s = 1
+    assert O.s_dir(1, 0, 3) == pytest.approx(1.0, abs=1e-16)
+    assert O.s_dir(1, 2, 3) == 0.0
+
+
+@pytest.mark.parametrize("L,N,lam,J0", [(32, 3, 2.0, 0), (64, 5, 2.0, 1), (50, 4, 3.0, 0),
+                                        (40, 2, 1.5, 2), (128, 3, 2.0, 2), (1024, 5, 2.0, 0)])
+def test_admissibility(L, N, lam, J0):
+    psi, phi = O.kernels(L, N, lam, J0)
+    total = phi ** 2 + (np.abs(psi) ** 2).sum(axis=(0, 2))
+    # Eq. (6) for every l < L, including l = 0 (carried by Phi)
+    assert np.abs(total - 1.0).max() < 2e-15
+
+
+# --- quadrature (Sec. 3.1) ----------------------------------------------------
+
+@pytest.mark.parametrize("L", [2, 5, 16, 33])
+def test_dh_weights(L):
+    q = O.dh_weights(L)
+    _, theta, _ = O.grids(L, 1)
+    assert abs(q.sum() - 2.0) < 1e-14
+    for k in range(0, 2 * L):
+        exact = 0.0 if k == 1 else (1 + math.cos(k * math.pi)) / (1 - k * k)
+        assert abs(np.sum(q * np.cos(k * theta)) - exact) < 1e-13
+    from scipy.special import eval_legendre
+    x = np.cos(theta)
+    for l in range(L):
+        for lp in range(L):
+            got = np.sum(q * eval_legendre(l, x) * eval_legendre(lp, x))
+            assert abs(got - (2.0 / (2 * l + 1) if l == lp else 0.0)) < 1e-13
+
+
+# --- Wigner d -----------------------------------------------------------------
+
+def test_wigner_closed_forms():
+    rng = np.random.default_rng(1)
+    for b in rng.uniform(0.05, math.pi - 0.05, 7):
+        for l in range(3):
+            for m in range(-l, l + 1):
+                for n in range(-l, l + 1):
+                    got = O.wigner_d(b, l + 1, m, n)[l]
+                    assert abs(got - d_closed(l, m, n, b)) < 1e-15, (l, m, n)
+
+
+def test_wigner_explicit_sum_high_precision():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+
+    def wig(l, m, n, beta):
+        c = mp.cos(mp.mpf(beta) / 2)
+        s = mp.sin(mp.mpf(beta) / 2)
+        pref = mp.sqrt(mp.factorial(l + m) * mp.factorial(l - m) * mp.factorial(l + n) * mp.factorial(l - n))
+        tot = mp.mpf(0)
+        for k in range(0, 2 * l + 1):
+            a, cc, d = l + n - k, m - n + k, l - m - k
+            if a < 0 or cc < 0 or d < 0:
+                continue
+            tot += (-1) ** (m - n + k) * c ** (2 * l + n - m - 2 * k) * s ** (m - n + 2 * k) / (
+                mp.factorial(a) * mp.factorial(k) * mp.factorial(cc) * mp.factorial(d))
+        return float(pref * tot)
+
+    rng = np.random.default_rng(2)
+    for _ in range(40):
+        l = int(rng.integers(0, 31))
+        m = int(rng.integers(-l, l + 1))
+        n = int(rng.integers(-l, l + 1))
+        b = float(rng.uniform(0.01, math.pi - 0.01))
+        got = O.wigner_d(b, l + 1, m, n)[l]
+        assert abs(got - wig(l, m, n, b)) < 5e-14, (l, m, n, b)
+
+
+def test_wigner_orthogonality():
+    for b in (0.3, 1.5707963, 2.9):
+        for l in (10, 77, 200):
+            ms = np.arange(-l, l + 1)
+            for k, kp in ((0, 0), (3, 3), (3, -2), (l, l - 1), (-l, -l)):
+                col = O.wigner_d(b, l + 1, ms, k)[l]
+                colp = O.wigner_d(b, l + 1, ms, kp)[l]
+                assert abs(col @ colp - (1.0 if k == kp else 0.0)) < 1e-12
+
+
+def test_delta_symmetries_and_fourier_expansion():
+    L = 13
+    ms = np.arange(-(L - 1), L)
+    Dl = O.delta(L, ms[:, None], ms[None, :])          # [l][m'][m]
+    for l in range(L):
+        sl = slice(L - 1 - l, L + l)
+        D = Dl[l][sl, sl]
+        mm = np.arange(-l, l + 1)
+        sgn_row = (-1.0) ** (l + mm)                  # Delta_{-m',m} = (-1)^(l+m) Delta_{m'm}
+        assert np.abs(D[::-1, :] - D * sgn_row[None, :]).max() < 1e-14
+        assert np.abs(D[:, ::-1] - D * sgn_row[:, None]).max() < 1e-14
+        par = (-1.0) ** (mm[:, None] - mm[None, :])
+        assert np.abs(D - D.T * par).max() < 1e-14
+    # Eq. (25): d^l_mn(beta) = e^{-i(n-m)pi/2} sum_m' Delta_{m'm} Delta_{m'n} e^{-i m' beta}
+    rng = np.random.default_rng(3)
+    for b in rng.uniform(0, math.pi, 5):
+        for l in range(L):
+            sl = slice(L - 1 - l, L + l)
+            D = Dl[l][sl, sl]
+            mm = np.arange(-l, l + 1)
+            for m in range(-l, l + 1):
+                for n in range(-l, l + 1):
+                    s = np.sum(D[:, m + l] * D[:, n + l] * np.exp(-1j * mm * b))
+                    val = np.exp(-1j * (n - m) * math.pi / 2) * s
+                    assert abs(val.imag) < 1e-13
+                    assert abs(val.real - O.wigner_d(b, l + 1, m, n)[l]) < 1e-13
+
+
+# --- whole transform ----------------------------------------------------------
+
+def _single_mode_f(L, l0, m0, c):
+    f = np.zeros(L * L, dtype=np.complex128)
+    f[l0 * l0 + l0 + m0] += c
+    if m0 != 0:
+        f[l0 * l0 + l0 - m0] += (-1) ** m0 * np.conj(c)
+    else:
+        f[l0 * l0 + l0] = c.real
+    return f
+
+
+@pytest.mark.parametrize("N,lam,J0", [(3, 2.0, 0), (2, 2.0, 1), (1, 2.0, 2), (4, 1.5, 0)])
+def test_single_mode_analysis_closed_form(N, lam, J0):
+    L = 6
+    psi, phi = O.kernels(L, N, lam, J0)
+    alpha, beta, gamma = O.grids(L, N)
+    ns = O.n_orders(N)
+    for (l0, m0, c) in ((1, 1, 0.3 - 0.7j), (2, 1, 1.1 + 0.2j), (2, 2, -0.4 + 0.9j), (1, 0, 0.8 + 0j), (2, 0, -1.3 + 0j)):
+        f = _single_mode_f(L, l0, m0, c)
+        W, Wphi = O.analysis(f, L, N, lam, J0)
+        for j in range(psi.shape[0]):
+            for (g, b, a) in ((0, 1, 2), (N - 1, 7, 10), (N // 2, 11, 0)):
+                ref = 0.0
+                for k, n in enumerate(ns):
+                    if abs(n) > l0:
+                        continue
+                    for mm, cc in ((m0, f[l0 * l0 + l0 + m0]), (-m0, f[l0 * l0 + l0 - m0])) if m0 else ((0, f[l0 * l0 + l0]),):
+                        ref += cc * np.conj(psi[j, l0, k]) * np.conj(D_closed(l0, mm, n, alpha[a], beta[b], gamma[g]))
+                assert abs(ref.imag) < 1e-14
+                assert abs(W[j, g, b, a] - ref.real) < 1e-14
+        # scaling coefficients: sum_m f_lm Phi_l D^l*_m0(phi, theta, 0)
+        for (b, a) in ((0, 0), (5, 3)):
+            ref = 0.0
+            for mm in ((m0, -m0) if m0 else (0,)):
+                ref += f[l0 * l0 + l0 + mm] * phi[l0] * np.conj(D_closed(l0, mm, 0, alpha[a], beta[b], 0.0))
+            assert abs(Wphi[b, a] - ref.real) < 1e-14
+
+
+@pytest.mark.parametrize("N", [1, 3, 4])
+def test_single_mode_synthesis_closed_form(N):
+    """W^j = D^{l0 *}_{m0 n0} on one scale -> f_{l0 m0} = Psi^j_{l0 n0} (Eqs. (32)-(33),
+    orthogonality of D); W^Phi = e^{i m0 phi} d^{l0}_{m0 0}(theta) -> f_{l0 m0} = Phi_{l0} (Eq. (41))."""
+    L, lam, J0 = 6, 2.0, 1
+    psi, phi = O.kernels(L, N, lam, J0)
+    alpha, beta, gamma = O.grids(L, N)
+    ns = O.n_orders(N)
+    J1 = psi.shape[0]
+    A, B, G = np.meshgrid(alpha, beta, gamma, indexing="ij")      # [a][b][g]
+    for (l0, m0, k0, j) in ((2, 1, 0, 0), (2, -2, N - 1, 1), (1, 0, N // 2, 1)):
+        n0 = int(ns[k0])
+        if abs(n0) > l0:
+            continue
+        W = np.zeros((J1, N, 2 * L, 2 * L - 1), dtype=np.complex128)
+        vals = np.vectorize(lambda a, b, g: np.conj(D_closed(l0, m0, n0, a, b, g)))(A, B, G)
+        W[j] = np.transpose(vals, (2, 1, 0))
+        f = O.synthesis(W, np.zeros((2 * L, 2 * L - 1)), L, N, lam, J0)
+        expect = np.zeros(L * L, dtype=np.complex128)
+        expect[l0 * l0 + l0 + m0] = psi[j, l0, k0]
+        assert np.abs(f - expect).max() < 1e-14
+    for (l0, m0) in ((2, 1), (0, 0), (1, -1)):
+        Wp = np.zeros((2 * L, 2 * L - 1), dtype=np.complex128)
+        for b in range(2 * L):
+            Wp[b] = np.exp(1j * m0 * alpha) * d_closed(l0, m0, 0, beta[b])
+        f = O.synthesis(np.zeros((J1, N, 2 * L, 2 * L - 1)), Wp, L, N, lam, J0)
+        expect = np.zeros(L * L, dtype=np.complex128)
+        expect[l0 * l0 + l0 + m0] = phi[l0]
+        assert np.abs(f - expect).max() < 1e-14
+
+
+def test_realness_and_steerability():
+    L, N, lam, J0 = 8, 3, 2.0, 0
+    f = flm_gaussian(L, 7)
+    W, Wphi, imag = O.analysis_rows(f, L, N, lam, J0, range(2 * L))
+    assert imag < 1e-13
+    # Eq. (10): W(gamma) = sum_g z(gamma - gamma_g) W(gamma_g) with z_n = 1/N,
+    # z(x) = sum_n z_n e^{i n x}; W at gamma off the grid by the direct sum.
+    psi, _ = O.kernels(L, N, lam, J0)
+    alpha, beta, gamma = O.grids(L, N)
+    ns = O.n_orders(N)
+    F = O.flm_to_grid(f, L)
+    ms = np.arange(-(L - 1), L)
+    gam = 0.7318
+    for (j, b, a) in ((0, 3, 4), (1, 10, 1)):
+        D = O.wigner_d(beta[b], L, ms[:, None], ns[None, :])
+        T = np.einsum("lm,lk,lmk->mk", F, np.conj(psi[j]), D)
+        direct = np.sum(T * np.exp(1j * ms[:, None] * alpha[a]) * np.exp(1j * ns[None, :] * gam)).real
+        z = lambda x: np.sum(np.exp(1j * ns * x)).real / N
+        steered = sum(z(gam - gamma[g]) * W[j, g, b, a] for g in range(N))
+        assert abs(direct - steered) < 1e-13
+
+
+@pytest.mark.parametrize("L,N,lam,J0,kind", [(8, 3, 2.0, 0, "unit"), (16, 5, 2.0, 0, "cl"),
+                                              (16, 2, 2.0, 1, "uniform"), (12, 1, 3.0, 0, "unit"),
+                                              (16, 4, 2.5, 1, "unit"), (32, 3, 2.0, 0, "unit"),
+                                              (10, 8, 2.0, 0, "unit")])
+def test_round_trip_exact(L, N, lam, J0, kind):
+    f = flm_uniform(L, 11) if kind == "uniform" else flm_gaussian(L, 3, kind)
+    W, Wphi = O.analysis(f, L, N, lam, J0)
+    fr = O.synthesis(W, Wphi, L, N, lam, J0)
+    # Sec. 3.4 metric: eps = max |f_rec - f_orig|
+    assert np.abs(fr - f).max() < 1e-12
+
+
+def test_fourier_cube_reproduces_analysis():
+    """Eq. (26): W = sum_{m m' n} U_{m m' n} e^{i(m alpha + m' beta + n gamma)}."""
+    L, N, lam, J0 = 8, 3, 2.0, 0
+    f = flm_gaussian(L, 9)
+    W, _ = O.analysis(f, L, N, lam, J0)
+    alpha, beta, gamma = O.grids(L, N)
+    ns = O.n_orders(N)
+    ms = np.arange(-(L - 1), L)
+    for j in (0, 2):
+        U = O.fourier_cube(f, L, N, lam, J0, j)          # [m][m'][k]
+        for (g, b, a) in ((0, 0, 0), (2, 9, 13), (1, 15, 6)):
+            val = np.einsum("mpk,m,p,k->", U, np.exp(1j * ms * alpha[a]), np.exp(1j * ms * beta[b]),
+                            np.exp(1j * ns * gamma[g]))
+            assert abs(val - W[j, g, b, a]) < 1e-13
