@@ -38,7 +38,7 @@ PARITY = {
     "k_lambda": "limits k=1 below 1/lam, 0 above 1; derivative vs -s^2/t/I by finite differences",
     "kernels": "admissibility Eq. (6); sum_n |s_ln|^2 = 1 (Eq. (8)); support edges (Sec. 2.2)",
     "dh_weights": "sum q = 2; exact integration of sin(t)cos(kt), k < 2L (Eq. (17))",
-    "wigner_d": "textbook closed forms at l=1,2; Wigner's explicit sum in 60-digit arithmetic; orthogonality",
+    "wigner_d": "textbook closed forms at l=1,2; Wigner's explicit sum in 60-digit arithmetic; orthogonality up to l=2047",
     "delta": "symmetries of d(pi/2); Fourier expansion Eq. (25) reproduces d(beta)",
     "analysis": "single-mode closed-form D at l=1,2; realness for real signals; steerability Eq. (10)",
     "synthesis": "exact round trip with analysis (Sec. 3.4 metric) to 1e-12",
@@ -91,8 +91,15 @@ def s_lambda(t, lam: float):
 @functools.lru_cache(maxsize=None)
 def _I(t: float, lam: float) -> float:
     """I(t) = int_t^1 s_lam(u)^2 / u du by adaptive Gauss-Kronrod (QUADPACK)."""
-    lo = max(t, 1.0 / lam)
-    if lo >= 1.0:
+    return _Iab(max(t, 1.0 / lam), 1.0, lam)
+
+
+@functools.lru_cache(maxsize=None)
+def _Iab(lo: float, hi: float, lam: float) -> float:
+    """int_lo^hi s_lam(u)^2 / u du (adaptive Gauss-Kronrod), 0 if lo >= hi."""
+    lo = max(lo, 1.0 / lam)
+    hi = min(hi, 1.0)
+    if lo >= hi:
         return 0.0
     c = 2.0 * lam / (lam - 1.0)
 
@@ -104,7 +111,7 @@ def _I(t: float, lam: float) -> float:
 
     with warnings.catch_warnings():
         warnings.simplefilter("ignore", integrate.IntegrationWarning)
-        val, _ = integrate.quad(f, lo, 1.0, epsabs=0.0, epsrel=1.2e-14, limit=1000)
+        val, _ = integrate.quad(f, lo, hi, epsabs=0.0, epsrel=1.2e-14, limit=1000)
     return val
 
 
@@ -119,9 +126,14 @@ def k_lambda(t: float, lam: float) -> float:
 
 
 def kappa_lambda(t: float, lam: float) -> float:
-    """kappa_lam(t) = sqrt(k_lam(t/lam) - k_lam(t)) (Eq. (14)); clamped at 0
-    where rounding makes the difference negative."""
-    return math.sqrt(max(0.0, k_lambda(t / lam, lam) - k_lambda(t, lam)))
+    """kappa_lam(t) = sqrt(k_lam(t/lam) - k_lam(t)) (Eq. (14)).
+
+    By Eq. (13) the difference is one integral,
+      k_lam(t/lam) - k_lam(t) = int_{t/lam}^{t} s_lam(u)^2/u du / I(1/lam)
+    (limits clipped to the support [1/lam, 1]); it is evaluated in that form,
+    which avoids the cancellation of two numbers near 1 at the support edges."""
+    t = float(t)
+    return math.sqrt(_Iab(t / lam, t, lam) / _I(1.0 / lam, lam))
 
 
 def kappa(j: int, l: int, L: int, lam: float) -> float:
@@ -200,7 +212,7 @@ def dh_weights(L: int) -> np.ndarray:
 # Wigner d-functions (convention of Eq. (24): D = e^{-im alpha} d e^{-in gamma})
 # ---------------------------------------------------------------------------
 
-def _d_first(beta, m, n):
+def _d_first_log(beta, m, n):
     """d^{l0}_{mn}(beta) at l0 = max(|m|, |n|), where Wigner's explicit sum has
     a single term:  d^l_{l,n} = (-1)^{l-n} sqrt(C(2l, l+n)) c^{l+n} s^{l-n},
     d^l_{-l,n} = sqrt(C(2l, l-n)) c^{l-n} s^{l+n}, c = cos(beta/2),
@@ -221,7 +233,7 @@ def _d_first(beta, m, n):
     with np.errstate(divide="ignore", invalid="ignore"):
         tc = np.where(a == 0, 0.0, a * np.log(c))
         ts = np.where(b == 0, 0.0, b * np.log(s))
-    return sign * np.exp(0.5 * logc + tc + ts)
+    return sign, 0.5 * logc + tc + ts     # d = sign * exp(log|d|), log|d| may be -inf
 
 
 def wigner_d(beta, L: int, m, n) -> np.ndarray:
@@ -237,7 +249,13 @@ def wigner_d(beta, L: int, m, n) -> np.ndarray:
     m = m.astype(np.int64)
     n = n.astype(np.int64)
     l0 = np.maximum(np.abs(m), np.abs(n))
-    first = _d_first(beta, m, n)
+    # The first value can lie far below the float64 range (e.g. ~e^-750 at
+    # l ~ 1400, beta = pi/2) while later degrees are O(1): the recurrence is
+    # linear, so it runs on values scaled by exp(-E) with E tracked per entry.
+    sgn, logd = _d_first_log(beta, m, n)
+    fin = np.isfinite(logd)
+    E = np.where(fin, np.floor(np.where(fin, logd, 0.0)), 0.0)
+    first = np.where(fin, sgn * np.exp(np.where(fin, logd, 0.0) - E), 0.0)
     cb = np.cos(beta)
     mf = m.astype(np.float64)
     nf = n.astype(np.float64)
@@ -259,8 +277,14 @@ def wigner_d(beta, L: int, m, n) -> np.ndarray:
                 cur = np.where(l0 == 0, cb, cur)
             cur = np.where(l > l0, cur, 0.0)
         cur = np.where(l == l0, first, cur)
-        out[l] = cur
+        with np.errstate(under="ignore", over="ignore"):
+            out[l] = cur * np.exp(E)
         prev2, prev = prev, cur
+        big = np.abs(prev) > 1e100
+        if np.any(big):
+            prev = np.where(big, prev * 1e-100, prev)
+            prev2 = np.where(big, prev2 * 1e-100, prev2)
+            E = np.where(big, E + 100.0 * np.log(10.0), E)
     return out
 
 

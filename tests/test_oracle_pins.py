@@ -181,13 +181,14 @@ def test_wigner_explicit_sum_high_precision():
 
 
 def test_wigner_orthogonality():
-    for b in (0.3, 1.5707963, 2.9):
-        for l in (10, 77, 200):
-            ms = np.arange(-l, l + 1)
-            for k, kp in ((0, 0), (3, 3), (3, -2), (l, l - 1), (-l, -l)):
-                col = O.wigner_d(b, l + 1, ms, k)[l]
-                colp = O.wigner_d(b, l + 1, ms, kp)[l]
-                assert abs(col @ colp - (1.0 if k == kp else 0.0)) < 1e-12
+    for b, l in ((0.3, 10), (1.5707963, 77), (2.9, 200), (np.pi / 2, 2047), (0.9, 1500)):
+        ms = np.arange(-l, l + 1)
+        for k, kp in ((0, 0), (3, 3), (3, -2), (l, l - 1), (-l, -l), (1323, 1323), (1323, 1201)):
+            if abs(k) > l or abs(kp) > l:
+                continue
+            col = O.wigner_d(b, l + 1, ms, k)[l]
+            colp = O.wigner_d(b, l + 1, ms, kp)[l]
+            assert abs(col @ colp - (1.0 if k == kp else 0.0)) < 1e-12
 
 
 def test_delta_symmetries_and_fourier_expansion():
