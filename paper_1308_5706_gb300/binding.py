@@ -1,0 +1,241 @@
+"""ctypes binding of libs2dw.so: the C ABI of include/s2dw.h under the same
+names, plus a thin ``Plan`` class.  Argument marshalling only -- every step
+of the transform runs in the library's CUDA kernels.  Device memory and
+streams come from PyTorch.  There is no CPU fallback: if the library is
+missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libs2dw.so")
+
+S2DW_OK, S2DW_EINVAL, S2DW_ENOMEM, S2DW_ECUDA, S2DW_ETIMEOUT, S2DW_EBUSY, S2DW_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+S2DW_FP64, S2DW_MIXED, S2DW_REAL_SIGNAL = 1, 2, 4
+
+_lib = None
+
+_c_p = ctypes.c_void_p
+_c_i = ctypes.c_int
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_c_ip = ctypes.POINTER(ctypes.c_int)
+_c_dp = ctypes.POINTER(ctypes.c_double)
+
+_SIGNATURES = {
+    "s2dw_plan": (_c_i, [ctypes.POINTER(_c_p), _c_i, _c_i, ctypes.c_double, _c_i, ctypes.c_uint]),
+    "s2dw_plan_destroy": (_c_i, [_c_p]),
+    "s2dw_query": (_c_i, [_c_p, _c_ip, _c_i64p, _c_i64p, _c_i64p, _c_i64p]),
+    "s2dw_kernels": (_c_i, [_c_p, _c_dp, _c_dp]),
+    "s2dw_analysis": (_c_i, [_c_p, _c_p, _c_p, _c_p, _c_p]),
+    "s2dw_synthesis": (_c_i, [_c_p, _c_p, _c_p, _c_p, _c_p]),
+    "s2dw_analysis_batch": (_c_i, [ctypes.POINTER(_c_p), ctypes.POINTER(_c_p), ctypes.POINTER(_c_p),
+                                   ctypes.POINTER(_c_p), _c_i, _c_p]),
+    "s2dw_synthesis_batch": (_c_i, [ctypes.POINTER(_c_p), ctypes.POINTER(_c_p), ctypes.POINTER(_c_p),
+                                    ctypes.POINTER(_c_p), _c_i, _c_p]),
+    "s2dw_strerror": (ctypes.c_char_p, [_c_i]),
+    "s2dw_scale_support": (_c_i, [_c_p, _c_i, _c_ip, _c_ip]),
+    "s2dw_delta_slab": (_c_i, [_c_p, _c_i, _c_dp]),
+    "s2dw_stage": (_c_i, [_c_p, _c_i, _c_i, _c_p, _c_i64p]),
+}
+
+
+class S2dwError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {s2dw_strerror(status)} ({status})")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load libs2dw.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != S2DW_OK:
+        raise S2dwError(rc, where)
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device pointer of {type(x)}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- C ABI, same names ------------------------------------------------------
+
+def s2dw_strerror(status: int) -> str:
+    return lib().s2dw_strerror(status).decode()
+
+
+def s2dw_plan(L: int, N: int, lam: float, J0: int, flags: int) -> int:
+    h = _c_p()
+    _check(lib().s2dw_plan(ctypes.byref(h), L, N, float(lam), J0, flags), "s2dw_plan")
+    return h.value
+
+
+def s2dw_plan_destroy(plan: int) -> None:
+    _check(lib().s2dw_plan_destroy(plan), "s2dw_plan_destroy")
+
+
+def s2dw_query(plan: int) -> dict:
+    J = ctypes.c_int()
+    w, wp, ws, tot = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().s2dw_query(plan, ctypes.byref(J), ctypes.byref(w), ctypes.byref(wp), ctypes.byref(ws),
+                            ctypes.byref(tot)), "s2dw_query")
+    return {"J": J.value, "w_elems_per_scale": w.value, "wphi_elems": wp.value,
+            "workspace_bytes": ws.value, "total_device_bytes": tot.value}
+
+
+def s2dw_kernels(plan: int, J: int, L: int, N: int):
+    psi = np.zeros((J + 1, L, N, 2), dtype=np.float64)
+    phi = np.zeros(L, dtype=np.float64)
+    _check(lib().s2dw_kernels(plan, psi.ctypes.data_as(_c_dp), phi.ctypes.data_as(_c_dp)), "s2dw_kernels")
+    return psi[..., 0] + 1j * psi[..., 1], phi
+
+
+def s2dw_analysis(plan: int, flm, W, Wphi, stream=None) -> None:
+    _check(lib().s2dw_analysis(plan, _ptr(flm), _ptr(W), _ptr(Wphi), _stream(stream)), "s2dw_analysis")
+
+
+def s2dw_synthesis(plan: int, W, Wphi, flm, stream=None) -> None:
+    _check(lib().s2dw_synthesis(plan, _ptr(W), _ptr(Wphi), _ptr(flm), _stream(stream)), "s2dw_synthesis")
+
+
+def _arr(vals):
+    a = (_c_p * len(vals))()
+    for i, v in enumerate(vals):
+        a[i] = _ptr(v)
+    return a
+
+
+def s2dw_analysis_batch(plans: Sequence[int], flm, W, Wphi, stream=None) -> None:
+    n = len(plans)
+    _check(lib().s2dw_analysis_batch(_arr(plans), _arr(flm), _arr(W), _arr(Wphi), n, _stream(stream)),
+           "s2dw_analysis_batch")
+
+
+def s2dw_synthesis_batch(plans: Sequence[int], W, Wphi, flm, stream=None) -> None:
+    n = len(plans)
+    _check(lib().s2dw_synthesis_batch(_arr(plans), _arr(W), _arr(Wphi), _arr(flm), n, _stream(stream)),
+           "s2dw_synthesis_batch")
+
+
+def s2dw_scale_support(plan: int, j: int):
+    lo, hi = ctypes.c_int(), ctypes.c_int()
+    _check(lib().s2dw_scale_support(plan, j, ctypes.byref(lo), ctypes.byref(hi)), "s2dw_scale_support")
+    return lo.value, hi.value
+
+
+def s2dw_delta_slab(plan: int, l: int) -> np.ndarray:
+    out = np.zeros((l + 1, l + 1), dtype=np.float64)
+    _check(lib().s2dw_delta_slab(plan, l, out.ctypes.data_as(_c_dp)), "s2dw_delta_slab")
+    return out
+
+
+def s2dw_stage(plan: int, stage: int, j: int, complex_dtype) -> np.ndarray:
+    nb = ctypes.c_int64()
+    _check(lib().s2dw_stage(plan, stage, j, None, ctypes.byref(nb)), "s2dw_stage")
+    out = np.zeros(nb.value // np.dtype(complex_dtype).itemsize, dtype=complex_dtype)
+    _check(lib().s2dw_stage(plan, stage, j, out.ctypes.data, ctypes.byref(nb)), "s2dw_stage")
+    return out
+
+
+# ---- thin object wrapper ----------------------------------------------------
+
+class Plan:
+    """A transform plan (owns the C plan handle).
+
+    precision: "fp64" (complex128 f, float64 W) or "mixed" (complex64 f,
+    float32 W).  Buffers are torch CUDA tensors; see ``alloc_*``.
+    """
+
+    def __init__(self, L: int, N: int, lam: float = 2.0, J0: int = 0, precision: str = "mixed"):
+        flags = (S2DW_FP64 if precision == "fp64" else S2DW_MIXED) | S2DW_REAL_SIGNAL
+        if precision not in ("fp64", "mixed"):
+            raise ValueError(precision)
+        self.L, self.N, self.lam, self.J0, self.precision = L, N, float(lam), J0, precision
+        self.handle = s2dw_plan(L, N, lam, J0, flags)
+        q = s2dw_query(self.handle)
+        self.J = q["J"]
+        self.nscale = self.J + 1
+        self.info = q
+
+    def close(self):
+        if getattr(self, "handle", None):
+            s2dw_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # shapes and dtypes
+    @property
+    def w_shape(self):
+        return (self.nscale, self.N, 2 * self.L, 2 * self.L - 1)
+
+    @property
+    def wphi_shape(self):
+        return (2 * self.L, 2 * self.L - 1)
+
+    def torch_dtypes(self):
+        import torch
+        return (torch.complex128, torch.float64) if self.precision == "fp64" else (torch.complex64, torch.float32)
+
+    def alloc_flm(self, device="cuda"):
+        import torch
+        return torch.zeros(self.L * self.L, dtype=self.torch_dtypes()[0], device=device)
+
+    def alloc_w(self, device="cuda"):
+        import torch
+        rd = self.torch_dtypes()[1]
+        return torch.empty(self.w_shape, dtype=rd, device=device), torch.empty(self.wphi_shape, dtype=rd, device=device)
+
+    def kernels(self):
+        return s2dw_kernels(self.handle, self.J, self.L, self.N)
+
+    def analysis(self, flm, W, Wphi, stream=None):
+        s2dw_analysis(self.handle, flm, W, Wphi, stream)
+
+    def synthesis(self, W, Wphi, flm, stream=None):
+        s2dw_synthesis(self.handle, W, Wphi, flm, stream)
+
+    def support(self, j):
+        return s2dw_scale_support(self.handle, j)
+
+    def delta_slab(self, l):
+        return s2dw_delta_slab(self.handle, l)
+
+    def stage(self, stage, j):
+        cd = np.complex128 if self.precision == "fp64" else np.complex64
+        return s2dw_stage(self.handle, stage, j, cd)

@@ -1,0 +1,915 @@
+// C ABI: plans, the shared Delta table, launch lists, analysis and synthesis.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/s2dw.h"
+#include "internal.h"
+#include "plan_kernels.h"
+
+using namespace s2dw;
+
+namespace {
+
+inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct CudaFail {
+  cudaError_t err;
+};
+inline void ck(cudaError_t e) {
+  if (e != cudaSuccess) throw CudaFail{e};
+}
+
+int jmax_of(int L, double lam) {
+  int J = 0;
+  double p = 1.0;
+  while (p < L) {
+    p *= lam;
+    ++J;
+  }
+  return J;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] (Newton iteration on P_Q).
+void gauss_legendre(int Q, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(Q, 0.0);
+  w.assign(Q, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < Q; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (Q + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= Q; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = Q * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Process-wide Delta tables, reference counted (one per band-limit reach).
+// ---------------------------------------------------------------------------
+struct DeltaTab {
+  int Lmax;
+  int device;
+  double* d64;
+  float* d32;
+  int refs;
+  size_t bytes;
+};
+std::mutex g_mu;
+std::vector<DeltaTab*> g_tabs;
+
+DeltaTab* delta_acquire(int L, cudaStream_t st) {
+  int dev = 0;
+  ck(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeltaTab* best = nullptr;
+  for (DeltaTab* t : g_tabs)
+    if (t->device == dev && t->Lmax >= L && (!best || t->Lmax < best->Lmax)) best = t;
+  if (best) {
+    best->refs++;
+    return best;
+  }
+  const int Lmax = round_up(L, 64);
+  const int64_t entries = delta_table_entries(Lmax) + 64;  // + read-ahead pad
+  DeltaTab* t = new DeltaTab{Lmax, dev, nullptr, nullptr, 1, 0};
+  double* em = nullptr;
+  int* ee = nullptr;
+  try {
+    ck(cudaMalloc(&t->d64, entries * sizeof(double)));
+    ck(cudaMalloc(&t->d32, entries * sizeof(float)));
+    t->bytes = entries * (sizeof(double) + sizeof(float));
+    ck(cudaMemsetAsync(t->d64, 0, entries * sizeof(double), st));
+    ck(cudaMemsetAsync(t->d32, 0, entries * sizeof(float), st));
+    const size_t ne = (size_t)Lmax * (Lmax + 1) / 2;
+    ck(cudaMalloc(&em, ne * sizeof(double)));
+    ck(cudaMalloc(&ee, ne * sizeof(int)));
+    ck(launch_delta_build(t->d64, t->d32, em, ee, Lmax, st));
+    ck(cudaStreamSynchronize(st));
+    cudaFree(em);
+    cudaFree(ee);
+  } catch (...) {
+    if (em) cudaFree(em);
+    if (ee) cudaFree(ee);
+    if (t->d64) cudaFree(t->d64);
+    if (t->d32) cudaFree(t->d32);
+    delete t;
+    throw;
+  }
+  g_tabs.push_back(t);
+  return t;
+}
+
+void delta_release(DeltaTab* t) {
+  if (!t) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (--t->refs == 0) {
+    cudaFree(t->d64);
+    cudaFree(t->d32);
+    g_tabs.erase(std::remove(g_tabs.begin(), g_tabs.end(), t), g_tabs.end());
+    delete t;
+  }
+}
+
+// Device-resident launch lists for a set of jobs (one plan = one job).
+struct Lists {
+  void* mem = nullptr;
+  void* desc_w = nullptr;     // ContractDesc<T>[njobs]
+  void* desc_phi = nullptr;   // ContractDesc<T>[njobs]
+  std::vector<std::pair<int, std::pair<void*, int>>> tiles_w;  // (N, (tiles, count))
+  void* tiles_phi = nullptr;
+  int ntiles_phi = 0;
+  void* segs[4] = {nullptr, nullptr, nullptr, nullptr};
+  int nseg[4] = {0, 0, 0, 0};
+  int items[4] = {0, 0, 0, 0};
+  int maxlogM = 0;
+  int Lmax = 0;
+  ~Lists() {
+    if (mem) cudaFree(mem);
+  }
+};
+
+}  // namespace
+
+struct s2dw_plan_s {
+  int L = 0, N = 0, J0 = 0, J = 0, nscale = 0;
+  unsigned flags = 0;
+  double lam = 0;
+  bool fp64 = false;
+  int E = 4, TMP = 32;
+  std::vector<int> lo, hi, Lj;
+  int lend_w = -1, L0 = 0, lphi = 0, Lphi = 1;
+  int logM = 0, M = 0;
+  int device = 0;
+  DeltaTab* tab = nullptr;
+  std::vector<double> psi_host, phi_host;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // workspace views
+  void* RS = nullptr;
+  void* RSphi = nullptr;
+  std::vector<void*> Y, X;  // [nscale + 1], last = scaling part
+  std::vector<int> Ycols;   // band-limit of each buffer (Lj, last = Lphi)
+  void* P = nullptr;
+  void* Pphi = nullptr;
+  int nbr = 0, nbr_phi = 0, Lp = 0, Lp32 = 0, Lphip = 0, Lphip32 = 0;
+  void* tw = nullptr;
+  void* chirp_a = nullptr;
+  void* pre_b = nullptr;
+  void* post_b = nullptr;
+  void* preS_b = nullptr;
+  void* postS_b = nullptr;
+  void* Hs = nullptr;  // 4 x M spectra
+  // host copies of the static descriptors (device copies live in `own`)
+  std::vector<unsigned char> desc_w_host, desc_phi_host;
+  std::vector<TileTask> tiles_w_host, tiles_phi_host;
+  Lists own;
+  ~s2dw_plan_s() {
+    if (ws) cudaFree(ws);
+    delta_release(tab);
+  }
+};
+
+namespace {
+
+std::mutex g_batch_mu;
+std::map<std::vector<s2dw_plan_t>, Lists*> g_batch_cache;
+
+void drop_batches_with(s2dw_plan_t p) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (auto it = g_batch_cache.begin(); it != g_batch_cache.end();) {
+    if (std::find(it->first.begin(), it->first.end(), p) != it->first.end()) {
+      delete it->second;
+      it = g_batch_cache.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+template <typename T>
+void fill_desc(s2dw_plan_s* p, ContractDesc<T>& dw, ContractDesc<T>& dp, const T* delta) {
+  std::memset(&dw, 0, sizeof(dw));
+  std::memset(&dp, 0, sizeof(dp));
+  dw.delta = delta;
+  dw.RS = reinterpret_cast<const T*>(p->RS);
+  dw.P = reinterpret_cast<cx<T>*>(p->P);
+  dw.L = p->L;
+  dw.Lp = p->Lp;
+  dw.Lp32 = p->Lp32;
+  dw.nbr = p->nbr;
+  dw.N = p->N;
+  dw.nslot = 2;
+  dw.eta_odd = (p->N % 2 == 0) ? 1 : 0;
+  for (int j = 0; j < p->nscale; ++j) {
+    dw.Lj[j] = p->Lj[j];
+    dw.Y[j] = reinterpret_cast<cx<T>*>(p->Y[j]);
+  }
+  // l-segments with constant slot occupancy, covering [0, L-1]
+  int ns = 0;
+  int prev0 = -2, prev1 = -2;
+  for (int l = 0; l < p->L; ++l) {
+    int s0 = -1, s1 = -1;
+    for (int j = 0; j < p->nscale; ++j) {
+      if (p->Lj[j] == 0 || l < p->lo[j] || l > p->hi[j]) continue;
+      if (j % 2 == 0) s0 = j;
+      else s1 = j;
+    }
+    if (s0 != prev0 || s1 != prev1) {
+      dw.seg[ns].lo = l;
+      dw.seg[ns].hi = l;
+      dw.seg[ns].j[0] = s0;
+      dw.seg[ns].j[1] = s1;
+      ++ns;
+      prev0 = s0;
+      prev1 = s1;
+    } else {
+      dw.seg[ns - 1].hi = l;
+    }
+  }
+  dw.nseg = ns;
+  // scaling part: one N = 1 "scale" with kernel Phi on [0, lphi]
+  dp.delta = delta;
+  dp.RS = reinterpret_cast<const T*>(p->RSphi);
+  dp.P = reinterpret_cast<cx<T>*>(p->Pphi);
+  dp.L = p->Lphi;
+  dp.Lp = p->Lphip;
+  dp.Lp32 = p->Lphip32;
+  dp.nbr = p->nbr_phi;
+  dp.N = 1;
+  dp.nslot = 1;
+  dp.eta_odd = 0;
+  dp.Lj[0] = p->Lphi;
+  dp.Y[0] = reinterpret_cast<cx<T>*>(p->Y[p->nscale]);
+  dp.seg[0].lo = 0;
+  dp.seg[0].hi = p->Lphi - 1;
+  dp.seg[0].j[0] = 0;
+  dp.seg[0].j[1] = -1;
+  dp.nseg = 1;
+}
+
+void build_tiles(int Lband, int lend, int TMP, int prob, std::vector<TileTask>& out) {
+  if (Lband <= 0 || lend < 0) return;
+  const int nbp = (Lband + TMP - 1) / TMP, nbm = (Lband + TILE - 1) / TILE;
+  for (int bp = 0; bp < nbp; ++bp)
+    for (int bm = 0; bm < nbm; ++bm) {
+      const int ls = std::max(bp * TMP, bm * TILE);
+      if (ls > lend) continue;
+      out.push_back(TileTask{prob, bp, bm, ls, lend});
+    }
+}
+
+void sort_tiles(std::vector<TileTask>& t) {
+  std::stable_sort(t.begin(), t.end(), [](const TileTask& a, const TileTask& b) {
+    return (a.lend - a.lstart) > (b.lend - b.lstart);
+  });
+}
+
+template <typename T>
+void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, int& start) {
+  const int L = p->L, n = 2 * L - 1;
+  const int64_t wscale = (int64_t)p->N * 2 * L * n;
+  const cx<T>* Hs = reinterpret_cast<const cx<T>*>(p->Hs);
+  for (int j = 0; j <= p->nscale; ++j) {
+    const bool phi = (j == p->nscale);
+    const int Nj = phi ? 1 : p->N;
+    const int Lj = p->Ycols[j];
+    CztSeg<T> s;
+    std::memset(&s, 0, sizeof(s));
+    s.job = job;
+    s.L = L;
+    s.Lj = Lj;
+    s.N = Nj;
+    s.logM = p->logM;
+    s.woff = phi ? 0 : (int64_t)j * wscale;
+    s.is_phi = phi ? 1 : 0;
+    s.tw = reinterpret_cast<const cx<T>*>(p->tw);
+    s.scale = (T)(2.0 * 3.14159265358979323846 / n);
+    switch (kind) {
+      case CZT_BETA_ANA:
+        s.items = Nj * Lj;
+        s.buf_in = reinterpret_cast<cx<T>*>(p->Y[j]);
+        s.buf_out = reinterpret_cast<cx<T>*>(p->X[j]);
+        s.H = Hs + 0 * (size_t)p->M;
+        s.pre = reinterpret_cast<const cx<T>*>(p->pre_b);
+        s.post = reinterpret_cast<const cx<T>*>(p->post_b);
+        break;
+      case CZT_ALPHA_ANA:
+        s.items = Nj * L;
+        s.buf_in = reinterpret_cast<cx<T>*>(p->X[j]);
+        s.H = Hs + 1 * (size_t)p->M;
+        s.pre = reinterpret_cast<const cx<T>*>(p->chirp_a);
+        s.post = reinterpret_cast<const cx<T>*>(p->chirp_a);
+        break;
+      case CZT_ALPHA_SYN:
+        s.items = Nj * L;
+        s.buf_out = reinterpret_cast<cx<T>*>(p->X[j]);
+        s.H = Hs + 2 * (size_t)p->M;
+        s.pre = reinterpret_cast<const cx<T>*>(p->chirp_a);
+        s.post = reinterpret_cast<const cx<T>*>(p->chirp_a);
+        break;
+      case CZT_BETA_SYN:
+        s.items = Nj * Lj;
+        s.buf_in = reinterpret_cast<cx<T>*>(p->X[j]);
+        s.buf_out = reinterpret_cast<cx<T>*>(p->Y[j]);
+        s.H = Hs + 3 * (size_t)p->M;
+        s.pre = reinterpret_cast<const cx<T>*>(p->preS_b);
+        s.post = reinterpret_cast<const cx<T>*>(p->postS_b);
+        break;
+    }
+    if (s.items <= 0) continue;
+    s.start = start;
+    start += s.items;
+    out.push_back(s);
+  }
+}
+
+// Build the device launch lists for a set of plans (same precision).
+template <typename T>
+Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
+  const int nj = (int)plans.size();
+  std::vector<ContractDesc<T>> dw(nj), dp(nj);
+  std::map<int, std::vector<TileTask>> tw_byN;
+  std::vector<TileTask> tphi;
+  std::vector<CztSeg<T>> segs[4];
+  int start[4] = {0, 0, 0, 0};
+  Lists* ls = new Lists();
+  for (int i = 0; i < nj; ++i) {
+    s2dw_plan_s* p = plans[i];
+    std::memcpy(&dw[i], p->desc_w_host.data(), sizeof(ContractDesc<T>));
+    std::memcpy(&dp[i], p->desc_phi_host.data(), sizeof(ContractDesc<T>));
+    for (TileTask t : p->tiles_w_host) {
+      t.prob = i;
+      tw_byN[p->N].push_back(t);
+    }
+    for (TileTask t : p->tiles_phi_host) {
+      t.prob = i;
+      tphi.push_back(t);
+    }
+    for (int k = 0; k < 4; ++k) build_segs<T>(p, i, k, segs[k], start[k]);
+    ls->maxlogM = std::max(ls->maxlogM, p->logM);
+    ls->Lmax = std::max(ls->Lmax, p->L);
+  }
+  for (auto& kv : tw_byN) sort_tiles(kv.second);
+  sort_tiles(tphi);
+  // one allocation for everything
+  size_t off = 0;
+  const size_t o_dw = off;
+  off = align256(off + nj * sizeof(ContractDesc<T>));
+  const size_t o_dp = off;
+  off = align256(off + nj * sizeof(ContractDesc<T>));
+  std::vector<size_t> o_tw;
+  for (auto& kv : tw_byN) {
+    o_tw.push_back(off);
+    off = align256(off + kv.second.size() * sizeof(TileTask));
+  }
+  const size_t o_tp = off;
+  off = align256(off + tphi.size() * sizeof(TileTask));
+  size_t o_sg[4];
+  for (int k = 0; k < 4; ++k) {
+    o_sg[k] = off;
+    off = align256(off + segs[k].size() * sizeof(CztSeg<T>));
+  }
+  std::vector<unsigned char> host(off, 0);
+  std::memcpy(host.data() + o_dw, dw.data(), nj * sizeof(ContractDesc<T>));
+  std::memcpy(host.data() + o_dp, dp.data(), nj * sizeof(ContractDesc<T>));
+  int q = 0;
+  for (auto& kv : tw_byN) {
+    std::memcpy(host.data() + o_tw[q], kv.second.data(), kv.second.size() * sizeof(TileTask));
+    ++q;
+  }
+  if (!tphi.empty()) std::memcpy(host.data() + o_tp, tphi.data(), tphi.size() * sizeof(TileTask));
+  for (int k = 0; k < 4; ++k)
+    if (!segs[k].empty()) std::memcpy(host.data() + o_sg[k], segs[k].data(), segs[k].size() * sizeof(CztSeg<T>));
+  try {
+    ck(cudaMalloc(&ls->mem, off));
+    ck(cudaMemcpy(ls->mem, host.data(), off, cudaMemcpyHostToDevice));
+  } catch (...) {
+    delete ls;
+    throw;
+  }
+  char* base = reinterpret_cast<char*>(ls->mem);
+  ls->desc_w = base + o_dw;
+  ls->desc_phi = base + o_dp;
+  q = 0;
+  for (auto& kv : tw_byN) {
+    ls->tiles_w.push_back({kv.first, {base + o_tw[q], (int)kv.second.size()}});
+    ++q;
+  }
+  ls->tiles_phi = base + o_tp;
+  ls->ntiles_phi = (int)tphi.size();
+  for (int k = 0; k < 4; ++k) {
+    ls->segs[k] = base + o_sg[k];
+    ls->nseg[k] = (int)segs[k].size();
+    ls->items[k] = start[k];
+  }
+  return ls;
+}
+
+template <typename T>
+void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st) {
+  const ContractDesc<T>* dw = reinterpret_cast<const ContractDesc<T>*>(ls.desc_w);
+  const ContractDesc<T>* dp = reinterpret_cast<const ContractDesc<T>*>(ls.desc_phi);
+  for (auto& t : ls.tiles_w)
+    launch_contract<T>(t.first, 2, false, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
+                       ptrs, st);
+  launch_contract<T>(1, 1, false, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+  launch_czt<T>(CZT_BETA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[0]), ls.nseg[0], ls.items[0], ls.maxlogM,
+                ptrs, st);
+  launch_czt<T>(CZT_ALPHA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1], ls.maxlogM,
+                ptrs, st);
+}
+
+template <typename T>
+void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, int njobs, cudaStream_t st) {
+  const ContractDesc<T>* dw = reinterpret_cast<const ContractDesc<T>*>(ls.desc_w);
+  const ContractDesc<T>* dp = reinterpret_cast<const ContractDesc<T>*>(ls.desc_phi);
+  launch_czt<T>(CZT_ALPHA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[2]), ls.nseg[2], ls.items[2], ls.maxlogM,
+                ptrs, st);
+  launch_czt<T>(CZT_BETA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[3]), ls.nseg[3], ls.items[3], ls.maxlogM,
+                ptrs, st);
+  for (auto& t : ls.tiles_w)
+    launch_contract<T>(t.first, 2, true, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
+                       ptrs, st);
+  launch_contract<T>(1, 1, true, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+  launch_syn_reduce<T>(rj, njobs, ls.Lmax, st);
+}
+
+template <typename T>
+void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, const double* sabs_d,
+                      const double* q_d, cudaStream_t st) {
+  const int L = p->L, N = p->N, n = 2 * L - 1, M = p->M;
+  // ---- workspace layout ----
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  const size_t o_RS = take((size_t)L * 2 * N * p->Lp * sizeof(T));
+  const size_t o_RSphi = take((size_t)p->Lphi * p->Lphip * sizeof(T));
+  std::vector<size_t> o_Y(p->nscale + 1), o_X(p->nscale + 1);
+  for (int j = 0; j <= p->nscale; ++j) {
+    const int Nj = (j == p->nscale) ? 1 : N;
+    const int Lj = p->Ycols[j];
+    o_Y[j] = take((size_t)Nj * Lj * Lj * sizeof(cx<T>));
+    o_X[j] = take((size_t)Nj * 2 * L * Lj * sizeof(cx<T>));
+  }
+  const size_t o_P = take((size_t)p->nbr * L * p->Lp32 * sizeof(cx<T>));
+  const size_t o_Pphi = take((size_t)p->nbr_phi * p->Lphi * p->Lphip32 * sizeof(cx<T>));
+  const size_t o_tw = take((size_t)M * sizeof(cx<T>));
+  const size_t o_ca = take((size_t)n * sizeof(cx<T>));
+  const size_t o_pb = take((size_t)(2 * L - 1) * sizeof(cx<T>));
+  const size_t o_qb = take((size_t)2 * L * sizeof(cx<T>));
+  const size_t o_pS = take((size_t)2 * L * sizeof(cx<T>));
+  const size_t o_qS = take((size_t)(2 * L - 1) * sizeof(cx<T>));
+  const size_t o_H = take((size_t)4 * M * sizeof(cx<T>));
+  p->ws_bytes = off;
+  ck(cudaMalloc(&p->ws, off));
+  char* b = reinterpret_cast<char*>(p->ws);
+  p->RS = b + o_RS;
+  p->RSphi = b + o_RSphi;
+  p->Y.resize(p->nscale + 1);
+  p->X.resize(p->nscale + 1);
+  for (int j = 0; j <= p->nscale; ++j) {
+    p->Y[j] = b + o_Y[j];
+    p->X[j] = b + o_X[j];
+  }
+  p->P = b + o_P;
+  p->Pphi = b + o_Pphi;
+  p->tw = b + o_tw;
+  p->chirp_a = b + o_ca;
+  p->pre_b = b + o_pb;
+  p->post_b = b + o_qb;
+  p->preS_b = b + o_pS;
+  p->postS_b = b + o_qS;
+  p->Hs = b + o_H;
+
+  // ---- R tables ----
+  std::vector<int> slot_w((size_t)L * 2, -1), slot_p(p->Lphi, 0);
+  for (int l = 0; l < L; ++l)
+    for (int j = 0; j < p->nscale; ++j)
+      if (p->Lj[j] > 0 && l >= p->lo[j] && l <= p->hi[j]) slot_w[(size_t)l * 2 + (j % 2)] = j;
+  int* slot_d = nullptr;
+  ck(cudaMalloc(&slot_d, (slot_w.size() + slot_p.size()) * sizeof(int)));
+  ck(cudaMemcpy(slot_d, slot_w.data(), slot_w.size() * sizeof(int), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(slot_d + slot_w.size(), slot_p.data(), slot_p.size() * sizeof(int), cudaMemcpyHostToDevice));
+  ck(launch_rtable<T>(reinterpret_cast<T*>(p->RS), p->tab->d64, kap_d, sabs_d, slot_d, L, p->Lp, N, 2, L, st));
+  ck(launch_rtable<T>(reinterpret_cast<T*>(p->RSphi), p->tab->d64, phi_d, nullptr, slot_d + slot_w.size(), p->Lphi,
+                      p->Lphip, 1, 1, L, st));
+  // ---- chirp tables (float64, then the working precision) ----
+  const size_t n64 = (size_t)M + n + (2 * L - 1) + 2 * L + 2 * L + (2 * L - 1) + 4 * (size_t)M;
+  double2* t64 = nullptr;
+  ck(cudaMalloc(&t64, n64 * sizeof(double2)));
+  double2* tw64 = t64;
+  double2* ca64 = tw64 + M;
+  double2* pb64 = ca64 + n;
+  double2* qb64 = pb64 + (2 * L - 1);
+  double2* pS64 = qb64 + 2 * L;
+  double2* qS64 = pS64 + 2 * L;
+  double2* H64 = qS64 + (2 * L - 1);
+  ck(launch_chirp_build64(tw64, ca64, pb64, qb64, pS64, qS64, H64, q_d, L, p->logM, st));
+  if (sizeof(T) == sizeof(double)) {
+    ck(cudaMemcpyAsync(p->tw, tw64, (size_t)M * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    ck(cudaMemcpyAsync(p->chirp_a, ca64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    ck(cudaMemcpyAsync(p->pre_b, pb64, (size_t)(2 * L - 1) * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    ck(cudaMemcpyAsync(p->post_b, qb64, (size_t)2 * L * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    ck(cudaMemcpyAsync(p->preS_b, pS64, (size_t)2 * L * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    ck(cudaMemcpyAsync(p->postS_b, qS64, (size_t)(2 * L - 1) * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    ck(cudaMemcpyAsync(p->Hs, H64, (size_t)4 * M * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  } else {
+    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->tw), tw64, M, st));
+    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->chirp_a), ca64, n, st));
+    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->pre_b), pb64, 2 * L - 1, st));
+    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->post_b), qb64, 2 * L, st));
+    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->preS_b), pS64, 2 * L, st));
+    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->postS_b), qS64, 2 * L - 1, st));
+    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->Hs), H64, (int64_t)4 * M, st));
+  }
+  ck(cudaStreamSynchronize(st));
+  cudaFree(t64);
+  cudaFree(slot_d);
+
+  // ---- descriptors, tiles, launch lists ----
+  ContractDesc<T> dw, dp;
+  const T* delta = (sizeof(T) == sizeof(double)) ? reinterpret_cast<const T*>(p->tab->d64)
+                                                 : reinterpret_cast<const T*>(p->tab->d32);
+  fill_desc<T>(p, dw, dp, delta);
+  p->desc_w_host.assign(reinterpret_cast<unsigned char*>(&dw), reinterpret_cast<unsigned char*>(&dw) + sizeof(dw));
+  p->desc_phi_host.assign(reinterpret_cast<unsigned char*>(&dp), reinterpret_cast<unsigned char*>(&dp) + sizeof(dp));
+  build_tiles(p->L0, p->lend_w, p->TMP, 0, p->tiles_w_host);
+  build_tiles(p->Lphi, p->lphi, p->TMP, 0, p->tiles_phi_host);
+  sort_tiles(p->tiles_w_host);
+  sort_tiles(p->tiles_phi_host);
+  Lists* ls = build_lists<T>(std::vector<s2dw_plan_t>{p});
+  // move into the plan (Lists owns device memory; transfer by swap)
+  std::swap(p->own.mem, ls->mem);
+  p->own.desc_w = ls->desc_w;
+  p->own.desc_phi = ls->desc_phi;
+  p->own.tiles_w = ls->tiles_w;
+  p->own.tiles_phi = ls->tiles_phi;
+  p->own.ntiles_phi = ls->ntiles_phi;
+  for (int k = 0; k < 4; ++k) {
+    p->own.segs[k] = ls->segs[k];
+    p->own.nseg[k] = ls->nseg[k];
+    p->own.items[k] = ls->items[k];
+  }
+  p->own.maxlogM = ls->maxlogM;
+  p->own.Lmax = ls->Lmax;
+  delete ls;
+  // the cap covers every plan size (M <= 8192 for L <= 2048), so plans of
+  // different sizes can share a batched launch
+  ck(sizeof(T) == sizeof(double) ? czt_prepare_f64(13) : czt_prepare_f32(13));
+}
+
+int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned flags) {
+  const int Jm = jmax_of(L, lam);
+  if (J0 < 0 || J0 > Jm) return S2DW_EINVAL;
+  const int J = Jm - J0;
+  if (J + 1 > 64) return S2DW_EINVAL;
+  s2dw_plan_s* p = new s2dw_plan_s();
+  p->L = L;
+  p->N = N;
+  p->J0 = J0;
+  p->J = J;
+  p->nscale = J + 1;
+  p->flags = flags | S2DW_REAL_SIGNAL;
+  p->lam = lam;
+  p->fp64 = (flags & S2DW_FP64) != 0;
+  p->E = contract_rows_per_thread(p->fp64);
+  p->TMP = 8 * p->E;
+  cudaStream_t st = nullptr;
+  double *kap = nullptr, *phi = nullptr, *sabs = nullptr, *q = nullptr, *gl = nullptr;
+  double2* psi = nullptr;
+  int rc = S2DW_OK;
+  try {
+    ck(cudaGetDevice(&p->device));
+    ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    std::vector<double> glx, glw;
+    const int Q = 16, PAN = 32;
+    gauss_legendre(Q, glx, glw);
+    ck(cudaMalloc(&gl, 2 * Q * sizeof(double)));
+    ck(cudaMemcpy(gl, glx.data(), Q * sizeof(double), cudaMemcpyHostToDevice));
+    ck(cudaMemcpy(gl + Q, glw.data(), Q * sizeof(double), cudaMemcpyHostToDevice));
+    ck(cudaMalloc(&kap, (size_t)(J + 1) * L * sizeof(double)));
+    ck(cudaMalloc(&phi, (size_t)L * sizeof(double)));
+    ck(cudaMalloc(&sabs, (size_t)L * N * sizeof(double)));
+    ck(cudaMalloc(&psi, (size_t)(J + 1) * L * N * sizeof(double2)));
+    ck(cudaMalloc(&q, (size_t)2 * L * sizeof(double)));
+    ck(launch_kernel_values(kap, phi, sabs, psi, q, L, N, J, lam, gl, gl + Q, Q, PAN, st));
+    ck(cudaStreamSynchronize(st));
+    std::vector<double> kap_h((size_t)(J + 1) * L);
+    p->phi_host.resize(L);
+    p->psi_host.resize((size_t)(J + 1) * L * N * 2);
+    ck(cudaMemcpy(kap_h.data(), kap, kap_h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    ck(cudaMemcpy(p->phi_host.data(), phi, L * sizeof(double), cudaMemcpyDeviceToHost));
+    ck(cudaMemcpy(p->psi_host.data(), psi, p->psi_host.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    // supports where kappa^j(l) > 0 and their overlaps
+    p->lo.assign(p->nscale, -1);
+    p->hi.assign(p->nscale, -1);
+    p->Lj.assign(p->nscale, 0);
+    std::vector<int> count(L, 0);
+    for (int j = 0; j < p->nscale; ++j)
+      for (int l = 0; l < L; ++l)
+        if (kap_h[(size_t)j * L + l] > 0.0) {
+          if (p->lo[j] < 0) p->lo[j] = l;
+          p->hi[j] = l;
+          count[l]++;
+        }
+    for (int l = 0; l < L; ++l)
+      if (count[l] > 2) throw CudaFail{cudaErrorInvalidValue};
+    for (int j = 0; j < p->nscale; ++j) {
+      if (p->hi[j] >= 0) p->Lj[j] = p->hi[j] + 1;
+      if (j >= 2 && p->hi[j] >= 0 && p->lo[j - 2] >= 0 && p->lo[j - 2] <= p->hi[j])
+        throw CudaFail{cudaErrorInvalidValue};
+      p->lend_w = std::max(p->lend_w, p->hi[j]);
+      p->L0 = std::max(p->L0, p->Lj[j]);
+    }
+    p->lphi = 0;
+    for (int l = 0; l < L; ++l)
+      if (p->phi_host[l] > 0.0) p->lphi = l;
+    p->Lphi = p->lphi + 1;
+    p->Ycols = p->Lj;
+    p->Ycols.push_back(p->Lphi);
+    p->Lp = round_up(L, 4);
+    p->Lp32 = round_up(L, 32);
+    p->Lphip = round_up(p->Lphi, 4);
+    p->Lphip32 = round_up(p->Lphi, 32);
+    p->nbr = (p->L0 + p->TMP - 1) / p->TMP;
+    p->nbr_phi = (p->Lphi + p->TMP - 1) / p->TMP;
+    p->logM = 4;
+    while ((1 << p->logM) < 4 * L - 2) ++p->logM;
+    p->M = 1 << p->logM;
+    p->tab = delta_acquire(L, st);
+    if (p->fp64) plan_build_typed<double>(p, kap, phi, sabs, q, st);
+    else plan_build_typed<float>(p, kap, phi, sabs, q, st);
+    ck(cudaStreamSynchronize(st));
+  } catch (const CudaFail& e) {
+    rc = (e.err == cudaErrorMemoryAllocation) ? S2DW_ENOMEM
+         : (e.err == cudaErrorInvalidValue) ? S2DW_EINVAL
+                                             : S2DW_ECUDA;
+  } catch (const std::bad_alloc&) {
+    rc = S2DW_ENOMEM;
+  } catch (...) {
+    rc = S2DW_ECUDA;
+  }
+  if (gl) cudaFree(gl);
+  if (kap) cudaFree(kap);
+  if (phi) cudaFree(phi);
+  if (sabs) cudaFree(sabs);
+  if (psi) cudaFree(psi);
+  if (q) cudaFree(q);
+  if (st) cudaStreamDestroy(st);
+  if (rc != S2DW_OK) {
+    cudaGetLastError();
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return S2DW_OK;
+}
+
+int err_of(cudaError_t e) {
+  if (e == cudaSuccess) return S2DW_OK;
+  if (e == cudaErrorMemoryAllocation) return S2DW_ENOMEM;
+  return S2DW_ECUDA;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* s2dw_strerror(int status) {
+  switch (status) {
+    case S2DW_OK: return "ok";
+    case S2DW_EINVAL: return "invalid argument";
+    case S2DW_ENOMEM: return "device allocation failed";
+    case S2DW_ECUDA: return "CUDA call or kernel launch failed";
+    case S2DW_ETIMEOUT: return "bounded device wait ran out";
+    case S2DW_EBUSY: return "resource busy";
+    case S2DW_ENOTSUP: return "not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+int s2dw_plan(s2dw_plan_t* out, int L, int N, double lambda, int J0, unsigned flags) {
+  if (!out) return S2DW_EINVAL;
+  *out = nullptr;
+  const unsigned prec = flags & (S2DW_FP64 | S2DW_MIXED);
+  if (prec != S2DW_FP64 && prec != S2DW_MIXED) return S2DW_EINVAL;
+  if (flags & ~(unsigned)(S2DW_FP64 | S2DW_MIXED | S2DW_REAL_SIGNAL)) return S2DW_EINVAL;
+  if (L < 2 || L > 2048) return S2DW_EINVAL;
+  if (N < 1 || N > 8 || N > L) return S2DW_EINVAL;
+  if (!(lambda > 1.0) || !std::isfinite(lambda)) return S2DW_EINVAL;
+  try {
+    return plan_create(out, L, N, lambda, J0, flags);
+  } catch (...) {
+    return S2DW_ECUDA;
+  }
+}
+
+int s2dw_plan_destroy(s2dw_plan_t plan) {
+  if (!plan) return S2DW_OK;
+  cudaDeviceSynchronize();
+  drop_batches_with(plan);
+  delete plan;
+  return err_of(cudaGetLastError());
+}
+
+int s2dw_query(s2dw_plan_t p, int* J, int64_t* w_elems_per_scale, int64_t* wphi_elems, int64_t* workspace_bytes,
+               int64_t* total_device_bytes) {
+  if (!p) return S2DW_EINVAL;
+  const int64_t L = p->L, n = 2 * L - 1;
+  const int64_t wps = (int64_t)p->N * 2 * L * n, wph = 2 * L * n;
+  const int64_t el = p->fp64 ? 8 : 4;
+  if (J) *J = p->J;
+  if (w_elems_per_scale) *w_elems_per_scale = wps;
+  if (wphi_elems) *wphi_elems = wph;
+  if (workspace_bytes) *workspace_bytes = (int64_t)p->ws_bytes;
+  if (total_device_bytes)
+    *total_device_bytes = (int64_t)p->ws_bytes + (wps * p->nscale + wph) * el + L * L * 2 * el;
+  return S2DW_OK;
+}
+
+int s2dw_kernels(s2dw_plan_t p, double* psi, double* phi) {
+  if (!p) return S2DW_EINVAL;
+  if (psi) std::memcpy(psi, p->psi_host.data(), p->psi_host.size() * sizeof(double));
+  if (phi) std::memcpy(phi, p->phi_host.data(), p->phi_host.size() * sizeof(double));
+  return S2DW_OK;
+}
+
+int s2dw_analysis(s2dw_plan_t p, const void* flm, void* W, void* Wphi, void* stream) {
+  if (!p || !flm || !W || !Wphi) return S2DW_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CallPtrs ptrs;
+  std::memset(&ptrs, 0, sizeof(ptrs));
+  ptrs.f[0] = flm;
+  ptrs.W[0] = W;
+  ptrs.Wphi[0] = Wphi;
+  if (p->fp64) run_analysis<double>(p->own, ptrs, st);
+  else run_analysis<float>(p->own, ptrs, st);
+  return err_of(cudaGetLastError());
+}
+
+int s2dw_synthesis(s2dw_plan_t p, const void* W, const void* Wphi, void* flm, void* stream) {
+  if (!p || !flm || !W || !Wphi) return S2DW_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CallPtrs ptrs;
+  std::memset(&ptrs, 0, sizeof(ptrs));
+  ptrs.out[0] = flm;
+  ptrs.W[0] = const_cast<void*>(W);
+  ptrs.Wphi[0] = const_cast<void*>(Wphi);
+  ReduceJobs rj;
+  std::memset(&rj, 0, sizeof(rj));
+  rj.dw[0] = p->own.desc_w;
+  rj.dp[0] = p->own.desc_phi;
+  rj.out[0] = flm;
+  rj.L[0] = p->L;
+  rj.lend[0] = p->lend_w;
+  rj.Lphi[0] = p->Lphi;
+  if (p->fp64) run_synthesis<double>(p->own, ptrs, rj, 1, st);
+  else run_synthesis<float>(p->own, ptrs, rj, 1, st);
+  return err_of(cudaGetLastError());
+}
+
+static int batch_lists(const s2dw_plan_t* plans, int njobs, Lists** out, bool* fp64) {
+  if (!plans || njobs < 1 || njobs > MAXB) return S2DW_EINVAL;
+  std::vector<s2dw_plan_t> key(plans, plans + njobs);
+  for (int i = 0; i < njobs; ++i) {
+    if (!key[i]) return S2DW_EINVAL;
+    for (int k = 0; k < i; ++k)
+      if (key[k] == key[i]) return S2DW_EINVAL;
+    if (key[i]->fp64 != key[0]->fp64) return S2DW_ENOTSUP;
+  }
+  *fp64 = key[0]->fp64;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  auto it = g_batch_cache.find(key);
+  if (it != g_batch_cache.end()) {
+    *out = it->second;
+    return S2DW_OK;
+  }
+  try {
+    Lists* ls = *fp64 ? build_lists<double>(key) : build_lists<float>(key);
+    g_batch_cache[key] = ls;
+    *out = ls;
+  } catch (const CudaFail& e) {
+    return err_of(e.err);
+  } catch (...) {
+    return S2DW_ENOMEM;
+  }
+  return S2DW_OK;
+}
+
+int s2dw_analysis_batch(const s2dw_plan_t* plans, const void* const* flm, void* const* W, void* const* Wphi,
+                        int njobs, void* stream) {
+  if (!flm || !W || !Wphi) return S2DW_EINVAL;
+  Lists* ls = nullptr;
+  bool fp64 = false;
+  int rc = batch_lists(plans, njobs, &ls, &fp64);
+  if (rc != S2DW_OK) return rc;
+  CallPtrs ptrs;
+  std::memset(&ptrs, 0, sizeof(ptrs));
+  for (int i = 0; i < njobs; ++i) {
+    if (!flm[i] || !W[i] || !Wphi[i]) return S2DW_EINVAL;
+    ptrs.f[i] = flm[i];
+    ptrs.W[i] = W[i];
+    ptrs.Wphi[i] = Wphi[i];
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (fp64) run_analysis<double>(*ls, ptrs, st);
+  else run_analysis<float>(*ls, ptrs, st);
+  return err_of(cudaGetLastError());
+}
+
+int s2dw_synthesis_batch(const s2dw_plan_t* plans, const void* const* W, const void* const* Wphi, void* const* flm,
+                         int njobs, void* stream) {
+  if (!flm || !W || !Wphi) return S2DW_EINVAL;
+  Lists* ls = nullptr;
+  bool fp64 = false;
+  int rc = batch_lists(plans, njobs, &ls, &fp64);
+  if (rc != S2DW_OK) return rc;
+  CallPtrs ptrs;
+  std::memset(&ptrs, 0, sizeof(ptrs));
+  ReduceJobs rj;
+  std::memset(&rj, 0, sizeof(rj));
+  const size_t dsz = fp64 ? sizeof(ContractDesc<double>) : sizeof(ContractDesc<float>);
+  for (int i = 0; i < njobs; ++i) {
+    if (!flm[i] || !W[i] || !Wphi[i]) return S2DW_EINVAL;
+    ptrs.out[i] = flm[i];
+    ptrs.W[i] = const_cast<void*>(W[i]);
+    ptrs.Wphi[i] = const_cast<void*>(Wphi[i]);
+    rj.dw[i] = reinterpret_cast<const char*>(ls->desc_w) + i * dsz;
+    rj.dp[i] = reinterpret_cast<const char*>(ls->desc_phi) + i * dsz;
+    rj.out[i] = flm[i];
+    rj.L[i] = plans[i]->L;
+    rj.lend[i] = plans[i]->lend_w;
+    rj.Lphi[i] = plans[i]->Lphi;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (fp64) run_synthesis<double>(*ls, ptrs, rj, njobs, st);
+  else run_synthesis<float>(*ls, ptrs, rj, njobs, st);
+  return err_of(cudaGetLastError());
+}
+
+int s2dw_scale_support(s2dw_plan_t p, int j, int* lo, int* hi) {
+  if (!p || j < 0 || j > p->nscale) return S2DW_EINVAL;
+  if (j == p->nscale) {
+    if (lo) *lo = 0;
+    if (hi) *hi = p->lphi;
+  } else {
+    if (lo) *lo = p->lo[j];
+    if (hi) *hi = p->hi[j];
+  }
+  return S2DW_OK;
+}
+
+int s2dw_delta_slab(s2dw_plan_t p, int l, double* host_out) {
+  if (!p || !host_out || l < 0 || l >= p->L) return S2DW_EINVAL;
+  const int64_t sz = delta_slab_size(l);
+  std::vector<double> slab(sz);
+  cudaError_t e = cudaMemcpy(slab.data(), p->tab->d64 + delta_slab_offset(l), sz * sizeof(double),
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return err_of(e);
+  for (int mp = 0; mp <= l; ++mp)
+    for (int m = 0; m <= l; ++m) {
+      double v;
+      if (m >= 4 * (mp >> 2)) v = slab[delta_entry(l, mp, m)];
+      else v = (((mp - m) & 1) ? -1.0 : 1.0) * slab[delta_entry(l, m, mp)];
+      host_out[(size_t)mp * (l + 1) + m] = v;
+    }
+  return S2DW_OK;
+}
+
+int s2dw_stage(s2dw_plan_t p, int stage, int j, void* host_out, int64_t* nbytes) {
+  if (!p || j < 0 || j > p->nscale || stage < 0 || stage > 1) return S2DW_EINVAL;
+  const int Nj = (j == p->nscale) ? 1 : p->N;
+  const int Lj = p->Ycols[j];
+  const int64_t el = p->fp64 ? 16 : 8;
+  const int64_t bytes = (stage == 0 ? (int64_t)Nj * Lj * Lj : (int64_t)Nj * 2 * p->L * Lj) * el;
+  if (nbytes) *nbytes = bytes;
+  if (!host_out) return S2DW_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return err_of(e);
+  e = cudaMemcpy(host_out, stage == 0 ? p->Y[j] : p->X[j], bytes, cudaMemcpyDeviceToHost);
+  return err_of(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Shared device helpers for the sm_103a wavelet transform kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace s2dw {
+
+template <typename T> struct CxT;
+template <> struct CxT<float> { typedef float2 type; };
+template <> struct CxT<double> { typedef double2 type; };
+template <typename T> using cx = typename CxT<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cx<T> mkc(T x, T y) {
+  cx<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mkc<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return mkc<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mkc<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {  // a * conj(b)
+  return mkc<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T> __device__ __forceinline__ cx<T> cconj(cx<T> a) { return mkc<T>(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return mkc<T>(a.x * s, a.y * s); }
+// a * i^k
+template <typename T> __device__ __forceinline__ cx<T> cmul_ipow(cx<T> a, int k) {
+  switch (k & 3) {
+    case 0: return a;
+    case 1: return mkc<T>(-a.y, a.x);
+    case 2: return mkc<T>(-a.x, -a.y);
+    default: return mkc<T>(a.y, -a.x);
+  }
+}
+
+// Padded eighth-domain layout of the Delta table (Delta^l_{m'm} = d^l_{m'm}(pi/2)).
+// Slab l holds c = floor(l/4)+1 groups of 4 rows; rows 4q..4q+3 store columns
+// 4q .. 4c-1 (zero beyond l), so every entry with m >= 4*floor(m'/4) is present
+// and 4 consecutive columns starting at a multiple of 4 are 16-byte aligned.
+__host__ __device__ __forceinline__ int64_t delta_slab_offset(int l) {
+  int64_t C = l >> 2, c = C + 1, r = l & 3;
+  return (32 * C * (C + 1) * (C + 2)) / 3 + r * 8 * c * (c + 1);
+}
+__host__ __device__ __forceinline__ int64_t delta_slab_size(int l) {
+  int64_t c = (l >> 2) + 1;
+  return 8 * c * (c + 1);
+}
+// Offset of entry (m', m) inside slab l (requires m >= 4*floor(m'/4)).
+__host__ __device__ __forceinline__ int delta_entry(int l, int mp, int m) {
+  int c = (l >> 2) + 1, q = mp >> 2, r = mp & 3;
+  return 16 * q * c - 8 * q * (q - 1) + r * 4 * (c - q) + (m - 4 * q);
+}
+// Entry index = slab_offset + B*c + A with per-row constants (used in hot loops):
+//   A(m', m) = -8q(q-1) - 4rq + m - 4q,  B(m') = 16q + 4r.
+__host__ __device__ __forceinline__ int delta_row_A(int mp, int m) {
+  int q = mp >> 2, r = mp & 3;
+  return -8 * q * (q - 1) - 4 * r * q + m - 4 * q;
+}
+__host__ __device__ __forceinline__ int delta_row_B(int mp) { return 16 * (mp >> 2) + 4 * (mp & 3); }
+
+static inline int64_t delta_table_entries(int Lmax) { return delta_slab_offset(Lmax); }
+
+}  // namespace s2dw

@@ -1,0 +1,103 @@
+// Internal descriptors shared by the plan, the launchers and the kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace s2dw {
+
+constexpr int MAXS = 66;   // wavelet scales (<= 64) plus headroom
+constexpr int MAXB = 64;   // transforms per batched launch
+constexpr int TILE = 32;   // contraction tile edge (m' and m)
+constexpr int LCH = 8;     // l-chunk of the synthesis in-tile reduction
+
+// One l-segment on which the scale held by each of the two accumulator
+// slots is constant (slot s holds the scale j with j % 2 == s, or -1).
+struct LSeg {
+  int lo, hi;
+  int j[2];
+};
+
+// Static, per-plan description of one contraction pass (wavelet scales with
+// N orders, or the scaling function with N = 1), device resident.
+template <typename T>
+struct ContractDesc {
+  const T* delta;    // Delta table (padded eighth domain), working precision
+  const T* RS;       // [L][nslot][N][Lp]: Delta^l_{m',n_k} kappa^j(l) |s_{l,n_k}|
+  cx<T>* P;          // synthesis partials [nbr][L][Lp32]
+  int L, Lp, Lp32, nbr;
+  int nseg;
+  int N, nslot, eta_odd;   // eta_odd: N even -> eta = i
+  int Lj[MAXS];            // per scale band-limit (support hi + 1)
+  cx<T>* Y[MAXS];          // per scale cube [N][Lj][Lj] (analysis out / synthesis in)
+  LSeg seg[2 * MAXS + 2];
+};
+
+struct TileTask {
+  int prob;    // index into the descriptor array of the launch
+  int bmp;     // m' block
+  int bm;      // m block
+  int lstart;  // first l of the tile (max(32 bmp, 32 bm))
+  int lend;    // last l with a nonzero contribution
+};
+
+// Per-call pointers, passed by value to the kernels.
+struct CallPtrs {
+  const void* f[MAXB];   // analysis input f_lm
+  void* out[MAXB];       // synthesis output f_lm
+  void* W[MAXB];         // wavelet coefficients
+  void* Wphi[MAXB];      // scaling coefficients
+};
+
+enum CztKind { CZT_BETA_ANA = 0, CZT_ALPHA_ANA = 1, CZT_ALPHA_SYN = 2, CZT_BETA_SYN = 3 };
+
+// One segment of a chirp-z launch: all columns / row pairs of one scale of
+// one transform.
+template <typename T>
+struct CztSeg {
+  int start;      // first CTA index of this segment
+  int items;
+  int job;        // index into CallPtrs
+  int L, Lj, N, logM;
+  int64_t woff;   // element offset of this scale in W (or 0 for Wphi)
+  int is_phi;     // 1: W pointer is CallPtrs::Wphi
+  cx<T>* buf_in;  // plan workspace input (X / Y buffers)
+  cx<T>* buf_out; // plan workspace output
+  const cx<T>* H; // bit-reversed chirp kernel spectrum, scaled by 1/M
+  const cx<T>* tw;
+  const cx<T>* pre;
+  const cx<T>* post;
+  T scale;
+};
+
+// Per-job parameters of the batched final synthesis reduction.
+struct ReduceJobs {
+  const void* dw[MAXB];
+  const void* dp[MAXB];
+  void* out[MAXB];
+  int L[MAXB];
+  int lend[MAXB];
+  int Lphi[MAXB];
+};
+
+template <typename T>
+void launch_contract(int N, int nslot, bool syn, const ContractDesc<T>* descs, const TileTask* tiles,
+                     int ntiles, const CallPtrs& ptrs, cudaStream_t st);
+template <typename T>
+void launch_czt(int kind, const CztSeg<T>* segs, int nseg, int total_items, int maxlogM,
+                const CallPtrs& ptrs, cudaStream_t st);
+template <typename T>
+void launch_syn_reduce(const ReduceJobs& jobs, int njobs, int Lmax, cudaStream_t st);
+
+template <> void launch_contract<float>(int, int, bool, const ContractDesc<float>*, const TileTask*, int,
+                                        const CallPtrs&, cudaStream_t);
+template <> void launch_contract<double>(int, int, bool, const ContractDesc<double>*, const TileTask*, int,
+                                         const CallPtrs&, cudaStream_t);
+template <> void launch_czt<float>(int, const CztSeg<float>*, int, int, int, const CallPtrs&, cudaStream_t);
+template <> void launch_czt<double>(int, const CztSeg<double>*, int, int, int, const CallPtrs&, cudaStream_t);
+template <> void launch_syn_reduce<float>(const ReduceJobs&, int, int, cudaStream_t);
+template <> void launch_syn_reduce<double>(const ReduceJobs&, int, int, cudaStream_t);
+cudaError_t czt_prepare_f32(int maxlogM);
+cudaError_t czt_prepare_f64(int maxlogM);
+int contract_rows_per_thread(bool fp64);
+
+}  // namespace s2dw
