@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of the directional scale-discretized wavelet transform on GB300.
+
+One step = one analysis + one synthesis (a round trip) of a real signal at
+L = 1024, N = 5, lambda = 2, J0 = 0 (11 wavelet scales) on the full-resolution
+Driscoll-Healy SO(3) grid, f_lm Gaussian with C_l = 1/(l(l+1)) (seed 2),
+mixed precision (FP32 arithmetic, FP64-generated Delta).  The metric is
+transforms/s; the plain FP64 path is timed beside it, and the error of both
+against the CPU oracle (spot rows) is reported.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1, launch under torch.distributed.run: every rank runs its own
+independent transforms (replicas; no data-path collective), rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1308_5706_gb300.inputs import flm_gaussian  # noqa: E402
+
+L, N, LAM, J0, SEED = 1024, 5, 2.0, 0, 2
+METRIC = "wavelet analysis+synthesis transforms/s at L=1024,N=5 (mixed vs FP64, 1 GB300) @max rel err; p99"
+UNIT = "transforms/s"
+WORKLOAD = "L=1024, N=5, lambda=2, J0=0 (11 scales), real Gaussian f_lm C_l=1/(l(l+1)), seed 2"
+FP32_LANES_PER_SM, N_SM = 128, 152
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Oracle timing (CPU): bounded samples, spawn pool over host cores
+# ---------------------------------------------------------------------------
+
+def _oracle_rows(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import oracle as O
+    b = args
+    f = flm_gaussian(L, SEED, "cl")
+    kern = O.kernels(L, N, LAM, J0)
+    t0 = time.perf_counter()
+    O.analysis_rows(f, L, N, LAM, J0, [b], kern)
+    t1 = time.perf_counter()
+    J1 = kern[0].shape[0]
+    rng = np.random.default_rng(b)
+    # only row b is read by the partial sum: a broadcast view stands for the full array
+    row = rng.standard_normal((J1, N, 1, 2 * L - 1))
+    W = np.broadcast_to(row, (J1, N, 2 * L, 2 * L - 1))
+    Wphi = np.broadcast_to(rng.standard_normal((1, 2 * L - 1)), (2 * L, 2 * L - 1))
+    O.synthesis(W, Wphi, L, N, LAM, J0, kern, b_list=[b])
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def _warm(_):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import oracle  # noqa: F401
+    return 0
+
+
+def oracle_pool(workers: int):
+    import multiprocessing as mp
+    pool = mp.get_context("spawn").Pool(workers)
+    pool.map(_warm, range(workers))  # interpreter start-up and imports outside the timing
+    return pool
+
+
+def oracle_sample(workers: int, pool=None):
+    """One bounded sample: each worker runs one analysis beta-row and one
+    synthesis beta-row of the L=1024 workload.  A full transform is 2L of
+    each, so transforms/s = (rows done / wall time) / (2 * 2L)."""
+    own = pool is None
+    if own:
+        pool = oracle_pool(workers)
+    rows = [int(x) for x in np.linspace(1, 2 * L - 2, workers)]
+    try:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_rows, rows)
+        wall = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    ana = statistics.mean(r[0] for r in res)
+    syn = statistics.mean(r[1] for r in res)
+    value = (len(rows) / wall) / (2 * 2 * L)
+    return value, wall, ana, syn
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    workers = max(1, os.cpu_count() or 1)
+    pool = oracle_pool(workers)
+    for _ in range(args.warmup):
+        oracle_sample(workers, pool)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, wall, ana, syn = oracle_sample(workers, pool)
+        vals.append(v)
+    total = time.perf_counter() - t0
+    pool.close()
+    pool.join()
+    value = statistics.mean(vals)
+    sample = (f"per step: {workers} spawn workers, each one analysis beta-row and one synthesis beta-row "
+              f"of the L=1024 workload (full transform = 2L rows of each); extrapolated")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, args.steps),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def contraction_flops(plan) -> float:
+    """Algorithmic flops of one contraction launch (analysis or synthesis):
+    per scale j and l in its support, (l+1)^2 (m', m >= 0) triples, each
+    Delta * f (2 flops) plus N complex-by-real multiply-adds (4N flops)."""
+    tot = 0.0
+    for j in range(plan.nscale):
+        lo, hi = plan.support(j)
+        if hi < 0:
+            continue
+        ls = np.arange(lo, hi + 1, dtype=np.float64)
+        tot += float(((ls + 1.0) ** 2).sum()) * (2 + 4 * plan.N)
+    return tot
+
+
+def alpha_bytes(plan, elem: int) -> float:
+    """Algorithmic bytes of one alpha launch: W written (or read) once plus
+    the [N][2L][Lj] complex input rows read once (scaling part included)."""
+    n = 2 * L - 1
+    w = (plan.nscale * N * 2 * L * n + 2 * L * n) * elem
+    xin = 0
+    for j in range(plan.nscale):
+        lo, hi = plan.support(j)
+        xin += N * 2 * L * (hi + 1) * 2 * elem
+    xin += 2 * L * (plan.support(plan.nscale)[1] + 1) * 2 * elem
+    return float(w + xin)
+
+
+def time_path(torch, plan, f_dev, steps, warmup, stream, profile=False):
+    W, Wphi = plan.alloc_w()
+    fr = plan.alloc_flm()
+    for _ in range(warmup):
+        plan.analysis(f_dev, W, Wphi, stream)
+        plan.synthesis(W, Wphi, fr, stream)
+    torch.cuda.synchronize()
+    if profile:
+        plan.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            ev[k][0].record(stream)
+            plan.analysis(f_dev, W, Wphi, stream)
+            plan.synthesis(W, Wphi, fr, stream)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    total = ev[0][0].elapsed_time(ev[-1][1])
+    prof = None
+    if profile:
+        prof = plan.profile_read()
+        plan.profile(False)
+    return per, total, W, Wphi, fr, prof
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # CPU baseline first (spawned pool, before the first GPU call)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        workers = max(1, os.cpu_count() or 1)
+        v, wall, ana, syn = oracle_sample(workers)
+        cpu = {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
+               "sample": (f"{workers} spawn workers x (1 analysis beta-row + 1 synthesis beta-row) of the "
+                          f"L=1024 workload in {wall:.1f} s (row: analysis {ana:.2f} s, synthesis {syn:.2f} s); "
+                          f"a transform is 2L=2048 rows of each, extrapolated")}
+
+    import torch
+    from paper_1308_5706_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    f64 = flm_gaussian(L, SEED + rank, "cl")
+    stream = torch.cuda.Stream()
+    pm = B.Plan(L, N, LAM, J0, "mixed")
+    f_mixed = torch.from_numpy(f64).to(torch.complex64).cuda()
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        per, total, Wm, Wpm, frm, prof = time_path(torch, pm, f_mixed, args.steps, args.warmup, stream,
+                                                    profile=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    value = args.steps * world / (total / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    fh = torch.from_numpy(f64).to(torch.complex64).pin_memory()
+    fo = torch.empty_like(fh).pin_memory()
+    fd = torch.empty(L * L, dtype=torch.complex64, device="cuda")
+    Wd, Wpd = pm.alloc_w()
+    frd = pm.alloc_flm()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            fd.copy_(fh, non_blocking=True)
+            pm.analysis(fd, Wd, Wpd, stream)
+            pm.synthesis(Wd, Wpd, frd, stream)
+            fo.copy_(frd, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fd.copy_(fh, non_blocking=True)
+            pm.analysis(fd, Wd, Wpd, stream)
+            pm.synthesis(Wd, Wpd, frd, stream)
+            fo.copy_(frd, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": args.steps * world / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(fh.numel() * fh.element_size()),
+           "d2h_bytes_per_step": int(fo.numel() * fo.element_size())}
+
+    # FP64 path (the baseline the mixed path is compared with)
+    p64 = B.Plan(L, N, LAM, J0, "fp64")
+    f_d64 = torch.from_numpy(f64).cuda()
+    per64, total64, W64, Wp64, fr64, _ = time_path(torch, p64, f_d64, args.fp64_steps, 1, stream)
+
+    # accuracy: mixed vs FP64 (whole arrays), both vs the oracle on spot rows, round trips
+    err = {}
+    Wm_d = Wm.double()
+    err["mixed_vs_fp64_W_max_rel_per_scale"] = max(
+        float((Wm_d[j] - W64[j]).abs().max() / W64[j].abs().max()) for j in range(pm.nscale))
+    err["round_trip_eps_mixed"] = float((frm.to(torch.complex128).cpu() - torch.from_numpy(f64)).abs().max())
+    err["round_trip_eps_fp64"] = float((fr64.cpu() - torch.from_numpy(f64)).abs().max())
+    if rank == 0:
+        import oracle as O
+        b_spot = [700]
+        kern = O.kernels(L, N, LAM, J0)
+        Wo, Wpo, _ = O.analysis_rows(f64, L, N, LAM, J0, b_spot, kern)
+        w64s = W64[:, :, b_spot, :].cpu().numpy()
+        wms = Wm_d[:, :, b_spot, :].cpu().numpy()
+        nz = [j for j in range(pm.nscale) if np.abs(Wo[j]).max() > 0]   # W^j = 0 where f vanishes on supp j
+        err["fp64_vs_oracle_spot_max_rel"] = max(
+            float(np.abs(w64s[j] - Wo[j]).max() / np.abs(Wo[j]).max()) for j in nz)
+        err["mixed_vs_oracle_spot_max_rel"] = max(
+            float(np.abs(wms[j] - Wo[j]).max() / np.abs(Wo[j]).max()) for j in nz)
+        err["zero_scales_max_abs"] = max([float(np.abs(w64s[j]).max()) for j in range(pm.nscale) if j not in nz]
+                                         + [0.0])
+        err["oracle_spot"] = "beta row b=700, all scales, gamma and alpha samples"
+
+    # roofline of the dominant kernel, from the stage events of the timed region
+    stage_ms, nana, nsyn = prof
+    mean_stage = {k: (v / (nana if k.startswith("ana") else nsyn)) for k, v in stage_ms.items()}
+    hbm, sm_max, peak_src = peaks()
+    dom = max(mean_stage, key=mean_stage.get)
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at max SM clock
+    if "contract" in dom:
+        achieved = contraction_flops(pm) / (mean_stage[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz"}
+    else:
+        achieved = alpha_bytes(pm, 4) / (mean_stage[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
+    roof["stage_ms"] = {k: round(v, 4) for k, v in mean_stage.items()}
+
+    per_sorted = sorted(per)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "mixed (FP32 arithmetic, FP64-generated Delta)",
+                   "grid": "full-resolution DH SO(3) grid per scale: 5 x 2048 x 2047",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (W 0.92 GB, Delta table 0.72 GB per step)"},
+        "latency_ms": {"p50": per_sorted[len(per) // 2],
+                       "p99": per_sorted[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]},
+        "fp64": {"value": args.fp64_steps / (total64 / 1e3), "ms_per_step": total64 / args.fp64_steps,
+                 "steps": args.fp64_steps},
+        "speedup_vs_fp64": (value / world) / (args.fp64_steps / (total64 / 1e3)),
+        "max_rel_err": err,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * 9,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    pm.close()
+    p64.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

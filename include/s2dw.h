@@ -114,10 +114,14 @@ int s2dw_analysis(s2dw_plan_t plan, const void* flm, void* W, void* Wphi, void* 
 int s2dw_synthesis(s2dw_plan_t plan, const void* W, const void* Wphi, void* flm, void* stream);
 
 /*
- * Batched forms: njobs transforms, each with its own plan (plans may differ
- * in L, N, lambda and precision, but must all be distinct objects), run as
- * one set of launches per stage (grouped by N and precision).  Arrays are
- * HOST arrays of njobs device pointers.  Same layouts as the single calls.
+ * Batched forms: njobs (1..64) transforms, each with its own plan (plans may
+ * differ in L, N, lambda and J0 but must be distinct objects of one precision;
+ * mixed precisions give S2DW_ENOTSUP), run as one set of launches per stage
+ * (the contraction once per distinct N).  Arrays are HOST arrays of njobs
+ * device pointers.  Same layouts as the single calls.  The launch lists of a
+ * plan set are built on first use and cached until one of its plans is
+ * destroyed, so repeated batches (e.g. under CUDA graph capture) make no
+ * host-to-device copies.
  */
 int s2dw_analysis_batch(const s2dw_plan_t* plans, const void* const* flm, void* const* W,
                         void* const* Wphi, int njobs, void* stream);
@@ -143,6 +147,21 @@ const char* s2dw_strerror(int status);
 int s2dw_scale_support(s2dw_plan_t plan, int j, int* lo, int* hi);
 int s2dw_delta_slab(s2dw_plan_t plan, int l, double* host_out);
 int s2dw_stage(s2dw_plan_t plan, int stage, int j, void* host_out, int64_t* nbytes);
+
+/*
+ * Stage timing (instrumentation; the paper has no counterpart).
+ *   s2dw_profile(plan, 1) resets the counters and makes the next (up to 256)
+ *   s2dw_analysis / s2dw_synthesis calls on this plan record CUDA events
+ *   around each of their launches, on the call's stream; 0 stops recording.
+ *   s2dw_profile_read(plan, ms, ncalls) waits for the recorded calls and
+ *   fills ms[9] with per-stage durations (ms) summed over them:
+ *   [0] analysis contraction + gamma step, [1] scaling contraction,
+ *   [2] beta step, [3] alpha step; [4] synthesis alpha step, [5] beta step,
+ *   [6] contraction, [7] scaling contraction, [8] final reduction;
+ *   ncalls[2] (may be NULL) gets the numbers of analysis and synthesis calls.
+ */
+int s2dw_profile(s2dw_plan_t plan, int enable);
+int s2dw_profile_read(s2dw_plan_t plan, double* ms, int* ncalls);
 
 #ifdef __cplusplus
 }

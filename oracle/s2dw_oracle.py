@@ -383,7 +383,7 @@ def _synth_factors(L, N):
     return alpha, beta, gamma, q
 
 
-def synthesis(W, Wphi, L: int, N: int, lam: float, J0: int, kern=None):
+def synthesis(W, Wphi, L: int, N: int, lam: float, J0: int, kern=None, b_list=None):
     """f_lm from wavelet and scaling coefficients.
 
     Wavelet part, Eqs. (32)-(33):
@@ -391,6 +391,7 @@ def synthesis(W, Wphi, L: int, N: int, lam: float, J0: int, kern=None):
       (W^j)^l_mn = int_SO(3) W^j D^l_mn, evaluated exactly by the quadratures
       of Sec. 3.1: 2pi/(2L-1) sum_a (Eq. (19)), sum_b q(beta_b) (Eq. (17)),
       and 2pi z_n sum_g with z_n = 1/N over gamma_g in [0, pi) (Eq. (39)).
+    b_list restricts the beta sum to those rows (a partial sum; default all).
     Scaling part, Eq. (41):
       f_lm += sqrt((2l+1)/4pi) W^Phi_lm Phi_l0, with
       W^Phi_lm = sqrt((2l+1)/4pi) int_S2 W^Phi e^{-im phi} d^l_m0(theta).
@@ -406,7 +407,7 @@ def synthesis(W, Wphi, L: int, N: int, lam: float, J0: int, kern=None):
     wg = 2.0 * np.pi / N
     Fw = np.zeros((L, 2 * L - 1), dtype=np.complex128)
     Fs = np.zeros((L, 2 * L - 1), dtype=np.complex128)
-    for b in range(2 * L):
+    for b in (range(2 * L) if b_list is None else b_list):
         D = wigner_d(beta[b], L, ms[:, None], ns[None, :])        # [l][m][k]
         D0 = wigner_d(beta[b], L, ms, 0)                          # [l][m]
         for j in range(J1):

@@ -41,7 +41,12 @@ _SIGNATURES = {
     "s2dw_scale_support": (_c_i, [_c_p, _c_i, _c_ip, _c_ip]),
     "s2dw_delta_slab": (_c_i, [_c_p, _c_i, _c_dp]),
     "s2dw_stage": (_c_i, [_c_p, _c_i, _c_i, _c_p, _c_i64p]),
+    "s2dw_profile": (_c_i, [_c_p, _c_i]),
+    "s2dw_profile_read": (_c_i, [_c_p, _c_dp, _c_ip]),
 }
+
+STAGES = ["ana_contract", "ana_contract_phi", "ana_beta", "ana_alpha", "syn_alpha", "syn_beta",
+          "syn_contract", "syn_contract_phi", "syn_reduce"]
 
 
 class S2dwError(RuntimeError):
@@ -168,6 +173,18 @@ def s2dw_stage(plan: int, stage: int, j: int, complex_dtype) -> np.ndarray:
     return out
 
 
+def s2dw_profile(plan: int, enable: bool) -> None:
+    _check(lib().s2dw_profile(plan, 1 if enable else 0), "s2dw_profile")
+
+
+def s2dw_profile_read(plan: int):
+    """(per-stage summed ms, number of analysis calls, number of synthesis calls)."""
+    ms = np.zeros(9, dtype=np.float64)
+    nc = (ctypes.c_int * 2)()
+    _check(lib().s2dw_profile_read(plan, ms.ctypes.data_as(_c_dp), nc), "s2dw_profile_read")
+    return dict(zip(STAGES, ms.tolist())), nc[0], nc[1]
+
+
 # ---- thin object wrapper ----------------------------------------------------
 
 class Plan:
@@ -235,6 +252,12 @@ class Plan:
 
     def delta_slab(self, l):
         return s2dw_delta_slab(self.handle, l)
+
+    def profile(self, enable=True):
+        s2dw_profile(self.handle, enable)
+
+    def profile_read(self):
+        return s2dw_profile_read(self.handle)
 
     def stage(self, stage, j):
         cd = np.complex128 if self.precision == "fp64" else np.complex64

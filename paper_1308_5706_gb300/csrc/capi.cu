@@ -179,7 +179,16 @@ struct s2dw_plan_s {
   std::vector<unsigned char> desc_w_host, desc_phi_host;
   std::vector<TileTask> tiles_w_host, tiles_phi_host;
   Lists own;
+  // stage timing (s2dw_profile): one set of events per call, up to kProfCalls
+  static constexpr int kProfCalls = 256;
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_ana, ev_syn;  // kProfCalls x 5, kProfCalls x 6
+  int nana = 0, nsyn = 0;
   ~s2dw_plan_s() {
+    for (auto e : ev_ana)
+      if (e) cudaEventDestroy(e);
+    for (auto e : ev_syn)
+      if (e) cudaEventDestroy(e);
     if (ws) cudaFree(ws);
     delta_release(tab);
   }
@@ -421,33 +430,51 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
   return ls;
 }
 
+inline void rec(cudaEvent_t* ev, int i, cudaStream_t st) {
+  if (ev) cudaEventRecord(ev[i], st);
+}
+
+// Analysis stages: [contraction + gamma | scaling contraction | beta | alpha].
 template <typename T>
-void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st) {
+void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   const ContractDesc<T>* dw = reinterpret_cast<const ContractDesc<T>*>(ls.desc_w);
   const ContractDesc<T>* dp = reinterpret_cast<const ContractDesc<T>*>(ls.desc_phi);
+  rec(ev, 0, st);
   for (auto& t : ls.tiles_w)
     launch_contract<T>(t.first, 2, false, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
                        ptrs, st);
+  rec(ev, 1, st);
   launch_contract<T>(1, 1, false, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+  rec(ev, 2, st);
   launch_czt<T>(CZT_BETA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[0]), ls.nseg[0], ls.items[0], ls.maxlogM,
                 ptrs, st);
+  rec(ev, 3, st);
   launch_czt<T>(CZT_ALPHA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1], ls.maxlogM,
                 ptrs, st);
+  rec(ev, 4, st);
 }
 
+// Synthesis stages: [alpha | beta | contraction | scaling contraction | reduction].
 template <typename T>
-void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, int njobs, cudaStream_t st) {
+void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, int njobs, cudaStream_t st,
+                   cudaEvent_t* ev = nullptr) {
   const ContractDesc<T>* dw = reinterpret_cast<const ContractDesc<T>*>(ls.desc_w);
   const ContractDesc<T>* dp = reinterpret_cast<const ContractDesc<T>*>(ls.desc_phi);
+  rec(ev, 0, st);
   launch_czt<T>(CZT_ALPHA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[2]), ls.nseg[2], ls.items[2], ls.maxlogM,
                 ptrs, st);
+  rec(ev, 1, st);
   launch_czt<T>(CZT_BETA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[3]), ls.nseg[3], ls.items[3], ls.maxlogM,
                 ptrs, st);
+  rec(ev, 2, st);
   for (auto& t : ls.tiles_w)
     launch_contract<T>(t.first, 2, true, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
                        ptrs, st);
+  rec(ev, 3, st);
   launch_contract<T>(1, 1, true, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+  rec(ev, 4, st);
   launch_syn_reduce<T>(rj, njobs, ls.Lmax, st);
+  rec(ev, 5, st);
 }
 
 template <typename T>
@@ -764,8 +791,10 @@ int s2dw_analysis(s2dw_plan_t p, const void* flm, void* W, void* Wphi, void* str
   ptrs.f[0] = flm;
   ptrs.W[0] = W;
   ptrs.Wphi[0] = Wphi;
-  if (p->fp64) run_analysis<double>(p->own, ptrs, st);
-  else run_analysis<float>(p->own, ptrs, st);
+  cudaEvent_t* ev = nullptr;
+  if (p->prof && p->nana < s2dw_plan_s::kProfCalls) ev = p->ev_ana.data() + 5 * (p->nana++);
+  if (p->fp64) run_analysis<double>(p->own, ptrs, st, ev);
+  else run_analysis<float>(p->own, ptrs, st, ev);
   return err_of(cudaGetLastError());
 }
 
@@ -785,9 +814,61 @@ int s2dw_synthesis(s2dw_plan_t p, const void* W, const void* Wphi, void* flm, vo
   rj.L[0] = p->L;
   rj.lend[0] = p->lend_w;
   rj.Lphi[0] = p->Lphi;
-  if (p->fp64) run_synthesis<double>(p->own, ptrs, rj, 1, st);
-  else run_synthesis<float>(p->own, ptrs, rj, 1, st);
+  cudaEvent_t* ev = nullptr;
+  if (p->prof && p->nsyn < s2dw_plan_s::kProfCalls) ev = p->ev_syn.data() + 6 * (p->nsyn++);
+  if (p->fp64) run_synthesis<double>(p->own, ptrs, rj, 1, st, ev);
+  else run_synthesis<float>(p->own, ptrs, rj, 1, st, ev);
   return err_of(cudaGetLastError());
+}
+
+int s2dw_profile(s2dw_plan_t p, int enable) {
+  if (!p) return S2DW_EINVAL;
+  if (enable && p->ev_ana.empty()) {
+    p->ev_ana.assign(5 * s2dw_plan_s::kProfCalls, nullptr);
+    p->ev_syn.assign(6 * s2dw_plan_s::kProfCalls, nullptr);
+    for (auto& e : p->ev_ana)
+      if (cudaEventCreate(&e) != cudaSuccess) return S2DW_ECUDA;
+    for (auto& e : p->ev_syn)
+      if (cudaEventCreate(&e) != cudaSuccess) return S2DW_ECUDA;
+  }
+  p->prof = enable != 0;
+  p->nana = 0;
+  p->nsyn = 0;
+  return S2DW_OK;
+}
+
+int s2dw_profile_read(s2dw_plan_t p, double* ms, int* ncalls) {
+  if (!p || !ms) return S2DW_EINVAL;
+  for (int i = 0; i < 9; ++i) ms[i] = 0.0;
+  if (ncalls) ncalls[0] = ncalls[1] = 0;
+  if (p->ev_ana.empty()) return S2DW_OK;
+  cudaError_t e = cudaSuccess;
+  int na = 0, ns = 0;
+  for (int c = 0; c < p->nana; ++c) {
+    cudaEvent_t* ev = p->ev_ana.data() + 5 * c;
+    if ((e = cudaEventSynchronize(ev[4])) != cudaSuccess) return err_of(e);
+    for (int i = 0; i < 4; ++i) {
+      float t = 0.f;
+      if ((e = cudaEventElapsedTime(&t, ev[i], ev[i + 1])) != cudaSuccess) return err_of(e);
+      ms[i] += t;
+    }
+    ++na;
+  }
+  for (int c = 0; c < p->nsyn; ++c) {
+    cudaEvent_t* ev = p->ev_syn.data() + 6 * c;
+    if ((e = cudaEventSynchronize(ev[5])) != cudaSuccess) return err_of(e);
+    for (int i = 0; i < 5; ++i) {
+      float t = 0.f;
+      if ((e = cudaEventElapsedTime(&t, ev[i], ev[i + 1])) != cudaSuccess) return err_of(e);
+      ms[4 + i] += t;
+    }
+    ++ns;
+  }
+  if (ncalls) {
+    ncalls[0] = na;
+    ncalls[1] = ns;
+  }
+  return S2DW_OK;
 }
 
 static int batch_lists(const s2dw_plan_t* plans, int njobs, Lists** out, bool* fp64) {
