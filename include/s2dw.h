@@ -163,6 +163,39 @@ int s2dw_stage(s2dw_plan_t plan, int stage, int j, void* host_out, int64_t* nbyt
 int s2dw_profile(s2dw_plan_t plan, int enable);
 int s2dw_profile_read(s2dw_plan_t plan, double* ms, int* ncalls);
 
+/*
+ * s2dw_delta_table_noalloc: build the Wigner Delta table without allocating.
+ *   The paper has no counterpart to this entry point.  It serves callers
+ *   that cannot let this library call cudaMalloc: code whose device memory
+ *   is owned by another allocator (a framework's caching pool, or a fixed
+ *   arena reserved at start-up), or code running where a new allocation
+ *   would synchronise the device or is not allowed at all.  Such a caller
+ *   allocates the output itself; the only other device memory used is one
+ *   fixed 6.3 MB scratch array inside this library, which every GPU that
+ *   loads the library keeps until the process exits.  No cudaMalloc,
+ *   cudaFree or other allocating call is made.
+ *   Lmax: the table covers 0 <= l < Lmax.  1 <= Lmax <= 1024 (the scratch
+ *     array's size); Lmax > 1024 returns S2DW_ENOTSUP, Lmax < 1 S2DW_EINVAL.
+ *   entries (may be NULL): receives the number of table entries,
+ *     32 C (C+1) (C+2) / 3 + (Lmax mod 4) * 8 (C+1) (C+2), C = floor(Lmax/4).
+ *   table64: device array of that many doubles (NULL: only report the size,
+ *     no device work); table32: NULL or a device array of that many floats
+ *     that receives the float32 copy.
+ *   Layout (the plans use the same one): slab l starts at entry
+ *     32 C(C+1)(C+2)/3 + (l mod 4) * 8 c(c+1), C = floor(l/4), c = C+1; in it,
+ *     Delta^l_{m'm} with m >= 4 floor(m'/4) sits at
+ *     16 q c - 8 q (q-1) + 4 r (c-q) + m - 4q, q = floor(m'/4), r = m' mod 4;
+ *     the remaining entries follow from Delta_{m'm} = (-1)^{m'-m} Delta_{m m'}
+ *     and Delta_{-m',m} = (-1)^{l+m} Delta_{m'm}; padding entries are zero.
+ *   Asynchronous on `stream`: the output buffers are cleared and written.
+ *   The first call on each device looks up the device address of the scratch
+ *   array (cudaGetSymbolAddress) -- make that first call before any stream
+ *   capture.  All calls share the one scratch array and its contents stay
+ *   from the previous call: calls whose GPU work overlaps (two streams, two
+ *   host threads) race and corrupt each other; serialise them.
+ */
+int s2dw_delta_table_noalloc(int Lmax, double* table64, float* table32, int64_t* entries, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,7 @@ _SIGNATURES = {
     "s2dw_stage": (_c_i, [_c_p, _c_i, _c_i, _c_p, _c_i64p]),
     "s2dw_profile": (_c_i, [_c_p, _c_i]),
     "s2dw_profile_read": (_c_i, [_c_p, _c_dp, _c_ip]),
+    "s2dw_delta_table_noalloc": (_c_i, [_c_i, _c_p, _c_p, _c_i64p, _c_p]),
 }
 
 STAGES = ["ana_contract", "ana_contract_phi", "ana_beta", "ana_alpha", "syn_alpha", "syn_beta",
@@ -183,6 +184,16 @@ def s2dw_profile_read(plan: int):
     nc = (ctypes.c_int * 2)()
     _check(lib().s2dw_profile_read(plan, ms.ctypes.data_as(_c_dp), nc), "s2dw_profile_read")
     return dict(zip(STAGES, ms.tolist())), nc[0], nc[1]
+
+
+def s2dw_delta_table_noalloc(Lmax: int, table64=None, table32=None, stream=None) -> int:
+    """Number of table entries; with table64 given, builds the table into the
+    caller's device buffers (no allocation by the library)."""
+    n = ctypes.c_int64()
+    st = _stream(stream) if table64 is not None else 0
+    _check(lib().s2dw_delta_table_noalloc(Lmax, _ptr(table64), _ptr(table32), ctypes.byref(n), st),
+           "s2dw_delta_table_noalloc")
+    return n.value
 
 
 # ---- thin object wrapper ----------------------------------------------------
