@@ -673,13 +673,13 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
     p->Lphi = p->lphi + 1;
     p->Ycols = p->Lj;
     p->Ycols.push_back(p->Lphi);
-    p->Lp = round_up(L, 4);
+    p->Lp = round_up(L, 32);  // R-table row pitch: whole 32-row tiles are staged
     p->Lp32 = round_up(L, 32);
-    p->Lphip = round_up(p->Lphi, 4);
+    p->Lphip = round_up(p->Lphi, 32);
     p->Lphip32 = round_up(p->Lphi, 32);
     p->nbr = (p->L0 + p->TMP - 1) / p->TMP;
     p->nbr_phi = (p->Lphi + p->TMP - 1) / p->TMP;
-    p->logM = 4;
+    p->logM = 5;  // the radix-16 convolution engine needs M >= 32
     while ((1 << p->logM) < 4 * L - 2) ++p->logM;
     p->M = 1 << p->logM;
     p->tab = delta_acquire(L, st);

@@ -18,52 +18,60 @@
 // Each l has at most two active scales (the open supports of kappa^j and
 // kappa^{j-2} are disjoint), held in two accumulator slots (j % 2).
 //
+// Data movement: per l, the tile's Delta block (stored rows m' x columns m,
+// and for tiles below the diagonal the stored rows m x columns m'), the 32
+// values f_lm and the R rows are copied by cp.async into a STAGES-deep ring
+// in shared memory, issued STAGES-1 iterations ahead; one barrier per l.
 // Thread layout: 256 threads, each owning E consecutive rows m' and one
-// column m of a (8E x 32) tile.  Tiles with every row above every column
-// ("transposed") map lanes along m' so that the Delta loads, which then read
-// the stored row m, stay coalesced.
+// column m of a (8E x 32) tile.  Tiles with every row above every column map
+// lanes along m' so that their reads of the transposed block stay conflict free.
 #pragma once
 
 #include "internal.h"
 
 namespace s2dw {
 
-template <typename T, int E> struct VecLd;
-template <> struct VecLd<float, 4> {
-  static __device__ __forceinline__ void ld(const float* p, float (&r)[4]) {
-    float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
-  }
-};
-template <> struct VecLd<double, 2> {
-  static __device__ __forceinline__ void ld(const double* p, double (&r)[2]) {
-    double2 v = __ldg(reinterpret_cast<const double2*>(p));
-    r[0] = v.x; r[1] = v.y;
-  }
-};
-template <> struct VecLd<float, 2> {
-  static __device__ __forceinline__ void ld(const float* p, float (&r)[2]) {
-    float2 v = __ldg(reinterpret_cast<const float2*>(p));
-    r[0] = v.x; r[1] = v.y;
-  }
-};
-template <> struct VecLd<double, 4> {
-  static __device__ __forceinline__ void ld(const double* p, double (&r)[4]) {
-    double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
-    r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y;
-  }
+constexpr int STAGES = 4;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory geometry of one pipeline stage (element counts of T).
+template <typename T, int N, int NSLOT, int E>
+struct StageGeom {
+  static constexpr int TMP = 8 * E;                 // tile rows (m')
+  static constexpr int EPC = 16 / sizeof(T);        // elements per 16-byte chunk
+  static constexpr int APITCH = TILE + EPC;         // block A: [TMP][APITCH], stored rows m' x cols m
+  static constexpr int BPITCH = TMP;                // block B: [TILE][BPITCH], stored rows m x cols m'
+  static constexpr int A_OFF = 0;
+  static constexpr int B_OFF = A_OFF + TMP * APITCH;
+  static constexpr int F_OFF = B_OFF + TILE * BPITCH;         // TILE complex = 2*TILE elements
+  static constexpr int R_OFF = F_OFF + 2 * TILE;              // [NSLOT][N][TMP]
+  static constexpr int SIZE = R_OFF + NSLOT * N * TMP;
+  static constexpr size_t BYTES = (size_t)SIZE * sizeof(T);
 };
 
-template <typename T> __device__ __forceinline__ cx<T> ldc(const cx<T>* p) { return __ldg(p); }
+template <typename T, int N, int NSLOT, bool SYN, int E>
+constexpr size_t contract_smem_bytes() {
+  return STAGES * StageGeom<T, N, NSLOT, E>::BYTES + (SYN ? 2 * LCH * 8 * TILE * sizeof(cx<T>) : 0);
+}
 
 template <typename T, int N, int NSLOT, bool SYN, int E>
 __global__ void __launch_bounds__(256)
 k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict__ tiles, CallPtrs ptrs) {
-  constexpr int RG = 8;            // row groups per tile (= 256 / 32 lanes)
-  constexpr int TMP = RG * E;      // tile rows (m')
+  using G = StageGeom<T, N, NSLOT, E>;
+  constexpr int RG = 8;
+  constexpr int TMP = G::TMP;
+  constexpr int EPC = G::EPC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  cx<T>* red = reinterpret_cast<cx<T>*>(smem_raw + STAGES * G::BYTES);  // [2][LCH][RG][TILE]
   __shared__ cx<T> cgk[N][N];
-  __shared__ cx<T> red[SYN ? 2 : 1][SYN ? LCH : 1][RG][32];
 
   const TileTask tk = tiles[blockIdx.x];
   const ContractDesc<T>* __restrict__ D = descs + tk.prob;
@@ -71,7 +79,9 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   const T* __restrict__ delta = D->delta;
   const T* __restrict__ RS = D->RS;
   const int mp0 = tk.bmp * TMP, m0 = tk.bm * TILE;
-  const bool ttile = mp0 > m0 + TILE - 1;
+  const bool ttile = mp0 > m0 + TILE - 1;                 // every row above every column
+  const bool need_a = m0 + TILE - 1 >= (mp0 & ~3);        // some entry stored as (m', m)
+  const bool need_b = m0 < ((mp0 + TMP - 1) & ~3);        // some entry stored as (m, m')
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int c, rg;
   if (!ttile) {
@@ -84,20 +94,6 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   const int m = m0 + c;
   const int mpb = mp0 + E * rg;
   const bool tr = m < (mpb & ~3);
-  int dA[E], dB[E];
-  if (!tr) {
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      dA[e] = delta_row_A(mpb + e, m);
-      dB[e] = delta_row_B(mpb + e);
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      dA[e] = delta_row_A(m, mpb);
-      dB[e] = delta_row_B(m);
-    }
-  }
   const T sg0 = ((mpb - m) & 1) ? T(-1) : T(1);
 
   if (threadIdx.x < N * N) {
@@ -107,20 +103,76 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
     sincospi((double)(n * g) / (double)N, &sn, &cs);
     cx<T> v;
     if (!SYN) {
-      // conj(eta) i^{n} e^{i n gamma_g}
-      v = mkc<T>((T)cs, (T)sn);
+      v = mkc<T>((T)cs, (T)sn);  // conj(eta) i^{n} e^{i n gamma_g}
       v = cmul_ipow<T>(v, ((n % 4) + 4) & 3);
       if (D->eta_odd) v = cmul_ipow<T>(v, 3);
     } else {
-      // eta (2 pi / N) i^{-n} e^{-i n gamma_g}
-      const double sc = 2.0 * 3.14159265358979323846 / N;
+      const double sc = 2.0 * 3.14159265358979323846 / N;  // eta (2 pi / N) i^{-n} e^{-i n gamma_g}
       v = mkc<T>((T)(cs * sc), (T)(-sn * sc));
       v = cmul_ipow<T>(v, (((-n) % 4) + 4) & 3);
       if (D->eta_odd) v = cmul_ipow<T>(v, 1);
     }
     cgk[k][g] = v;
   }
-  __syncthreads();
+
+  const cx<T>* __restrict__ f = SYN ? nullptr : reinterpret_cast<const cx<T>*>(ptrs.f[tk.prob]);
+  const int l_start = tk.lstart, l_end = tk.lend;
+
+  // ---- producer: stage the operands of iteration l into ring slot st ----
+  auto issue = [&](int l, int st) {
+    if (l <= l_end) {
+      T* S = ring + st * G::SIZE;
+      const int cl = (l >> 2) + 1, rows_in_slab = 4 * cl;
+      const T* __restrict__ slab = delta + delta_slab_offset(l);
+      const int t = threadIdx.x;
+      // block A: rows mp0 + i (i < TMP), columns m0 .. m0 + TILE - 1
+      if (need_a) {
+        constexpr int CPR = TILE / EPC;  // chunks per row
+        if (t < TMP * CPR) {
+          const int i = t / CPR, ch = t % CPR, r = mp0 + i;
+          const T* src = slab + delta_row_A(r, m0 + ch * EPC) + (int64_t)delta_row_B(r) * cl;
+          cp_async16(S + G::A_OFF + i * G::APITCH + ch * EPC, r < rows_in_slab ? src : slab,
+                     r < rows_in_slab ? 16 : 0);
+        }
+      }
+      // block B: rows m0 + i (i < TILE), columns mp0 .. mp0 + TMP - 1
+      if (need_b) {
+        constexpr int CPR = TMP / EPC;
+        if (t < TILE * CPR) {
+          const int i = t / CPR, ch = t % CPR, r = m0 + i;
+          const T* src = slab + delta_row_A(r, mp0 + ch * EPC) + (int64_t)delta_row_B(r) * cl;
+          cp_async16(S + G::B_OFF + i * G::BPITCH + ch * EPC, r < rows_in_slab ? src : slab,
+                     r < rows_in_slab ? 16 : 0);
+        }
+      }
+      if (!SYN) {
+        // f_lm for m in [m0, m0 + TILE), zero beyond m = l (the array ends at l = L-1)
+        constexpr int FCH = 2 * TILE / EPC;
+        constexpr int CPC = EPC / 2;  // complex values per chunk
+        const int q = t - 256 + FCH;  // use the last FCH threads
+        if (q >= 0) {
+          const int mm = m0 + q * CPC;
+          const int nvalid = min(CPC, max(0, l + 1 - mm));
+          const cx<T>* src = f + (nvalid > 0 ? l * l + l + mm : 0);
+          cp_async16(S + G::F_OFF + q * EPC, src, nvalid * (int)sizeof(cx<T>));
+        }
+      }
+      // R rows: [s][k][mp0 .. mp0 + TMP)
+      {
+        constexpr int CPR = TMP / EPC;
+        constexpr int NCH = NSLOT * N * CPR;
+        for (int u = t; u < NCH; u += 256) {
+          const int sk = u / CPR, ch = u % CPR;
+          const T* src = RS + ((size_t)l * (NSLOT * N) + sk) * Lp + mp0 + ch * EPC;
+          cp_async16(S + G::R_OFF + sk * TMP + ch * EPC, src, 16);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+#pragma unroll
+  for (int i = 0; i < STAGES - 1; ++i) issue(l_start + i, i);
 
   cx<T> acc[E][NSLOT][N];
 #pragma unroll
@@ -130,169 +182,168 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
 #pragma unroll
       for (int k = 0; k < N; ++k) acc[e][s][k] = mkc<T>(0, 0);
 
-  const cx<T>* __restrict__ f = SYN ? nullptr : reinterpret_cast<const cx<T>*>(ptrs.f[tk.prob]);
-  const int l_start = tk.lstart, l_end = tk.lend;
   int cur[2] = {-1, -1};
   int sidx = 0;
   while (sidx < D->nseg && D->seg[sidx].hi < l_start) ++sidx;
-  int l = l_start;
-  int buf = 0;
+  int seg_hi = -1;
+  int rbuf = 0;
 
-  for (; sidx < D->nseg; ++sidx) {
-    const int slo = D->seg[sidx].lo, shi = D->seg[sidx].hi;
-    if (slo > l_end) break;
+  // analysis epilogue (gamma step) for slot s holding scale j
+  auto flush = [&](int s, int j) {
+    const int Lj = D->Lj[j];
+    cx<T>* __restrict__ Y = D->Y[j];
 #pragma unroll
-    for (int s = 0; s < NSLOT; ++s) {
-      const int jn = D->seg[sidx].j[s];
-      if (jn != cur[s]) {
-        if (!SYN) {
-          if (cur[s] >= 0) {
-            // ---- analysis epilogue: gamma step, write Y^j ----
-            const int Lj = D->Lj[cur[s]];
-            cx<T>* __restrict__ Y = D->Y[cur[s]];
+    for (int e = 0; e < E; ++e) {
+      const int mp = mpb + e;
+      if (mp < Lj && m < Lj) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-              const int mp = mpb + e;
-              if (mp < Lj && m < Lj) {
+        for (int g = 0; g < N; ++g) {
+          cx<T> v = mkc<T>(0, 0);
 #pragma unroll
-                for (int g = 0; g < N; ++g) {
-                  cx<T> v = mkc<T>(0, 0);
+          for (int k = 0; k < N; ++k) v = cadd<T>(v, cmul<T>(acc[e][s][k], cgk[k][g]));
+          Y[((size_t)g * Lj + mp) * Lj + m] = cmul_ipow<T>(v, (-m) & 3);
+        }
+      }
+    }
+  };
+  // synthesis prologue (gamma adjoint) for slot s, scale j (or clear)
+  auto load = [&](int s, int j) {
 #pragma unroll
-                  for (int k = 0; k < N; ++k) v = cadd<T>(v, cmul<T>(acc[e][s][k], cgk[k][g]));
-                  Y[((size_t)g * Lj + mp) * Lj + m] = cmul_ipow<T>(v, (-m) & 3);
-                }
-              }
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc[e][s][k] = mkc<T>(0, 0);
+    if (j < 0) return;
+    const int Lj = D->Lj[j];
+    const cx<T>* __restrict__ V = D->Y[j];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int mp = mpb + e;
+      if (mp < Lj && m < Lj) {
+#pragma unroll
+        for (int g = 0; g < N; ++g) {
+          const cx<T> vg = V[((size_t)g * Lj + mp) * Lj + m];
+#pragma unroll
+          for (int k = 0; k < N; ++k) acc[e][s][k] = cadd<T>(acc[e][s][k], cmul<T>(vg, cgk[k][g]));
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc[e][s][k] = cmul_ipow<T>(acc[e][s][k], m & 3);
+      }
+    }
+  };
+  auto reduce_chunk = [&](int buf, int lfirst, int count) {
+    const int lc2 = threadIdx.x >> 5, c2 = threadIdx.x & 31;
+    if (lc2 < count) {
+      const cx<T>* rb = red + (size_t)buf * LCH * RG * TILE;
+      cx<T> sum = mkc<T>(0, 0);
+#pragma unroll
+      for (int r2 = 0; r2 < RG; ++r2) sum = cadd<T>(sum, rb[(lc2 * RG + r2) * TILE + c2]);
+      D->P[((size_t)tk.bmp * D->L + lfirst + lc2) * D->Lp32 + m0 + c2] = sum;
+    }
+  };
+
+  __syncthreads();  // cgk visible
+  for (int l = l_start; l <= l_end; ++l) {
+    const int it = l - l_start;
+    cp_async_wait<STAGES - 2>();
+    __syncthreads();
+    issue(l + STAGES - 1, (it + STAGES - 1) % STAGES);
+    if (SYN && it > 0 && (it % LCH) == 0) reduce_chunk(rbuf ^ 1, l - LCH, LCH);
+    // slot occupancy changes at segment boundaries
+    if (l > seg_hi) {
+      while (D->seg[sidx].hi < l) ++sidx;
+      seg_hi = D->seg[sidx].hi;
+#pragma unroll
+      for (int s = 0; s < NSLOT; ++s) {
+        const int jn = D->seg[sidx].j[s];
+        if (jn != cur[s]) {
+          if (!SYN) {
+            if (cur[s] >= 0) flush(s, cur[s]);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
 #pragma unroll
               for (int k = 0; k < N; ++k) acc[e][s][k] = mkc<T>(0, 0);
-            }
+          } else {
+            load(s, jn);
           }
-        } else {
-          // ---- synthesis prologue: gamma adjoint, load H^j ----
+          cur[s] = jn;
+        }
+      }
+    }
+    const T* S = ring + (it % STAGES) * G::SIZE;
+    const bool valid = (m <= l) && (mpb <= l);
+    cx<T> part = mkc<T>(0, 0);
+    if (valid) {
+      T dv[E];
+      if (!tr) {
 #pragma unroll
-          for (int e = 0; e < E; ++e)
+        for (int e = 0; e < E; ++e) dv[e] = S[G::A_OFF + (mpb - mp0 + e) * G::APITCH + c];
+      } else {
 #pragma unroll
-            for (int k = 0; k < N; ++k) acc[e][s][k] = mkc<T>(0, 0);
-          if (jn >= 0) {
-            const int Lj = D->Lj[jn];
-            const cx<T>* __restrict__ V = D->Y[jn];
+        for (int e = 0; e < E; ++e) dv[e] = ((e & 1) ? -sg0 : sg0) * S[G::B_OFF + c * G::BPITCH + (mpb - mp0 + e)];
+      }
+      const T* Rr = S + G::R_OFF + (mpb - mp0);
+      if (!SYN) {
+        const cx<T> fv = reinterpret_cast<const cx<T>*>(S + G::F_OFF)[c];
+        cx<T> tt[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) tt[e] = mkc<T>(dv[e] * fv.x, dv[e] * fv.y);
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s) {
+          if (cur[s] < 0) continue;
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const T* rp = Rr + (s * N + k) * TMP;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-              const int mp = mpb + e;
-              if (mp < Lj && m < Lj) {
-#pragma unroll
-                for (int g = 0; g < N; ++g) {
-                  const cx<T> vg = V[((size_t)g * Lj + mp) * Lj + m];
-#pragma unroll
-                  for (int k = 0; k < N; ++k) acc[e][s][k] = cadd<T>(acc[e][s][k], cmul<T>(vg, cgk[k][g]));
-                }
-#pragma unroll
-                for (int k = 0; k < N; ++k) acc[e][s][k] = cmul_ipow<T>(acc[e][s][k], m & 3);
-              }
+              const T r = rp[e];
+              acc[e][s][k].x = fma(tt[e].x, r, acc[e][s][k].x);
+              acc[e][s][k].y = fma(tt[e].y, r, acc[e][s][k].y);
             }
           }
         }
-        cur[s] = jn;
+      } else {
+        cx<T> p[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) p[e] = mkc<T>(0, 0);
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s) {
+          if (cur[s] < 0) continue;
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const T* rp = Rr + (s * N + k) * TMP;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const T r = rp[e];
+              p[e].x = fma(acc[e][s][k].x, r, p[e].x);
+              p[e].y = fma(acc[e][s][k].y, r, p[e].y);
+            }
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          part.x = fma(dv[e], p[e].x, part.x);
+          part.y = fma(dv[e], p[e].y, part.y);
+        }
       }
     }
-    const int lhi = min(shi, l_end);
-    for (; l <= lhi; ++l) {
-      const bool valid = (m <= l) && (mpb <= l);
-      cx<T> part = mkc<T>(0, 0);
-      if (valid) {
-        const int cl = (l >> 2) + 1;
-        const T* __restrict__ slab = delta + delta_slab_offset(l);
-        T dv[E];
-        if (!tr) {
-#pragma unroll
-          for (int e = 0; e < E; ++e) dv[e] = __ldg(slab + dA[e] + dB[e] * cl);
-        } else {
-          VecLd<T, E>::ld(slab + dA[0] + dB[0] * cl, dv);
-#pragma unroll
-          for (int e = 0; e < E; ++e) dv[e] *= (e & 1) ? -sg0 : sg0;
-        }
-        const T* __restrict__ rrow = RS + (size_t)l * (NSLOT * N) * Lp + mpb;
-        if (!SYN) {
-          const cx<T> fv = ldc<T>(f + l * l + l + m);
-          cx<T> t[E];
-#pragma unroll
-          for (int e = 0; e < E; ++e) t[e] = mkc<T>(dv[e] * fv.x, dv[e] * fv.y);
-#pragma unroll
-          for (int s = 0; s < NSLOT; ++s) {
-            if (cur[s] < 0) continue;
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-              T r[E];
-              VecLd<T, E>::ld(rrow + (size_t)(s * N + k) * Lp, r);
-#pragma unroll
-              for (int e = 0; e < E; ++e) {
-                acc[e][s][k].x = fma(t[e].x, r[e], acc[e][s][k].x);
-                acc[e][s][k].y = fma(t[e].y, r[e], acc[e][s][k].y);
-              }
-            }
-          }
-        } else {
-          cx<T> p[E];
-#pragma unroll
-          for (int e = 0; e < E; ++e) p[e] = mkc<T>(0, 0);
-#pragma unroll
-          for (int s = 0; s < NSLOT; ++s) {
-            if (cur[s] < 0) continue;
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-              T r[E];
-              VecLd<T, E>::ld(rrow + (size_t)(s * N + k) * Lp, r);
-#pragma unroll
-              for (int e = 0; e < E; ++e) {
-                p[e].x = fma(acc[e][s][k].x, r[e], p[e].x);
-                p[e].y = fma(acc[e][s][k].y, r[e], p[e].y);
-              }
-            }
-          }
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            part.x = fma(dv[e], p[e].x, part.x);
-            part.y = fma(dv[e], p[e].y, part.y);
-          }
-        }
-      }
-      if (SYN) {
-        const int lc = (l - l_start) % LCH;
-        red[buf][lc][rg][c] = part;
-        if (lc == LCH - 1 || l == l_end) {
-          __syncthreads();
-          const int lc2 = threadIdx.x >> 5, c2 = threadIdx.x & 31;
-          if (lc2 <= lc) {
-            cx<T> sum = mkc<T>(0, 0);
-#pragma unroll
-            for (int r2 = 0; r2 < RG; ++r2) sum = cadd<T>(sum, red[buf][lc2][r2][c2]);
-            const int lrow = l - lc + lc2;
-            D->P[((size_t)tk.bmp * D->L + lrow) * D->Lp32 + m0 + c2] = sum;
-          }
-          buf ^= 1;
-        }
-      }
+    if (SYN) {
+      const int lc = it % LCH;
+      red[((size_t)rbuf * LCH + lc) * RG * TILE + rg * TILE + c] = part;
+      if (lc == LCH - 1) rbuf ^= 1;
     }
   }
-  if (!SYN) {
+  cp_async_wait<0>();
+  if (SYN) {
+    __syncthreads();
+    const int n_it = l_end - l_start + 1;
+    const int last = (n_it - 1) % LCH + 1;         // entries in the final chunk
+    const int lfirst = l_end - last + 1;
+    const int buf = (last == LCH) ? (rbuf ^ 1) : rbuf;
+    reduce_chunk(buf, lfirst, last);
+  } else {
 #pragma unroll
-    for (int s = 0; s < NSLOT; ++s) {
-      if (cur[s] < 0) continue;
-      const int Lj = D->Lj[cur[s]];
-      cx<T>* __restrict__ Y = D->Y[cur[s]];
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int mp = mpb + e;
-        if (mp < Lj && m < Lj) {
-#pragma unroll
-          for (int g = 0; g < N; ++g) {
-            cx<T> v = mkc<T>(0, 0);
-#pragma unroll
-            for (int k = 0; k < N; ++k) v = cadd<T>(v, cmul<T>(acc[e][s][k], cgk[k][g]));
-            Y[((size_t)g * Lj + mp) * Lj + m] = cmul_ipow<T>(v, (-m) & 3);
-          }
-        }
-      }
-    }
+    for (int s = 0; s < NSLOT; ++s)
+      if (cur[s] >= 0) flush(s, cur[s]);
   }
 }
 
@@ -326,19 +377,33 @@ __global__ void k_syn_reduce(ReduceJobs jobs, int tmp) {
   }
 }
 
+template <typename T, int N, int NSLOT, bool SYN, int E>
+void launch_one(dim3 grid, const ContractDesc<T>* descs, const TileTask* tiles, const CallPtrs& ptrs,
+                cudaStream_t st) {
+  constexpr size_t smem = contract_smem_bytes<T, N, NSLOT, SYN, E>();
+  static unsigned long long dev_done = 0;  // devices on which the smem cap is set
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !(dev_done & (1ull << dev))) {
+    cudaFuncSetAttribute(k_contract<T, N, NSLOT, SYN, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev < 64) dev_done |= 1ull << dev;
+  }
+  k_contract<T, N, NSLOT, SYN, E><<<grid, 256, smem, st>>>(descs, tiles, ptrs);
+}
+
 template <typename T, int E>
 void launch_contract_impl(int N, int nslot, bool syn, const ContractDesc<T>* descs, const TileTask* tiles,
                           int ntiles, const CallPtrs& ptrs, cudaStream_t st) {
   if (ntiles <= 0) return;
-  dim3 grid(ntiles), block(256);
-#define S2DW_CASE(NN)                                                                          \
-  case NN:                                                                                     \
-    if (syn) k_contract<T, NN, 2, true, E><<<grid, block, 0, st>>>(descs, tiles, ptrs);        \
-    else k_contract<T, NN, 2, false, E><<<grid, block, 0, st>>>(descs, tiles, ptrs);           \
+  dim3 grid(ntiles);
+#define S2DW_CASE(NN)                                                        \
+  case NN:                                                                   \
+    if (syn) launch_one<T, NN, 2, true, E>(grid, descs, tiles, ptrs, st);    \
+    else launch_one<T, NN, 2, false, E>(grid, descs, tiles, ptrs, st);       \
     break;
   if (N == 1 && nslot == 1) {
-    if (syn) k_contract<T, 1, 1, true, E><<<grid, block, 0, st>>>(descs, tiles, ptrs);
-    else k_contract<T, 1, 1, false, E><<<grid, block, 0, st>>>(descs, tiles, ptrs);
+    if (syn) launch_one<T, 1, 1, true, E>(grid, descs, tiles, ptrs, st);
+    else launch_one<T, 1, 1, false, E>(grid, descs, tiles, ptrs, st);
     return;
   }
   switch (N) {

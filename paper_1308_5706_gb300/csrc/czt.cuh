@@ -5,7 +5,8 @@
 // Every sum has the form X_d = sum_s x_s e^{i 2 theta s d} over a contiguous
 // range of s and d, evaluated as
 //   X_d = e^{i theta d^2} sum_s (x_s e^{i theta s^2}) e^{-i theta (d-s)^2}
-// with a circular convolution of power-of-two length M >= 4L-2: inputs sit at
+// with a circular convolution of power-of-two length M >= 4L-2 (the radix-16
+// engine of fft16.cuh, one CTA per transform): inputs sit at
 // s mod M, outputs are read at d mod M, and the kernel h_u is stored at
 // u mod M for the whole u-range any scale can need, so one spectrum per
 // plan serves every scale.  theta = pi/(4L) for beta (beta_b = theta(2b+1))
@@ -21,7 +22,7 @@
 //   folded over +-m' so that every integrand is a cosine series).
 #pragma once
 
-#include "fft.cuh"
+#include "fft16.cuh"
 #include "internal.h"
 
 namespace s2dw {
@@ -39,17 +40,6 @@ __device__ __forceinline__ int czt_find_seg(const CztSeg<T>* segs, int nseg) {
 }
 
 template <typename T>
-__device__ __forceinline__ void czt_convolve(cx<T>* A, int logM, const cx<T>* __restrict__ H,
-                                             const cx<T>* __restrict__ tw) {
-  __syncthreads();
-  fft_dif<T>(A, logM, tw);
-  const int M = 1 << logM;
-  for (int v = threadIdx.x; v < M; v += blockDim.x) A[v] = cmul<T>(A[v], __ldg(H + v));
-  __syncthreads();
-  fft_dit_inv<T>(A, logM, tw);
-}
-
-template <typename T>
 __global__ void __launch_bounds__(256) k_czt_beta_ana(const CztSeg<T>* __restrict__ segs, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
@@ -58,17 +48,22 @@ __global__ void __launch_bounds__(256) k_czt_beta_ana(const CztSeg<T>* __restric
   const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM;
   const int g = item / Lj, m = item % Lj;
   const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
-  for (int v = threadIdx.x; v < M; v += blockDim.x) A[v] = mkc<T>(0, 0);
-  __syncthreads();
   const cx<T>* __restrict__ Y = sg.buf_in + (size_t)g * Lj * Lj + m;
-  for (int mp = threadIdx.x; mp < Lj; mp += blockDim.x) {
-    const cx<T> y = Y[(size_t)mp * Lj];
-    A[mp] = cmul<T>(y, __ldg(sg.pre + mp + L - 1));
-    if (mp > 0) A[M - mp] = cmul<T>(cscale<T>(y, sigma), __ldg(sg.pre + L - 1 - mp));
-  }
-  czt_convolve<T>(A, sg.logM, sg.H, sg.tw);
+  const cx<T>* __restrict__ pre = sg.pre + (L - 1);
+  auto in = [&](int v) -> cx<T> {
+    int mp;
+    if (v < Lj) mp = v;
+    else if (v > M - Lj) mp = v - M;
+    else return mkc<T>(0, 0);
+    cx<T> y = Y[(size_t)(mp < 0 ? -mp : mp) * Lj];
+    if (mp < 0) y = cscale<T>(y, sigma);
+    return cmul<T>(y, __ldg(pre + mp));
+  };
   cx<T>* __restrict__ X = sg.buf_out + (size_t)g * 2 * L * Lj + m;
-  for (int b = threadIdx.x; b < 2 * L; b += blockDim.x) X[(size_t)b * Lj] = cmul<T>(A[b], __ldg(sg.post + b));
+  auto out = [&](int v, cx<T> val) {
+    if (v < 2 * L) X[(size_t)v * Lj] = cmul<T>(val, __ldg(sg.post + v));
+  };
+  fft_convolve<T, false>(A, sg.logM, sg.H, sg.tw, in, out);
 }
 
 template <typename T>
@@ -79,25 +74,36 @@ __global__ void __launch_bounds__(256) k_czt_alpha_ana(const CztSeg<T>* __restri
   const int item = blockIdx.x - sg.start;
   const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM, n = 2 * L - 1;
   const int r1 = 2 * item;  // rows r1, r1 + 1 of the [N * 2L] row space
-  for (int v = threadIdx.x; v < M; v += blockDim.x) A[v] = mkc<T>(0, 0);
-  __syncthreads();
   const cx<T>* __restrict__ X1 = sg.buf_in + (size_t)r1 * Lj;
   const cx<T>* __restrict__ X2 = X1 + Lj;
-  for (int mm = threadIdx.x; mm < Lj; mm += blockDim.x) {
+  auto in = [&](int v) -> cx<T> {
+    int mm;
+    bool neg;
+    if (v < Lj) {
+      mm = v;
+      neg = false;
+    } else if (v > M - Lj) {
+      mm = M - v;
+      neg = true;
+    } else {
+      return mkc<T>(0, 0);
+    }
     const cx<T> x1 = X1[mm], x2 = X2[mm];
-    const cx<T> ch = __ldg(sg.pre + mm);
-    A[mm] = cmul<T>(mkc<T>(x1.x - x2.y, x1.y + x2.x), ch);              // X1 + i X2
-    if (mm > 0) A[M - mm] = cmul<T>(mkc<T>(x1.x + x2.y, x2.x - x1.y), ch);  // conj(X1) + i conj(X2)
-  }
-  czt_convolve<T>(A, sg.logM, sg.H, sg.tw);
+    const cx<T> z = neg ? mkc<T>(x1.x + x2.y, x2.x - x1.y)    // conj(X1) + i conj(X2)
+                        : mkc<T>(x1.x - x2.y, x1.y + x2.x);   // X1 + i X2
+    return cmul<T>(z, __ldg(sg.pre + mm));
+  };
   T* __restrict__ Wb = reinterpret_cast<T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff;
   T* __restrict__ W1 = Wb + (size_t)r1 * n;
   T* __restrict__ W2 = W1 + n;
-  for (int a = threadIdx.x; a < n; a += blockDim.x) {
-    const cx<T> v = cmul<T>(A[a], __ldg(sg.post + a));
-    W1[a] = v.x;
-    W2[a] = v.y;
-  }
+  auto out = [&](int v, cx<T> val) {
+    if (v < n) {
+      const cx<T> w = cmul<T>(val, __ldg(sg.post + v));
+      W1[v] = w.x;
+      W2[v] = w.y;
+    }
+  };
+  fft_convolve<T, false>(A, sg.logM, sg.H, sg.tw, in, out);
 }
 
 template <typename T>
@@ -111,19 +117,19 @@ __global__ void __launch_bounds__(256) k_czt_alpha_syn(const CztSeg<T>* __restri
   const T* __restrict__ Wb = reinterpret_cast<const T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff;
   const T* __restrict__ W1 = Wb + (size_t)r1 * n;
   const T* __restrict__ W2 = W1 + n;
-  for (int v = threadIdx.x; v < M; v += blockDim.x) {
-    cx<T> z = mkc<T>(0, 0);
-    if (v < n) z = cmulc<T>(mkc<T>(W1[v], W2[v]), __ldg(sg.pre + v));
-    A[v] = z;
-  }
-  czt_convolve<T>(A, sg.logM, sg.H, sg.tw);
+  auto in = [&](int v) -> cx<T> {
+    if (v >= n) return mkc<T>(0, 0);
+    return cmulc<T>(mkc<T>(W1[v], W2[v]), __ldg(sg.pre + v));
+  };
+  auto none = [](int, cx<T>) {};
+  fft_convolve<T, true>(A, sg.logM, sg.H, sg.tw, in, none);
   cx<T>* __restrict__ V1 = sg.buf_out + (size_t)r1 * Lj;
   cx<T>* __restrict__ V2 = V1 + Lj;
   const T h = sg.scale * T(0.5);
   for (int mm = threadIdx.x; mm < Lj; mm += blockDim.x) {
     const cx<T> ch = __ldg(sg.post + mm);
-    const cx<T> zp = cmulc<T>(A[mm], ch);
-    const cx<T> zm = cmulc<T>(A[(M - mm) & (M - 1)], ch);
+    const cx<T> zp = cmulc<T>(A[fpad(mm)], ch);
+    const cx<T> zm = cmulc<T>(A[fpad((M - mm) & (M - 1))], ch);
     // V1 = (Zp + conj(Zm))/2, V2 = (Zp - conj(Zm))/(2i)
     V1[mm] = mkc<T>((zp.x + zm.x) * h, (zp.y - zm.y) * h);
     V2[mm] = mkc<T>((zp.y + zm.y) * h, (zm.x - zp.x) * h);
@@ -140,21 +146,21 @@ __global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restric
   const int g = item / Lj, m = item % Lj;
   const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
   const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * 2 * L * Lj + m;
-  for (int v = threadIdx.x; v < M; v += blockDim.x) {
-    cx<T> z = mkc<T>(0, 0);
-    if (v < 2 * L) z = cmul<T>(V[(size_t)v * Lj], __ldg(sg.pre + v));
-    A[v] = z;
-  }
-  czt_convolve<T>(A, sg.logM, sg.H, sg.tw);
+  auto in = [&](int v) -> cx<T> {
+    if (v >= 2 * L) return mkc<T>(0, 0);
+    return cmul<T>(V[(size_t)v * Lj], __ldg(sg.pre + v));
+  };
+  auto none = [](int, cx<T>) {};
+  fft_convolve<T, true>(A, sg.logM, sg.H, sg.tw, in, none);
   cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m;
   for (int mp = threadIdx.x; mp < Lj; mp += blockDim.x) {
-    const cx<T> tp = cmul<T>(A[mp], __ldg(sg.post + L - 1 + mp));
-    cx<T> out = tp;
+    const cx<T> tp = cmul<T>(A[fpad(mp)], __ldg(sg.post + L - 1 + mp));
+    cx<T> o = tp;
     if (mp > 0) {
-      const cx<T> tm = cmul<T>(A[M - mp], __ldg(sg.post + L - 1 - mp));
-      out = mkc<T>(tp.x + sigma * tm.x, tp.y + sigma * tm.y);
+      const cx<T> tm = cmul<T>(A[fpad(M - mp)], __ldg(sg.post + L - 1 - mp));
+      o = mkc<T>(tp.x + sigma * tm.x, tp.y + sigma * tm.y);
     }
-    Vh[(size_t)mp * Lj] = out;
+    Vh[(size_t)mp * Lj] = o;
   }
 }
 
@@ -162,7 +168,7 @@ template <typename T>
 void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items, int maxlogM,
                      const CallPtrs& ptrs, cudaStream_t st) {
   if (total_items <= 0) return;
-  const size_t smem = sizeof(cx<T>) << maxlogM;
+  const size_t smem = sizeof(cx<T>) * (size_t)fft_smem_elems(1 << maxlogM);
   dim3 grid(total_items), block(256);
   switch (kind) {
     case CZT_BETA_ANA: k_czt_beta_ana<T><<<grid, block, smem, st>>>(segs, nseg); break;
@@ -175,7 +181,7 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
 
 template <typename T>
 cudaError_t czt_set_smem(int maxlogM) {
-  const int smem = (int)(sizeof(cx<T>) << maxlogM);
+  const int smem = (int)(sizeof(cx<T>) * (size_t)fft_smem_elems(1 << maxlogM));
   cudaError_t e = cudaSuccess;
   e = cudaFuncSetAttribute(k_czt_beta_ana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

@@ -1,0 +1,323 @@
+// Register-resident radix-16 FFT engine for one CTA of 256 threads.
+//
+// A power-of-two length M = 2^logM (5 <= logM <= 13) is split into stages of
+// radix 16, 16, ..., R_last (R_last in {2, 4, 8, 16}).  Forward stages are
+// decimation in frequency, in place: a block of size S = R*Q holding x[j+Q r]
+// (r < R) becomes X[j+Q k] = (sum_r x[j+Q r] e^{-2 pi i rk/R}) e^{-2 pi i jk/S}.
+// The output is in mixed-radix digit-reversed order, so a convolution needs
+// the kernel spectrum in that same order (computed with the same stages) and
+// an inverse that runs the stages backwards (decimation in time, conjugate
+// twiddles, unnormalised: it returns M times the inverse DFT).
+//
+// The first forward stage reads its inputs through a functor and the last
+// inverse stage hands its outputs to a functor, so inputs/outputs never pass
+// through shared memory on the way in or out; the last forward stage, the
+// pointwise product with the spectrum and the first inverse stage run on the
+// same registers.  Shared memory holds M (+M/16 padding) complex values.
+#pragma once
+
+#include "common.cuh"
+
+namespace s2dw {
+
+__host__ __device__ __forceinline__ int fpad(int v) { return v + (v >> 4); }
+__host__ __device__ constexpr int fft_smem_elems(int M) { return M + (M >> 4); }
+
+// e^{-2 pi i k/16}, k = 0..15 (cos, sin of multiples of pi/8)
+template <typename T> __device__ __forceinline__ cx<T> w16(int k, bool inv) {
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173, h = (T)0.70710678118654752440;
+  T re, im;
+  switch (k & 15) {
+    case 0: re = 1; im = 0; break;
+    case 1: re = c1; im = -s1; break;
+    case 2: re = h; im = -h; break;
+    case 3: re = s1; im = -c1; break;
+    case 4: re = 0; im = -1; break;
+    case 5: re = -s1; im = -c1; break;
+    case 6: re = -h; im = -h; break;
+    case 7: re = -c1; im = -s1; break;
+    case 8: re = -1; im = 0; break;
+    case 9: re = -c1; im = s1; break;
+    case 10: re = -h; im = h; break;
+    case 11: re = -s1; im = c1; break;
+    case 12: re = 0; im = 1; break;
+    case 13: re = s1; im = c1; break;
+    case 14: re = h; im = h; break;
+    default: re = c1; im = s1; break;
+  }
+  return mkc<T>(re, inv ? -im : im);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft2(cx<T>& a, cx<T>& b) {
+  const cx<T> s = cadd<T>(a, b), d = csub<T>(a, b);
+  a = s;
+  b = d;
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(cx<T>& a0, cx<T>& a1, cx<T>& a2, cx<T>& a3) {
+  const cx<T> s02 = cadd<T>(a0, a2), d02 = csub<T>(a0, a2);
+  const cx<T> s13 = cadd<T>(a1, a3), d13 = csub<T>(a1, a3);
+  a0 = cadd<T>(s02, s13);
+  a2 = csub<T>(s02, s13);
+  if (!INV) {
+    a1 = mkc<T>(d02.x + d13.y, d02.y - d13.x);  // d02 - i d13
+    a3 = mkc<T>(d02.x - d13.y, d02.y + d13.x);  // d02 + i d13
+  } else {
+    a1 = mkc<T>(d02.x - d13.y, d02.y + d13.x);
+    a3 = mkc<T>(d02.x + d13.y, d02.y - d13.x);
+  }
+}
+
+// In-register DFT of size R in natural order (X_k = sum_r v_r e^{-+2 pi i rk/R}).
+template <typename T, int R, bool INV> struct DftR;
+template <typename T, bool INV> struct DftR<T, 2, INV> {
+  static __device__ __forceinline__ void run(cx<T> (&v)[2]) { dft2<T, INV>(v[0], v[1]); }
+};
+template <typename T, bool INV> struct DftR<T, 4, INV> {
+  static __device__ __forceinline__ void run(cx<T> (&v)[4]) { dft4<T, INV>(v[0], v[1], v[2], v[3]); }
+};
+template <typename T, bool INV> struct DftR<T, 8, INV> {
+  static __device__ __forceinline__ void run(cx<T> (&v)[8]) {
+    // n = r + 2q (r < 2, q < 4), k = k1 + 4 k2
+    dft4<T, INV>(v[0], v[2], v[4], v[6]);
+    dft4<T, INV>(v[1], v[3], v[5], v[7]);
+    // twiddle e^{-2 pi i r k1 / 8} = w16^{2 r k1}
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) v[1 + 2 * k1] = cmul<T>(v[1 + 2 * k1], w16<T>(2 * k1, INV));
+    cx<T> o[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      cx<T> a = v[2 * k1], b = v[2 * k1 + 1];
+      dft2<T, INV>(a, b);
+      o[k1] = a;
+      o[k1 + 4] = b;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = o[i];
+  }
+};
+template <typename T, bool INV> struct DftR<T, 16, INV> {
+  static __device__ __forceinline__ void run(cx<T> (&v)[16]) {
+    // n = r + 4q, k = k1 + 4 k2: inner DFT4 over q, twiddle w16^{r k1}, outer DFT4 over r
+#pragma unroll
+    for (int r = 0; r < 4; ++r) dft4<T, INV>(v[r], v[r + 4], v[r + 8], v[r + 12]);
+#pragma unroll
+    for (int r = 1; r < 4; ++r)
+#pragma unroll
+      for (int k1 = 1; k1 < 4; ++k1) v[r + 4 * k1] = cmul<T>(v[r + 4 * k1], w16<T>(r * k1, INV));
+    cx<T> o[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      cx<T> a0 = v[4 * k1], a1 = v[4 * k1 + 1], a2 = v[4 * k1 + 2], a3 = v[4 * k1 + 3];
+      dft4<T, INV>(a0, a1, a2, a3);
+      o[k1] = a0;
+      o[k1 + 4] = a1;
+      o[k1 + 8] = a2;
+      o[k1 + 12] = a3;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = o[i];
+  }
+};
+
+// w^k for k = 1..R-1 from one table value w (at most 4 products deep:
+// squares and one product), replacing R-1 scattered table reads.
+template <typename T, int R>
+__device__ __forceinline__ void twiddle_powers(cx<T> w1, cx<T> (&p)[R]) {
+  p[0] = mkc<T>(1, 0);
+  if (R > 1) p[1] = w1;
+  if (R > 2) p[2] = cmul<T>(w1, w1);
+  if (R > 3) p[3] = cmul<T>(p[2], w1);
+  if (R > 4) {
+    const cx<T> w4 = cmul<T>(p[2], p[2]);
+#pragma unroll
+    for (int k = 4; k < (R < 8 ? R : 8); ++k) p[k] = (k == 4) ? w4 : cmul<T>(w4, p[k - 4]);
+  }
+  if (R > 8) {
+    const cx<T> w8 = cmul<T>(p[4], p[4]);
+#pragma unroll
+    for (int k = 8; k < R; ++k) p[k] = (k == 8) ? w8 : cmul<T>(w8, p[k - 8]);
+  }
+}
+
+// One in-place forward (DIF) stage of radix R on blocks of size S, smem -> smem.
+template <typename T, int R>
+__device__ __forceinline__ void fft_fwd_stage(cx<T>* A, int M, int S, const cx<T>* __restrict__ tw) {
+  const int Q = S / R, tws = M / S;
+  for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
+    const int j = u & (Q - 1), base = (u - j) * R + j;
+    cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = A[fpad(base + Q * r)];
+    DftR<T, R, false>::run(v);
+    if (j) {
+      cx<T> p[R];
+      twiddle_powers<T, R>(__ldg(tw + j * tws), p);
+#pragma unroll
+      for (int k = 1; k < R; ++k) v[k] = cmul<T>(v[k], p[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) A[fpad(base + Q * k)] = v[k];
+  }
+}
+
+// Inverse (DIT) of fft_fwd_stage, smem -> smem, unnormalised (x R).
+template <typename T, int R>
+__device__ __forceinline__ void fft_inv_stage(cx<T>* A, int M, int S, const cx<T>* __restrict__ tw) {
+  const int Q = S / R, tws = M / S;
+  for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
+    const int j = u & (Q - 1), base = (u - j) * R + j;
+    cx<T> v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = A[fpad(base + Q * k)];
+    if (j) {
+      cx<T> p[R];
+      twiddle_powers<T, R>(__ldg(tw + j * tws), p);
+#pragma unroll
+      for (int k = 1; k < R; ++k) v[k] = cmulc<T>(v[k], p[k]);
+    }
+    DftR<T, R, true>::run(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) A[fpad(base + Q * r)] = v[r];
+  }
+}
+
+// Innermost stage (Q = 1): forward DFT, product with the spectrum (same
+// order), inverse DFT.  H == nullptr: forward only (used to build spectra).
+template <typename T, int R>
+__device__ __forceinline__ void fft_mid_stage(cx<T>* A, int M, const cx<T>* __restrict__ H, T scale) {
+  for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
+    const int base = u * R;
+    cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = A[fpad(base + r)];
+    DftR<T, R, false>::run(v);
+    if (H) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) v[k] = cmul<T>(v[k], __ldg(H + base + k));
+      DftR<T, R, true>::run(v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < R; ++k) v[k] = cscale<T>(v[k], scale);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) A[fpad(base + k)] = v[k];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void fft_mid_dispatch(cx<T>* A, int M, int Rl, const cx<T>* H, T scale) {
+  switch (Rl) {
+    case 2: fft_mid_stage<T, 2>(A, M, H, scale); break;
+    case 4: fft_mid_stage<T, 4>(A, M, H, scale); break;
+    case 8: fft_mid_stage<T, 8>(A, M, H, scale); break;
+    default: fft_mid_stage<T, 16>(A, M, H, scale); break;
+  }
+}
+
+// Radix schedule: logM = 4a + b; stages of 16 (a of them, the first fused with
+// the input) then R_last = 2^b if b > 0, else the a-th radix-16 stage is the
+// innermost one.  Returns the innermost radix and the number of smem-to-smem
+// radix-16 stages between the first and the innermost.
+__device__ __forceinline__ void fft_schedule(int logM, int& Rl, int& nmid16) {
+  const int a = logM >> 2, b = logM & 3;
+  if (b) {
+    Rl = 1 << b;
+    nmid16 = a - 1;
+  } else {
+    Rl = 16;
+    nmid16 = a - 2;
+  }
+}
+
+// Full convolution-by-FFT on one CTA:
+//   A = DIT( DIF(input) .* H ),  input(v) supplies element v (natural order),
+//   output(v, value) receives element v of M * (x conv h) for v < M.
+// Requires logM >= 5.  Ends with a __syncthreads() only if WRITE_SMEM (the
+// final values are then left in A, in natural order, with padding).
+template <typename T, bool WRITE_SMEM, typename In, typename Out>
+__device__ __forceinline__ void fft_convolve(cx<T>* A, int logM, const cx<T>* __restrict__ H,
+                                             const cx<T>* __restrict__ tw, In input, Out output) {
+  const int M = 1 << logM;
+  int Rl, nmid;
+  fft_schedule(logM, Rl, nmid);
+  // first forward stage (S = M), inputs from the functor
+  {
+    const int Q = M / 16;
+    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+      cx<T> v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = input(j + Q * r);
+      DftR<T, 16, false>::run(v);
+      if (j) {
+        cx<T> p[16];
+        twiddle_powers<T, 16>(__ldg(tw + j), p);
+#pragma unroll
+        for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], p[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) A[fpad(j + Q * k)] = v[k];
+    }
+  }
+  __syncthreads();
+  int S = M / 16;
+  for (int s = 0; s < nmid; ++s) {
+    fft_fwd_stage<T, 16>(A, M, S, tw);
+    __syncthreads();
+    S /= 16;
+  }
+  fft_mid_dispatch<T>(A, M, Rl, H, T(1));
+  __syncthreads();
+  for (int s = 0; s < nmid; ++s) {
+    S *= 16;
+    fft_inv_stage<T, 16>(A, M, S, tw);
+    __syncthreads();
+  }
+  // last inverse stage (S = M), outputs to the functor (or back to smem)
+  {
+    const int Q = M / 16;
+    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+      cx<T> v[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = A[fpad(j + Q * k)];
+      if (j) {
+        cx<T> p[16];
+        twiddle_powers<T, 16>(__ldg(tw + j), p);
+#pragma unroll
+        for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], p[k]);
+      }
+      DftR<T, 16, true>::run(v);
+      if (WRITE_SMEM) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) A[fpad(j + Q * r)] = v[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) output(j + Q * r, v[r]);
+      }
+    }
+  }
+  if (WRITE_SMEM) __syncthreads();
+}
+
+// Forward transform only (smem in natural order -> smem in the engine's
+// order), values scaled by `scale`; used to build the kernel spectra.
+template <typename T>
+__device__ __forceinline__ void fft_forward_inplace(cx<T>* A, int logM, const cx<T>* __restrict__ tw, T scale) {
+  const int M = 1 << logM;
+  int Rl, nmid;
+  fft_schedule(logM, Rl, nmid);
+  fft_fwd_stage<T, 16>(A, M, M, tw);
+  __syncthreads();
+  int S = M / 16;
+  for (int s = 0; s < nmid; ++s) {
+    fft_fwd_stage<T, 16>(A, M, S, tw);
+    __syncthreads();
+    S /= 16;
+  }
+  fft_mid_dispatch<T>(A, M, Rl, nullptr, scale);
+  __syncthreads();
+}
+
+}  // namespace s2dw

@@ -3,7 +3,7 @@
 //   * Driscoll-Healy weights q(theta_t) (Sec. 3.1, Eq. (18));
 //   * the Wigner table Delta^l_{m'm} = d^l_{m'm}(pi/2) (Sec. 3.2, Eq. (25));
 //   * the per-plan R tables and the chirp-z tables.
-#include "fft.cuh"
+#include "fft16.cuh"
 #include "plan_kernels.h"
 
 namespace s2dw {
@@ -271,17 +271,17 @@ __global__ void k_chirp_kernels(double2* H, int L, int M) {
   H[(size_t)kind * M + v] = make_double2(c, sign * s);
 }
 
-// Spectrum of each chirp kernel: DIF FFT (bit-reversed output) scaled by 1/M.
-__global__ void k_chirp_spectra(double2* H, const double2* tw, int logM) {
+// Spectrum of each chirp kernel: the forward stages of the convolution engine
+// (its digit-reversed order), scaled by 1/M.
+__global__ void __launch_bounds__(256) k_chirp_spectra(double2* H, const double2* tw, int logM) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* A = reinterpret_cast<double2*>(smem_raw);
   const int M = 1 << logM;
   double2* h = H + (size_t)blockIdx.x * M;
-  for (int v = threadIdx.x; v < M; v += blockDim.x) A[v] = h[v];
+  for (int v = threadIdx.x; v < M; v += blockDim.x) A[fpad(v)] = h[v];
   __syncthreads();
-  fft_dif<double>(A, logM, tw);
-  const double inv = 1.0 / M;
-  for (int v = threadIdx.x; v < M; v += blockDim.x) h[v] = make_double2(A[v].x * inv, A[v].y * inv);
+  fft_forward_inplace<double>(A, logM, tw, 1.0 / M);
+  for (int v = threadIdx.x; v < M; v += blockDim.x) h[v] = A[fpad(v)];
 }
 
 template <typename T>
@@ -338,7 +338,7 @@ cudaError_t launch_chirp_build64(double2* tw, double2* chirp_a, double2* pre_b, 
   k_chirp_kernels<<<dim3(nblk(M, 256), 4), 256, 0, st>>>(H, L, M);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  const int smem = (int)sizeof(double2) * M;
+  const int smem = (int)sizeof(double2) * fft_smem_elems(M);
   err = cudaFuncSetAttribute(k_chirp_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
   k_chirp_spectra<<<4, 256, smem, st>>>(H, tw, logM);
