@@ -41,6 +41,21 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// E consecutive values from 16-byte aligned shared memory.
+template <typename T, int E> struct VecLdS;
+template <> struct VecLdS<float, 4> {
+  static __device__ __forceinline__ void ld(const float* p, float (&r)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+  }
+};
+template <> struct VecLdS<double, 2> {
+  static __device__ __forceinline__ void ld(const double* p, double (&r)[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    r[0] = v.x; r[1] = v.y;
+  }
+};
+
 // Shared-memory geometry of one pipeline stage (element counts of T).
 template <typename T, int N, int NSLOT, int E>
 struct StageGeom {
@@ -119,60 +134,58 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   const int l_start = tk.lstart, l_end = tk.lend;
 
   // ---- producer: stage the operands of iteration l into ring slot st ----
-  auto issue = [&](int l, int st) {
+  // Per-thread copy roles are fixed for the whole tile; only the slab, f and
+  // R offsets move with l, and they advance incrementally (issue() is called
+  // for l_start, l_start+1, ... in order).
+  const int t = threadIdx.x;
+  constexpr int CPRA = TILE / EPC, CPRB = TMP / EPC, CPRR = TMP / EPC;
+  constexpr int FCH = 2 * TILE / EPC, CPC = EPC / 2, NRCH = NSLOT * N * CPRR;
+  const bool do_a = need_a && t < TMP * CPRA;
+  const bool do_b = need_b && t < TILE * CPRB;
+  const int ra = mp0 + t / CPRA, rb = m0 + t / CPRB;
+  const int a_A = delta_row_A(ra, m0 + (t % CPRA) * EPC), a_B = delta_row_B(ra);
+  const int b_A = delta_row_A(rb, mp0 + (t % CPRB) * EPC), b_B = delta_row_B(rb);
+  const int a_dst = G::A_OFF + (t / CPRA) * G::APITCH + (t % CPRA) * EPC;
+  const int b_dst = G::B_OFF + (t / CPRB) * G::BPITCH + (t % CPRB) * EPC;
+  const int fq = t - 256 + FCH;
+  const int f_mm = m0 + fq * CPC;
+  const bool do_r = t < NRCH;
+  const int r_src = (t / CPRR) * Lp + mp0 + (t % CPRR) * EPC;
+  const int r_dst = G::R_OFF + (t / CPRR) * TMP + (t % CPRR) * EPC;
+  int64_t is_slab = delta_slab_offset(l_start);  // state of the next issue
+  int64_t is_f = (int64_t)l_start * l_start + l_start;
+  const T* is_rs = RS + (size_t)l_start * (NSLOT * N) * Lp;
+  int is_l = l_start;
+  auto issue = [&](int st) {
+    const int l = is_l;
     if (l <= l_end) {
       T* S = ring + st * G::SIZE;
       const int cl = (l >> 2) + 1, rows_in_slab = 4 * cl;
-      const T* __restrict__ slab = delta + delta_slab_offset(l);
-      const int t = threadIdx.x;
-      // block A: rows mp0 + i (i < TMP), columns m0 .. m0 + TILE - 1
-      if (need_a) {
-        constexpr int CPR = TILE / EPC;  // chunks per row
-        if (t < TMP * CPR) {
-          const int i = t / CPR, ch = t % CPR, r = mp0 + i;
-          const T* src = slab + delta_row_A(r, m0 + ch * EPC) + (int64_t)delta_row_B(r) * cl;
-          cp_async16(S + G::A_OFF + i * G::APITCH + ch * EPC, r < rows_in_slab ? src : slab,
-                     r < rows_in_slab ? 16 : 0);
-        }
+      const T* __restrict__ slab = delta + is_slab;
+      if (do_a) {
+        const bool ok = ra < rows_in_slab;
+        cp_async16(S + a_dst, ok ? slab + a_A + a_B * cl : slab, ok ? 16 : 0);
       }
-      // block B: rows m0 + i (i < TILE), columns mp0 .. mp0 + TMP - 1
-      if (need_b) {
-        constexpr int CPR = TMP / EPC;
-        if (t < TILE * CPR) {
-          const int i = t / CPR, ch = t % CPR, r = m0 + i;
-          const T* src = slab + delta_row_A(r, mp0 + ch * EPC) + (int64_t)delta_row_B(r) * cl;
-          cp_async16(S + G::B_OFF + i * G::BPITCH + ch * EPC, r < rows_in_slab ? src : slab,
-                     r < rows_in_slab ? 16 : 0);
-        }
+      if (do_b) {
+        const bool ok = rb < rows_in_slab;
+        cp_async16(S + b_dst, ok ? slab + b_A + b_B * cl : slab, ok ? 16 : 0);
       }
-      if (!SYN) {
+      if (!SYN && fq >= 0) {
         // f_lm for m in [m0, m0 + TILE), zero beyond m = l (the array ends at l = L-1)
-        constexpr int FCH = 2 * TILE / EPC;
-        constexpr int CPC = EPC / 2;  // complex values per chunk
-        const int q = t - 256 + FCH;  // use the last FCH threads
-        if (q >= 0) {
-          const int mm = m0 + q * CPC;
-          const int nvalid = min(CPC, max(0, l + 1 - mm));
-          const cx<T>* src = f + (nvalid > 0 ? l * l + l + mm : 0);
-          cp_async16(S + G::F_OFF + q * EPC, src, nvalid * (int)sizeof(cx<T>));
-        }
+        const int nvalid = min(CPC, max(0, l + 1 - f_mm));
+        cp_async16(S + G::F_OFF + fq * EPC, f + (nvalid > 0 ? is_f + f_mm : 0), nvalid * (int)sizeof(cx<T>));
       }
-      // R rows: [s][k][mp0 .. mp0 + TMP)
-      {
-        constexpr int CPR = TMP / EPC;
-        constexpr int NCH = NSLOT * N * CPR;
-        for (int u = t; u < NCH; u += 256) {
-          const int sk = u / CPR, ch = u % CPR;
-          const T* src = RS + ((size_t)l * (NSLOT * N) + sk) * Lp + mp0 + ch * EPC;
-          cp_async16(S + G::R_OFF + sk * TMP + ch * EPC, src, 16);
-        }
-      }
+      if (do_r) cp_async16(S + r_dst, is_rs + r_src, 16);
+      is_slab += 8 * (int64_t)cl * (cl + 1);
+      is_f += 2 * (l + 1);
+      is_rs += (size_t)(NSLOT * N) * Lp;
+      is_l = l + 1;
     }
     cp_async_commit();
   };
 
 #pragma unroll
-  for (int i = 0; i < STAGES - 1; ++i) issue(l_start + i, i);
+  for (int i = 0; i < STAGES - 1; ++i) issue(i);
 
   cx<T> acc[E][NSLOT][N];
 #pragma unroll
@@ -246,7 +259,7 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
     const int it = l - l_start;
     cp_async_wait<STAGES - 2>();
     __syncthreads();
-    issue(l + STAGES - 1, (it + STAGES - 1) % STAGES);
+    issue((it + STAGES - 1) % STAGES);
     if (SYN && it > 0 && (it % LCH) == 0) reduce_chunk(rbuf ^ 1, l - LCH, LCH);
     // slot occupancy changes at segment boundaries
     if (l > seg_hi) {
@@ -279,7 +292,9 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
         for (int e = 0; e < E; ++e) dv[e] = S[G::A_OFF + (mpb - mp0 + e) * G::APITCH + c];
       } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e) dv[e] = ((e & 1) ? -sg0 : sg0) * S[G::B_OFF + c * G::BPITCH + (mpb - mp0 + e)];
+        VecLdS<T, E>::ld(S + G::B_OFF + c * G::BPITCH + (mpb - mp0), dv);
+#pragma unroll
+        for (int e = 0; e < E; ++e) dv[e] *= (e & 1) ? -sg0 : sg0;
       }
       const T* Rr = S + G::R_OFF + (mpb - mp0);
       if (!SYN) {
@@ -292,12 +307,12 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
           if (cur[s] < 0) continue;
 #pragma unroll
           for (int k = 0; k < N; ++k) {
-            const T* rp = Rr + (s * N + k) * TMP;
+            T r[E];
+            VecLdS<T, E>::ld(Rr + (s * N + k) * TMP, r);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-              const T r = rp[e];
-              acc[e][s][k].x = fma(tt[e].x, r, acc[e][s][k].x);
-              acc[e][s][k].y = fma(tt[e].y, r, acc[e][s][k].y);
+              acc[e][s][k].x = fma(tt[e].x, r[e], acc[e][s][k].x);
+              acc[e][s][k].y = fma(tt[e].y, r[e], acc[e][s][k].y);
             }
           }
         }
@@ -310,12 +325,12 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
           if (cur[s] < 0) continue;
 #pragma unroll
           for (int k = 0; k < N; ++k) {
-            const T* rp = Rr + (s * N + k) * TMP;
+            T r[E];
+            VecLdS<T, E>::ld(Rr + (s * N + k) * TMP, r);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-              const T r = rp[e];
-              p[e].x = fma(acc[e][s][k].x, r, p[e].x);
-              p[e].y = fma(acc[e][s][k].y, r, p[e].y);
+              p[e].x = fma(acc[e][s][k].x, r[e], p[e].x);
+              p[e].y = fma(acc[e][s][k].y, r[e], p[e].y);
             }
           }
         }

@@ -1,0 +1,66 @@
+"""Batched launches (s2dw_analysis_batch / s2dw_synthesis_batch): jobs of
+mixed L, N, lambda and J0 in one set of launches give exactly the results of
+the same jobs run alone (the kernels are deterministic: no atomics, fixed
+reduction order)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1308_5706_gb300 import binding as B
+from paper_1308_5706_gb300.inputs import flm_gaussian
+from tests.gpu_helpers import relerr
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [(64, 3, 2.0, 0), (33, 1, 2.0, 1), (48, 5, 3.0, 0), (64, 3, 2.0, 0), (20, 2, 2.0, 0),
+         (128, 5, 2.0, 2), (40, 8, 2.0, 1)]
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batch_equals_single(prec):
+    import torch
+    plans = [B.Plan(L, N, lam, J0, prec) for (L, N, lam, J0) in SPECS]
+    cd, rd = plans[0].torch_dtypes()
+    fs = [torch.from_numpy(flm_gaussian(p.L, 40 + i, "cl")).to(cd).cuda() for i, p in enumerate(plans)]
+    Wb = [p.alloc_w() for p in plans]
+    Ws = [p.alloc_w() for p in plans]
+    B.s2dw_analysis_batch([p.handle for p in plans], fs, [w[0] for w in Wb], [w[1] for w in Wb])
+    for p, f, w in zip(plans, fs, Ws):
+        p.analysis(f, w[0], w[1])
+    torch.cuda.synchronize()
+    for wb, ws in zip(Wb, Ws):
+        assert torch.equal(wb[0], ws[0]) and torch.equal(wb[1], ws[1])
+    fb = [p.alloc_flm() for p in plans]
+    fsn = [p.alloc_flm() for p in plans]
+    B.s2dw_synthesis_batch([p.handle for p in plans], [w[0] for w in Wb], [w[1] for w in Wb], fb)
+    for p, w, f in zip(plans, Ws, fsn):
+        p.synthesis(w[0], w[1], f)
+    torch.cuda.synchronize()
+    for a, b in zip(fb, fsn):
+        assert torch.equal(a, b)
+    # one member against the oracle, and every round trip
+    L, N, lam, J0 = SPECS[1]
+    Wo, Wpo = O.analysis(flm_gaussian(L, 41, "cl"), L, N, lam, J0)
+    tol = 1e-11 if prec == "fp64" else 1e-5
+    assert relerr(Wb[1][0].double().cpu().numpy(), Wo) < tol
+    for i, (p, f) in enumerate(zip(plans, fb)):
+        ref = flm_gaussian(p.L, 40 + i, "cl")
+        eps = np.abs(f.to(torch.complex128).cpu().numpy() - ref).max()
+        assert eps < (1e-12 if prec == "fp64" else 1e-5)
+    for p in plans:
+        p.close()
+
+
+def test_batch_argument_errors():
+    a = B.Plan(16, 3, 2.0, 0, "mixed")
+    b = B.Plan(16, 3, 2.0, 0, "fp64")
+    W, Wp = a.alloc_w()
+    f = a.alloc_flm()
+    with pytest.raises(B.S2dwError) as ei:
+        B.s2dw_analysis_batch([a.handle, a.handle], [f, f], [W, W], [Wp, Wp])
+    assert ei.value.status == B.S2DW_EINVAL
+    with pytest.raises(B.S2dwError) as ei:
+        B.s2dw_analysis_batch([a.handle, b.handle], [f, f], [W, W], [Wp, Wp])
+    assert ei.value.status == B.S2DW_ENOTSUP
+    a.close()
+    b.close()
