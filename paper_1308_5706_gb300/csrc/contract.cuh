@@ -27,6 +27,8 @@
 // lanes along m' so that their reads of the transposed block stay conflict free.
 #pragma once
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace s2dw {
@@ -41,6 +43,28 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Packed float pairs (two FP32 lanes per 64-bit register) for the sm_100+
+// f32x2 instructions: one instruction per two multiply-adds.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p pk2(float a, float b) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(f2p v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+  f2p d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
+  f2p d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // E consecutive values from 16-byte aligned shared memory.
 template <typename T, int E> struct VecLdS;
 template <> struct VecLdS<float, 4> {
@@ -53,6 +77,39 @@ template <> struct VecLdS<double, 2> {
   static __device__ __forceinline__ void ld(const double* p, double (&r)[2]) {
     const double2 v = *reinterpret_cast<const double2*>(p);
     r[0] = v.x; r[1] = v.y;
+  }
+};
+
+// Accumulators of a thread: E elements x NSLOT slots x N orders, complex.
+// Generic form: cx<T> per entry.  float with E = 4: real and imaginary parts
+// of element pairs (0,1), (2,3) packed for f32x2 instructions.
+template <typename T, int E, int NSLOT, int N, bool PACK> struct Acc;
+template <typename T, int E, int NSLOT, int N> struct Acc<T, E, NSLOT, N, false> {
+  cx<T> v[E][NSLOT][N];
+  __device__ __forceinline__ cx<T> get(int e, int s, int k) const { return v[e][s][k]; }
+  __device__ __forceinline__ void set(int e, int s, int k, cx<T> x) { v[e][s][k] = x; }
+};
+template <int E, int NSLOT, int N> struct Acc<float, E, NSLOT, N, true> {
+  f2p x[E / 2][NSLOT][N], y[E / 2][NSLOT][N];
+  __device__ __forceinline__ cx<float> get(int e, int s, int k) const {
+    float a0, a1, b0, b1;
+    upk2(x[e >> 1][s][k], a0, a1);
+    upk2(y[e >> 1][s][k], b0, b1);
+    return (e & 1) ? mkc<float>(a1, b1) : mkc<float>(a0, b0);
+  }
+  __device__ __forceinline__ void set(int e, int s, int k, cx<float> v) {
+    float a0, a1, b0, b1;
+    upk2(x[e >> 1][s][k], a0, a1);
+    upk2(y[e >> 1][s][k], b0, b1);
+    if (e & 1) {
+      a1 = v.x;
+      b1 = v.y;
+    } else {
+      a0 = v.x;
+      b0 = v.y;
+    }
+    x[e >> 1][s][k] = pk2(a0, a1);
+    y[e >> 1][s][k] = pk2(b0, b1);
   }
 };
 
@@ -187,13 +244,14 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
 #pragma unroll
   for (int i = 0; i < STAGES - 1; ++i) issue(i);
 
-  cx<T> acc[E][NSLOT][N];
+  constexpr bool PACK = std::is_same<T, float>::value && E == 4;
+  Acc<T, E, NSLOT, N, PACK> acc;
 #pragma unroll
   for (int e = 0; e < E; ++e)
 #pragma unroll
     for (int s = 0; s < NSLOT; ++s)
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc[e][s][k] = mkc<T>(0, 0);
+      for (int k = 0; k < N; ++k) acc.set(e, s, k, mkc<T>(0, 0));
 
   int cur[2] = {-1, -1};
   int sidx = 0;
@@ -213,7 +271,7 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
         for (int g = 0; g < N; ++g) {
           cx<T> v = mkc<T>(0, 0);
 #pragma unroll
-          for (int k = 0; k < N; ++k) v = cadd<T>(v, cmul<T>(acc[e][s][k], cgk[k][g]));
+          for (int k = 0; k < N; ++k) v = cadd<T>(v, cmul<T>(acc.get(e, s, k), cgk[k][g]));
           Y[((size_t)g * Lj + mp) * Lj + m] = cmul_ipow<T>(v, (-m) & 3);
         }
       }
@@ -221,26 +279,26 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   };
   // synthesis prologue (gamma adjoint) for slot s, scale j (or clear)
   auto load = [&](int s, int j) {
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-#pragma unroll
-      for (int k = 0; k < N; ++k) acc[e][s][k] = mkc<T>(0, 0);
-    if (j < 0) return;
-    const int Lj = D->Lj[j];
-    const cx<T>* __restrict__ V = D->Y[j];
+    const int Lj = j >= 0 ? D->Lj[j] : 0;
+    const cx<T>* __restrict__ V = j >= 0 ? D->Y[j] : nullptr;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int mp = mpb + e;
+      cx<T> h[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) h[k] = mkc<T>(0, 0);
       if (mp < Lj && m < Lj) {
 #pragma unroll
         for (int g = 0; g < N; ++g) {
           const cx<T> vg = V[((size_t)g * Lj + mp) * Lj + m];
 #pragma unroll
-          for (int k = 0; k < N; ++k) acc[e][s][k] = cadd<T>(acc[e][s][k], cmul<T>(vg, cgk[k][g]));
+          for (int k = 0; k < N; ++k) h[k] = cadd<T>(h[k], cmul<T>(vg, cgk[k][g]));
         }
 #pragma unroll
-        for (int k = 0; k < N; ++k) acc[e][s][k] = cmul_ipow<T>(acc[e][s][k], m & 3);
+        for (int k = 0; k < N; ++k) h[k] = cmul_ipow<T>(h[k], m & 3);
       }
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc.set(e, s, k, h[k]);
     }
   };
   auto reduce_chunk = [&](int buf, int lfirst, int count) {
@@ -274,7 +332,7 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
 #pragma unroll
             for (int e = 0; e < E; ++e)
 #pragma unroll
-              for (int k = 0; k < N; ++k) acc[e][s][k] = mkc<T>(0, 0);
+              for (int k = 0; k < N; ++k) acc.set(e, s, k, mkc<T>(0, 0));
           } else {
             load(s, jn);
           }
@@ -283,61 +341,100 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
       }
     }
     const T* S = ring + (it % STAGES) * G::SIZE;
-    const bool valid = (m <= l) && (mpb <= l);
+    // Every element computes: out-of-range rows and columns contribute exact
+    // zeros (zero R rows for m' > l or inactive slots, zero-filled f for
+    // m > l, zero H outside a scale's band), and synthesis partials of
+    // columns m > l are never read.
     cx<T> part = mkc<T>(0, 0);
-    if (valid) {
+    {
       T dv[E];
       if (!tr) {
 #pragma unroll
         for (int e = 0; e < E; ++e) dv[e] = S[G::A_OFF + (mpb - mp0 + e) * G::APITCH + c];
       } else {
-#pragma unroll
         VecLdS<T, E>::ld(S + G::B_OFF + c * G::BPITCH + (mpb - mp0), dv);
 #pragma unroll
         for (int e = 0; e < E; ++e) dv[e] *= (e & 1) ? -sg0 : sg0;
       }
       const T* Rr = S + G::R_OFF + (mpb - mp0);
-      if (!SYN) {
-        const cx<T> fv = reinterpret_cast<const cx<T>*>(S + G::F_OFF)[c];
-        cx<T> tt[E];
+      if constexpr (PACK) {
+        // float, E = 4: pairs (0,1) and (2,3) per f32x2 instruction
+        if (!SYN) {
+          const cx<T> fv = reinterpret_cast<const cx<T>*>(S + G::F_OFF)[c];
+          const f2p fx = pk2(fv.x, fv.x), fy = pk2(fv.y, fv.y);
+          const f2p d01 = pk2(dv[0], dv[1]), d23 = pk2(dv[2], dv[3]);
+          const f2p tx0 = mul2(d01, fx), tx1 = mul2(d23, fx), ty0 = mul2(d01, fy), ty1 = mul2(d23, fy);
 #pragma unroll
-        for (int e = 0; e < E; ++e) tt[e] = mkc<T>(dv[e] * fv.x, dv[e] * fv.y);
+          for (int s = 0; s < NSLOT; ++s)
 #pragma unroll
-        for (int s = 0; s < NSLOT; ++s) {
-          if (cur[s] < 0) continue;
-#pragma unroll
-          for (int k = 0; k < N; ++k) {
-            T r[E];
-            VecLdS<T, E>::ld(Rr + (s * N + k) * TMP, r);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-              acc[e][s][k].x = fma(tt[e].x, r[e], acc[e][s][k].x);
-              acc[e][s][k].y = fma(tt[e].y, r[e], acc[e][s][k].y);
+            for (int k = 0; k < N; ++k) {
+              const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(Rr + (s * N + k) * TMP);
+              acc.x[0][s][k] = fma2(tx0, r.x, acc.x[0][s][k]);
+              acc.y[0][s][k] = fma2(ty0, r.x, acc.y[0][s][k]);
+              acc.x[1][s][k] = fma2(tx1, r.y, acc.x[1][s][k]);
+              acc.y[1][s][k] = fma2(ty1, r.y, acc.y[1][s][k]);
             }
-          }
+        } else {
+          f2p px0 = 0, py0 = 0, px1 = 0, py1 = 0;
+#pragma unroll
+          for (int s = 0; s < NSLOT; ++s)
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(Rr + (s * N + k) * TMP);
+              px0 = fma2(acc.x[0][s][k], r.x, px0);
+              py0 = fma2(acc.y[0][s][k], r.x, py0);
+              px1 = fma2(acc.x[1][s][k], r.y, px1);
+              py1 = fma2(acc.y[1][s][k], r.y, py1);
+            }
+          const f2p d01 = pk2(dv[0], dv[1]), d23 = pk2(dv[2], dv[3]);
+          const f2p sx = fma2(d23, px1, mul2(d01, px0)), sy = fma2(d23, py1, mul2(d01, py0));
+          float a, b;
+          upk2(sx, a, b);
+          part.x = a + b;
+          upk2(sy, a, b);
+          part.y = a + b;
         }
       } else {
-        cx<T> p[E];
+        if (!SYN) {
+          const cx<T> fv = reinterpret_cast<const cx<T>*>(S + G::F_OFF)[c];
+          cx<T> tt[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) p[e] = mkc<T>(0, 0);
+          for (int e = 0; e < E; ++e) tt[e] = mkc<T>(dv[e] * fv.x, dv[e] * fv.y);
 #pragma unroll
-        for (int s = 0; s < NSLOT; ++s) {
-          if (cur[s] < 0) continue;
+          for (int s = 0; s < NSLOT; ++s)
 #pragma unroll
-          for (int k = 0; k < N; ++k) {
-            T r[E];
-            VecLdS<T, E>::ld(Rr + (s * N + k) * TMP, r);
+            for (int k = 0; k < N; ++k) {
+              T r[E];
+              VecLdS<T, E>::ld(Rr + (s * N + k) * TMP, r);
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-              p[e].x = fma(acc[e][s][k].x, r[e], p[e].x);
-              p[e].y = fma(acc[e][s][k].y, r[e], p[e].y);
+              for (int e = 0; e < E; ++e) {
+                cx<T>& a = acc.v[e][s][k];
+                a.x = fma(tt[e].x, r[e], a.x);
+                a.y = fma(tt[e].y, r[e], a.y);
+              }
             }
-          }
-        }
+        } else {
+          cx<T> p[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          part.x = fma(dv[e], p[e].x, part.x);
-          part.y = fma(dv[e], p[e].y, part.y);
+          for (int e = 0; e < E; ++e) p[e] = mkc<T>(0, 0);
+#pragma unroll
+          for (int s = 0; s < NSLOT; ++s)
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              T r[E];
+              VecLdS<T, E>::ld(Rr + (s * N + k) * TMP, r);
+#pragma unroll
+              for (int e = 0; e < E; ++e) {
+                const cx<T> a = acc.v[e][s][k];
+                p[e].x = fma(a.x, r[e], p[e].x);
+                p[e].y = fma(a.y, r[e], p[e].y);
+              }
+            }
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            part.x = fma(dv[e], p[e].x, part.x);
+            part.y = fma(dv[e], p[e].y, part.y);
+          }
         }
       }
     }
