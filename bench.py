@@ -190,6 +190,20 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_replicas(total_ms: float, steps: int, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank ran `steps`
+    transforms in `total_ms`; the job time is the maximum over ranks (one
+    all-reduce, outside the data path) and the value counts all ranks' work."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, steps * world / (total_ms / 1e3)
+
+
 def contraction_flops(plan) -> float:
     """Algorithmic flops of one contraction launch (analysis or synthesis):
     per scale j and l in its support, (l+1)^2 (m', m >= 0) triples, each
@@ -243,6 +257,75 @@ def time_path(torch, plan, f_dev, steps, warmup, stream, profile=False):
     return per, total, W, Wphi, fr, prof
 
 
+def run_batch_workload(args):
+    """64 real signals, L from {64,128,256,512}, N from {1,3,5}, lambda=2,
+    C_l spectrum (seed 3): batched analysis + synthesis of all signals, both
+    launch sets captured once in a CUDA graph and replayed."""
+    import torch
+    from paper_1308_5706_gb300 import binding as B
+    rng = np.random.default_rng(3)
+    Ls, Ns = rng.choice([64, 128, 256, 512], 64), rng.choice([1, 3, 5], 64)
+    plans = [B.Plan(int(a), int(b), 2.0, 0, "mixed") for a, b in zip(Ls, Ns)]
+    fs = [torch.from_numpy(flm_gaussian(p.L, 300 + i, "cl")).to(torch.complex64).cuda() for i, p in enumerate(plans)]
+    Ws = [p.alloc_w() for p in plans]
+    fr = [p.alloc_flm() for p in plans]
+    hs = [p.handle for p in plans]
+    stream = torch.cuda.Stream()
+
+    def step():
+        B.s2dw_analysis_batch(hs, fs, [w[0] for w in Ws], [w[1] for w in Ws], stream)
+        B.s2dw_synthesis_batch(hs, [w[0] for w in Ws], [w[1] for w in Ws], fr, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    eps = max(float((f.to(torch.complex128).cpu() - torch.from_numpy(flm_gaussian(p.L, 300 + i, "cl"))).abs().max())
+              for i, (p, f) in enumerate(zip(plans, fr)))
+    out = {"metric": "batched signals/s (64 signals, analysis+synthesis per signal)", "value": 64 / (ms / 1e3),
+           "unit": "signals/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+           "config": {"workload": "64 real signals, L in {64,128,256,512}, N in {1,3,5}, lambda=2, C_l, seed 3",
+                      "launches_per_step": "analysis: 1 contraction per distinct N + scaling + beta + alpha; "
+                                           "synthesis: alpha + beta + contractions + scaling + reduction; "
+                                           "one CUDA graph replay", "precision": "mixed"},
+           "round_trip_eps_max": eps}
+    print(json.dumps(out))
+    for p in plans:
+        p.close()
+    return 0
+
+
+def run_serve_workload(args):
+    """Poisson arrivals (mean 200 req/s) of analysis/synthesis requests (50/50,
+    a synthesis consumes an earlier analysis' W), L log-uniform in [32, 2048],
+    N uniform in 1..8, lambda in {2, 3}, seed 4."""
+    import torch
+    from paper_1308_5706_gb300.serve import Server, poisson_workload
+    reqs = poisson_workload(rate=200.0, duration=args.serve_seconds, seed=4)
+    srv = Server("mixed", slots=4, max_batch=16)
+    rep = srv.run(reqs)
+    srv.close()
+    torch.cuda.synchronize()
+    out = {"metric": "served transforms/s with p50/p99 latency", "value": rep["transforms_per_s"],
+           "unit": "transforms/s", "latency_ms": rep["latency_ms"], "report": rep,
+           "config": {"workload": f"Poisson 200 req/s for {args.serve_seconds:g} s, analysis/synthesis 50/50, "
+                                  "L log-uniform [32,2048], N 1..8, lambda {2,3}, seed 4", "precision": "mixed"}}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -251,10 +334,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="roundtrip", choices=["roundtrip", "batch", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch_workload(args)
+    if args.workload == "serve":
+        return run_serve_workload(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -293,10 +382,7 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = args.steps * world / (total / 1e3)
+    total, value = aggregate_replicas(total, args.steps, dist, device="cuda")
 
     # end to end through the C ABI with pinned host buffers
     fh = torch.from_numpy(f64).to(torch.complex64).pin_memory()

@@ -140,9 +140,9 @@ const char* s2dw_strerror(int status);
  *     requires l < L of the plan.
  *   s2dw_stage: copy intermediate `stage` of scale j from the last call on
  *     this plan into host memory: 0 = analysis Fourier cube after the gamma
- *     step, complex [N][Lj][Lj] (m' rows, m >= 0 columns); 1 = after the beta
- *     step, complex [N][2L][Lj]; *nbytes gets the size; host may be NULL to
- *     query only.  Scale j = J+1 is the scaling part (N = 1).
+ *     step, complex [N][Lj (m >= 0)][Lj (m' >= 0)]; 1 = after the beta step,
+ *     complex [N][2L (beta_b)][Lj (m)]; *nbytes gets the size; host may be
+ *     NULL to query only.  Scale j = J+1 is the scaling part (N = 1).
  */
 int s2dw_scale_support(s2dw_plan_t plan, int j, int* lo, int* hi);
 int s2dw_delta_slab(s2dw_plan_t plan, int l, double* host_out);

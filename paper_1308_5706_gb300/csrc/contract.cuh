@@ -4,7 +4,10 @@
 //   G^j_{m'mk} = sum_{l in supp kappa^j} Delta^l_{m'm} f_lm R^j_{l m' k},
 //   R^j_{l m' k} = Delta^l_{m' n_k} kappa^j(l) |s_{l n_k}|,
 // followed by the gamma step (Eq. (28)) as an epilogue:
-//   Y^j_g[m'][m] = i^{-m} sum_k G^j_{m'mk} conj(eta) i^{n_k} e^{i n_k gamma_g}.
+//   Y^j_g[m][m'] = i^{-m} sum_k G^j_{m'mk} conj(eta) i^{n_k} e^{i n_k gamma_g}
+// (stored with m' fastest, so the beta step reads contiguous columns; the
+// synthesis input Vhat_g[m'][m] is stored with m fastest, so this prologue
+// reads it coalesced).
 // Since Psi^j*_ln = kappa^j(l) conj(eta) |s_ln|, conj(eta) i^{n-m} G is the
 // cube U_{m m' n} of Eq. (27) for m' >= 0 (U_{m,-m',n} = (-1)^{m+n} U_{m m' n}).
 //
@@ -272,7 +275,7 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
           cx<T> v = mkc<T>(0, 0);
 #pragma unroll
           for (int k = 0; k < N; ++k) v = cadd<T>(v, cmul<T>(acc.get(e, s, k), cgk[k][g]));
-          Y[((size_t)g * Lj + mp) * Lj + m] = cmul_ipow<T>(v, (-m) & 3);
+          Y[((size_t)g * Lj + m) * Lj + mp] = cmul_ipow<T>(v, (-m) & 3);
         }
       }
     }

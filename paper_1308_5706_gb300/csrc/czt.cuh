@@ -12,6 +12,11 @@
 // plan serves every scale.  theta = pi/(4L) for beta (beta_b = theta(2b+1))
 // and pi/(2L-1) for alpha (alpha_a = 2 theta a).
 //
+// Layouts (measured choices): analysis Y_g[m][m'] (m' fastest: the beta
+// step reads contiguous columns) and X_g[b][m] (m fastest: alpha reads rows);
+// synthesis V_g[b][m] (alpha writes rows) and Vhat_g[m'][m] (the contraction
+// prologue reads it coalesced), so the synthesis beta step reads and writes
+// strided columns.
 // beta, analysis:  X_g[b][m] = sum_{|m'|<Lj} Yhat_{m'} e^{i m' beta_b},
 //   Yhat_{-m'} = sigma_m Yhat_{m'}, sigma_m = (-1)^{m+N-1}   (one column / CTA)
 // alpha, analysis: W[a] = sum_{|m|<Lj} X_m e^{i m alpha_a}, X_{-m} = conj(X_m);
@@ -48,14 +53,14 @@ __global__ void __launch_bounds__(256) k_czt_beta_ana(const CztSeg<T>* __restric
   const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM;
   const int g = item / Lj, m = item % Lj;
   const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
-  const cx<T>* __restrict__ Y = sg.buf_in + (size_t)g * Lj * Lj + m;
+  const cx<T>* __restrict__ Y = sg.buf_in + ((size_t)g * Lj + m) * Lj;  // Y_g[m][.], m' fastest
   const cx<T>* __restrict__ pre = sg.pre + (L - 1);
   auto in = [&](int v) -> cx<T> {
     int mp;
     if (v < Lj) mp = v;
     else if (v > M - Lj) mp = v - M;
     else return mkc<T>(0, 0);
-    cx<T> y = Y[(size_t)(mp < 0 ? -mp : mp) * Lj];
+    cx<T> y = Y[mp < 0 ? -mp : mp];
     if (mp < 0) y = cscale<T>(y, sigma);
     return cmul<T>(y, __ldg(pre + mp));
   };
@@ -123,7 +128,7 @@ __global__ void __launch_bounds__(256) k_czt_alpha_syn(const CztSeg<T>* __restri
   };
   auto none = [](int, cx<T>) {};
   fft_convolve<T, true>(A, sg.logM, sg.H, sg.tw, in, none);
-  cx<T>* __restrict__ V1 = sg.buf_out + (size_t)r1 * Lj;
+  cx<T>* __restrict__ V1 = sg.buf_out + (size_t)r1 * Lj;  // V_g[b][m] rows, m fastest
   cx<T>* __restrict__ V2 = V1 + Lj;
   const T h = sg.scale * T(0.5);
   for (int mm = threadIdx.x; mm < Lj; mm += blockDim.x) {
@@ -145,14 +150,14 @@ __global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restric
   const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM;
   const int g = item / Lj, m = item % Lj;
   const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
-  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * 2 * L * Lj + m;
+  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * 2 * L * Lj + m;  // column m of V_g[b][m]
   auto in = [&](int v) -> cx<T> {
     if (v >= 2 * L) return mkc<T>(0, 0);
     return cmul<T>(V[(size_t)v * Lj], __ldg(sg.pre + v));
   };
   auto none = [](int, cx<T>) {};
   fft_convolve<T, true>(A, sg.logM, sg.H, sg.tw, in, none);
-  cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m;
+  cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m;  // column m of Vhat_g[m'][m]
   for (int mp = threadIdx.x; mp < Lj; mp += blockDim.x) {
     const cx<T> tp = cmul<T>(A[fpad(mp)], __ldg(sg.post + L - 1 + mp));
     cx<T> o = tp;

@@ -14,6 +14,11 @@
 // through shared memory on the way in or out; the last forward stage, the
 // pointwise product with the spectrum and the first inverse stage run on the
 // same registers.  Shared memory holds M (+M/16 padding) complex values.
+//
+// Twiddle table (fft_twiddle_*): for each radix-16 level d = 0, 1, ... with
+// block size S_d = M / 16^d and Q_d = S_d / 16, entries [k-1][j] =
+// e^{-2 pi i j k / S_d} (k = 1..15, j < Q_d), levels stored one after the
+// other; a butterfly's 15 twiddles are then coalesced loads across a warp.
 #pragma once
 
 #include "common.cuh"
@@ -122,30 +127,23 @@ template <typename T, bool INV> struct DftR<T, 16, INV> {
   }
 };
 
-// w^k for k = 1..R-1 from one table value w (at most 4 products deep:
-// squares and one product), replacing R-1 scattered table reads.
-template <typename T, int R>
-__device__ __forceinline__ void twiddle_powers(cx<T> w1, cx<T> (&p)[R]) {
-  p[0] = mkc<T>(1, 0);
-  if (R > 1) p[1] = w1;
-  if (R > 2) p[2] = cmul<T>(w1, w1);
-  if (R > 3) p[3] = cmul<T>(p[2], w1);
-  if (R > 4) {
-    const cx<T> w4 = cmul<T>(p[2], p[2]);
-#pragma unroll
-    for (int k = 4; k < (R < 8 ? R : 8); ++k) p[k] = (k == 4) ? w4 : cmul<T>(w4, p[k - 4]);
-  }
-  if (R > 8) {
-    const cx<T> w8 = cmul<T>(p[4], p[4]);
-#pragma unroll
-    for (int k = 8; k < R; ++k) p[k] = (k == 8) ? w8 : cmul<T>(w8, p[k - 8]);
-  }
+// Element offset of twiddle level d (block size M / 16^d) in the table.
+__host__ __device__ __forceinline__ int fft_twiddle_level_offset(int logM, int d) {
+  int off = 0;
+  for (int i = 0; i < d; ++i) off += 15 * (1 << (logM - 4 * (i + 1)));
+  return off;
+}
+// Entries of the whole table for length 2^logM (levels with twiddles only).
+__host__ __device__ __forceinline__ int fft_twiddle_entries(int logM) {
+  const int nlev = (logM & 3) ? (logM >> 2) : (logM >> 2) - 1;
+  return fft_twiddle_level_offset(logM, nlev);
 }
 
 // One in-place forward (DIF) stage of radix R on blocks of size S, smem -> smem.
+// tw: this stage's twiddle level ([k-1][j], k < 16, j < Q).
 template <typename T, int R>
 __device__ __forceinline__ void fft_fwd_stage(cx<T>* A, int M, int S, const cx<T>* __restrict__ tw) {
-  const int Q = S / R, tws = M / S;
+  const int Q = S / R;
   for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
     const int j = u & (Q - 1), base = (u - j) * R + j;
     cx<T> v[R];
@@ -153,10 +151,8 @@ __device__ __forceinline__ void fft_fwd_stage(cx<T>* A, int M, int S, const cx<T
     for (int r = 0; r < R; ++r) v[r] = A[fpad(base + Q * r)];
     DftR<T, R, false>::run(v);
     if (j) {
-      cx<T> p[R];
-      twiddle_powers<T, R>(__ldg(tw + j * tws), p);
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmul<T>(v[k], p[k]);
+      for (int k = 1; k < R; ++k) v[k] = cmul<T>(v[k], __ldg(tw + (k - 1) * Q + j));
     }
 #pragma unroll
     for (int k = 0; k < R; ++k) A[fpad(base + Q * k)] = v[k];
@@ -166,17 +162,15 @@ __device__ __forceinline__ void fft_fwd_stage(cx<T>* A, int M, int S, const cx<T
 // Inverse (DIT) of fft_fwd_stage, smem -> smem, unnormalised (x R).
 template <typename T, int R>
 __device__ __forceinline__ void fft_inv_stage(cx<T>* A, int M, int S, const cx<T>* __restrict__ tw) {
-  const int Q = S / R, tws = M / S;
+  const int Q = S / R;
   for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
     const int j = u & (Q - 1), base = (u - j) * R + j;
     cx<T> v[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = A[fpad(base + Q * k)];
     if (j) {
-      cx<T> p[R];
-      twiddle_powers<T, R>(__ldg(tw + j * tws), p);
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmulc<T>(v[k], p[k]);
+      for (int k = 1; k < R; ++k) v[k] = cmulc<T>(v[k], __ldg(tw + (k - 1) * Q + j));
     }
     DftR<T, R, true>::run(v);
 #pragma unroll
@@ -252,10 +246,8 @@ __device__ __forceinline__ void fft_convolve(cx<T>* A, int logM, const cx<T>* __
       for (int r = 0; r < 16; ++r) v[r] = input(j + Q * r);
       DftR<T, 16, false>::run(v);
       if (j) {
-        cx<T> p[16];
-        twiddle_powers<T, 16>(__ldg(tw + j), p);
 #pragma unroll
-        for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], p[k]);
+        for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], __ldg(tw + (k - 1) * Q + j));
       }
 #pragma unroll
       for (int k = 0; k < 16; ++k) A[fpad(j + Q * k)] = v[k];
@@ -264,15 +256,15 @@ __device__ __forceinline__ void fft_convolve(cx<T>* A, int logM, const cx<T>* __
   __syncthreads();
   int S = M / 16;
   for (int s = 0; s < nmid; ++s) {
-    fft_fwd_stage<T, 16>(A, M, S, tw);
+    fft_fwd_stage<T, 16>(A, M, S, tw + fft_twiddle_level_offset(logM, s + 1));
     __syncthreads();
     S /= 16;
   }
   fft_mid_dispatch<T>(A, M, Rl, H, T(1));
   __syncthreads();
-  for (int s = 0; s < nmid; ++s) {
+  for (int s = nmid - 1; s >= 0; --s) {
     S *= 16;
-    fft_inv_stage<T, 16>(A, M, S, tw);
+    fft_inv_stage<T, 16>(A, M, S, tw + fft_twiddle_level_offset(logM, s + 1));
     __syncthreads();
   }
   // last inverse stage (S = M), outputs to the functor (or back to smem)
@@ -283,10 +275,8 @@ __device__ __forceinline__ void fft_convolve(cx<T>* A, int logM, const cx<T>* __
 #pragma unroll
       for (int k = 0; k < 16; ++k) v[k] = A[fpad(j + Q * k)];
       if (j) {
-        cx<T> p[16];
-        twiddle_powers<T, 16>(__ldg(tw + j), p);
 #pragma unroll
-        for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], p[k]);
+        for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], __ldg(tw + (k - 1) * Q + j));
       }
       DftR<T, 16, true>::run(v);
       if (WRITE_SMEM) {
@@ -312,7 +302,7 @@ __device__ __forceinline__ void fft_forward_inplace(cx<T>* A, int logM, const cx
   __syncthreads();
   int S = M / 16;
   for (int s = 0; s < nmid; ++s) {
-    fft_fwd_stage<T, 16>(A, M, S, tw);
+    fft_fwd_stage<T, 16>(A, M, S, tw + fft_twiddle_level_offset(logM, s + 1));
     __syncthreads();
     S /= 16;
   }

@@ -224,12 +224,22 @@ __global__ void k_rtable(T* RS, const double* d64, const double* kap, const doub
 // Chirp tables (angles reduced exactly in integers before sincospi).
 template <typename T>
 __global__ void k_chirp_tables(cx<T>* tw, cx<T>* chirp_a, cx<T>* pre_b, cx<T>* post_b, cx<T>* preS_b,
-                               cx<T>* postS_b, const double* q, int L, int M) {
+                               cx<T>* postS_b, const double* q, int L, int logM) {
+  const int M = 1 << logM;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = 2 * L - 1;
   double s, c;
-  if (i < M) {
-    sincospi(-2.0 * i / M, &s, &c);
+  if (i < fft_twiddle_entries(logM)) {
+    // locate level d, then (k, j) in it: e^{-2 pi i j k / S_d}
+    int d = 0, off = 0;
+    while (i >= off + 15 * (M >> (4 * (d + 1)))) {
+      off += 15 * (M >> (4 * (d + 1)));
+      ++d;
+    }
+    const int Q = M >> (4 * (d + 1)), S = 16 * Q;
+    const int k = (i - off) / Q + 1, j = (i - off) % Q;
+    const long long p = ((long long)j * k) % S;
+    sincospi(-2.0 * (double)p / S, &s, &c);
     tw[i] = mkc<T>((T)c, (T)s);
   }
   if (i < n) {
@@ -334,7 +344,7 @@ cudaError_t launch_chirp_build64(double2* tw, double2* chirp_a, double2* pre_b, 
                                  double2* postS_b, double2* H, const double* q, int L, int logM, cudaStream_t st) {
   const int M = 1 << logM;
   const int cnt = (M > 2 * L) ? M : 2 * L;
-  k_chirp_tables<double><<<nblk(cnt, 256), 256, 0, st>>>(tw, chirp_a, pre_b, post_b, preS_b, postS_b, q, L, M);
+  k_chirp_tables<double><<<nblk(cnt, 256), 256, 0, st>>>(tw, chirp_a, pre_b, post_b, preS_b, postS_b, q, L, logM);
   k_chirp_kernels<<<dim3(nblk(M, 256), 4), 256, 0, st>>>(H, L, M);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;

@@ -137,6 +137,6 @@ def test_stage_fourier_cube_fp64():
         ns = O.n_orders(N)
         gam = np.pi * np.arange(N) / N
         for g in range(N):
-            ref = np.einsum("mpk,k->pm", U[L - 1:L - 1 + Lj, L - 1:L - 1 + Lj, :], np.exp(1j * ns * gam[g]))
+            ref = np.einsum("mpk,k->mp", U[L - 1:L - 1 + Lj, L - 1:L - 1 + Lj, :], np.exp(1j * ns * gam[g]))
             assert np.abs(Y[g] - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
     p.close()
