@@ -90,6 +90,14 @@ int s2dw_query(s2dw_plan_t plan, int* J, int64_t* w_elems_per_scale, int64_t* wp
                int64_t* workspace_bytes, int64_t* total_device_bytes);
 
 /*
+ * s2dw_launch_counts: number of kernel launches one s2dw_analysis and one
+ * s2dw_synthesis call of this plan issue (stages with no work launch
+ * nothing).  Either pointer may be NULL.  Host only; no counterpart in the
+ * paper (launch accounting of this implementation).
+ */
+int s2dw_launch_counts(s2dw_plan_t plan, int* analysis, int* synthesis);
+
+/*
  * s2dw_kernels: copy the plan's kernels to HOST memory (synchronous).
  *   psi: complex128 as interleaved doubles [J+1][L][N][2]: Psi^j_{l,n_k},
  *        n_k = -(N-1) + 2k  (Eq. (7));  phi: double [L]: Phi_l0 (Eq. (16)).

@@ -30,6 +30,7 @@ _SIGNATURES = {
     "s2dw_plan": (_c_i, [ctypes.POINTER(_c_p), _c_i, _c_i, ctypes.c_double, _c_i, ctypes.c_uint]),
     "s2dw_plan_destroy": (_c_i, [_c_p]),
     "s2dw_query": (_c_i, [_c_p, _c_ip, _c_i64p, _c_i64p, _c_i64p, _c_i64p]),
+    "s2dw_launch_counts": (_c_i, [_c_p, _c_ip, _c_ip]),
     "s2dw_kernels": (_c_i, [_c_p, _c_dp, _c_dp]),
     "s2dw_analysis": (_c_i, [_c_p, _c_p, _c_p, _c_p, _c_p]),
     "s2dw_synthesis": (_c_i, [_c_p, _c_p, _c_p, _c_p, _c_p]),
@@ -118,6 +119,13 @@ def s2dw_query(plan: int) -> dict:
                             ctypes.byref(tot)), "s2dw_query")
     return {"J": J.value, "w_elems_per_scale": w.value, "wphi_elems": wp.value,
             "workspace_bytes": ws.value, "total_device_bytes": tot.value}
+
+
+def s2dw_launch_counts(plan: int):
+    """(analysis, synthesis) kernel launches issued by one call of the plan."""
+    a, s = ctypes.c_int(), ctypes.c_int()
+    _check(lib().s2dw_launch_counts(plan, ctypes.byref(a), ctypes.byref(s)), "s2dw_launch_counts")
+    return a.value, s.value
 
 
 def s2dw_kernels(plan: int, J: int, L: int, N: int):
@@ -251,6 +259,9 @@ class Plan:
 
     def kernels(self):
         return s2dw_kernels(self.handle, self.J, self.L, self.N)
+
+    def launch_counts(self):
+        return s2dw_launch_counts(self.handle)
 
     def analysis(self, flm, W, Wphi, stream=None):
         s2dw_analysis(self.handle, flm, W, Wphi, stream)

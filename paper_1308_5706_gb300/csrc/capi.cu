@@ -60,6 +60,36 @@ void gauss_legendre(int Q, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
+// Library-wide non-blocking stream for set-up copies and frees, and the
+// device's stream-ordered memory pool configured to keep freed memory cached:
+// creating and destroying plans then never synchronises the whole device
+// (plain cudaFree / cudaMemcpy on the legacy stream would drain every stream
+// of a serving process).
+std::mutex g_setup_mu;
+cudaStream_t g_setup_stream[64] = {};
+cudaStream_t setup_stream() {
+  int dev = 0;
+  ck(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  if (dev < 0 || dev >= 64) throw CudaFail{cudaErrorInvalidDevice};
+  if (!g_setup_stream[dev]) {
+    ck(cudaStreamCreateWithFlags(&g_setup_stream[dev], cudaStreamNonBlocking));
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = 16ull << 30;  // keep up to 16 GiB of freed blocks cached
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  return g_setup_stream[dev];
+}
+template <typename P>
+void amalloc(P** p, size_t bytes, cudaStream_t st) {
+  ck(cudaMallocAsync(reinterpret_cast<void**>(p), bytes, st));
+}
+inline void afree(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
 // ---------------------------------------------------------------------------
 // Process-wide Delta tables, reference counted (one per band-limit reach).
 // ---------------------------------------------------------------------------
@@ -91,23 +121,24 @@ DeltaTab* delta_acquire(int L, cudaStream_t st) {
   double* em = nullptr;
   int* ee = nullptr;
   try {
-    ck(cudaMalloc(&t->d64, entries * sizeof(double)));
-    ck(cudaMalloc(&t->d32, entries * sizeof(float)));
+    amalloc(&t->d64, entries * sizeof(double), st);
+    amalloc(&t->d32, entries * sizeof(float), st);
     t->bytes = entries * (sizeof(double) + sizeof(float));
     ck(cudaMemsetAsync(t->d64, 0, entries * sizeof(double), st));
     ck(cudaMemsetAsync(t->d32, 0, entries * sizeof(float), st));
     const size_t ne = (size_t)Lmax * (Lmax + 1) / 2;
-    ck(cudaMalloc(&em, ne * sizeof(double)));
-    ck(cudaMalloc(&ee, ne * sizeof(int)));
+    amalloc(&em, ne * sizeof(double), st);
+    amalloc(&ee, ne * sizeof(int), st);
     ck(launch_delta_build(t->d64, t->d32, em, ee, Lmax, st));
+    afree(em, st);
+    afree(ee, st);
     ck(cudaStreamSynchronize(st));
-    cudaFree(em);
-    cudaFree(ee);
   } catch (...) {
-    if (em) cudaFree(em);
-    if (ee) cudaFree(ee);
-    if (t->d64) cudaFree(t->d64);
-    if (t->d32) cudaFree(t->d32);
+    cudaStreamSynchronize(st);
+    afree(em, st);
+    afree(ee, st);
+    afree(t->d64, st);
+    afree(t->d32, st);
     delete t;
     throw;
   }
@@ -119,8 +150,9 @@ void delta_release(DeltaTab* t) {
   if (!t) return;
   std::lock_guard<std::mutex> lk(g_mu);
   if (--t->refs == 0) {
-    cudaFree(t->d64);
-    cudaFree(t->d32);
+    cudaStream_t st = setup_stream();
+    afree(t->d64, st);
+    afree(t->d32, st);
     g_tabs.erase(std::remove(g_tabs.begin(), g_tabs.end(), t), g_tabs.end());
     delete t;
   }
@@ -134,13 +166,19 @@ struct Lists {
   std::vector<std::pair<int, std::pair<void*, int>>> tiles_w;  // (N, (tiles, count))
   void* tiles_phi = nullptr;
   int ntiles_phi = 0;
-  void* segs[4] = {nullptr, nullptr, nullptr, nullptr};
-  int nseg[4] = {0, 0, 0, 0};
-  int items[4] = {0, 0, 0, 0};
+  static constexpr int NK = 6;  // chirp-z kinds 0..3, direct alpha kinds 4..5
+  void* segs[NK] = {};
+  int nseg[NK] = {};
+  int items[NK] = {};
   int maxlogM = 0;
   int Lmax = 0;
   ~Lists() {
-    if (mem) cudaFree(mem);
+    if (mem) {
+      try {
+        afree(mem, setup_stream());
+      } catch (...) {
+      }
+    }
   }
 };
 
@@ -158,6 +196,8 @@ struct s2dw_plan_s {
   int device = 0;
   DeltaTab* tab = nullptr;
   std::vector<double> psi_host, phi_host;
+  cudaStream_t pst = nullptr;       // private non-blocking stream (set-up, frees)
+  cudaEvent_t last_use = nullptr;   // recorded after every call using the plan
   void* ws = nullptr;
   size_t ws_bytes = 0;
   // workspace views
@@ -174,7 +214,8 @@ struct s2dw_plan_s {
   void* post_b = nullptr;
   void* preS_b = nullptr;
   void* postS_b = nullptr;
-  void* Hs = nullptr;  // 4 x M spectra
+  void* root_a = nullptr;  // e^{2 pi i t/(2L-1)}
+  void* Hs = nullptr;      // 4 x M spectra
   // host copies of the static descriptors (device copies live in `own`)
   std::vector<unsigned char> desc_w_host, desc_phi_host;
   std::vector<TileTask> tiles_w_host, tiles_phi_host;
@@ -189,9 +230,17 @@ struct s2dw_plan_s {
       if (e) cudaEventDestroy(e);
     for (auto e : ev_syn)
       if (e) cudaEventDestroy(e);
-    if (ws) cudaFree(ws);
+    if (last_use) {
+      cudaEventSynchronize(last_use);  // only this plan's work, not the device
+      cudaEventDestroy(last_use);
+    }
+    if (ws) cudaFreeAsync(ws, pst);
+    own.mem = nullptr;
+    if (own_mem) cudaFreeAsync(own_mem, pst);
+    if (pst) cudaStreamDestroy(pst);  // releases after the queued frees
     delta_release(tab);
   }
+  void* own_mem = nullptr;
 };
 
 namespace {
@@ -291,6 +340,10 @@ void sort_tiles(std::vector<TileTask>& t) {
 
 template <typename T>
 void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, int& start) {
+  // kinds 4 / 5 collect the alpha segments of scales with Lj <= kDirectMaxLj
+  const int base_kind = (kind == CZT_ALPHA_ANA_DIRECT) ? CZT_ALPHA_ANA
+                        : (kind == CZT_ALPHA_SYN_DIRECT) ? CZT_ALPHA_SYN : kind;
+  const bool direct_list = kind >= CZT_ALPHA_ANA_DIRECT;
   const int L = p->L, n = 2 * L - 1;
   const int64_t wscale = (int64_t)p->N * 2 * L * n;
   const cx<T>* Hs = reinterpret_cast<const cx<T>*>(p->Hs);
@@ -309,7 +362,10 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     s.is_phi = phi ? 1 : 0;
     s.tw = reinterpret_cast<const cx<T>*>(p->tw);
     s.scale = (T)(2.0 * 3.14159265358979323846 / n);
-    switch (kind) {
+    const bool is_alpha = base_kind == CZT_ALPHA_ANA || base_kind == CZT_ALPHA_SYN;
+    const bool direct = is_alpha && Lj <= kDirectMaxLj;
+    if (direct != direct_list) continue;
+    switch (base_kind) {
       case CZT_BETA_ANA:
         s.items = Nj * Lj;
         s.buf_in = reinterpret_cast<cx<T>*>(p->Y[j]);
@@ -341,6 +397,11 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
         s.post = reinterpret_cast<const cx<T>*>(p->postS_b);
         break;
     }
+    if (direct) {
+      const int rows = (base_kind == CZT_ALPHA_ANA) ? kDirectRowsAna : direct_rows_syn(sizeof(T) == 8);
+      s.items = (Nj * 2 * L + rows - 1) / rows;
+      s.pre = reinterpret_cast<const cx<T>*>(p->root_a);
+    }
     if (s.items <= 0) continue;
     s.start = start;
     start += s.items;
@@ -355,8 +416,8 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
   std::vector<ContractDesc<T>> dw(nj), dp(nj);
   std::map<int, std::vector<TileTask>> tw_byN;
   std::vector<TileTask> tphi;
-  std::vector<CztSeg<T>> segs[4];
-  int start[4] = {0, 0, 0, 0};
+  std::vector<CztSeg<T>> segs[Lists::NK];
+  int start[Lists::NK] = {};
   Lists* ls = new Lists();
   for (int i = 0; i < nj; ++i) {
     s2dw_plan_s* p = plans[i];
@@ -370,7 +431,7 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
       t.prob = i;
       tphi.push_back(t);
     }
-    for (int k = 0; k < 4; ++k) build_segs<T>(p, i, k, segs[k], start[k]);
+    for (int k = 0; k < Lists::NK; ++k) build_segs<T>(p, i, k, segs[k], start[k]);
     ls->maxlogM = std::max(ls->maxlogM, p->logM);
     ls->Lmax = std::max(ls->Lmax, p->L);
   }
@@ -389,8 +450,8 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
   }
   const size_t o_tp = off;
   off = align256(off + tphi.size() * sizeof(TileTask));
-  size_t o_sg[4];
-  for (int k = 0; k < 4; ++k) {
+  size_t o_sg[Lists::NK];
+  for (int k = 0; k < Lists::NK; ++k) {
     o_sg[k] = off;
     off = align256(off + segs[k].size() * sizeof(CztSeg<T>));
   }
@@ -403,11 +464,13 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
     ++q;
   }
   if (!tphi.empty()) std::memcpy(host.data() + o_tp, tphi.data(), tphi.size() * sizeof(TileTask));
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < Lists::NK; ++k)
     if (!segs[k].empty()) std::memcpy(host.data() + o_sg[k], segs[k].data(), segs[k].size() * sizeof(CztSeg<T>));
   try {
-    ck(cudaMalloc(&ls->mem, off));
-    ck(cudaMemcpy(ls->mem, host.data(), off, cudaMemcpyHostToDevice));
+    cudaStream_t st = setup_stream();
+    amalloc(&ls->mem, off, st);
+    ck(cudaMemcpyAsync(ls->mem, host.data(), off, cudaMemcpyHostToDevice, st));
+    ck(cudaStreamSynchronize(st));  // host staging buffer is local
   } catch (...) {
     delete ls;
     throw;
@@ -422,7 +485,7 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
   }
   ls->tiles_phi = base + o_tp;
   ls->ntiles_phi = (int)tphi.size();
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < Lists::NK; ++k) {
     ls->segs[k] = base + o_sg[k];
     ls->nseg[k] = (int)segs[k].size();
     ls->items[k] = start[k];
@@ -451,6 +514,8 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
   rec(ev, 3, st);
   launch_czt<T>(CZT_ALPHA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1], ls.maxlogM,
                 ptrs, st);
+  launch_czt<T>(CZT_ALPHA_ANA_DIRECT, reinterpret_cast<const CztSeg<T>*>(ls.segs[4]), ls.nseg[4], ls.items[4],
+                ls.maxlogM, ptrs, st);
   rec(ev, 4, st);
 }
 
@@ -463,6 +528,8 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
   rec(ev, 0, st);
   launch_czt<T>(CZT_ALPHA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[2]), ls.nseg[2], ls.items[2], ls.maxlogM,
                 ptrs, st);
+  launch_czt<T>(CZT_ALPHA_SYN_DIRECT, reinterpret_cast<const CztSeg<T>*>(ls.segs[5]), ls.nseg[5], ls.items[5],
+                ls.maxlogM, ptrs, st);
   rec(ev, 1, st);
   launch_czt<T>(CZT_BETA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[3]), ls.nseg[3], ls.items[3], ls.maxlogM,
                 ptrs, st);
@@ -505,9 +572,10 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   const size_t o_qb = take((size_t)2 * L * sizeof(cx<T>));
   const size_t o_pS = take((size_t)2 * L * sizeof(cx<T>));
   const size_t o_qS = take((size_t)(2 * L - 1) * sizeof(cx<T>));
+  const size_t o_root = take((size_t)n * sizeof(cx<T>));
   const size_t o_H = take((size_t)4 * M * sizeof(cx<T>));
   p->ws_bytes = off;
-  ck(cudaMalloc(&p->ws, off));
+  amalloc(&p->ws, off, st);
   char* b = reinterpret_cast<char*>(p->ws);
   p->RS = b + o_RS;
   p->RSphi = b + o_RSphi;
@@ -525,6 +593,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   p->post_b = b + o_qb;
   p->preS_b = b + o_pS;
   p->postS_b = b + o_qS;
+  p->root_a = b + o_root;
   p->Hs = b + o_H;
 
   // ---- R tables ----
@@ -533,24 +602,26 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     for (int j = 0; j < p->nscale; ++j)
       if (p->Lj[j] > 0 && l >= p->lo[j] && l <= p->hi[j]) slot_w[(size_t)l * 2 + (j % 2)] = j;
   int* slot_d = nullptr;
-  ck(cudaMalloc(&slot_d, (slot_w.size() + slot_p.size()) * sizeof(int)));
-  ck(cudaMemcpy(slot_d, slot_w.data(), slot_w.size() * sizeof(int), cudaMemcpyHostToDevice));
-  ck(cudaMemcpy(slot_d + slot_w.size(), slot_p.data(), slot_p.size() * sizeof(int), cudaMemcpyHostToDevice));
+  amalloc(&slot_d, (slot_w.size() + slot_p.size()) * sizeof(int), st);
+  ck(cudaMemcpyAsync(slot_d, slot_w.data(), slot_w.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  ck(cudaMemcpyAsync(slot_d + slot_w.size(), slot_p.data(), slot_p.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     st));
   ck(launch_rtable<T>(reinterpret_cast<T*>(p->RS), p->tab->d64, kap_d, sabs_d, slot_d, L, p->Lp, N, 2, L, st));
   ck(launch_rtable<T>(reinterpret_cast<T*>(p->RSphi), p->tab->d64, phi_d, nullptr, slot_d + slot_w.size(), p->Lphi,
                       p->Lphip, 1, 1, L, st));
   // ---- chirp tables (float64, then the working precision) ----
-  const size_t n64 = (size_t)M + n + (2 * L - 1) + 2 * L + 2 * L + (2 * L - 1) + 4 * (size_t)M;
+  const size_t n64 = (size_t)M + n + (2 * L - 1) + 2 * L + 2 * L + (2 * L - 1) + n + 4 * (size_t)M;
   double2* t64 = nullptr;
-  ck(cudaMalloc(&t64, n64 * sizeof(double2)));
+  amalloc(&t64, n64 * sizeof(double2), st);
   double2* tw64 = t64;
   double2* ca64 = tw64 + M;
   double2* pb64 = ca64 + n;
   double2* qb64 = pb64 + (2 * L - 1);
   double2* pS64 = qb64 + 2 * L;
   double2* qS64 = pS64 + 2 * L;
-  double2* H64 = qS64 + (2 * L - 1);
-  ck(launch_chirp_build64(tw64, ca64, pb64, qb64, pS64, qS64, H64, q_d, L, p->logM, st));
+  double2* rt64 = qS64 + (2 * L - 1);
+  double2* H64 = rt64 + n;
+  ck(launch_chirp_build64(tw64, ca64, pb64, qb64, pS64, qS64, rt64, H64, q_d, L, p->logM, st));
   if (sizeof(T) == sizeof(double)) {
     ck(cudaMemcpyAsync(p->tw, tw64, (size_t)M * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     ck(cudaMemcpyAsync(p->chirp_a, ca64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -558,6 +629,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     ck(cudaMemcpyAsync(p->post_b, qb64, (size_t)2 * L * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     ck(cudaMemcpyAsync(p->preS_b, pS64, (size_t)2 * L * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     ck(cudaMemcpyAsync(p->postS_b, qS64, (size_t)(2 * L - 1) * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    ck(cudaMemcpyAsync(p->root_a, rt64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     ck(cudaMemcpyAsync(p->Hs, H64, (size_t)4 * M * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   } else {
     ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->tw), tw64, M, st));
@@ -566,11 +638,12 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->post_b), qb64, 2 * L, st));
     ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->preS_b), pS64, 2 * L, st));
     ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->postS_b), qS64, 2 * L - 1, st));
+    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->root_a), rt64, n, st));
     ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->Hs), H64, (int64_t)4 * M, st));
   }
-  ck(cudaStreamSynchronize(st));
-  cudaFree(t64);
-  cudaFree(slot_d);
+  afree(t64, st);
+  afree(slot_d, st);
+  ck(cudaStreamSynchronize(st));  // slot_w / slot_p host vectors are local
 
   // ---- descriptors, tiles, launch lists ----
   ContractDesc<T> dw, dp;
@@ -584,14 +657,16 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   sort_tiles(p->tiles_w_host);
   sort_tiles(p->tiles_phi_host);
   Lists* ls = build_lists<T>(std::vector<s2dw_plan_t>{p});
-  // move into the plan (Lists owns device memory; transfer by swap)
-  std::swap(p->own.mem, ls->mem);
+  // move into the plan (the plan frees the list memory at destruction)
+  p->own_mem = ls->mem;
+  p->own.mem = nullptr;
+  ls->mem = nullptr;
   p->own.desc_w = ls->desc_w;
   p->own.desc_phi = ls->desc_phi;
   p->own.tiles_w = ls->tiles_w;
   p->own.tiles_phi = ls->tiles_phi;
   p->own.ntiles_phi = ls->ntiles_phi;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < Lists::NK; ++k) {
     p->own.segs[k] = ls->segs[k];
     p->own.nseg[k] = ls->nseg[k];
     p->own.items[k] = ls->items[k];
@@ -626,26 +701,29 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
   int rc = S2DW_OK;
   try {
     ck(cudaGetDevice(&p->device));
-    ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    setup_stream();  // configures the caching memory pool once per device
+    ck(cudaStreamCreateWithFlags(&p->pst, cudaStreamNonBlocking));
+    ck(cudaEventCreateWithFlags(&p->last_use, cudaEventDisableTiming));
+    st = p->pst;
     std::vector<double> glx, glw;
     const int Q = 16, PAN = 32;
     gauss_legendre(Q, glx, glw);
-    ck(cudaMalloc(&gl, 2 * Q * sizeof(double)));
-    ck(cudaMemcpy(gl, glx.data(), Q * sizeof(double), cudaMemcpyHostToDevice));
-    ck(cudaMemcpy(gl + Q, glw.data(), Q * sizeof(double), cudaMemcpyHostToDevice));
-    ck(cudaMalloc(&kap, (size_t)(J + 1) * L * sizeof(double)));
-    ck(cudaMalloc(&phi, (size_t)L * sizeof(double)));
-    ck(cudaMalloc(&sabs, (size_t)L * N * sizeof(double)));
-    ck(cudaMalloc(&psi, (size_t)(J + 1) * L * N * sizeof(double2)));
-    ck(cudaMalloc(&q, (size_t)2 * L * sizeof(double)));
+    amalloc(&gl, 2 * Q * sizeof(double), st);
+    ck(cudaMemcpyAsync(gl, glx.data(), Q * sizeof(double), cudaMemcpyHostToDevice, st));
+    ck(cudaMemcpyAsync(gl + Q, glw.data(), Q * sizeof(double), cudaMemcpyHostToDevice, st));
+    amalloc(&kap, (size_t)(J + 1) * L * sizeof(double), st);
+    amalloc(&phi, (size_t)L * sizeof(double), st);
+    amalloc(&sabs, (size_t)L * N * sizeof(double), st);
+    amalloc(&psi, (size_t)(J + 1) * L * N * sizeof(double2), st);
+    amalloc(&q, (size_t)2 * L * sizeof(double), st);
     ck(launch_kernel_values(kap, phi, sabs, psi, q, L, N, J, lam, gl, gl + Q, Q, PAN, st));
-    ck(cudaStreamSynchronize(st));
     std::vector<double> kap_h((size_t)(J + 1) * L);
     p->phi_host.resize(L);
     p->psi_host.resize((size_t)(J + 1) * L * N * 2);
-    ck(cudaMemcpy(kap_h.data(), kap, kap_h.size() * sizeof(double), cudaMemcpyDeviceToHost));
-    ck(cudaMemcpy(p->phi_host.data(), phi, L * sizeof(double), cudaMemcpyDeviceToHost));
-    ck(cudaMemcpy(p->psi_host.data(), psi, p->psi_host.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    ck(cudaMemcpyAsync(kap_h.data(), kap, kap_h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ck(cudaMemcpyAsync(p->phi_host.data(), phi, L * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ck(cudaMemcpyAsync(p->psi_host.data(), psi, p->psi_host.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ck(cudaStreamSynchronize(st));
     // supports where kappa^j(l) > 0 and their overlaps
     p->lo.assign(p->nscale, -1);
     p->hi.assign(p->nscale, -1);
@@ -695,13 +773,14 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
   } catch (...) {
     rc = S2DW_ECUDA;
   }
-  if (gl) cudaFree(gl);
-  if (kap) cudaFree(kap);
-  if (phi) cudaFree(phi);
-  if (sabs) cudaFree(sabs);
-  if (psi) cudaFree(psi);
-  if (q) cudaFree(q);
-  if (st) cudaStreamDestroy(st);
+  if (st) {
+    afree(gl, st);
+    afree(kap, st);
+    afree(phi, st);
+    afree(sabs, st);
+    afree(psi, st);
+    afree(q, st);
+  }
   if (rc != S2DW_OK) {
     cudaGetLastError();
     delete p;
@@ -755,7 +834,7 @@ int s2dw_plan(s2dw_plan_t* out, int L, int N, double lambda, int J0, unsigned fl
 
 int s2dw_plan_destroy(s2dw_plan_t plan) {
   if (!plan) return S2DW_OK;
-  cudaDeviceSynchronize();
+  if (plan->last_use) cudaEventSynchronize(plan->last_use);
   drop_batches_with(plan);
   delete plan;
   return err_of(cudaGetLastError());
@@ -773,6 +852,17 @@ int s2dw_query(s2dw_plan_t p, int* J, int64_t* w_elems_per_scale, int64_t* wphi_
   if (workspace_bytes) *workspace_bytes = (int64_t)p->ws_bytes;
   if (total_device_bytes)
     *total_device_bytes = (int64_t)p->ws_bytes + (wps * p->nscale + wph) * el + L * L * 2 * el;
+  return S2DW_OK;
+}
+
+int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {
+  if (!p) return S2DW_EINVAL;
+  const Lists& ls = p->own;
+  int contract = ls.ntiles_phi > 0 ? 1 : 0;
+  for (auto& t : ls.tiles_w) contract += t.second.second > 0 ? 1 : 0;
+  auto has = [&](int k) { return ls.items[k] > 0 ? 1 : 0; };
+  if (analysis) *analysis = contract + has(0) + has(1) + has(4);
+  if (synthesis) *synthesis = contract + has(2) + has(3) + has(5) + 1;
   return S2DW_OK;
 }
 
@@ -795,6 +885,7 @@ int s2dw_analysis(s2dw_plan_t p, const void* flm, void* W, void* Wphi, void* str
   if (p->prof && p->nana < s2dw_plan_s::kProfCalls) ev = p->ev_ana.data() + 5 * (p->nana++);
   if (p->fp64) run_analysis<double>(p->own, ptrs, st, ev);
   else run_analysis<float>(p->own, ptrs, st, ev);
+  cudaEventRecord(p->last_use, st);
   return err_of(cudaGetLastError());
 }
 
@@ -818,6 +909,7 @@ int s2dw_synthesis(s2dw_plan_t p, const void* W, const void* Wphi, void* flm, vo
   if (p->prof && p->nsyn < s2dw_plan_s::kProfCalls) ev = p->ev_syn.data() + 6 * (p->nsyn++);
   if (p->fp64) run_synthesis<double>(p->own, ptrs, rj, 1, st, ev);
   else run_synthesis<float>(p->own, ptrs, rj, 1, st, ev);
+  cudaEventRecord(p->last_use, st);
   return err_of(cudaGetLastError());
 }
 
@@ -917,6 +1009,7 @@ int s2dw_analysis_batch(const s2dw_plan_t* plans, const void* const* flm, void* 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (fp64) run_analysis<double>(*ls, ptrs, st);
   else run_analysis<float>(*ls, ptrs, st);
+  for (int i = 0; i < njobs; ++i) cudaEventRecord(plans[i]->last_use, st);
   return err_of(cudaGetLastError());
 }
 
@@ -947,6 +1040,7 @@ int s2dw_synthesis_batch(const s2dw_plan_t* plans, const void* const* W, const v
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (fp64) run_synthesis<double>(*ls, ptrs, rj, njobs, st);
   else run_synthesis<float>(*ls, ptrs, rj, njobs, st);
+  for (int i = 0; i < njobs; ++i) cudaEventRecord(plans[i]->last_use, st);
   return err_of(cudaGetLastError());
 }
 

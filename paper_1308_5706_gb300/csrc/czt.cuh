@@ -169,6 +169,193 @@ __global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// Direct evaluation of the alpha sums for scales with a small band-limit
+// L_j <= kDirectMax: the chirp-z cost does not shrink with L_j (the output
+// grid has 2L-1 points for every scale) while a direct sum costs ~L_j per
+// output.  Twiddles e^{i m alpha_a} advance by one complex product per step
+// of m (or a) and are re-read exactly from the root table every 16 steps.
+// ---------------------------------------------------------------------------
+constexpr int kDirectMax = kDirectMaxLj;
+constexpr int kDRowsAna = kDirectRowsAna;
+
+// W[row][a] = X_0 + 2 sum_{m=1}^{Lj-1} Re(X_m e^{2 pi i m a / n})   (Eq. (30), Hermitian in m)
+template <typename T>
+__global__ void __launch_bounds__(256) k_alpha_ana_direct(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+  __shared__ cx<T> Xs[kDRowsAna][kDirectMax];
+  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
+  const int item = blockIdx.x - sg.start;
+  const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1;
+  const int nrows = sg.N * 2 * L, row0 = item * kDRowsAna, nr = min(kDRowsAna, nrows - row0);
+  const cx<T>* __restrict__ root = sg.pre;  // e^{2 pi i t / n}, t < n
+  for (int i = threadIdx.x; i < kDRowsAna * Lj; i += blockDim.x) {
+    const int r = i / Lj, m = i % Lj;
+    Xs[r][m] = r < nr ? sg.buf_in[(size_t)(row0 + r) * Lj + m] : mkc<T>(0, 0);
+  }
+  __syncthreads();
+  T* __restrict__ Wb = reinterpret_cast<T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff;
+  for (int a0 = threadIdx.x; a0 < n; a0 += 4 * blockDim.x) {
+    int aq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) aq[q] = min(a0 + q * (int)blockDim.x, n - 1);
+    for (int rg = 0; rg < kDRowsAna; rg += 8) {
+      T acc[4][8];
+      cx<T> w[4], st[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        st[q] = __ldg(root + aq[q]);
+        w[q] = st[q];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[q][r] = Xs[rg + r][0].x;
+      }
+      for (int m = 1; m < Lj; ++m) {
+        if ((m & 15) == 0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) w[q] = __ldg(root + (int)(((long long)m * aq[q]) % n));
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const cx<T> x = Xs[rg + r][m];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q][r] += T(2) * (x.x * w[q].x - x.y * w[q].y);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = cmul<T>(w[q], st[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int a = a0 + q * (int)blockDim.x;
+        if (a < n) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+            if (rg + r < nr) Wb[(size_t)(row0 + rg + r) * n + a] = acc[q][r];
+        }
+      }
+    }
+  }
+}
+
+// V[row][m] = (2 pi / n) sum_{a<n} W[row][a] e^{-2 pi i m a / n}, m < Lj   (Eq. (37))
+// A CTA takes R = 32 / sizeof(T) rows, staged in shared memory as one 32-byte
+// line per sample a (Ws[a][r]) so that a lane reads all R rows with two
+// 16-byte loads; loads are issued in unrolled batches (rows have odd length,
+// so neither 16-byte copies nor TMA tiles apply).  Warp w sums the a-range
+// chunk w; its lanes are (sub, m) with P = 32 / Lj lanes per m splitting the
+// chunk further.  Partials are reduced over sub by shuffles when Lj divides
+// 32, then over the chunks in shared memory.
+template <typename T>
+__device__ __forceinline__ void syn_direct_line(const T* p, T (&x)[32 / sizeof(T)]) {
+  const float4 u = reinterpret_cast<const float4*>(p)[0];
+  const float4 v = reinterpret_cast<const float4*>(p)[1];
+  if constexpr (sizeof(T) == 4) {
+    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
+    x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(&u), b = *reinterpret_cast<const double2*>(&v);
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_alpha_syn_direct(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int R = 32 / sizeof(T);
+  constexpr int U = 4;  // samples per thread per load batch (R * U loads in flight)
+  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
+  const int item = blockIdx.x - sg.start;
+  const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1;
+  const int nrows = sg.N * 2 * L, row0 = item * R, nr = min(R, nrows - row0);
+  T* Ws = reinterpret_cast<T*>(smem_raw);  // [n][R], later the partials
+  const T* __restrict__ Wb = reinterpret_cast<const T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff +
+                             (size_t)row0 * n;
+  const int tid = threadIdx.x;
+  for (int a0 = 0; a0 < n; a0 += U * 256) {
+    T x[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int a = a0 + u * 256 + tid;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[u][r] = (a < n && r < nr) ? __ldg(Wb + (size_t)r * n + a) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int a = a0 + u * 256 + tid;
+      if (a < n) {
+        float4* d = reinterpret_cast<float4*>(Ws + (size_t)a * R);
+        if constexpr (sizeof(T) == 4) {
+          d[0] = make_float4(x[u][0], x[u][1], x[u][2], x[u][3]);
+          d[1] = make_float4(x[u][4], x[u][5], x[u][6], x[u][7]);
+        } else {
+          reinterpret_cast<double2*>(d)[0] = make_double2(x[u][0], x[u][1]);
+          reinterpret_cast<double2*>(d)[1] = make_double2(x[u][2], x[u][3]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const cx<T>* __restrict__ root = sg.pre;  // e^{2 pi i t / n}
+  const int warp = tid >> 5, lane = tid & 31;
+  const int P = 32 / Lj, m = lane % Lj, sub = lane / Lj;
+  const bool active = sub < P;
+  cx<T> acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = mkc<T>(0, 0);
+  if (active) {
+    const int c_lo = (int)(((long long)n * warp) / 8), c_hi = (int)(((long long)n * (warp + 1)) / 8);
+    const int a_lo = c_lo + (int)(((long long)(c_hi - c_lo) * sub) / P);
+    const int a_hi = c_lo + (int)(((long long)(c_hi - c_lo) * (sub + 1)) / P);
+    const cx<T> st = cconj<T>(__ldg(root + m));
+    cx<T> w = mkc<T>(1, 0);
+    for (int a = a_lo; a < a_hi; ++a) {
+      if (((a - a_lo) & 15) == 0) w = cconj<T>(__ldg(root + (m * a) % n));
+      T x[R];
+      syn_direct_line<T>(Ws + (size_t)a * R, x);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        acc[r].x = fma(x[r], w.x, acc[r].x);
+        acc[r].y = fma(x[r], w.y, acc[r].y);
+      }
+      w = cmul<T>(w, st);
+    }
+  }
+  // in-warp reduction over sub (lanes m, m + Lj, m + 2 Lj, ...) when Lj | 32
+  const bool shfl = (32 % Lj) == 0;
+  if (shfl) {
+    for (int off = Lj; off < 32; off <<= 1) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, off);
+        acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, off);
+      }
+    }
+  }
+  const int nchunk = shfl ? 8 : 8 * P;
+  __syncthreads();  // Ws is reused for the partials [nchunk][Lj][R]
+  cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);
+  if (active && (!shfl || sub == 0)) {
+    const int c = shfl ? warp : warp * P + sub;
+#pragma unroll
+    for (int r = 0; r < R; ++r) part[((size_t)c * Lj + m) * R + r] = acc[r];
+  }
+  __syncthreads();
+  for (int i = tid; i < Lj * R; i += blockDim.x) {
+    const int mm = i / R, r = i % R;
+    if (r >= nr) continue;
+    cx<T> s = mkc<T>(0, 0);
+    for (int c2 = 0; c2 < nchunk; ++c2) s = cadd<T>(s, part[((size_t)c2 * Lj + mm) * R + r]);
+    sg.buf_out[(size_t)(row0 + r) * Lj + mm] = cscale<T>(s, sg.scale);
+  }
+}
+
+// shared memory of k_alpha_syn_direct for band-limits up to L: the staged
+// rows, or the partials (at most 256 x R complex) if larger
+template <typename T>
+size_t alpha_syn_direct_smem(int L) {
+  const size_t n = 2 * (size_t)L - 1;
+  const size_t rows = n * 32, parts = (size_t)256 * (32 / sizeof(T)) * sizeof(cx<T>);
+  return rows > parts ? rows : parts;
+}
+
 template <typename T>
 void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items, int maxlogM,
                      const CallPtrs& ptrs, cudaStream_t st) {
@@ -180,6 +367,10 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
     case CZT_ALPHA_ANA: k_czt_alpha_ana<T><<<grid, block, smem, st>>>(segs, nseg, ptrs); break;
     case CZT_ALPHA_SYN: k_czt_alpha_syn<T><<<grid, block, smem, st>>>(segs, nseg, ptrs); break;
     case CZT_BETA_SYN: k_czt_beta_syn<T><<<grid, block, smem, st>>>(segs, nseg); break;
+    case CZT_ALPHA_ANA_DIRECT: k_alpha_ana_direct<T><<<grid, block, 0, st>>>(segs, nseg, ptrs); break;
+    case CZT_ALPHA_SYN_DIRECT:
+      k_alpha_syn_direct<T><<<grid, block, alpha_syn_direct_smem<T>(1 << (maxlogM - 2)), st>>>(segs, nseg, ptrs);
+      break;
     default: break;
   }
 }
@@ -193,6 +384,9 @@ cudaError_t czt_set_smem(int maxlogM) {
   e = cudaFuncSetAttribute(k_czt_alpha_ana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_czt_alpha_syn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_alpha_syn_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)alpha_syn_direct_smem<T>(2048));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_czt_beta_syn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }

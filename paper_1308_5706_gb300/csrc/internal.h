@@ -48,7 +48,17 @@ struct CallPtrs {
   void* Wphi[MAXB];      // scaling coefficients
 };
 
-enum CztKind { CZT_BETA_ANA = 0, CZT_ALPHA_ANA = 1, CZT_ALPHA_SYN = 2, CZT_BETA_SYN = 3 };
+enum CztKind {
+  CZT_BETA_ANA = 0,
+  CZT_ALPHA_ANA = 1,
+  CZT_ALPHA_SYN = 2,
+  CZT_BETA_SYN = 3,
+  CZT_ALPHA_ANA_DIRECT = 4,  // small-band scales, direct sums
+  CZT_ALPHA_SYN_DIRECT = 5
+};
+constexpr int kDirectMaxLj = 32;
+constexpr int kDirectRowsAna = 16;
+inline int direct_rows_syn(bool fp64) { return fp64 ? 4 : 8; }  // 32-byte line per alpha sample
 
 // One segment of a chirp-z launch: all columns / row pairs of one scale of
 // one transform.

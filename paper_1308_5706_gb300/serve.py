@@ -54,9 +54,11 @@ class Request:
 
 
 def poisson_workload(rate: float, duration: float, seed: int, L_range=(32, 2048), N_range=(1, 8),
-                     lams=(2.0, 3.0), p_synthesis=0.5) -> List[Request]:
-    """Poisson arrivals; L log-uniform, N uniform, lambda uniform in `lams`;
-    each synthesis request consumes the oldest not yet consumed analysis."""
+                     lams=(2.0, 3.0), p_synthesis=0.5, Ls=None) -> List[Request]:
+    """Poisson arrivals; L uniform over the set `Ls` when given (e.g. the
+    powers of two a survey pipeline uses), else log-uniform in `L_range`;
+    N uniform, lambda uniform in `lams`; each synthesis request consumes the
+    oldest not yet consumed analysis."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t, reqs, unconsumed = 0.0, [], collections.deque()
     while True:
@@ -68,7 +70,10 @@ def poisson_workload(rate: float, duration: float, seed: int, L_range=(32, 2048)
             par = reqs[unconsumed.popleft()]
             reqs.append(Request(rid, "synthesis", par.L, par.N, par.lam, t, parent=par.rid))
         else:
-            L = int(round(math.exp(rng.uniform(math.log(L_range[0]), math.log(L_range[1])))))
+            if Ls is not None:
+                L = int(Ls[int(rng.integers(0, len(Ls)))])
+            else:
+                L = int(round(math.exp(rng.uniform(math.log(L_range[0]), math.log(L_range[1])))))
             N = int(rng.integers(N_range[0], N_range[1] + 1))
             N = min(N, L)
             lam = float(lams[int(rng.integers(0, len(lams)))])
@@ -108,6 +113,17 @@ class Server:
         self.stats["plan_create"] += 1
         return B.Plan(r.L, r.N, r.lam, r.J0, self.precision)
 
+    def prewarm(self, reqs: List[Request], per_key: int = 1) -> float:
+        """Create `per_key` plans for every configuration in `reqs` ahead of
+        serving (plan creation computes kernels and tables on the device and
+        blocks the host thread for milliseconds).  Returns the seconds spent."""
+        t0 = time.perf_counter()
+        for key in sorted({self._key(r) for r in reqs}):
+            L, N, lam, J0, prec = key
+            while len(self.pool[key]) < per_key:
+                self._give_plan(B.Plan(L, N, lam, J0, prec))
+        return time.perf_counter() - t0
+
     def _give_plan(self, p: B.Plan):
         self.pool[(p.L, p.N, p.lam, p.J0, p.precision)].append(p)
         self.pool_bytes += p.info["workspace_bytes"]
@@ -129,7 +145,10 @@ class Server:
         return (w + f if r.kind == "analysis" else f) + ws
 
     # ---- run ---------------------------------------------------------------
-    def run(self, reqs: List[Request], keep_outputs: bool = False, time_scale: float = 1.0):
+    def run(self, reqs: List[Request], keep_outputs: bool = False, time_scale: float = 1.0, payload=None):
+        """Serve `reqs`; `payload(r)` gives an analysis request's f_lm as a pinned
+        host tensor (the bytes a client sends; by default generated from r.seed
+        when the request is admitted)."""
         torch = self.torch
         cd = torch.complex64 if self.precision == "mixed" else torch.complex128
         rd = torch.float32 if self.precision == "mixed" else torch.float64
@@ -193,7 +212,8 @@ class Server:
                 with torch.cuda.stream(stream):
                     if kind == "analysis":
                         for r, p in zip(batch, plans):
-                            fh = torch.from_numpy(flm_gaussian(r.L, r.seed, "cl")).to(cd).pin_memory()
+                            fh = payload(r) if payload is not None else \
+                                torch.from_numpy(flm_gaussian(r.L, r.seed, "cl")).to(cd).pin_memory()
                             r.f = torch.empty(r.L * r.L, dtype=cd, device="cuda")
                             r.f.copy_(fh, non_blocking=True)
                             r.W = torch.empty(p.w_shape, dtype=rd, device="cuda")

@@ -1,0 +1,40 @@
+"""The launch counts a plan reports match the kernels one call really runs
+(counted by the CUDA profiler), and every launched kernel is one of ours."""
+import pytest
+
+from paper_1308_5706_gb300 import binding as B
+from paper_1308_5706_gb300.inputs import flm_gaussian
+
+pytestmark = pytest.mark.gpu
+
+
+def _kernels_of(fn):
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        fn()
+        torch.cuda.synchronize()
+    names = [e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA
+             and "memcpy" not in e.name.lower() and "memset" not in e.name.lower()]
+    return names
+
+
+@pytest.mark.parametrize("L,N,prec", [(16, 3, "mixed"), (96, 4, "fp64"), (256, 5, "mixed")])
+def test_launch_counts(L, N, prec):
+    import torch
+    p = B.Plan(L, N, 2.0, 0, prec)
+    cd = torch.complex64 if prec == "mixed" else torch.complex128
+    f = torch.from_numpy(flm_gaussian(L, 1, "cl")).to(cd).cuda()
+    W, Wp = p.alloc_w()
+    g = p.alloc_flm()
+    p.analysis(f, W, Wp)
+    p.synthesis(W, Wp, g)
+    na, ns = p.launch_counts()
+    ka = _kernels_of(lambda: p.analysis(f, W, Wp))
+    ks = _kernels_of(lambda: p.synthesis(W, Wp, g))
+    if not ka:
+        pytest.skip("profiler recorded no CUDA kernels")
+    assert len(ka) == na and len(ks) == ns
+    assert all(k.startswith("void s2dw::") or "s2dw" in k for k in ka + ks), ka + ks
+    p.close()
