@@ -166,7 +166,7 @@ struct Lists {
   std::vector<std::pair<int, std::pair<void*, int>>> tiles_w;  // (N, (tiles, count))
   void* tiles_phi = nullptr;
   int ntiles_phi = 0;
-  static constexpr int NK = 6;  // chirp-z kinds 0..3, direct alpha kinds 4..5
+  static constexpr int NK = 8;  // chirp-z kinds 0..3, direct alpha 4..5, single-FFT beta 6..7
   void* segs[NK] = {};
   int nseg[NK] = {};
   int items[NK] = {};
@@ -215,6 +215,7 @@ struct s2dw_plan_s {
   void* preS_b = nullptr;
   void* postS_b = nullptr;
   void* root_a = nullptr;  // e^{2 pi i t/(2L-1)}
+  void* bfft = nullptr;    // e^{i pi m'/(4L)} (|m'| < L), then q_b (b < 2L): single-FFT beta
   void* Hs = nullptr;      // 4 x M spectra
   // host copies of the static descriptors (device copies live in `own`)
   std::vector<unsigned char> desc_w_host, desc_phi_host;
@@ -340,11 +341,18 @@ void sort_tiles(std::vector<TileTask>& t) {
 
 template <typename T>
 void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, int& start) {
-  // kinds 4 / 5 collect the alpha segments of scales with Lj <= kDirectMaxLj
+  // kinds 4 / 5 collect the alpha segments of scales with Lj <= kDirectMaxLj,
+  // kinds 6 / 7 the beta segments of plans whose FFT length M is 4L
   const int base_kind = (kind == CZT_ALPHA_ANA_DIRECT) ? CZT_ALPHA_ANA
-                        : (kind == CZT_ALPHA_SYN_DIRECT) ? CZT_ALPHA_SYN : kind;
-  const bool direct_list = kind >= CZT_ALPHA_ANA_DIRECT;
+                        : (kind == CZT_ALPHA_SYN_DIRECT) ? CZT_ALPHA_SYN
+                        : (kind == CZT_BETA_ANA_FFT)     ? CZT_BETA_ANA
+                        : (kind == CZT_BETA_SYN_FFT)     ? CZT_BETA_SYN
+                                                         : kind;
+  const bool direct_list = kind == CZT_ALPHA_ANA_DIRECT || kind == CZT_ALPHA_SYN_DIRECT;
+  const bool fft_list = kind == CZT_BETA_ANA_FFT || kind == CZT_BETA_SYN_FFT;
   const int L = p->L, n = 2 * L - 1;
+  const bool beta_fft = (4 * L == p->M);
+  if ((base_kind == CZT_BETA_ANA || base_kind == CZT_BETA_SYN) && beta_fft != fft_list) return;
   const int64_t wscale = (int64_t)p->N * 2 * L * n;
   const cx<T>* Hs = reinterpret_cast<const cx<T>*>(p->Hs);
   for (int j = 0; j <= p->nscale; ++j) {
@@ -396,6 +404,10 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
         s.pre = reinterpret_cast<const cx<T>*>(p->preS_b);
         s.post = reinterpret_cast<const cx<T>*>(p->postS_b);
         break;
+    }
+    if (fft_list) {
+      s.pre = reinterpret_cast<const cx<T>*>(p->bfft);
+      s.post = reinterpret_cast<const cx<T>*>(p->bfft) + (2 * L - 1);
     }
     if (direct) {
       const int rows = (base_kind == CZT_ALPHA_ANA) ? kDirectRowsAna : direct_rows_syn(sizeof(T) == 8);
@@ -511,6 +523,8 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
   rec(ev, 2, st);
   launch_czt<T>(CZT_BETA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[0]), ls.nseg[0], ls.items[0], ls.maxlogM,
                 ptrs, st);
+  launch_czt<T>(CZT_BETA_ANA_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[6]), ls.nseg[6], ls.items[6],
+                ls.maxlogM, ptrs, st);
   rec(ev, 3, st);
   launch_czt<T>(CZT_ALPHA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1], ls.maxlogM,
                 ptrs, st);
@@ -533,6 +547,8 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
   rec(ev, 1, st);
   launch_czt<T>(CZT_BETA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[3]), ls.nseg[3], ls.items[3], ls.maxlogM,
                 ptrs, st);
+  launch_czt<T>(CZT_BETA_SYN_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[7]), ls.nseg[7], ls.items[7],
+                ls.maxlogM, ptrs, st);
   rec(ev, 2, st);
   for (auto& t : ls.tiles_w)
     launch_contract<T>(t.first, 2, true, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
@@ -573,6 +589,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   const size_t o_pS = take((size_t)2 * L * sizeof(cx<T>));
   const size_t o_qS = take((size_t)(2 * L - 1) * sizeof(cx<T>));
   const size_t o_root = take((size_t)n * sizeof(cx<T>));
+  const size_t o_bf = take((size_t)(4 * L - 1) * sizeof(cx<T>));
   const size_t o_H = take((size_t)4 * M * sizeof(cx<T>));
   p->ws_bytes = off;
   amalloc(&p->ws, off, st);
@@ -594,6 +611,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   p->preS_b = b + o_pS;
   p->postS_b = b + o_qS;
   p->root_a = b + o_root;
+  p->bfft = b + o_bf;
   p->Hs = b + o_H;
 
   // ---- R tables ----
@@ -610,7 +628,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   ck(launch_rtable<T>(reinterpret_cast<T*>(p->RSphi), p->tab->d64, phi_d, nullptr, slot_d + slot_w.size(), p->Lphi,
                       p->Lphip, 1, 1, L, st));
   // ---- chirp tables (float64, then the working precision) ----
-  const size_t n64 = (size_t)M + n + (2 * L - 1) + 2 * L + 2 * L + (2 * L - 1) + n + 4 * (size_t)M;
+  const size_t n64 = (size_t)M + n + (2 * L - 1) + 2 * L + 2 * L + (2 * L - 1) + n + (4 * L - 1) + 4 * (size_t)M;
   double2* t64 = nullptr;
   amalloc(&t64, n64 * sizeof(double2), st);
   double2* tw64 = t64;
@@ -620,8 +638,9 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   double2* pS64 = qb64 + 2 * L;
   double2* qS64 = pS64 + 2 * L;
   double2* rt64 = qS64 + (2 * L - 1);
-  double2* H64 = rt64 + n;
-  ck(launch_chirp_build64(tw64, ca64, pb64, qb64, pS64, qS64, rt64, H64, q_d, L, p->logM, st));
+  double2* bf64 = rt64 + n;
+  double2* H64 = bf64 + (4 * L - 1);
+  ck(launch_chirp_build64(tw64, ca64, pb64, qb64, pS64, qS64, rt64, bf64, H64, q_d, L, p->logM, st));
   if (sizeof(T) == sizeof(double)) {
     ck(cudaMemcpyAsync(p->tw, tw64, (size_t)M * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     ck(cudaMemcpyAsync(p->chirp_a, ca64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -630,6 +649,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     ck(cudaMemcpyAsync(p->preS_b, pS64, (size_t)2 * L * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     ck(cudaMemcpyAsync(p->postS_b, qS64, (size_t)(2 * L - 1) * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     ck(cudaMemcpyAsync(p->root_a, rt64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    ck(cudaMemcpyAsync(p->bfft, bf64, (size_t)(4 * L - 1) * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     ck(cudaMemcpyAsync(p->Hs, H64, (size_t)4 * M * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   } else {
     ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->tw), tw64, M, st));
@@ -639,6 +659,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->preS_b), pS64, 2 * L, st));
     ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->postS_b), qS64, 2 * L - 1, st));
     ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->root_a), rt64, n, st));
+    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->bfft), bf64, 4 * L - 1, st));
     ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->Hs), H64, (int64_t)4 * M, st));
   }
   afree(t64, st);
@@ -861,8 +882,8 @@ int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {
   int contract = ls.ntiles_phi > 0 ? 1 : 0;
   for (auto& t : ls.tiles_w) contract += t.second.second > 0 ? 1 : 0;
   auto has = [&](int k) { return ls.items[k] > 0 ? 1 : 0; };
-  if (analysis) *analysis = contract + has(0) + has(1) + has(4);
-  if (synthesis) *synthesis = contract + has(2) + has(3) + has(5) + 1;
+  if (analysis) *analysis = contract + has(0) + has(1) + has(4) + has(6);
+  if (synthesis) *synthesis = contract + has(2) + has(3) + has(5) + has(7) + 1;
   return S2DW_OK;
 }
 

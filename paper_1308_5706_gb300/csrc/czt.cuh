@@ -170,6 +170,66 @@ __global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restric
 }
 
 // ---------------------------------------------------------------------------
+// Beta sums when 4L is the FFT length M (L a power of two): the samples
+// beta_b = pi (2b+1)/(4L) lie on the grid 2 pi b / M shifted by pi/(4L), so
+//   analysis:  X_b = sum_{|m'|<Lj} (Yhat_{m'} e^{i pi m'/(4L)}) e^{2 pi i m' b/M}
+//   synthesis: T_{m'} = e^{-i pi m'/(4L)} sum_{b<2L} (q_b V_b) e^{-2 pi i m' b/M}
+// are one FFT each instead of a chirp-z convolution (two FFTs).
+// pre: e^{i pi m'/(4L)} at index m' + L - 1; post: q_b (real part), b < 2L.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_beta_ana_fft(const CztSeg<T>* __restrict__ segs, int nseg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
+  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
+  const int item = blockIdx.x - sg.start;
+  const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM;
+  const int g = item / Lj, m = item % Lj;
+  const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
+  for (int i = threadIdx.x; i < fft_smem_elems(M); i += blockDim.x) A[i] = mkc<T>(0, 0);
+  __syncthreads();
+  const cx<T>* __restrict__ Y = sg.buf_in + ((size_t)g * Lj + m) * Lj;  // Y_g[m][.], m' fastest
+  const cx<T>* __restrict__ tb = sg.pre + (L - 1);
+  for (int mp = threadIdx.x - (Lj - 1); mp < Lj; mp += blockDim.x) {
+    cx<T> y = Y[mp < 0 ? -mp : mp];
+    if (mp < 0) y = cscale<T>(y, sigma);
+    A[fpad(fft_pos(mp & (M - 1), logM))] = cmul<T>(y, __ldg(tb + mp));
+  }
+  __syncthreads();
+  cx<T>* __restrict__ X = sg.buf_out + (size_t)g * 2 * L * Lj + m;
+  fft_inverse_to<T>(A, logM, sg.tw, [&](int v, cx<T> val) {
+    if (v < 2 * L) X[(size_t)v * Lj] = val;
+  });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_beta_syn_fft(const CztSeg<T>* __restrict__ segs, int nseg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
+  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
+  const int item = blockIdx.x - sg.start;
+  const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM;
+  const int g = item / Lj, m = item % Lj;
+  const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
+  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * 2 * L * Lj + m;  // column m of V_g[b][m]
+  const cx<T>* __restrict__ q = sg.post;
+  fft_forward_from<T>(A, logM, sg.tw, [&](int v) -> cx<T> {
+    if (v >= 2 * L) return mkc<T>(0, 0);
+    return cscale<T>(V[(size_t)v * Lj], __ldg(q + v).x);
+  });
+  const cx<T>* __restrict__ tb = sg.pre + (L - 1);
+  cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m;  // column m of Vhat_g[m'][m]
+  for (int mp = threadIdx.x; mp < Lj; mp += blockDim.x) {
+    cx<T> o = cmulc<T>(A[fpad(fft_pos(mp, logM))], __ldg(tb + mp));
+    if (mp > 0) {
+      const cx<T> tm = cmulc<T>(A[fpad(fft_pos(M - mp, logM))], __ldg(tb - mp));
+      o = mkc<T>(o.x + sigma * tm.x, o.y + sigma * tm.y);
+    }
+    Vh[(size_t)mp * Lj] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Direct evaluation of the alpha sums for scales with a small band-limit
 // L_j <= kDirectMax: the chirp-z cost does not shrink with L_j (the output
 // grid has 2L-1 points for every scale) while a direct sum costs ~L_j per
@@ -368,6 +428,8 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
     case CZT_ALPHA_SYN: k_czt_alpha_syn<T><<<grid, block, smem, st>>>(segs, nseg, ptrs); break;
     case CZT_BETA_SYN: k_czt_beta_syn<T><<<grid, block, smem, st>>>(segs, nseg); break;
     case CZT_ALPHA_ANA_DIRECT: k_alpha_ana_direct<T><<<grid, block, 0, st>>>(segs, nseg, ptrs); break;
+    case CZT_BETA_ANA_FFT: k_beta_ana_fft<T><<<grid, block, smem, st>>>(segs, nseg); break;
+    case CZT_BETA_SYN_FFT: k_beta_syn_fft<T><<<grid, block, smem, st>>>(segs, nseg); break;
     case CZT_ALPHA_SYN_DIRECT:
       k_alpha_syn_direct<T><<<grid, block, alpha_syn_direct_smem<T>(1 << (maxlogM - 2)), st>>>(segs, nseg, ptrs);
       break;
@@ -384,6 +446,10 @@ cudaError_t czt_set_smem(int maxlogM) {
   e = cudaFuncSetAttribute(k_czt_alpha_ana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_czt_alpha_syn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_beta_ana_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_alpha_syn_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)alpha_syn_direct_smem<T>(2048));

@@ -291,6 +291,105 @@ __device__ __forceinline__ void fft_convolve(cx<T>* A, int logM, const cx<T>* __
   if (WRITE_SMEM) __syncthreads();
 }
 
+// Position in shared memory of frequency f after the forward stages: the
+// digits of f in the radices (16, ..., 16, R_last), least significant first,
+// weighted by the strides M/16, M/256, ..., 1 of the stages that produce them.
+__device__ __forceinline__ int fft_pos(int f, int logM) {
+  const int a = logM >> 2, b = logM & 3;
+  int p = 0;
+  for (int i = 0; i < a; ++i) p += ((f >> (4 * i)) & 15) << (logM - 4 * (i + 1));
+  if (b) p += (f >> (4 * a)) & ((1 << b) - 1);
+  return p;
+}
+
+// Innermost stage (Q = 1) alone, forward or inverse.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void fft_inner_stage(cx<T>* A, int M) {
+  for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
+    const int base = u * R;
+    cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = A[fpad(base + r)];
+    DftR<T, R, INV>::run(v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) A[fpad(base + k)] = v[k];
+  }
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void fft_inner_dispatch(cx<T>* A, int M, int Rl) {
+  switch (Rl) {
+    case 2: fft_inner_stage<T, 2, INV>(A, M); break;
+    case 4: fft_inner_stage<T, 4, INV>(A, M); break;
+    case 8: fft_inner_stage<T, 8, INV>(A, M); break;
+    default: fft_inner_stage<T, 16, INV>(A, M); break;
+  }
+}
+
+// Forward DFT F_f = sum_v x_v e^{-2 pi i f v/M} of input(v) (natural order),
+// left in A with F_f at fpad(fft_pos(f)).  Ends with __syncthreads().
+template <typename T, typename In>
+__device__ __forceinline__ void fft_forward_from(cx<T>* A, int logM, const cx<T>* __restrict__ tw, In input) {
+  const int M = 1 << logM;
+  int Rl, nmid;
+  fft_schedule(logM, Rl, nmid);
+  {
+    const int Q = M / 16;
+    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+      cx<T> v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = input(j + Q * r);
+      DftR<T, 16, false>::run(v);
+      if (j) {
+#pragma unroll
+        for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) A[fpad(j + Q * k)] = v[k];
+    }
+  }
+  __syncthreads();
+  int S = M / 16;
+  for (int s = 0; s < nmid; ++s) {
+    fft_fwd_stage<T, 16>(A, M, S, tw + fft_twiddle_level_offset(logM, s + 1));
+    __syncthreads();
+    S /= 16;
+  }
+  fft_inner_dispatch<T, false>(A, M, Rl);
+  __syncthreads();
+}
+
+// Unnormalised inverse DFT x_v = sum_f F_f e^{+2 pi i f v/M} of a spectrum
+// stored with F_f at fpad(fft_pos(f)); output(v, x_v) receives every v < M.
+// Expects A complete (call after a __syncthreads()).
+template <typename T, typename Out>
+__device__ __forceinline__ void fft_inverse_to(cx<T>* A, int logM, const cx<T>* __restrict__ tw, Out output) {
+  const int M = 1 << logM;
+  int Rl, nmid;
+  fft_schedule(logM, Rl, nmid);
+  fft_inner_dispatch<T, true>(A, M, Rl);
+  __syncthreads();
+  int S = M >> (4 * (nmid + 1));
+  for (int s = nmid - 1; s >= 0; --s) {
+    S *= 16;
+    fft_inv_stage<T, 16>(A, M, S, tw + fft_twiddle_level_offset(logM, s + 1));
+    __syncthreads();
+  }
+  const int Q = M / 16;
+  for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+    cx<T> v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = A[fpad(j + Q * k)];
+    if (j) {
+#pragma unroll
+      for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+    }
+    DftR<T, 16, true>::run(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) output(j + Q * r, v[r]);
+  }
+}
+
 // Forward transform only (smem in natural order -> smem in the engine's
 // order), values scaled by `scale`; used to build the kernel spectra.
 template <typename T>

@@ -54,7 +54,9 @@ enum CztKind {
   CZT_ALPHA_SYN = 2,
   CZT_BETA_SYN = 3,
   CZT_ALPHA_ANA_DIRECT = 4,  // small-band scales, direct sums
-  CZT_ALPHA_SYN_DIRECT = 5
+  CZT_ALPHA_SYN_DIRECT = 5,
+  CZT_BETA_ANA_FFT = 6,      // beta sums as one FFT of length 4L (L a power of two)
+  CZT_BETA_SYN_FFT = 7
 };
 constexpr int kDirectMaxLj = 32;
 constexpr int kDirectRowsAna = 16;

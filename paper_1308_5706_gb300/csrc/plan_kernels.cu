@@ -224,7 +224,7 @@ __global__ void k_rtable(T* RS, const double* d64, const double* kap, const doub
 // Chirp tables (angles reduced exactly in integers before sincospi).
 template <typename T>
 __global__ void k_chirp_tables(cx<T>* tw, cx<T>* chirp_a, cx<T>* pre_b, cx<T>* post_b, cx<T>* preS_b,
-                               cx<T>* postS_b, cx<T>* root_a, const double* q, int L, int logM) {
+                               cx<T>* postS_b, cx<T>* root_a, cx<T>* bfft, const double* q, int L, int logM) {
   const int M = 1 << logM;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = 2 * L - 1;
@@ -255,12 +255,15 @@ __global__ void k_chirp_tables(cx<T>* tw, cx<T>* chirp_a, cx<T>* pre_b, cx<T>* p
     sincospi((double)p / (4.0 * L), &s, &c);
     pre_b[i] = mkc<T>((T)c, (T)s);
     postS_b[i] = mkc<T>((T)c, (T)(-s));
+    sincospi((double)mp / (4.0 * L), &s, &c);  // e^{i pi m'/(4L)}: shift of the beta grid
+    bfft[i] = mkc<T>((T)c, (T)s);
   }
   if (i < 2 * L) {
     const long long p = ((long long)i * i) % (8LL * L);
     sincospi((double)p / (4.0 * L), &s, &c);
     post_b[i] = mkc<T>((T)c, (T)s);
     preS_b[i] = mkc<T>((T)(q[i] * c), (T)(-q[i] * s));
+    bfft[2 * L - 1 + i] = mkc<T>((T)q[i], (T)0);
   }
 }
 
@@ -343,12 +346,13 @@ cudaError_t launch_rtable(T* RS, const double* d64, const double* kap, const dou
 }
 
 cudaError_t launch_chirp_build64(double2* tw, double2* chirp_a, double2* pre_b, double2* post_b, double2* preS_b,
-                                 double2* postS_b, double2* root_a, double2* H, const double* q, int L, int logM,
+                                 double2* postS_b, double2* root_a, double2* bfft, double2* H, const double* q, int L,
+                                 int logM,
                                  cudaStream_t st) {
   const int M = 1 << logM;
   const int cnt = (M > 2 * L) ? M : 2 * L;
-  k_chirp_tables<double><<<nblk(cnt, 256), 256, 0, st>>>(tw, chirp_a, pre_b, post_b, preS_b, postS_b, root_a, q, L,
-                                                         logM);
+  k_chirp_tables<double><<<nblk(cnt, 256), 256, 0, st>>>(tw, chirp_a, pre_b, post_b, preS_b, postS_b, root_a, bfft,
+                                                         q, L, logM);
   k_chirp_kernels<<<dim3(nblk(M, 256), 4), 256, 0, st>>>(H, L, M);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;

@@ -13,7 +13,8 @@ template <typename T>
 cudaError_t launch_rtable(T* RS, const double* d64, const double* kap, const double* sabs, const int* slotj, int L,
                           int Lp, int N, int nslot, int kapL, cudaStream_t st);
 cudaError_t launch_chirp_build64(double2* tw, double2* chirp_a, double2* pre_b, double2* post_b, double2* preS_b,
-                                 double2* postS_b, double2* root_a, double2* H, const double* q, int L, int logM,
+                                 double2* postS_b, double2* root_a, double2* bfft, double2* H, const double* q, int L,
+                                 int logM,
                                  cudaStream_t st);
 template <typename T>
 cudaError_t launch_to_prec(cx<T>* dst, const double2* src, int64_t n, cudaStream_t st);
