@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -34,6 +35,7 @@ METRIC = "wavelet analysis+synthesis transforms/s at L=1024,N=5 (mixed vs FP64, 
 UNIT = "transforms/s"
 WORKLOAD = "L=1024, N=5, lambda=2, J0=0 (11 scales), real Gaussian f_lm C_l=1/(l(l+1)), seed 2"
 FP32_LANES_PER_SM, N_SM = 128, 152
+DIRECT_MAX_LJ = 32  # scales with L_j <= 32 take the direct alpha sums
 
 
 def peaks():
@@ -48,12 +50,22 @@ def peaks():
 # Oracle timing (CPU): bounded samples, spawn pool over host cores
 # ---------------------------------------------------------------------------
 
-def _oracle_rows(args):
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+_ORACLE = {}
+
+
+def _init_worker():
+    """Spawned oracle worker: one thread, the workload's f_lm and kernels."""
+    os.environ["OMP_NUM_THREADS"] = "1"
     import oracle as O
-    b = args
-    f = flm_gaussian(L, SEED, "cl")
-    kern = O.kernels(L, N, LAM, J0)
+    _ORACLE["O"] = O
+    _ORACLE["f"] = flm_gaussian(L, SEED, "cl")
+    _ORACLE["kern"] = O.kernels(L, N, LAM, J0)
+
+
+def _oracle_task(b):
+    """One sample unit: the analysis of beta-row b and the synthesis
+    contribution of beta-row b (a round trip is 2L of each)."""
+    O, f, kern = _ORACLE["O"], _ORACLE["f"], _ORACLE["kern"]
     t0 = time.perf_counter()
     O.analysis_rows(f, L, N, LAM, J0, [b], kern)
     t1 = time.perf_counter()
@@ -68,62 +80,45 @@ def _oracle_rows(args):
     return t1 - t0, t2 - t1
 
 
-def _warm(_):
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    import oracle  # noqa: F401
-    return 0
-
-
 def oracle_pool(workers: int):
+    """Spawned pool (safe after CUDA initialisation), warmed outside timing."""
     import multiprocessing as mp
-    pool = mp.get_context("spawn").Pool(workers)
-    pool.map(_warm, range(workers))  # interpreter start-up and imports outside the timing
+    pool = mp.get_context("spawn").Pool(workers, initializer=_init_worker)
+    pool.map(_oracle_task, [1] * workers, chunksize=1)
     return pool
 
 
-def oracle_sample(workers: int, pool=None):
-    """One bounded sample: each worker runs one analysis beta-row and one
-    synthesis beta-row of the L=1024 workload.  A full transform is 2L of
-    each, so transforms/s = (rows done / wall time) / (2 * 2L)."""
-    own = pool is None
-    if own:
-        pool = oracle_pool(workers)
-    rows = [int(x) for x in np.linspace(1, 2 * L - 2, workers)]
-    try:
-        t0 = time.perf_counter()
-        res = pool.map(_oracle_rows, rows)
-        wall = time.perf_counter() - t0
-    finally:
-        if own:
-            pool.close()
-            pool.join()
+def oracle_run(pool, ntasks: int):
+    """Run ntasks sample units (rows spread over the 2L beta rows) on the
+    pool; returns (transforms/s, wall s, mean analysis-row s, mean synthesis-row s)."""
+    rows = [int(x) for x in np.linspace(1, 2 * L - 2, max(1, ntasks))][:ntasks]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_task, rows, chunksize=1)
+    wall = time.perf_counter() - t0
     ana = statistics.mean(r[0] for r in res)
     syn = statistics.mean(r[1] for r in res)
-    value = (len(rows) / wall) / (2 * 2 * L)
-    return value, wall, ana, syn
+    return (ntasks / (2 * L)) / wall, wall, ana, syn
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step is one sample unit (one
+    analysis beta-row and one synthesis beta-row of the L=1024 workload);
+    the K timed steps run in parallel on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     workers = max(1, os.cpu_count() or 1)
     pool = oracle_pool(workers)
-    for _ in range(args.warmup):
-        oracle_sample(workers, pool)
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        v, wall, ana, syn = oracle_sample(workers, pool)
-        vals.append(v)
-    total = time.perf_counter() - t0
+    if args.warmup > 0:
+        oracle_run(pool, args.warmup)
+    value, wall, ana, syn = oracle_run(pool, args.steps)
     pool.close()
     pool.join()
-    value = statistics.mean(vals)
-    sample = (f"per step: {workers} spawn workers, each one analysis beta-row and one synthesis beta-row "
-              f"of the L=1024 workload (full transform = 2L rows of each); extrapolated")
+    sample = (f"{args.steps} steps, each one analysis beta-row and one synthesis beta-row of the L=1024 "
+              f"workload (a round trip is 2L = {2 * L} of each), run on {workers} spawn workers in "
+              f"{wall:.1f} s (row: analysis {ana:.2f} s, synthesis {syn:.2f} s); extrapolated")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, args.steps),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": WORKLOAD},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
@@ -218,17 +213,102 @@ def contraction_flops(plan) -> float:
     return tot
 
 
-def alpha_bytes(plan, elem: int) -> float:
-    """Algorithmic bytes of one alpha launch: W written (or read) once plus
-    the [N][2L][Lj] complex input rows read once (scaling part included)."""
+def alpha_bytes(plan, elem: int, direct: bool) -> float:
+    """Algorithmic bytes of one alpha launch over the scales it handles
+    (direct: L_j <= 32, else chirp-z): W written (or read) once plus the
+    [N][2L][L_j] complex rows read (or written) once."""
     n = 2 * L - 1
-    w = (plan.nscale * N * 2 * L * n + 2 * L * n) * elem
-    xin = 0
-    for j in range(plan.nscale):
+    tot = 0.0
+    for j in range(plan.nscale + 1):
+        phi = j == plan.nscale
         lo, hi = plan.support(j)
-        xin += N * 2 * L * (hi + 1) * 2 * elem
-    xin += 2 * L * (plan.support(plan.nscale)[1] + 1) * 2 * elem
-    return float(w + xin)
+        Lj = hi + 1
+        if Lj <= 0 or (Lj <= DIRECT_MAX_LJ) != direct:
+            continue
+        rows = (1 if phi else N) * 2 * L
+        tot += rows * n * elem + rows * Lj * 2 * elem
+    return tot
+
+
+def fft_len(L_: int) -> int:
+    """The chirp-z / FFT length of a plan: the power of two >= 4L - 2 (at least 32)."""
+    M = 32
+    while M < 4 * L_ - 2:
+        M *= 2
+    return M
+
+
+def fft_flops(M: int) -> float:
+    """Conventional flop count of one complex FFT of power-of-two length M."""
+    return 5.0 * M * math.log2(M)
+
+
+def alpha_czt_flops(plan) -> float:
+    """Algorithmic flops of one chirp-z alpha launch: per complex transform
+    (two real rows) two length-M FFTs and the spectrum product (6M)."""
+    M, pairs = fft_len(plan.L), 0
+    for j in range(plan.nscale + 1):
+        Lj = plan.support(j)[1] + 1
+        if Lj > DIRECT_MAX_LJ:
+            pairs += (1 if j == plan.nscale else N) * L
+    return pairs * (2 * fft_flops(M) + 6.0 * M)
+
+
+def beta_flops(plan) -> float:
+    """Algorithmic flops of one beta launch: one length-4L FFT per (g, m)
+    column when 4L is a power of two (else a chirp-z convolution)."""
+    M = fft_len(plan.L)
+    cols = sum((1 if j == plan.nscale else N) * (plan.support(j)[1] + 1) for j in range(plan.nscale + 1))
+    per = fft_flops(M) if M == 4 * L else 2 * fft_flops(M) + 6.0 * M
+    return cols * per
+
+
+# DRAM bytes per launch (read + write) of kernels captured with ncu on this
+# workload; None once the kernel has changed since the capture.
+NCU_TRAFFIC = {
+    "syn_alpha_czt": (0.503252e9 + 0.244352e9, "profiles/k_czt_alpha_L1024_N5.md"),
+    "ana_alpha_czt": (0.246607e9 + 0.465727e9, "profiles/k_czt_alpha_L1024_N5.md"),
+    "ana_contract": (1.089100e9 + 0.068842e9, "profiles/k_contract_L1024_N5.md"),
+    "syn_contract": (1.386839e9 + 0.092072e9, "profiles/k_contract_L1024_N5.md"),
+}
+
+
+def roofline(pm, mean_stage):
+    """Roofline of the dominant kernel (largest mean duration) and of every
+    other timed kernel, from the live CUDA-event durations."""
+    hbm, sm_max, peak_src = peaks()
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at max SM clock
+    alu_src = f"derived FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz"
+    work = {
+        "ana_contract": ("alu", contraction_flops(pm)), "syn_contract": ("alu", contraction_flops(pm)),
+        "ana_alpha_czt": ("alu", alpha_czt_flops(pm)), "syn_alpha_czt": ("alu", alpha_czt_flops(pm)),
+        "ana_beta": ("alu", beta_flops(pm)), "syn_beta": ("alu", beta_flops(pm)),
+        "ana_alpha_direct": ("hbm", alpha_bytes(pm, 4, True)), "syn_alpha_direct": ("hbm", alpha_bytes(pm, 4, True)),
+    }
+    per = {}
+    for k, (bound, w) in work.items():
+        ms = mean_stage.get(k, 0.0)
+        if ms <= 0:
+            continue
+        if bound == "alu":
+            a = w / (ms * 1e-3) / 1e12
+            per[k] = {"bound": "alu", "ms": round(ms, 4), "achieved": a, "peak": fp32_peak, "unit": "TFLOP/s",
+                      "frac": a / fp32_peak}
+        else:
+            a = w / (ms * 1e-3) / 1e9
+            per[k] = {"bound": "hbm", "ms": round(ms, 4), "achieved": a, "peak": hbm, "unit": "GB/s",
+                      "frac": a / hbm}
+    dom = max(per, key=lambda k: per[k]["ms"])
+    r = dict(per[dom])
+    r["kernel"] = dom
+    tr = NCU_TRAFFIC.get(dom)
+    r["traffic"] = tr[0] if tr else None
+    r["traffic_source"] = tr[1] if tr else None
+    r["peak_source"] = alu_src if r["bound"] == "alu" else f"{peak_src} hbm_gbs (of {peak_src})"
+    r["work_per_launch"] = work[dom][1]
+    r["kernels"] = {k: {"ms": v["ms"], "frac": round(v["frac"], 4), "bound": v["bound"]} for k, v in per.items()}
+    r["stage_ms"] = {k: round(v, 4) for k, v in mean_stage.items()}
+    return r
 
 
 def time_path(torch, plan, f_dev, steps, warmup, stream, profile=False):
@@ -339,8 +419,8 @@ def run_serve_workload(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -364,11 +444,15 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         workers = max(1, os.cpu_count() or 1)
-        v, wall, ana, syn = oracle_sample(workers)
+        pool = oracle_pool(workers)
+        v, wall, ana, syn = oracle_run(pool, workers)
+        pool.close()
+        pool.join()
         cpu = {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
-               "sample": (f"{workers} spawn workers x (1 analysis beta-row + 1 synthesis beta-row) of the "
-                          f"L=1024 workload in {wall:.1f} s (row: analysis {ana:.2f} s, synthesis {syn:.2f} s); "
-                          f"a transform is 2L=2048 rows of each, extrapolated")}
+               "sample": (f"{workers} sample units (1 analysis beta-row + 1 synthesis beta-row each) of the "
+                          f"L=1024 workload on {workers} spawn workers in {wall:.1f} s (row: analysis "
+                          f"{ana:.2f} s, synthesis {syn:.2f} s); a round trip is 2L = {2 * L} rows of each, "
+                          f"extrapolated")}
 
     import torch
     from paper_1308_5706_gb300 import binding as B
@@ -454,19 +538,7 @@ def main():
     # roofline of the dominant kernel, from the stage events of the timed region
     stage_ms, nana, nsyn = prof
     mean_stage = {k: (v / (nana if k.startswith("ana") else nsyn)) for k, v in stage_ms.items()}
-    hbm, sm_max, peak_src = peaks()
-    dom = max(mean_stage, key=mean_stage.get)
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at max SM clock
-    if "contract" in dom:
-        achieved = contraction_flops(pm) / (mean_stage[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
-                "peak_source": f"FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz"}
-    else:
-        achieved = alpha_bytes(pm, 4) / (mean_stage[dom] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
-    roof["stage_ms"] = {k: round(v, 4) for k, v in mean_stage.items()}
+    roof = roofline(pm, mean_stage)
 
     per_sorted = sorted(per)
     out = {

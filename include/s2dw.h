@@ -70,12 +70,16 @@ typedef struct s2dw_plan_s* s2dw_plan_t;
  * optionally | S2DW_REAL_SIGNAL.  Otherwise S2DW_EINVAL.
  * Work: evaluates the kernels, the DH weights (Eq. (18)) and the Delta table
  * on the device (FP64 recursion, grown to cover l < L on first need) and
- * allocates the workspace.  Synchronises the device before returning.
+ * allocates the workspace (stream-ordered, on a private stream; other
+ * streams keep running).  Returns once the plan is ready for any stream.
  * *out receives the plan; on failure *out is NULL and nothing leaks.
  */
 int s2dw_plan(s2dw_plan_t* out, int L, int N, double lambda, int J0, unsigned flags);
 
-/* Release a plan (NULL is accepted).  Synchronises the device first. */
+/* Release a plan (NULL is accepted).  Waits only for this plan's last
+ * recorded call (not the whole device), then frees its workspace.  Calls
+ * captured into a CUDA graph are not tracked: destroy a plan only once no
+ * graph that captured it can run again (as for the buffers passed to it). */
 int s2dw_plan_destroy(s2dw_plan_t plan);
 
 /*
@@ -162,10 +166,12 @@ int s2dw_stage(s2dw_plan_t plan, int stage, int j, void* host_out, int64_t* nbyt
  *   s2dw_analysis / s2dw_synthesis calls on this plan record CUDA events
  *   around each of their launches, on the call's stream; 0 stops recording.
  *   s2dw_profile_read(plan, ms, ncalls) waits for the recorded calls and
- *   fills ms[9] with per-stage durations (ms) summed over them:
+ *   fills ms[11] with per-stage durations (ms) summed over them:
  *   [0] analysis contraction + gamma step, [1] scaling contraction,
- *   [2] beta step, [3] alpha step; [4] synthesis alpha step, [5] beta step,
- *   [6] contraction, [7] scaling contraction, [8] final reduction;
+ *   [2] beta step, [3] alpha step (chirp-z part), [4] alpha step (direct
+ *   sums of the small-band scales); [5] synthesis alpha step (direct sums),
+ *   [6] alpha step (chirp-z part), [7] beta step, [8] contraction,
+ *   [9] scaling contraction, [10] final reduction;
  *   ncalls[2] (may be NULL) gets the numbers of analysis and synthesis calls.
  */
 int s2dw_profile(s2dw_plan_t plan, int enable);

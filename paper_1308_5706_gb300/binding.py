@@ -47,8 +47,8 @@ _SIGNATURES = {
     "s2dw_delta_table_noalloc": (_c_i, [_c_i, _c_p, _c_p, _c_i64p, _c_p]),
 }
 
-STAGES = ["ana_contract", "ana_contract_phi", "ana_beta", "ana_alpha", "syn_alpha", "syn_beta",
-          "syn_contract", "syn_contract_phi", "syn_reduce"]
+STAGES = ["ana_contract", "ana_contract_phi", "ana_beta", "ana_alpha_czt", "ana_alpha_direct",
+          "syn_alpha_direct", "syn_alpha_czt", "syn_beta", "syn_contract", "syn_contract_phi", "syn_reduce"]
 
 
 class S2dwError(RuntimeError):
@@ -188,7 +188,7 @@ def s2dw_profile(plan: int, enable: bool) -> None:
 
 def s2dw_profile_read(plan: int):
     """(per-stage summed ms, number of analysis calls, number of synthesis calls)."""
-    ms = np.zeros(9, dtype=np.float64)
+    ms = np.zeros(len(STAGES), dtype=np.float64)
     nc = (ctypes.c_int * 2)()
     _check(lib().s2dw_profile_read(plan, ms.ctypes.data_as(_c_dp), nc), "s2dw_profile_read")
     return dict(zip(STAGES, ms.tolist())), nc[0], nc[1]

@@ -224,7 +224,8 @@ struct s2dw_plan_s {
   // stage timing (s2dw_profile): one set of events per call, up to kProfCalls
   static constexpr int kProfCalls = 256;
   bool prof = false;
-  std::vector<cudaEvent_t> ev_ana, ev_syn;  // kProfCalls x 5, kProfCalls x 6
+  static constexpr int kEvAna = 6, kEvSyn = 7;  // events per call (stages + 1)
+  std::vector<cudaEvent_t> ev_ana, ev_syn;      // kProfCalls x kEvAna, kProfCalls x kEvSyn
   int nana = 0, nsyn = 0;
   ~s2dw_plan_s() {
     for (auto e : ev_ana)
@@ -383,14 +384,14 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
         s.post = reinterpret_cast<const cx<T>*>(p->post_b);
         break;
       case CZT_ALPHA_ANA:
-        s.items = Nj * L;
+        s.items = (Nj * L + alpha_czt_nt(sizeof(T) == 8) - 1) / alpha_czt_nt(sizeof(T) == 8);
         s.buf_in = reinterpret_cast<cx<T>*>(p->X[j]);
         s.H = Hs + 1 * (size_t)p->M;
         s.pre = reinterpret_cast<const cx<T>*>(p->chirp_a);
         s.post = reinterpret_cast<const cx<T>*>(p->chirp_a);
         break;
       case CZT_ALPHA_SYN:
-        s.items = Nj * L;
+        s.items = (Nj * L + alpha_czt_nt(sizeof(T) == 8) - 1) / alpha_czt_nt(sizeof(T) == 8);
         s.buf_out = reinterpret_cast<cx<T>*>(p->X[j]);
         s.H = Hs + 2 * (size_t)p->M;
         s.pre = reinterpret_cast<const cx<T>*>(p->chirp_a);
@@ -509,7 +510,20 @@ inline void rec(cudaEvent_t* ev, int i, cudaStream_t st) {
   if (ev) cudaEventRecord(ev[i], st);
 }
 
-// Analysis stages: [contraction + gamma | scaling contraction | beta | alpha].
+// True while `st` is being captured into a CUDA graph.  The library's own
+// events (last use, stage timing) are not recorded then: a captured record
+// would tie the plan's events to the caller's graph (and cannot be waited
+// on), so keeping a plan alive while a graph that captured it may still run
+// is the caller's responsibility, as for the buffers it passed.
+inline bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+inline void mark_use(s2dw_plan_t p, cudaStream_t st) {
+  if (!capturing(st)) cudaEventRecord(p->last_use, st);
+}
+
+// Analysis stages: [contraction + gamma | scaling contraction | beta | alpha chirp-z | alpha direct].
 template <typename T>
 void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   const ContractDesc<T>* dw = reinterpret_cast<const ContractDesc<T>*>(ls.desc_w);
@@ -528,36 +542,38 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
   rec(ev, 3, st);
   launch_czt<T>(CZT_ALPHA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1], ls.maxlogM,
                 ptrs, st);
+  rec(ev, 4, st);
   launch_czt<T>(CZT_ALPHA_ANA_DIRECT, reinterpret_cast<const CztSeg<T>*>(ls.segs[4]), ls.nseg[4], ls.items[4],
                 ls.maxlogM, ptrs, st);
-  rec(ev, 4, st);
+  rec(ev, 5, st);
 }
 
-// Synthesis stages: [alpha | beta | contraction | scaling contraction | reduction].
+// Synthesis stages: [alpha direct | alpha chirp-z | beta | contraction | scaling contraction | reduction].
 template <typename T>
 void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, int njobs, cudaStream_t st,
                    cudaEvent_t* ev = nullptr) {
   const ContractDesc<T>* dw = reinterpret_cast<const ContractDesc<T>*>(ls.desc_w);
   const ContractDesc<T>* dp = reinterpret_cast<const ContractDesc<T>*>(ls.desc_phi);
   rec(ev, 0, st);
-  launch_czt<T>(CZT_ALPHA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[2]), ls.nseg[2], ls.items[2], ls.maxlogM,
-                ptrs, st);
   launch_czt<T>(CZT_ALPHA_SYN_DIRECT, reinterpret_cast<const CztSeg<T>*>(ls.segs[5]), ls.nseg[5], ls.items[5],
                 ls.maxlogM, ptrs, st);
   rec(ev, 1, st);
+  launch_czt<T>(CZT_ALPHA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[2]), ls.nseg[2], ls.items[2], ls.maxlogM,
+                ptrs, st);
+  rec(ev, 2, st);
   launch_czt<T>(CZT_BETA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[3]), ls.nseg[3], ls.items[3], ls.maxlogM,
                 ptrs, st);
   launch_czt<T>(CZT_BETA_SYN_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[7]), ls.nseg[7], ls.items[7],
                 ls.maxlogM, ptrs, st);
-  rec(ev, 2, st);
+  rec(ev, 3, st);
   for (auto& t : ls.tiles_w)
     launch_contract<T>(t.first, 2, true, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
                        ptrs, st);
-  rec(ev, 3, st);
-  launch_contract<T>(1, 1, true, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
   rec(ev, 4, st);
-  launch_syn_reduce<T>(rj, njobs, ls.Lmax, st);
+  launch_contract<T>(1, 1, true, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
   rec(ev, 5, st);
+  launch_syn_reduce<T>(rj, njobs, ls.Lmax, st);
+  rec(ev, 6, st);
 }
 
 template <typename T>
@@ -855,9 +871,8 @@ int s2dw_plan(s2dw_plan_t* out, int L, int N, double lambda, int J0, unsigned fl
 
 int s2dw_plan_destroy(s2dw_plan_t plan) {
   if (!plan) return S2DW_OK;
-  if (plan->last_use) cudaEventSynchronize(plan->last_use);
   drop_batches_with(plan);
-  delete plan;
+  delete plan;  // waits for the plan's last recorded call, frees stream-ordered
   return err_of(cudaGetLastError());
 }
 
@@ -903,10 +918,11 @@ int s2dw_analysis(s2dw_plan_t p, const void* flm, void* W, void* Wphi, void* str
   ptrs.W[0] = W;
   ptrs.Wphi[0] = Wphi;
   cudaEvent_t* ev = nullptr;
-  if (p->prof && p->nana < s2dw_plan_s::kProfCalls) ev = p->ev_ana.data() + 5 * (p->nana++);
+  if (p->prof && p->nana < s2dw_plan_s::kProfCalls && !capturing(st))
+    ev = p->ev_ana.data() + s2dw_plan_s::kEvAna * (p->nana++);
   if (p->fp64) run_analysis<double>(p->own, ptrs, st, ev);
   else run_analysis<float>(p->own, ptrs, st, ev);
-  cudaEventRecord(p->last_use, st);
+  mark_use(p, st);
   return err_of(cudaGetLastError());
 }
 
@@ -927,18 +943,19 @@ int s2dw_synthesis(s2dw_plan_t p, const void* W, const void* Wphi, void* flm, vo
   rj.lend[0] = p->lend_w;
   rj.Lphi[0] = p->Lphi;
   cudaEvent_t* ev = nullptr;
-  if (p->prof && p->nsyn < s2dw_plan_s::kProfCalls) ev = p->ev_syn.data() + 6 * (p->nsyn++);
+  if (p->prof && p->nsyn < s2dw_plan_s::kProfCalls && !capturing(st))
+    ev = p->ev_syn.data() + s2dw_plan_s::kEvSyn * (p->nsyn++);
   if (p->fp64) run_synthesis<double>(p->own, ptrs, rj, 1, st, ev);
   else run_synthesis<float>(p->own, ptrs, rj, 1, st, ev);
-  cudaEventRecord(p->last_use, st);
+  mark_use(p, st);
   return err_of(cudaGetLastError());
 }
 
 int s2dw_profile(s2dw_plan_t p, int enable) {
   if (!p) return S2DW_EINVAL;
   if (enable && p->ev_ana.empty()) {
-    p->ev_ana.assign(5 * s2dw_plan_s::kProfCalls, nullptr);
-    p->ev_syn.assign(6 * s2dw_plan_s::kProfCalls, nullptr);
+    p->ev_ana.assign(s2dw_plan_s::kEvAna * s2dw_plan_s::kProfCalls, nullptr);
+    p->ev_syn.assign(s2dw_plan_s::kEvSyn * s2dw_plan_s::kProfCalls, nullptr);
     for (auto& e : p->ev_ana)
       if (cudaEventCreate(&e) != cudaSuccess) return S2DW_ECUDA;
     for (auto& e : p->ev_syn)
@@ -952,15 +969,16 @@ int s2dw_profile(s2dw_plan_t p, int enable) {
 
 int s2dw_profile_read(s2dw_plan_t p, double* ms, int* ncalls) {
   if (!p || !ms) return S2DW_EINVAL;
-  for (int i = 0; i < 9; ++i) ms[i] = 0.0;
+  constexpr int A = s2dw_plan_s::kEvAna, S = s2dw_plan_s::kEvSyn;
+  for (int i = 0; i < A + S - 2; ++i) ms[i] = 0.0;
   if (ncalls) ncalls[0] = ncalls[1] = 0;
   if (p->ev_ana.empty()) return S2DW_OK;
   cudaError_t e = cudaSuccess;
   int na = 0, ns = 0;
   for (int c = 0; c < p->nana; ++c) {
-    cudaEvent_t* ev = p->ev_ana.data() + 5 * c;
-    if ((e = cudaEventSynchronize(ev[4])) != cudaSuccess) return err_of(e);
-    for (int i = 0; i < 4; ++i) {
+    cudaEvent_t* ev = p->ev_ana.data() + A * c;
+    if ((e = cudaEventSynchronize(ev[A - 1])) != cudaSuccess) return err_of(e);
+    for (int i = 0; i < A - 1; ++i) {
       float t = 0.f;
       if ((e = cudaEventElapsedTime(&t, ev[i], ev[i + 1])) != cudaSuccess) return err_of(e);
       ms[i] += t;
@@ -968,12 +986,12 @@ int s2dw_profile_read(s2dw_plan_t p, double* ms, int* ncalls) {
     ++na;
   }
   for (int c = 0; c < p->nsyn; ++c) {
-    cudaEvent_t* ev = p->ev_syn.data() + 6 * c;
-    if ((e = cudaEventSynchronize(ev[5])) != cudaSuccess) return err_of(e);
-    for (int i = 0; i < 5; ++i) {
+    cudaEvent_t* ev = p->ev_syn.data() + S * c;
+    if ((e = cudaEventSynchronize(ev[S - 1])) != cudaSuccess) return err_of(e);
+    for (int i = 0; i < S - 1; ++i) {
       float t = 0.f;
       if ((e = cudaEventElapsedTime(&t, ev[i], ev[i + 1])) != cudaSuccess) return err_of(e);
-      ms[4 + i] += t;
+      ms[A - 1 + i] += t;
     }
     ++ns;
   }
@@ -1030,7 +1048,7 @@ int s2dw_analysis_batch(const s2dw_plan_t* plans, const void* const* flm, void* 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (fp64) run_analysis<double>(*ls, ptrs, st);
   else run_analysis<float>(*ls, ptrs, st);
-  for (int i = 0; i < njobs; ++i) cudaEventRecord(plans[i]->last_use, st);
+  for (int i = 0; i < njobs; ++i) mark_use(plans[i], st);
   return err_of(cudaGetLastError());
 }
 
@@ -1061,7 +1079,7 @@ int s2dw_synthesis_batch(const s2dw_plan_t* plans, const void* const* W, const v
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (fp64) run_synthesis<double>(*ls, ptrs, rj, njobs, st);
   else run_synthesis<float>(*ls, ptrs, rj, njobs, st);
-  for (int i = 0; i < njobs; ++i) cudaEventRecord(plans[i]->last_use, st);
+  for (int i = 0; i < njobs; ++i) mark_use(plans[i], st);
   return err_of(cudaGetLastError());
 }
 

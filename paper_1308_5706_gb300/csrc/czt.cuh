@@ -27,15 +27,17 @@
 //   folded over +-m' so that every integrand is a cosine series).
 #pragma once
 
+#include <algorithm>
+
 #include "fft16.cuh"
 #include "internal.h"
 
 namespace s2dw {
 
 template <typename T>
-__device__ __forceinline__ int czt_find_seg(const CztSeg<T>* segs, int nseg) {
+__device__ __forceinline__ int czt_find_seg(const CztSeg<T>* segs, int nseg, int b = -1) {
   int lo = 0, hi = nseg - 1;
-  const int b = blockIdx.x;
+  if (b < 0) b = blockIdx.x;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (segs[mid].start <= b) lo = mid;
@@ -71,74 +73,123 @@ __global__ void __launch_bounds__(256) k_czt_beta_ana(const CztSeg<T>* __restric
   fft_convolve<T, false>(A, sg.logM, sg.H, sg.tw, in, out);
 }
 
+// alpha sums: item `it` is NT row pairs (rows 2(it' NT + t), +1, t < NT, it'
+// the item's index in its segment).  The synthesis kernel is persistent (a
+// grid of a few CTAs per SM walks the items): while a CTA computes one item,
+// cp.async stages the W rows of its next item in shared memory, so the HBM
+// latency of the inputs is hidden behind the FFT work.
+// Shared memory: NT FFT buffers of ST = fft_smem_elems(2^maxlogM) complex,
+// then (synthesis) the staging rows (2 NT rows of pitch 2^(maxlogM-1) of T).
 template <typename T>
-__global__ void __launch_bounds__(256) k_czt_alpha_ana(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+__host__ __device__ constexpr size_t alpha_czt_smem(int maxlogM, bool staging) {
+  return (size_t)alpha_czt_nt(sizeof(T) == 8) *
+         ((size_t)fft_smem_elems(1 << maxlogM) * sizeof(cx<T>) +
+          (staging ? 2 * ((size_t)1 << (maxlogM - 1)) * sizeof(T) : 0));
+}
+
+// The analysis form is not persistent: its inputs (the X rows the beta step
+// has just written) are mostly L2-resident and few, so one CTA per item with
+// direct loads measured faster than staging them ahead.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __restrict__ segs, int nseg, int maxlogM,
+                                                          CallPtrs ptrs) {
+  constexpr int NT = alpha_czt_nt(sizeof(T) == 8);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
+  const int ST = fft_smem_elems(1 << maxlogM);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
-  const int item = blockIdx.x - sg.start;
   const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM, n = 2 * L - 1;
-  const int r1 = 2 * item;  // rows r1, r1 + 1 of the [N * 2L] row space
-  const cx<T>* __restrict__ X1 = sg.buf_in + (size_t)r1 * Lj;
-  const cx<T>* __restrict__ X2 = X1 + Lj;
-  auto in = [&](int v) -> cx<T> {
-    int mm;
-    bool neg;
+  const int p0 = (blockIdx.x - sg.start) * NT;
+  const int nt = min(NT, sg.N * L - p0);  // transforms present in this CTA
+  const cx<T>* __restrict__ X = sg.buf_in + (size_t)(2 * p0) * Lj;
+  // input position v holds m = v (v < Lj) or m = v - M (v > M - Lj)
+  auto pre = [&](int v) -> cx<T> {
+    if (v < Lj) return __ldg(sg.pre + v);
+    if (v > M - Lj) return __ldg(sg.pre + (M - v));
+    return mkc<T>(0, 0);
+  };
+  auto in = [&](int v, int t, cx<T> c) -> cx<T> {
+    if (t >= nt) return mkc<T>(0, 0);
     if (v < Lj) {
-      mm = v;
-      neg = false;
-    } else if (v > M - Lj) {
-      mm = M - v;
-      neg = true;
-    } else {
-      return mkc<T>(0, 0);
+      const cx<T> x1 = X[(size_t)(2 * t) * Lj + v], x2 = X[(size_t)(2 * t + 1) * Lj + v];
+      return cmul<T>(mkc<T>(x1.x - x2.y, x1.y + x2.x), c);  // X1 + i X2
     }
-    const cx<T> x1 = X1[mm], x2 = X2[mm];
-    const cx<T> z = neg ? mkc<T>(x1.x + x2.y, x2.x - x1.y)    // conj(X1) + i conj(X2)
-                        : mkc<T>(x1.x - x2.y, x1.y + x2.x);   // X1 + i X2
-    return cmul<T>(z, __ldg(sg.pre + mm));
+    if (v > M - Lj) {
+      const int mm = M - v;
+      const cx<T> x1 = X[(size_t)(2 * t) * Lj + mm], x2 = X[(size_t)(2 * t + 1) * Lj + mm];
+      return cmul<T>(mkc<T>(x1.x + x2.y, x2.x - x1.y), c);  // conj(X1) + i conj(X2)
+    }
+    return mkc<T>(0, 0);
   };
-  T* __restrict__ Wb = reinterpret_cast<T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff;
-  T* __restrict__ W1 = Wb + (size_t)r1 * n;
-  T* __restrict__ W2 = W1 + n;
-  auto out = [&](int v, cx<T> val) {
-    if (v < n) {
-      const cx<T> w = cmul<T>(val, __ldg(sg.post + v));
-      W1[v] = w.x;
-      W2[v] = w.y;
+  T* __restrict__ Wb = reinterpret_cast<T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff +
+                       (size_t)(2 * p0) * n;
+  auto post = [&](int v) -> cx<T> { return v < n ? __ldg(sg.post + v) : mkc<T>(0, 0); };
+  auto out = [&](int v, int t, cx<T> y, cx<T> c) {
+    if (v < n && t < nt) {
+      const cx<T> w = cmul<T>(y, c);
+      Wb[(size_t)(2 * t) * n + v] = w.x;
+      Wb[(size_t)(2 * t + 1) * n + v] = w.y;
     }
   };
-  fft_convolve<T, false>(A, sg.logM, sg.H, sg.tw, in, out);
+  fft_convolve_n<T, NT, false>(A, ST, sg.logM, sg.H, sg.tw, pre, in, post, out, []() {});
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_czt_alpha_syn(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+__global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __restrict__ segs, int nseg, int total,
+                                                          int maxlogM, CallPtrs ptrs) {
+  constexpr int NT = alpha_czt_nt(sizeof(T) == 8);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
-  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
-  const int item = blockIdx.x - sg.start;
-  const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM, n = 2 * L - 1;
-  const int r1 = 2 * item;
-  const T* __restrict__ Wb = reinterpret_cast<const T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff;
-  const T* __restrict__ W1 = Wb + (size_t)r1 * n;
-  const T* __restrict__ W2 = W1 + n;
-  auto in = [&](int v) -> cx<T> {
-    if (v >= n) return mkc<T>(0, 0);
-    return cmulc<T>(mkc<T>(W1[v], W2[v]), __ldg(sg.pre + v));
+  const int ST = fft_smem_elems(1 << maxlogM);
+  const int P = 1 << (maxlogM - 1);  // staging pitch in elements of T (>= 2L > n)
+  T* stg = reinterpret_cast<T*>(A + NT * ST);  // [2 NT][P] W rows of the next item
+  auto prefetch = [&](int it) {
+    if (it < total) {
+      const CztSeg<T> sp = segs[czt_find_seg<T>(segs, nseg, it)];
+      const int p0 = (it - sp.start) * NT, nr = 2 * min(NT, sp.N * sp.L - p0), n = 2 * sp.L - 1;
+      const T* __restrict__ Wr = reinterpret_cast<const T*>(sp.is_phi ? ptrs.Wphi[sp.job] : ptrs.W[sp.job]) +
+                                 sp.woff + (size_t)(2 * p0) * n;
+      for (int r = 0; r < nr; ++r)
+        for (int a = threadIdx.x; a < n; a += blockDim.x)
+          cp_async_ca<sizeof(T)>(stg + r * P + a, Wr + (size_t)r * n + a);
+    }
+    cp_async_commit();
   };
-  auto none = [](int, cx<T>) {};
-  fft_convolve<T, true>(A, sg.logM, sg.H, sg.tw, in, none);
-  cx<T>* __restrict__ V1 = sg.buf_out + (size_t)r1 * Lj;  // V_g[b][m] rows, m fastest
-  cx<T>* __restrict__ V2 = V1 + Lj;
-  const T h = sg.scale * T(0.5);
-  for (int mm = threadIdx.x; mm < Lj; mm += blockDim.x) {
-    const cx<T> ch = __ldg(sg.post + mm);
-    const cx<T> zp = cmulc<T>(A[fpad(mm)], ch);
-    const cx<T> zm = cmulc<T>(A[fpad((M - mm) & (M - 1))], ch);
-    // V1 = (Zp + conj(Zm))/2, V2 = (Zp - conj(Zm))/(2i)
-    V1[mm] = mkc<T>((zp.x + zm.x) * h, (zp.y - zm.y) * h);
-    V2[mm] = mkc<T>((zp.y + zm.y) * h, (zm.x - zp.x) * h);
+  int it = blockIdx.x;
+  prefetch(it);
+  for (; it < total; it += gridDim.x) {
+    const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg, it)];
+    const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM, n = 2 * L - 1;
+    const int p0 = (it - sg.start) * NT;
+    const int nt = min(NT, sg.N * L - p0);
+    cp_async_wait<0>();
+    __syncthreads();
+    auto pre = [&](int v) -> cx<T> { return v < n ? __ldg(sg.pre + v) : mkc<T>(0, 0); };
+    auto in = [&](int v, int t, cx<T> c) -> cx<T> {
+      if (v >= n || t >= nt) return mkc<T>(0, 0);
+      return cmulc<T>(mkc<T>(stg[(2 * t) * P + v], stg[(2 * t + 1) * P + v]), c);
+    };
+    auto nopost = [](int) -> cx<T> { return mkc<T>(0, 0); };
+    auto none = [](int, int, cx<T>, cx<T>) {};
+    const int next = it + gridDim.x;
+    fft_convolve_n<T, NT, true>(A, ST, sg.logM, sg.H, sg.tw, pre, in, nopost, none, [&]() { prefetch(next); });
+    const T h = sg.scale * T(0.5);
+    for (int mm = threadIdx.x; mm < Lj; mm += blockDim.x) {
+      const cx<T> ch = __ldg(sg.post + mm);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        if (t >= nt) break;
+        const cx<T> zp = cmulc<T>(A[t * ST + fpad(mm)], ch);
+        const cx<T> zm = cmulc<T>(A[t * ST + fpad((M - mm) & (M - 1))], ch);
+        // V1 = (Zp + conj(Zm))/2, V2 = (Zp - conj(Zm))/(2i), rows 2(p0 + t), 2(p0 + t) + 1
+        cx<T>* __restrict__ V1 = sg.buf_out + (size_t)(2 * (p0 + t)) * Lj;  // V_g[b][m] rows, m fastest
+        V1[mm] = mkc<T>((zp.x + zm.x) * h, (zp.y - zm.y) * h);
+        V1[Lj + mm] = mkc<T>((zp.y + zm.y) * h, (zm.x - zp.x) * h);
+      }
+    }
+    __syncthreads();  // A is rewritten by the next item
   }
+  cp_async_wait<0>();
 }
 
 template <typename T>
@@ -178,7 +229,7 @@ __global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restric
 // pre: e^{i pi m'/(4L)} at index m' + L - 1; post: q_b (real part), b < 2L.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_beta_ana_fft(const CztSeg<T>* __restrict__ segs, int nseg) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_beta_ana_fft(const CztSeg<T>* __restrict__ segs, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
@@ -203,7 +254,7 @@ __global__ void __launch_bounds__(256) k_beta_ana_fft(const CztSeg<T>* __restric
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_beta_syn_fft(const CztSeg<T>* __restrict__ segs, int nseg) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_beta_syn_fft(const CztSeg<T>* __restrict__ segs, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
@@ -416,16 +467,44 @@ size_t alpha_syn_direct_smem(int L) {
   return rows > parts ? rows : parts;
 }
 
+// Resident CTAs of a persistent alpha kernel on this device (cached per
+// device, precision and shared-memory size): 2 per SM when they fit.
+template <typename T, typename K>
+int alpha_czt_grid(K kernel, size_t smem) {
+  static int cache_dev[64][2] = {};
+  static size_t cache_smem[64][2] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int slot = (dev >= 0 && dev < 64) ? dev : 0;
+  const int pi = sizeof(T) == 8 ? 1 : 0;
+  if (cache_dev[slot][pi] > 0 && cache_smem[slot][pi] == smem) return cache_dev[slot][pi];
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, smem);
+  const int g = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  cache_dev[slot][pi] = g;
+  cache_smem[slot][pi] = smem;
+  return g;
+}
+
 template <typename T>
 void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items, int maxlogM,
                      const CallPtrs& ptrs, cudaStream_t st) {
   if (total_items <= 0) return;
+  if (kind == CZT_ALPHA_ANA) {
+    k_czt_alpha_ana<T><<<total_items, 256, alpha_czt_smem<T>(maxlogM, false), st>>>(segs, nseg, maxlogM, ptrs);
+    return;
+  }
+  if (kind == CZT_ALPHA_SYN) {
+    const size_t sm = alpha_czt_smem<T>(maxlogM, true);
+    const int g = std::min(total_items, alpha_czt_grid<T>(k_czt_alpha_syn<T>, sm));
+    k_czt_alpha_syn<T><<<g, 256, sm, st>>>(segs, nseg, total_items, maxlogM, ptrs);
+    return;
+  }
   const size_t smem = sizeof(cx<T>) * (size_t)fft_smem_elems(1 << maxlogM);
   dim3 grid(total_items), block(256);
   switch (kind) {
     case CZT_BETA_ANA: k_czt_beta_ana<T><<<grid, block, smem, st>>>(segs, nseg); break;
-    case CZT_ALPHA_ANA: k_czt_alpha_ana<T><<<grid, block, smem, st>>>(segs, nseg, ptrs); break;
-    case CZT_ALPHA_SYN: k_czt_alpha_syn<T><<<grid, block, smem, st>>>(segs, nseg, ptrs); break;
     case CZT_BETA_SYN: k_czt_beta_syn<T><<<grid, block, smem, st>>>(segs, nseg); break;
     case CZT_ALPHA_ANA_DIRECT: k_alpha_ana_direct<T><<<grid, block, 0, st>>>(segs, nseg, ptrs); break;
     case CZT_BETA_ANA_FFT: k_beta_ana_fft<T><<<grid, block, smem, st>>>(segs, nseg); break;
@@ -443,9 +522,11 @@ cudaError_t czt_set_smem(int maxlogM) {
   cudaError_t e = cudaSuccess;
   e = cudaFuncSetAttribute(k_czt_beta_ana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_czt_alpha_ana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(k_czt_alpha_ana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)alpha_czt_smem<T>(maxlogM, false));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_czt_alpha_syn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(k_czt_alpha_syn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)alpha_czt_smem<T>(maxlogM, true));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_beta_ana_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

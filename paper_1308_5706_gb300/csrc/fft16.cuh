@@ -139,75 +139,104 @@ __host__ __device__ __forceinline__ int fft_twiddle_entries(int logM) {
   return fft_twiddle_level_offset(logM, nlev);
 }
 
+// Stages below work on NT transforms per CTA (buffers ST elements apart in
+// shared memory): a thread loads its table values (twiddles, spectrum) once
+// into registers and applies them to the NT transforms in turn, which
+// divides the L1 table traffic by NT while only one transform's data is live.
+
 // One in-place forward (DIF) stage of radix R on blocks of size S, smem -> smem.
-// tw: this stage's twiddle level ([k-1][j], k < 16, j < Q).
-template <typename T, int R>
-__device__ __forceinline__ void fft_fwd_stage(cx<T>* A, int M, int S, const cx<T>* __restrict__ tw) {
+// tw: this stage's twiddle level ([k-1][j], k < 16, j < Q; j = 0 entries are 1).
+template <typename T, int R, int NT = 1>
+__device__ __forceinline__ void fft_fwd_stage(cx<T>* A, int M, int S, const cx<T>* __restrict__ tw, int ST = 0) {
   const int Q = S / R;
   for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
     const int j = u & (Q - 1), base = (u - j) * R + j;
-    cx<T> v[R];
+    cx<T> w[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = A[fpad(base + Q * r)];
-    DftR<T, R, false>::run(v);
-    if (j) {
+    for (int t = 0; t < NT; ++t) {
+      cx<T> v[R];
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmul<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+      for (int r = 0; r < R; ++r) v[r] = A[t * ST + fpad(base + Q * r)];
+      DftR<T, R, false>::run(v);
+#pragma unroll
+      for (int k = 1; k < R; ++k) {
+        if (t == 0) w[k] = __ldg(tw + (k - 1) * Q + j);
+        v[k] = cmul<T>(v[k], w[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < R; ++k) A[t * ST + fpad(base + Q * k)] = v[k];
     }
-#pragma unroll
-    for (int k = 0; k < R; ++k) A[fpad(base + Q * k)] = v[k];
   }
 }
 
 // Inverse (DIT) of fft_fwd_stage, smem -> smem, unnormalised (x R).
-template <typename T, int R>
-__device__ __forceinline__ void fft_inv_stage(cx<T>* A, int M, int S, const cx<T>* __restrict__ tw) {
+template <typename T, int R, int NT = 1>
+__device__ __forceinline__ void fft_inv_stage(cx<T>* A, int M, int S, const cx<T>* __restrict__ tw, int ST = 0) {
   const int Q = S / R;
   for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
     const int j = u & (Q - 1), base = (u - j) * R + j;
-    cx<T> v[R];
+    cx<T> w[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = A[fpad(base + Q * k)];
-    if (j) {
+    for (int t = 0; t < NT; ++t) {
+      cx<T> v[R];
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmulc<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+      for (int k = 0; k < R; ++k) v[k] = A[t * ST + fpad(base + Q * k)];
+#pragma unroll
+      for (int k = 1; k < R; ++k) {
+        if (t == 0) w[k] = __ldg(tw + (k - 1) * Q + j);
+        v[k] = cmulc<T>(v[k], w[k]);
+      }
+      DftR<T, R, true>::run(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) A[t * ST + fpad(base + Q * r)] = v[r];
     }
-    DftR<T, R, true>::run(v);
-#pragma unroll
-    for (int r = 0; r < R; ++r) A[fpad(base + Q * r)] = v[r];
   }
 }
 
 // Innermost stage (Q = 1): forward DFT, product with the spectrum (same
 // order), inverse DFT.  H == nullptr: forward only (used to build spectra).
-template <typename T, int R>
-__device__ __forceinline__ void fft_mid_stage(cx<T>* A, int M, const cx<T>* __restrict__ H, T scale) {
+template <typename T, int R, int NT = 1>
+__device__ __forceinline__ void fft_mid_stage(cx<T>* A, int M, const cx<T>* __restrict__ H, T scale, int ST = 0) {
   for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
     const int base = u * R;
-    cx<T> v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = A[fpad(base + r)];
-    DftR<T, R, false>::run(v);
     if (H) {
+      cx<T> h[R];
 #pragma unroll
-      for (int k = 0; k < R; ++k) v[k] = cmul<T>(v[k], __ldg(H + base + k));
-      DftR<T, R, true>::run(v);
+      for (int t = 0; t < NT; ++t) {
+        cx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = A[t * ST + fpad(base + r)];
+        DftR<T, R, false>::run(v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          if (t == 0) h[k] = __ldg(H + base + k);
+          v[k] = cmul<T>(v[k], h[k]);
+        }
+        DftR<T, R, true>::run(v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) A[t * ST + fpad(base + k)] = v[k];
+      }
     } else {
 #pragma unroll
-      for (int k = 0; k < R; ++k) v[k] = cscale<T>(v[k], scale);
-    }
+      for (int t = 0; t < NT; ++t) {
+        cx<T> v[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) A[fpad(base + k)] = v[k];
+        for (int r = 0; r < R; ++r) v[r] = A[t * ST + fpad(base + r)];
+        DftR<T, R, false>::run(v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) A[t * ST + fpad(base + k)] = cscale<T>(v[k], scale);
+      }
+    }
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void fft_mid_dispatch(cx<T>* A, int M, int Rl, const cx<T>* H, T scale) {
+template <typename T, int NT = 1>
+__device__ __forceinline__ void fft_mid_dispatch(cx<T>* A, int M, int Rl, const cx<T>* H, T scale, int ST = 0) {
   switch (Rl) {
-    case 2: fft_mid_stage<T, 2>(A, M, H, scale); break;
-    case 4: fft_mid_stage<T, 4>(A, M, H, scale); break;
-    case 8: fft_mid_stage<T, 8>(A, M, H, scale); break;
-    default: fft_mid_stage<T, 16>(A, M, H, scale); break;
+    case 2: fft_mid_stage<T, 2, NT>(A, M, H, scale, ST); break;
+    case 4: fft_mid_stage<T, 4, NT>(A, M, H, scale, ST); break;
+    case 8: fft_mid_stage<T, 8, NT>(A, M, H, scale, ST); break;
+    default: fft_mid_stage<T, 16, NT>(A, M, H, scale, ST); break;
   }
 }
 
@@ -388,6 +417,81 @@ __device__ __forceinline__ void fft_inverse_to(cx<T>* A, int logM, const cx<T>* 
 #pragma unroll
     for (int r = 0; r < 16; ++r) output(j + Q * r, v[r]);
   }
+}
+
+// fft_convolve on NT transforms per CTA (buffers ST elements apart):
+//   input(v, t, pre(v)) -> element v of transform t;
+//   output(v, t, value, post(v)) consumes element v of transform t;
+//   after_first() runs once all inputs have been read (after the first stage).
+template <typename T, int NT, bool WRITE_SMEM, typename Pre, typename In, typename Post, typename Out,
+          typename AfterFirst>
+__device__ __forceinline__ void fft_convolve_n(cx<T>* A, int ST, int logM, const cx<T>* __restrict__ H,
+                                               const cx<T>* __restrict__ tw, Pre pre, In input, Post post,
+                                               Out output, AfterFirst after_first) {
+  const int M = 1 << logM;
+  int Rl, nmid;
+  fft_schedule(logM, Rl, nmid);
+  {
+    const int Q = M / 16;
+    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+      cx<T> w[16];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        cx<T> v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = input(j + Q * r, t, pre(j + Q * r));
+        DftR<T, 16, false>::run(v);
+#pragma unroll
+        for (int k = 1; k < 16; ++k) {
+          if (t == 0) w[k] = __ldg(tw + (k - 1) * Q + j);
+          v[k] = cmul<T>(v[k], w[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) A[t * ST + fpad(j + Q * k)] = v[k];
+      }
+    }
+  }
+  __syncthreads();
+  after_first();  // every input has been read: the caller may refill its input buffers
+  int S = M / 16;
+  for (int s = 0; s < nmid; ++s) {
+    fft_fwd_stage<T, 16, NT>(A, M, S, tw + fft_twiddle_level_offset(logM, s + 1), ST);
+    __syncthreads();
+    S /= 16;
+  }
+  fft_mid_dispatch<T, NT>(A, M, Rl, H, T(1), ST);
+  __syncthreads();
+  for (int s = nmid - 1; s >= 0; --s) {
+    S *= 16;
+    fft_inv_stage<T, 16, NT>(A, M, S, tw + fft_twiddle_level_offset(logM, s + 1), ST);
+    __syncthreads();
+  }
+  {
+    const int Q = M / 16;
+    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+      cx<T> w[16];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        cx<T> v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = A[t * ST + fpad(j + Q * k)];
+#pragma unroll
+        for (int k = 1; k < 16; ++k) {
+          if (t == 0) w[k] = __ldg(tw + (k - 1) * Q + j);
+          v[k] = cmulc<T>(v[k], w[k]);
+        }
+        DftR<T, 16, true>::run(v);
+        if (WRITE_SMEM) {
+#pragma unroll
+          for (int r = 0; r < 16; ++r) A[t * ST + fpad(j + Q * r)] = v[r];
+        } else {
+#pragma unroll
+          for (int r = 0; r < 16; ++r) output(j + Q * r, t, v[r], post(j + Q * r));
+        }
+      }
+    }
+  }
+  if (WRITE_SMEM) __syncthreads();
 }
 
 // Forward transform only (smem in natural order -> smem in the engine's

@@ -59,6 +59,9 @@ enum CztKind {
   CZT_BETA_SYN_FFT = 7
 };
 constexpr int kDirectMaxLj = 32;
+// row pairs (complex transforms) per CTA of the alpha chirp-z kernels: FP32
+// runs two so that each table value serves both (FP64 buffers would not fit)
+__host__ __device__ constexpr int alpha_czt_nt(bool fp64) { return fp64 ? 1 : 2; }
 constexpr int kDirectRowsAna = 16;
 inline int direct_rows_syn(bool fp64) { return fp64 ? 4 : 8; }  // 32-byte line per alpha sample
 

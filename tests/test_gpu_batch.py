@@ -64,3 +64,42 @@ def test_batch_argument_errors():
     assert ei.value.status == B.S2DW_ENOTSUP
     a.close()
     b.close()
+
+
+def test_batch_in_cuda_graph_then_destroy():
+    """Batched calls captured in a CUDA graph replay to the eager result, and
+    the plans are destroyed cleanly afterwards (the library records none of
+    its own events into the caller's graph)."""
+    import torch
+    plans = [B.Plan(L, N, lam, J0, "mixed") for (L, N, lam, J0) in SPECS[:4]]
+    fs = [torch.from_numpy(flm_gaussian(p.L, 70 + i, "cl")).to(torch.complex64).cuda() for i, p in enumerate(plans)]
+    Wg = [p.alloc_w() for p in plans]
+    fg = [p.alloc_flm() for p in plans]
+    hs = [p.handle for p in plans]
+    s = torch.cuda.Stream()
+
+    def step():
+        B.s2dw_analysis_batch(hs, fs, [w[0] for w in Wg], [w[1] for w in Wg], s)
+        B.s2dw_synthesis_batch(hs, [w[0] for w in Wg], [w[1] for w in Wg], fg, s)
+
+    with torch.cuda.stream(s):
+        step()  # warm-up outside capture (builds the cached launch lists)
+    torch.cuda.synchronize()
+    for f in fg:
+        f.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        step()
+    g.replay()
+    torch.cuda.synchronize()
+    for p, f, out in zip(plans, fs, fg):
+        W, Wp = p.alloc_w()
+        ref = p.alloc_flm()
+        p.analysis(f, W, Wp)
+        p.synthesis(W, Wp, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    del g
+    torch.cuda.synchronize()
+    for p in plans:
+        p.close()  # raises on a non-zero status

@@ -38,3 +38,31 @@ def test_launch_counts(L, N, prec):
     assert len(ka) == na and len(ks) == ns
     assert all(k.startswith("void s2dw::") or "s2dw" in k for k in ka + ks), ka + ks
     p.close()
+
+
+def test_stage_profile_covers_the_calls():
+    """Stage events bracket every launch: two calls of each direction are
+    counted, every stage is timed, and the stages add up to the calls."""
+    import torch
+    p = B.Plan(64, 3, 2.0, 0, "mixed")
+    f = torch.from_numpy(flm_gaussian(64, 2, "cl")).to(torch.complex64).cuda()
+    W, Wp = p.alloc_w()
+    g = p.alloc_flm()
+    p.analysis(f, W, Wp)
+    p.synthesis(W, Wp, g)
+    torch.cuda.synchronize()
+    p.profile(True)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(2):
+        p.analysis(f, W, Wp)
+        p.synthesis(W, Wp, g)
+    e.record()
+    torch.cuda.synchronize()
+    ms, na, ns = p.profile_read()
+    p.profile(False)
+    assert (na, ns) == (2, 2)
+    assert list(ms) == B.STAGES and all(v >= 0 for v in ms.values())
+    total = s.elapsed_time(e)
+    assert 0 < sum(ms.values()) <= total * 1.05 + 0.05
+    p.close()
