@@ -121,11 +121,13 @@ DeltaTab* delta_acquire(int L, cudaStream_t st) {
   double* em = nullptr;
   int* ee = nullptr;
   try {
-    amalloc(&t->d64, entries * sizeof(double), st);
-    amalloc(&t->d32, entries * sizeof(float), st);
+    // kDeltaPad spare entries: the contraction copies 16-byte chunks of row
+    // segments that may run past the last row of the last slab
+    amalloc(&t->d64, (entries + kDeltaPad) * sizeof(double), st);
+    amalloc(&t->d32, (entries + kDeltaPad) * sizeof(float), st);
     t->bytes = entries * (sizeof(double) + sizeof(float));
-    ck(cudaMemsetAsync(t->d64, 0, entries * sizeof(double), st));
-    ck(cudaMemsetAsync(t->d32, 0, entries * sizeof(float), st));
+    ck(cudaMemsetAsync(t->d64, 0, (entries + kDeltaPad) * sizeof(double), st));
+    ck(cudaMemsetAsync(t->d32, 0, (entries + kDeltaPad) * sizeof(float), st));
     const size_t ne = (size_t)Lmax * (Lmax + 1) / 2;
     amalloc(&em, ne * sizeof(double), st);
     amalloc(&ee, ne * sizeof(int), st);

@@ -114,5 +114,6 @@ template <> void launch_syn_reduce<double>(const ReduceJobs&, int, int, cudaStre
 cudaError_t czt_prepare_f32(int maxlogM);
 cudaError_t czt_prepare_f64(int maxlogM);
 int contract_rows_per_thread(bool fp64);
+constexpr int kDeltaPad = 64;  // spare entries after a Delta table (row-segment copies)
 
 }  // namespace s2dw
