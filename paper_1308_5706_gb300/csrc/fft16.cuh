@@ -62,6 +62,25 @@ __device__ __forceinline__ void dft2(cx<T>& a, cx<T>& b) {
 
 template <typename T, bool INV>
 __device__ __forceinline__ void dft4(cx<T>& a0, cx<T>& a1, cx<T>& a2, cx<T>& a3) {
+  if constexpr (sizeof(T) == 4) {
+    // the six complex additions as packed f32x2 operations (one instruction
+    // each instead of two); the +-i products stay scalar (they swap parts)
+    const f2p p0 = pk2(a0.x, a0.y), p1 = pk2(a1.x, a1.y), p2 = pk2(a2.x, a2.y), p3 = pk2(a3.x, a3.y);
+    const f2p s02 = add2(p0, p2), d02 = sub2(p0, p2), s13 = add2(p1, p3), d13 = sub2(p1, p3);
+    upk2(add2(s02, s13), a0.x, a0.y);
+    upk2(sub2(s02, s13), a2.x, a2.y);
+    T dx, dy, ex, ey;
+    upk2(d02, dx, dy);
+    upk2(d13, ex, ey);
+    if (!INV) {
+      a1 = mkc<T>(dx + ey, dy - ex);  // d02 - i d13
+      a3 = mkc<T>(dx - ey, dy + ex);  // d02 + i d13
+    } else {
+      a1 = mkc<T>(dx - ey, dy + ex);
+      a3 = mkc<T>(dx + ey, dy - ex);
+    }
+    return;
+  }
   const cx<T> s02 = cadd<T>(a0, a2), d02 = csub<T>(a0, a2);
   const cx<T> s13 = cadd<T>(a1, a3), d13 = csub<T>(a1, a3);
   a0 = cadd<T>(s02, s13);
