@@ -416,6 +416,43 @@ def run_serve_workload(args):
     return 0
 
 
+def run_steer_workload(args):
+    """Steering (Eq. (10)) of the L=1024, N=5 mixed W to one arbitrary
+    orientation per step: one pass over W (read) and out (write)."""
+    import torch
+    from paper_1308_5706_gb300 import binding as B
+    pm = B.Plan(L, N, LAM, J0, "mixed")
+    f = torch.from_numpy(flm_gaussian(L, SEED, "cl")).to(torch.complex64).cuda()
+    W, Wp = pm.alloc_w()
+    pm.analysis(f, W, Wp)
+    gam = [0.3141]
+    out = pm.steer(W, gam)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pm.steer(W, gam, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        pm.steer(W, gam, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    nbytes = (W.numel() + out.numel()) * 4
+    hbm, _, src = peaks()
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    out_line = {"metric": "steering passes/s (W of 11 scales to one orientation)", "value": 1e3 / ms,
+                "unit": "passes/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                "config": {"workload": "L=1024, N=5, lambda=2, 11 scales, mixed; 1 orientation per pass",
+                           "l2": "W (0.92 GB) larger than L2"},
+                "roofline": {"kernel": "k_steer", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                             "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                             "peak_source": f"{src} hbm_gbs"}}
+    print(json.dumps(out_line))
+    pm.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,7 +461,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="roundtrip", choices=["roundtrip", "batch", "serve"])
+    ap.add_argument("--workload", default="roundtrip", choices=["roundtrip", "batch", "serve", "steer"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=300.0)
     args = ap.parse_args()
@@ -435,6 +472,8 @@ def main():
         return run_batch_workload(args)
     if args.workload == "serve":
         return run_serve_workload(args)
+    if args.workload == "steer":
+        return run_steer_workload(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

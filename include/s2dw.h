@@ -141,6 +141,21 @@ int s2dw_synthesis_batch(const s2dw_plan_t* plans, const void* const* W, const v
                          void* const* flm, int njobs, void* stream);
 
 /* Static text for a status code. */
+/*
+ * s2dw_steer: wavelet coefficients at arbitrary orientations from the N
+ * sampled ones (steerability, Sec. 2.2 Eq. (10)):
+ *   out[j][t][b][a] = sum_{g<N} z(gamma_t - gamma_g) W[j][g][b][a],
+ *   z(x) = (1/N) sum_{n in S_N} e^{i n x}, gamma_g = pi g / N (z_n = 1/N,
+ *   the even/odd directional kernels of Eq. (11)).
+ *   W: device [J+1][N][2L][2L-1] real, as written by s2dw_analysis;
+ *   gammas: HOST double[ngamma], any real angles (1 <= ngamma <= 32);
+ *   out: device [J+1][ngamma][2L][2L-1] real (the plan's precision).
+ * Asynchronous on stream (one pass over W, HBM-bound).  The scaling
+ * coefficients have no orientation and are not involved.
+ * S2DW_EINVAL for a NULL pointer or ngamma outside [1, 32].
+ */
+int s2dw_steer(s2dw_plan_t plan, const void* W, const double* gammas, int ngamma, void* out, void* stream);
+
 const char* s2dw_strerror(int status);
 
 /*

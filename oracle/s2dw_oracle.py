@@ -28,7 +28,7 @@ __all__ = [
     "kappa_lambda", "kappa", "phi_l", "s_dir", "kernels", "dh_weights", "grids",
     "wigner_d", "delta", "flm_to_grid", "grid_to_flm", "analysis",
     "analysis_rows", "synthesis", "synthesis_modes", "fourier_cube",
-    "support",
+    "support", "steer", "sht_inverse", "sht_forward",
 ]
 
 # How each function is pinned to something other than itself (tests named in
@@ -42,6 +42,9 @@ PARITY = {
     "delta": "symmetries of d(pi/2); Fourier expansion Eq. (25) reproduces d(beta)",
     "analysis": "single-mode closed-form D at l=1,2; realness for real signals; steerability Eq. (10)",
     "synthesis": "exact round trip with analysis (Sec. 3.4 metric) to 1e-12",
+    "steer": "reproduces the samples at gamma = gamma_g; equals the direct sum of Eq. (20) at off-grid gamma",
+    "sht_inverse": "textbook Y_lm (Condon-Shortley) at l <= 2; exact round trip with sht_forward",
+    "sht_forward": "textbook Y_lm maps give unit coefficients; exact round trip with sht_inverse",
 }
 
 
@@ -450,3 +453,69 @@ def synthesis_modes(W, Wphi, L: int, N: int, lam: float, J0: int, lm_list, kern=
             acc += wa * (2 * l + 1) / (4 * np.pi) * phi[l] * np.sum(q * D0[l] * Es)
             out[(l, m)] = acc
     return out
+
+
+# ---------------------------------------------------------------------------
+# Steerability (Sec. 2.2, Eq. (10))
+# ---------------------------------------------------------------------------
+
+def steer(W, N: int, gammas):
+    """Wavelet coefficients at arbitrary orientations from the N samples:
+    W(alpha, beta, gamma) = sum_{g<N} z(gamma - gamma_g) W(alpha, beta, gamma_g)
+    (Eq. (10)), gamma_g = pi g / N (Sec. 3.1), with the interpolating function
+    z(x) = sum_{n in S_N} z_n e^{i n x}, z_n = 1/N for the orders n_k of the
+    even/odd kernels (Eq. (11)).
+
+    W: [J+1][N][2L][2L-1] real; returns [J+1][len(gammas)][2L][2L-1]."""
+    W = np.asarray(W, dtype=np.float64)
+    ns = n_orders(N)
+    gamma_g = np.pi * np.arange(N) / N
+    gammas = np.asarray(gammas, dtype=np.float64)
+    x = gammas[:, None] - gamma_g[None, :]                       # [t][g]
+    z = np.real(np.exp(1j * x[:, :, None] * ns[None, None, :]).sum(axis=2)) / N
+    return np.einsum("tg,jgba->jtba", z, W)
+
+
+# ---------------------------------------------------------------------------
+# Spherical harmonic transforms on the DH grid (Sec. 2.1, Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def _ylm_factor(L: int) -> np.ndarray:
+    """sqrt((2l+1)/(4 pi)), the normalisation of Y_lm = sqrt((2l+1)/(4 pi))
+    D^l*_m0(phi, theta, 0) (Sec. 2.1)."""
+    return np.sqrt((2.0 * np.arange(L) + 1.0) / (4.0 * np.pi))
+
+
+def sht_inverse(flm, L: int) -> np.ndarray:
+    """f(theta_t, phi_p) = sum_{l<L} sum_{|m|<=l} f_lm Y_lm(theta_t, phi_p) on the
+    DH sphere grid of Sec. 3.1 (theta_t = pi(2t+1)/(4L), t < 2L; phi_p =
+    2 pi p/(2L-1)), Y_lm(theta, phi) = sqrt((2l+1)/(4 pi)) e^{i m phi} d^l_m0(theta).
+    Returns the complex samples [2L][2L-1] (real for a real signal)."""
+    phi, theta, _ = grids(L, 1)
+    ms = np.arange(-(L - 1), L)
+    F = flm_to_grid(np.asarray(flm, np.complex128), L) * _ylm_factor(L)[:, None]
+    E = np.exp(1j * np.outer(ms, phi))                      # [m][p]
+    out = np.zeros((2 * L, 2 * L - 1), dtype=np.complex128)
+    for t in range(2 * L):
+        d = wigner_d(theta[t], L, ms, 0)                    # [l][m]
+        out[t] = (F * d).sum(axis=0) @ E
+    return out
+
+
+def sht_forward(fpix, L: int) -> np.ndarray:
+    """f_lm = sum_{t, p} q_t (2 pi/(2L-1)) f(theta_t, phi_p) Y*_lm(theta_t, phi_p):
+    the integral of f Y*_lm over the sphere by the DH quadrature of Eqs.
+    (17)-(18), exact for band-limited f.  Returns the flat f[l*l + l + m]."""
+    phi, theta, _ = grids(L, 1)
+    q = dh_weights(L)
+    ms = np.arange(-(L - 1), L)
+    E = np.exp(-1j * np.outer(phi, ms)) * (2.0 * np.pi / (2 * L - 1))  # [p][m]
+    F = np.zeros((L, 2 * L - 1), dtype=np.complex128)
+    fpix = np.asarray(fpix)
+    for t in range(2 * L):
+        G = fpix[t] @ E                                     # [m]
+        d = wigner_d(theta[t], L, ms, 0)                    # [l][m]
+        F += q[t] * d * G[None, :]
+    F *= _ylm_factor(L)[:, None]
+    # entries with |m| > l are exactly zero in d; keep only the valid ones
+    return grid_to_flm(F, L)

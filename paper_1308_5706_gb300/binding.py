@@ -31,6 +31,7 @@ _SIGNATURES = {
     "s2dw_plan_destroy": (_c_i, [_c_p]),
     "s2dw_query": (_c_i, [_c_p, _c_ip, _c_i64p, _c_i64p, _c_i64p, _c_i64p]),
     "s2dw_launch_counts": (_c_i, [_c_p, _c_ip, _c_ip]),
+    "s2dw_steer": (_c_i, [_c_p, _c_p, _c_dp, _c_i, _c_p, _c_p]),
     "s2dw_kernels": (_c_i, [_c_p, _c_dp, _c_dp]),
     "s2dw_analysis": (_c_i, [_c_p, _c_p, _c_p, _c_p, _c_p]),
     "s2dw_synthesis": (_c_i, [_c_p, _c_p, _c_p, _c_p, _c_p]),
@@ -119,6 +120,13 @@ def s2dw_query(plan: int) -> dict:
                             ctypes.byref(tot)), "s2dw_query")
     return {"J": J.value, "w_elems_per_scale": w.value, "wphi_elems": wp.value,
             "workspace_bytes": ws.value, "total_device_bytes": tot.value}
+
+
+def s2dw_steer(plan: int, W, gammas, out, stream=None) -> None:
+    """out[j][t] = W steered to orientation gammas[t] (Eq. (10))."""
+    g = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64).ravel())
+    _check(lib().s2dw_steer(plan, _ptr(W), g.ctypes.data_as(_c_dp), int(g.size), _ptr(out), _stream(stream)),
+           "s2dw_steer")
 
 
 def s2dw_launch_counts(plan: int):
@@ -262,6 +270,15 @@ class Plan:
 
     def launch_counts(self):
         return s2dw_launch_counts(self.handle)
+
+    def steer(self, W, gammas, out=None, stream=None):
+        """W steered to the orientations `gammas` (Eq. (10)); allocates out if None."""
+        import torch
+        ng = len(np.atleast_1d(gammas))
+        if out is None:
+            out = torch.empty((self.J + 1, ng, 2 * self.L, 2 * self.L - 1), dtype=W.dtype, device=W.device)
+        s2dw_steer(self.handle, W, gammas, out, stream)
+        return out
 
     def analysis(self, flm, W, Wphi, stream=None):
         s2dw_analysis(self.handle, flm, W, Wphi, stream)

@@ -10,6 +10,7 @@
 #include "../../include/s2dw.h"
 #include "internal.h"
 #include "plan_kernels.h"
+#include "steer.h"
 
 using namespace s2dw;
 
@@ -891,6 +892,25 @@ int s2dw_query(s2dw_plan_t p, int* J, int64_t* w_elems_per_scale, int64_t* wphi_
   if (total_device_bytes)
     *total_device_bytes = (int64_t)p->ws_bytes + (wps * p->nscale + wph) * el + L * L * 2 * el;
   return S2DW_OK;
+}
+
+int s2dw_steer(s2dw_plan_t p, const void* W, const double* gammas, int ngamma, void* out, void* stream) {
+  if (!p || !W || !gammas || !out || ngamma < 1 || ngamma > kSteerMaxGamma) return S2DW_EINVAL;
+  const int N = p->N;
+  SteerWeights sw;
+  std::memset(&sw, 0, sizeof(sw));
+  for (int t = 0; t < ngamma; ++t)
+    for (int g = 0; g < N; ++g) {
+      const double x = gammas[t] - 3.14159265358979323846 * g / N;
+      double z = 0.0;
+      for (int k = 0; k < N; ++k) z += std::cos((-(N - 1) + 2 * k) * x);
+      sw.w[t][g] = z / N;
+    }
+  const int64_t per_scale = (int64_t)2 * p->L * (2 * p->L - 1);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = p->fp64 ? launch_steer<double>(W, out, sw, p->nscale, N, ngamma, per_scale, st)
+                          : launch_steer<float>(W, out, sw, p->nscale, N, ngamma, per_scale, st);
+  return err_of(e);
 }
 
 int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {

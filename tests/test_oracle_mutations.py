@@ -68,6 +68,22 @@ def _wigner_sign(beta, L, m, n):
     return _orig_wigner_d(beta, L, m, -np.asarray(n))
 
 
+_orig_steer = OS.steer
+
+
+def _steer_2pi_spacing(W, N, gammas):
+    # samples taken as if gamma_g = 2 pi g / N (the full circle)
+    W = np.asarray(W, dtype=np.float64)
+    ns = OS.n_orders(N)
+    x = np.asarray(gammas)[:, None] - 2 * np.pi * np.arange(N)[None, :] / N
+    z = np.real(np.exp(1j * x[:, :, None] * ns[None, None, :]).sum(axis=2)) / N
+    return np.einsum("tg,jgba->jtba", z, W)
+
+
+def _steer_no_norm(W, N, gammas):
+    return _orig_steer(W, N, gammas) * N
+
+
 PINS = [
     lambda: P.test_single_mode_analysis_closed_form(3, 2.0, 0),
     lambda: P.test_single_mode_analysis_closed_form(2, 2.0, 1),
@@ -79,6 +95,9 @@ PINS = [
     lambda: P.test_dh_weights(5),
     lambda: P.test_k_lambda_limits_and_derivative(),
     lambda: P.test_realness_and_steerability(),
+    lambda: P.test_steer_reproduces_samples(3),
+    lambda: P.test_sht_round_trip_exact(9),
+    lambda: P.test_sht_textbook_harmonics(1, 1),
 ]
 
 
@@ -91,6 +110,8 @@ PINS = [
     ("alpha grid 2L points", "grids", _grids_alpha_2L),
     ("k_lambda normalisation", "k_lambda", _k_bad_norm),
     ("sign of n in d", "wigner_d", _wigner_sign),
+    ("steering samples on [0, 2pi)", "steer", _steer_2pi_spacing),
+    ("steering without z_n = 1/N", "steer", _steer_no_norm),
 ])
 def test_planted_mistake_is_caught(monkeypatch, name, attr, bad):
     monkeypatch.setattr(OS, attr, bad)

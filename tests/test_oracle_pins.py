@@ -309,6 +309,21 @@ def test_realness_and_steerability():
         z = lambda x: np.sum(np.exp(1j * ns * x)).real / N
         steered = sum(z(gam - gamma[g]) * W[j, g, b, a] for g in range(N))
         assert abs(direct - steered) < 1e-13
+        # the oracle's steer() is the same interpolation
+        assert abs(O.steer(W, N, [gam])[j, 0, b, a] - direct) < 1e-13
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 8])
+def test_steer_reproduces_samples(N):
+    """z(gamma_g' - gamma_g) = delta_gg' (Dirichlet kernel of the odd-spaced
+    orders at multiples of pi/N), so steering to the sample angles returns W."""
+    rng = np.random.default_rng(N)
+    W = rng.standard_normal((2, N, 6, 5))
+    gamma_g = np.pi * np.arange(N) / N
+    assert np.abs(O.steer(W, N, gamma_g) - W).max() < 1e-13
+    # period: gamma and gamma + 2 pi give the same coefficients
+    g = rng.uniform(0, np.pi, 3)
+    assert np.abs(O.steer(W, N, g) - O.steer(W, N, g + 2 * np.pi)).max() < 1e-12
 
 
 @pytest.mark.parametrize("L,N,lam,J0,kind", [(8, 3, 2.0, 0, "unit"), (16, 5, 2.0, 0, "cl"),
@@ -337,3 +352,39 @@ def test_fourier_cube_reproduces_analysis():
             val = np.einsum("mpk,m,p,k->", U, np.exp(1j * ms * alpha[a]), np.exp(1j * ms * beta[b]),
                             np.exp(1j * ns * gamma[g]))
             assert abs(val - W[j, g, b, a]) < 1e-13
+
+
+# ---- spherical harmonic transforms on the DH grid ----
+
+def _ylm_textbook(l, m, theta, phi):
+    """Textbook spherical harmonics (Condon-Shortley phase), l <= 2, m >= 0."""
+    c, s = np.cos(theta), np.sin(theta)
+    table = {
+        (0, 0): 0.5 * np.sqrt(1 / np.pi) + 0 * theta,
+        (1, 0): np.sqrt(3 / (4 * np.pi)) * c,
+        (1, 1): -np.sqrt(3 / (8 * np.pi)) * s,
+        (2, 0): np.sqrt(5 / (16 * np.pi)) * (3 * c * c - 1),
+        (2, 1): -np.sqrt(15 / (8 * np.pi)) * s * c,
+        (2, 2): np.sqrt(15 / (32 * np.pi)) * s * s,
+    }
+    return table[(l, m)][:, None] * np.exp(1j * m * phi)[None, :]
+
+
+@pytest.mark.parametrize("l,m", [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)])
+def test_sht_textbook_harmonics(l, m):
+    L = 5
+    phi, theta, _ = O.grids(L, 1)
+    Y = _ylm_textbook(l, m, theta, phi)
+    flm = np.zeros(L * L, dtype=np.complex128)
+    flm[l * l + l + m] = 1.0
+    assert np.abs(O.sht_inverse(flm, L) - Y).max() < 1e-14
+    back = O.sht_forward(Y, L)
+    assert np.abs(back - flm).max() < 1e-14
+
+
+@pytest.mark.parametrize("L", [4, 9, 16])
+def test_sht_round_trip_exact(L):
+    f = flm_gaussian(L, 13)
+    pix = O.sht_inverse(f, L)
+    assert np.abs(pix.imag).max() < 1e-13          # real signal -> real samples
+    assert np.abs(O.sht_forward(pix.real, L) - f).max() < 1e-13
