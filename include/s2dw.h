@@ -142,6 +142,23 @@ int s2dw_synthesis_batch(const s2dw_plan_t* plans, const void* const* W, const v
 
 /* Static text for a status code. */
 /*
+ * Spherical harmonic transforms of a real signal on the DH sphere grid of
+ * Sec. 3.1 (theta_t = pi(2t+1)/(4L), t < 2L; phi_p = 2 pi p/(2L-1)), with
+ * Y_lm(theta, phi) = sqrt((2l+1)/(4 pi)) e^{i m phi} d^l_m0(theta) (Sec. 2.1):
+ *   s2dw_sht_inverse: fpix[t][p] = sum_{l<L, |m|<=l} f_lm Y_lm(theta_t, phi_p);
+ *   s2dw_sht_forward: f_lm = sum_{t,p} q_t (2 pi/(2L-1)) fpix[t][p] Y*_lm, the
+ *     DH quadrature of Eqs. (17)-(18), exact for band-limited samples.
+ *   flm: device [L*L] complex (index l*l + l + m); fpix: device [2L][2L-1]
+ *   real, in the plan's precision.  They let a caller start from pixel
+ *   values: W = analysis(sht_forward(f)), f = sht_inverse(synthesis(W)).
+ * The first call builds a companion plan (no wavelet scales, Phi_l =
+ * sqrt((2l+1)/(4 pi))) on the plan's private stream; later calls are
+ * asynchronous on `stream`.  S2DW_EINVAL for NULL pointers.
+ */
+int s2dw_sht_inverse(s2dw_plan_t plan, const void* flm, void* fpix, void* stream);
+int s2dw_sht_forward(s2dw_plan_t plan, const void* fpix, void* flm, void* stream);
+
+/*
  * s2dw_steer: wavelet coefficients at arbitrary orientations from the N
  * sampled ones (steerability, Sec. 2.2 Eq. (10)):
  *   out[j][t][b][a] = sum_{g<N} z(gamma_t - gamma_g) W[j][g][b][a],

@@ -32,6 +32,8 @@ _SIGNATURES = {
     "s2dw_query": (_c_i, [_c_p, _c_ip, _c_i64p, _c_i64p, _c_i64p, _c_i64p]),
     "s2dw_launch_counts": (_c_i, [_c_p, _c_ip, _c_ip]),
     "s2dw_steer": (_c_i, [_c_p, _c_p, _c_dp, _c_i, _c_p, _c_p]),
+    "s2dw_sht_inverse": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
+    "s2dw_sht_forward": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
     "s2dw_kernels": (_c_i, [_c_p, _c_dp, _c_dp]),
     "s2dw_analysis": (_c_i, [_c_p, _c_p, _c_p, _c_p, _c_p]),
     "s2dw_synthesis": (_c_i, [_c_p, _c_p, _c_p, _c_p, _c_p]),
@@ -127,6 +129,16 @@ def s2dw_steer(plan: int, W, gammas, out, stream=None) -> None:
     g = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64).ravel())
     _check(lib().s2dw_steer(plan, _ptr(W), g.ctypes.data_as(_c_dp), int(g.size), _ptr(out), _stream(stream)),
            "s2dw_steer")
+
+
+def s2dw_sht_inverse(plan: int, flm, fpix, stream=None) -> None:
+    """Pixel values on the DH sphere grid from f_lm (inverse SHT)."""
+    _check(lib().s2dw_sht_inverse(plan, _ptr(flm), _ptr(fpix), _stream(stream)), "s2dw_sht_inverse")
+
+
+def s2dw_sht_forward(plan: int, fpix, flm, stream=None) -> None:
+    """f_lm from pixel values on the DH sphere grid (forward SHT, exact quadrature)."""
+    _check(lib().s2dw_sht_forward(plan, _ptr(fpix), _ptr(flm), _stream(stream)), "s2dw_sht_forward")
 
 
 def s2dw_launch_counts(plan: int):
@@ -270,6 +282,16 @@ class Plan:
 
     def launch_counts(self):
         return s2dw_launch_counts(self.handle)
+
+    def alloc_pix(self, device="cuda"):
+        import torch
+        return torch.empty((2 * self.L, 2 * self.L - 1), dtype=self.torch_dtypes()[1], device=device)
+
+    def sht_inverse(self, flm, fpix, stream=None):
+        s2dw_sht_inverse(self.handle, flm, fpix, stream)
+
+    def sht_forward(self, fpix, flm, stream=None):
+        s2dw_sht_forward(self.handle, fpix, flm, stream)
 
     def steer(self, W, gammas, out=None, stream=None):
         """W steered to the orientations `gammas` (Eq. (10)); allocates out if None."""

@@ -199,6 +199,8 @@ struct s2dw_plan_s {
   int device = 0;
   DeltaTab* tab = nullptr;
   std::vector<double> psi_host, phi_host;
+  bool sht = false;                 // companion plan of the spherical harmonic transforms
+  s2dw_plan_s* sht_child = nullptr; // created on the first s2dw_sht_* call
   cudaStream_t pst = nullptr;       // private non-blocking stream (set-up, frees)
   cudaEvent_t last_use = nullptr;   // recorded after every call using the plan
   void* ws = nullptr;
@@ -235,6 +237,7 @@ struct s2dw_plan_s {
       if (e) cudaEventDestroy(e);
     for (auto e : ev_syn)
       if (e) cudaEventDestroy(e);
+    delete sht_child;
     if (last_use) {
       cudaEventSynchronize(last_use);  // only this plan's work, not the device
       cudaEventDestroy(last_use);
@@ -719,7 +722,15 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   ck(sizeof(T) == sizeof(double) ? czt_prepare_f64(13) : czt_prepare_f32(13));
 }
 
-int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned flags) {
+// sht_mode: the companion plan of s2dw_sht_*: no wavelet scales, N = 1 and
+// Phi_l = sqrt((2l+1)/(4 pi)) for every l < L, so that its scaling part is
+// the spherical harmonic transform pair on the DH sphere grid.
+int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned flags, bool sht_mode = false) {
+  if (sht_mode) {
+    N = 1;
+    lam = 2.0;
+    J0 = jmax_of(L, lam);
+  }
   const int Jm = jmax_of(L, lam);
   if (J0 < 0 || J0 > Jm) return S2DW_EINVAL;
   const int J = Jm - J0;
@@ -764,6 +775,13 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
     ck(cudaMemcpyAsync(p->phi_host.data(), phi, L * sizeof(double), cudaMemcpyDeviceToHost, st));
     ck(cudaMemcpyAsync(p->psi_host.data(), psi, p->psi_host.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     ck(cudaStreamSynchronize(st));
+    if (sht_mode) {
+      for (int l = 0; l < L; ++l) p->phi_host[l] = std::sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846));
+      ck(cudaMemcpyAsync(phi, p->phi_host.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+      ck(cudaStreamSynchronize(st));
+      p->nscale = 0;
+      p->sht = true;
+    }
     // supports where kappa^j(l) > 0 and their overlaps
     p->lo.assign(p->nscale, -1);
     p->hi.assign(p->nscale, -1);
@@ -911,6 +929,60 @@ int s2dw_steer(s2dw_plan_t p, const void* W, const double* gammas, int ngamma, v
   cudaError_t e = p->fp64 ? launch_steer<double>(W, out, sw, p->nscale, N, ngamma, per_scale, st)
                           : launch_steer<float>(W, out, sw, p->nscale, N, ngamma, per_scale, st);
   return err_of(e);
+}
+
+namespace {
+int sht_child(s2dw_plan_t p, s2dw_plan_t* c) {
+  if (!p->sht_child) {
+    const int rc = plan_create(&p->sht_child, p->L, 1, 2.0, 0, p->fp64 ? S2DW_FP64 : S2DW_MIXED, true);
+    if (rc != S2DW_OK) {
+      p->sht_child = nullptr;
+      return rc;
+    }
+  }
+  *c = p->sht_child;
+  return S2DW_OK;
+}
+}  // namespace
+
+int s2dw_sht_inverse(s2dw_plan_t p, const void* flm, void* fpix, void* stream) {
+  if (!p || !flm || !fpix) return S2DW_EINVAL;
+  s2dw_plan_t c = nullptr;
+  const int rc = sht_child(p, &c);
+  if (rc != S2DW_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CallPtrs ptrs;
+  std::memset(&ptrs, 0, sizeof(ptrs));
+  ptrs.f[0] = flm;
+  ptrs.Wphi[0] = fpix;
+  if (c->fp64) run_analysis<double>(c->own, ptrs, st);
+  else run_analysis<float>(c->own, ptrs, st);
+  mark_use(c, st);
+  return err_of(cudaGetLastError());
+}
+
+int s2dw_sht_forward(s2dw_plan_t p, const void* fpix, void* flm, void* stream) {
+  if (!p || !flm || !fpix) return S2DW_EINVAL;
+  s2dw_plan_t c = nullptr;
+  const int rc = sht_child(p, &c);
+  if (rc != S2DW_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CallPtrs ptrs;
+  std::memset(&ptrs, 0, sizeof(ptrs));
+  ptrs.Wphi[0] = const_cast<void*>(fpix);
+  ReduceJobs rj;
+  std::memset(&rj, 0, sizeof(rj));
+  rj.dw[0] = c->own.desc_w;
+  rj.dp[0] = c->own.desc_phi;
+  rj.out[0] = flm;
+  rj.L[0] = c->L;
+  rj.lend[0] = c->lend_w;
+  rj.Lphi[0] = c->Lphi;
+  rj.sht[0] = 1;
+  if (c->fp64) run_synthesis<double>(c->own, ptrs, rj, 1, st);
+  else run_synthesis<float>(c->own, ptrs, rj, 1, st);
+  mark_use(c, st);
+  return err_of(cudaGetLastError());
 }
 
 int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {

@@ -453,7 +453,11 @@ __global__ void k_syn_reduce(ReduceJobs jobs, int tmp) {
     const int nb = min(l / tmp, dp->nbr - 1);
     for (int b = 0; b <= nb; ++b) sum = cadd<T>(sum, dp->P[((size_t)b * dp->L + l) * dp->Lp32 + m]);
   }
-  const T fac = (T)((2.0 * l + 1.0) / (8.0 * 3.14159265358979323846 * 3.14159265358979323846));
+  // (2l+1)/(8 pi^2) of the synthesis (Eq. (32)); the forward SHT's plan has
+  // Phi_l = sqrt((2l+1)/(4 pi)) and needs f_lm = Phi_l S where the partials
+  // carry 2 pi Phi_l S (the N = 1 gamma quadrature), hence 1/(2 pi)
+  const T fac = jobs.sht[job] ? (T)(0.5 / 3.14159265358979323846)
+                              : (T)((2.0 * l + 1.0) / (8.0 * 3.14159265358979323846 * 3.14159265358979323846));
   sum = cscale<T>(sum, fac);
   cx<T>* __restrict__ out = reinterpret_cast<cx<T>*>(jobs.out[job]);
   out[l * l + l + m] = sum;

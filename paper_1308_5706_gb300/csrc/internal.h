@@ -92,6 +92,7 @@ struct ReduceJobs {
   int L[MAXB];
   int lend[MAXB];
   int Lphi[MAXB];
+  int sht[MAXB];  // 1: forward spherical harmonic transform (factor 1/(2 pi), see s2dw_sht_forward)
 };
 
 template <typename T>
