@@ -54,7 +54,8 @@ enum {
 enum {
   S2DW_FP64 = 1,        /* plain float64 path                              */
   S2DW_MIXED = 2,       /* float32 arithmetic, FP64-generated Delta        */
-  S2DW_REAL_SIGNAL = 4  /* real signals (required; set implicitly)         */
+  S2DW_REAL_SIGNAL = 4, /* real signals (required; set implicitly)         */
+  S2DW_MULTIRES = 8     /* each scale on the grid of its own band-limit     */
 };
 
 typedef struct s2dw_plan_s* s2dw_plan_t;
@@ -67,7 +68,14 @@ typedef struct s2dw_plan_s* s2dw_plan_t;
  *   Kernels: Psi^j_ln = kappa^j(l) s_ln (Eqs. (7), (11)-(15)).
  * Valid ranges: 2 <= L <= 2048, 1 <= N <= min(8, L), lambda > 1 (at most 64
  * scales), 0 <= J0 <= J_max; flags = exactly one of S2DW_FP64 / S2DW_MIXED,
- * optionally | S2DW_REAL_SIGNAL.  Otherwise S2DW_EINVAL.
+ * optionally | S2DW_REAL_SIGNAL and | S2DW_MULTIRES.  Otherwise S2DW_EINVAL.
+ * S2DW_MULTIRES samples each W^j on the DH SO(3) grid of its own band-limit
+ * L_j = 1 + the largest l with kappa^j(l) > 0 (and W^Phi on the sphere grid
+ * of L_Phi): W^j is band-limited there, so the samples are exact and the
+ * synthesis stays exact, with fewer samples and less work (the paper notes
+ * that not every scale needs the full band-limit, Sec. 3.2).  W is then one
+ * array holding the scales one after the other (s2dw_scale_grid gives each
+ * scale's band-limit, offset and size).
  * Work: evaluates the kernels, the DH weights (Eq. (18)) and the Delta table
  * on the device (FP64 recursion, grown to cover l < L on first need) and
  * allocates the workspace (stream-ordered, on a private stream; other
@@ -85,13 +93,24 @@ int s2dw_plan_destroy(s2dw_plan_t plan);
 /*
  * s2dw_query: sizes of a plan, any pointer may be NULL.
  *   J: largest scale index (scales 0..J);
- *   w_elems_per_scale: N * 2L * (2L-1);  wphi_elems: 2L * (2L-1);
+ *   w_elems_per_scale: N * 2L * (2L-1) (0 for S2DW_MULTIRES plans, whose
+ *   scales differ in size); wphi_elems: 2L_Phi * (2L_Phi-1), L_Phi = L unless
+ *   S2DW_MULTIRES;
  *   workspace_bytes: device bytes owned by the plan (intermediates, tables);
  *   total_device_bytes: workspace_bytes + the caller's f, W, Wphi bytes for
  *   one transform (used for admission by HBM footprint).
  */
 int s2dw_query(s2dw_plan_t plan, int* J, int64_t* w_elems_per_scale, int64_t* wphi_elems,
                int64_t* workspace_bytes, int64_t* total_device_bytes);
+
+/*
+ * s2dw_scale_grid: sampling grid of scale j (0 <= j <= J) or, for j = J+1,
+ * of the scaling part: its band-limit Lg (2Lg beta and 2Lg-1 alpha samples),
+ * the element offset of W^j in W (0 for j = J+1: W^Phi is its own array) and
+ * the element count (N 2Lg (2Lg-1), or 2Lg (2Lg-1)).  Any output may be NULL.
+ * S2DW_EINVAL for j outside [0, J+1].
+ */
+int s2dw_scale_grid(s2dw_plan_t plan, int j, int* Lgrid, int64_t* offset, int64_t* elems);
 
 /*
  * s2dw_launch_counts: number of kernel launches one s2dw_analysis and one
@@ -166,7 +185,8 @@ int s2dw_sht_forward(s2dw_plan_t plan, const void* fpix, void* flm, void* stream
  *   the even/odd directional kernels of Eq. (11)).
  *   W: device [J+1][N][2L][2L-1] real, as written by s2dw_analysis;
  *   gammas: HOST double[ngamma], any real angles (1 <= ngamma <= 32);
- *   out: device [J+1][ngamma][2L][2L-1] real (the plan's precision).
+ *   out: device [J+1][ngamma][2L][2L-1] real (the plan's precision); for an
+ *   S2DW_MULTIRES plan each scale's [ngamma][2Lg][2Lg-1] block, in order.
  * Asynchronous on stream (one pass over W, HBM-bound).  The scaling
  * coefficients have no orientation and are not involved.
  * S2DW_EINVAL for a NULL pointer or ngamma outside [1, 32].

@@ -29,6 +29,7 @@ __all__ = [
     "wigner_d", "delta", "flm_to_grid", "grid_to_flm", "analysis",
     "analysis_rows", "synthesis", "synthesis_modes", "fourier_cube",
     "support", "steer", "sht_inverse", "sht_forward",
+    "band_limits", "analysis_multires", "synthesis_multires",
 ]
 
 # How each function is pinned to something other than itself (tests named in
@@ -45,6 +46,8 @@ PARITY = {
     "steer": "reproduces the samples at gamma = gamma_g; equals the direct sum of Eq. (20) at off-grid gamma",
     "sht_inverse": "textbook Y_lm (Condon-Shortley) at l <= 2; exact round trip with sht_forward",
     "sht_forward": "textbook Y_lm maps give unit coefficients; exact round trip with sht_inverse",
+    "analysis_multires": "equals the full-resolution W at the samples the two grids share; exact round trip",
+    "synthesis_multires": "exact round trip with analysis_multires (Sec. 3.4 metric)",
 }
 
 
@@ -519,3 +522,56 @@ def sht_forward(fpix, L: int) -> np.ndarray:
     F *= _ylm_factor(L)[:, None]
     # entries with |m| > l are exactly zero in d; keep only the valid ones
     return grid_to_flm(F, L)
+
+
+# ---------------------------------------------------------------------------
+# Multi-resolution sampling (Sec. 3.2 / 3.3 remark: a scale need not be
+# transformed at the full band-limit)
+# ---------------------------------------------------------------------------
+
+def band_limits(L: int, N: int, lam: float, J0: int, kern=None):
+    """Band-limit of every scale and of the scaling part: 1 + the largest l
+    with a nonzero kernel (kappa^j(l) > 0, resp. Phi_l > 0); W^j and W^Phi are
+    band-limited there, so the DH grid of that band-limit samples them
+    exactly (at least 1)."""
+    psi, phi = kern if kern is not None else kernels(L, N, lam, J0)
+    Ls = []
+    for j in range(psi.shape[0]):
+        nz = np.nonzero(np.abs(psi[j]).max(axis=1) > 0)[0]
+        Ls.append(int(nz[-1]) + 1 if nz.size else 1)
+    nz = np.nonzero(phi > 0)[0]
+    return Ls, (int(nz[-1]) + 1 if nz.size else 1)
+
+
+def analysis_multires(flm, L: int, N: int, lam: float, J0: int, kern=None):
+    """W^j on the SO(3) grid of its own band-limit L_j and W^Phi on the sphere
+    grid of L_Phi: the sums of Eq. (20) / Eq. (3) (analysis_rows) with only the
+    l < L_j that carry kernel weight.  Returns ([W^j: [N][2L_j][2L_j-1]],
+    W^Phi: [2L_Phi][2L_Phi-1])."""
+    psi, phi = kern if kern is not None else kernels(L, N, lam, J0)
+    Ls, Lp = band_limits(L, N, lam, J0, (psi, phi))
+    flm = np.asarray(flm, np.complex128)
+    Ws = []
+    for j, Lj in enumerate(Ls):
+        W, _, _ = analysis_rows(flm[:Lj * Lj], Lj, N, lam, J0, range(2 * Lj),
+                                (psi[j:j + 1, :Lj], np.zeros(Lj)))
+        Ws.append(W[0])
+    _, Wphi, _ = analysis_rows(flm[:Lp * Lp], Lp, N, lam, J0, range(2 * Lp),
+                               (psi[:0, :Lp], phi[:Lp]))
+    return Ws, Wphi
+
+
+def synthesis_multires(Ws, Wphi, L: int, N: int, lam: float, J0: int, kern=None):
+    """f_lm from multi-resolution coefficients: the synthesis of Eqs. (32)-(33)
+    and (41) with each scale's integrals evaluated by the quadrature of its own
+    grid (exact, the integrands being band-limited to L_j)."""
+    psi, phi = kern if kern is not None else kernels(L, N, lam, J0)
+    Ls, Lp = band_limits(L, N, lam, J0, (psi, phi))
+    out = np.zeros(L * L, dtype=np.complex128)
+    for j, Lj in enumerate(Ls):
+        fj = synthesis(np.asarray(Ws[j])[None], np.zeros((2 * Lj, 2 * Lj - 1)), Lj, N, lam, J0,
+                       (psi[j:j + 1, :Lj], np.zeros(Lj)))
+        out[:Lj * Lj] += fj
+    fs = synthesis(np.zeros((0, N, 2 * Lp, 2 * Lp - 1)), Wphi, Lp, N, lam, J0, (psi[:0, :Lp], phi[:Lp]))
+    out[:Lp * Lp] += fs
+    return out

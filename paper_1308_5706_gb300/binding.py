@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libs2dw.so")
 
 S2DW_OK, S2DW_EINVAL, S2DW_ENOMEM, S2DW_ECUDA, S2DW_ETIMEOUT, S2DW_EBUSY, S2DW_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-S2DW_FP64, S2DW_MIXED, S2DW_REAL_SIGNAL = 1, 2, 4
+S2DW_FP64, S2DW_MIXED, S2DW_REAL_SIGNAL, S2DW_MULTIRES = 1, 2, 4, 8
 
 _lib = None
 
@@ -31,6 +31,7 @@ _SIGNATURES = {
     "s2dw_plan_destroy": (_c_i, [_c_p]),
     "s2dw_query": (_c_i, [_c_p, _c_ip, _c_i64p, _c_i64p, _c_i64p, _c_i64p]),
     "s2dw_launch_counts": (_c_i, [_c_p, _c_ip, _c_ip]),
+    "s2dw_scale_grid": (_c_i, [_c_p, _c_i, _c_ip, _c_i64p, _c_i64p]),
     "s2dw_steer": (_c_i, [_c_p, _c_p, _c_dp, _c_i, _c_p, _c_p]),
     "s2dw_sht_inverse": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
     "s2dw_sht_forward": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
@@ -141,6 +142,13 @@ def s2dw_sht_forward(plan: int, fpix, flm, stream=None) -> None:
     _check(lib().s2dw_sht_forward(plan, _ptr(fpix), _ptr(flm), _stream(stream)), "s2dw_sht_forward")
 
 
+def s2dw_scale_grid(plan: int, j: int):
+    """(band-limit Lg, element offset in W, element count) of scale j's grid."""
+    Lg, off, n = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().s2dw_scale_grid(plan, j, ctypes.byref(Lg), ctypes.byref(off), ctypes.byref(n)), "s2dw_scale_grid")
+    return Lg.value, off.value, n.value
+
+
 def s2dw_launch_counts(plan: int):
     """(analysis, synthesis) kernel launches issued by one call of the plan."""
     a, s = ctypes.c_int(), ctypes.c_int()
@@ -233,16 +241,22 @@ class Plan:
     float32 W).  Buffers are torch CUDA tensors; see ``alloc_*``.
     """
 
-    def __init__(self, L: int, N: int, lam: float = 2.0, J0: int = 0, precision: str = "mixed"):
+    def __init__(self, L: int, N: int, lam: float = 2.0, J0: int = 0, precision: str = "mixed",
+                 multires: bool = False):
         flags = (S2DW_FP64 if precision == "fp64" else S2DW_MIXED) | S2DW_REAL_SIGNAL
+        if multires:
+            flags |= S2DW_MULTIRES
         if precision not in ("fp64", "mixed"):
             raise ValueError(precision)
         self.L, self.N, self.lam, self.J0, self.precision = L, N, float(lam), J0, precision
+        self.multires = bool(multires)
         self.handle = s2dw_plan(L, N, lam, J0, flags)
         q = s2dw_query(self.handle)
         self.J = q["J"]
         self.nscale = self.J + 1
         self.info = q
+        # (band-limit, offset, elements) of every scale's grid; last: scaling part
+        self.grids = [s2dw_scale_grid(self.handle, j) for j in range(self.nscale + 1)]
 
     def close(self):
         if getattr(self, "handle", None):
@@ -258,11 +272,22 @@ class Plan:
     # shapes and dtypes
     @property
     def w_shape(self):
+        if self.multires:  # the scales one after the other, each [N][2Lg][2Lg-1]
+            Lg, off, n = self.grids[self.nscale - 1]
+            return (off + n,)
         return (self.nscale, self.N, 2 * self.L, 2 * self.L - 1)
 
     @property
     def wphi_shape(self):
-        return (2 * self.L, 2 * self.L - 1)
+        Lg = self.grids[self.nscale][0]
+        return (2 * Lg, 2 * Lg - 1)
+
+    def w_scale(self, W, j):
+        """View of scale j of W as [N][2Lg][2Lg-1]."""
+        if not self.multires:
+            return W[j]
+        Lg, off, n = self.grids[j]
+        return W[off:off + n].view(self.N, 2 * Lg, 2 * Lg - 1)
 
     def torch_dtypes(self):
         import torch
@@ -298,7 +323,9 @@ class Plan:
         import torch
         ng = len(np.atleast_1d(gammas))
         if out is None:
-            out = torch.empty((self.J + 1, ng, 2 * self.L, 2 * self.L - 1), dtype=W.dtype, device=W.device)
+            shape = ((self.w_shape[0] // self.N) * ng,) if self.multires else \
+                (self.J + 1, ng, 2 * self.L, 2 * self.L - 1)
+            out = torch.empty(shape, dtype=W.dtype, device=W.device)
         s2dw_steer(self.handle, W, gammas, out, stream)
         return out
 

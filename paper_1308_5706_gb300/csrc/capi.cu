@@ -213,15 +213,23 @@ struct s2dw_plan_s {
   void* P = nullptr;
   void* Pphi = nullptr;
   int nbr = 0, nbr_phi = 0, Lp = 0, Lp32 = 0, Lphip = 0, Lphip32 = 0;
-  void* tw = nullptr;
-  void* chirp_a = nullptr;
-  void* pre_b = nullptr;
-  void* post_b = nullptr;
-  void* preS_b = nullptr;
-  void* postS_b = nullptr;
-  void* root_a = nullptr;  // e^{2 pi i t/(2L-1)}
-  void* bfft = nullptr;    // e^{i pi m'/(4L)} (|m'| < L), then q_b (b < 2L): single-FFT beta
-  void* Hs = nullptr;      // 4 x M spectra
+  // Tables of one sampling grid (band-limit Lg: 2Lg beta, 2Lg-1 alpha samples).
+  struct GridTables {
+    int L = 0, logM = 0, M = 0;
+    void* tw = nullptr;
+    void* chirp_a = nullptr;
+    void* pre_b = nullptr;
+    void* post_b = nullptr;
+    void* preS_b = nullptr;
+    void* postS_b = nullptr;
+    void* root_a = nullptr;  // e^{2 pi i t/(2Lg-1)}
+    void* bfft = nullptr;    // e^{i pi m'/(4Lg)} (|m'| < Lg), then q_b (b < 2Lg): single-FFT beta
+    void* Hs = nullptr;      // 4 x M spectra
+  };
+  bool multires = false;       // every scale on the grid of its own band-limit
+  std::vector<GridTables> gt;  // one set per distinct grid band-limit
+  std::vector<int> grid_of;    // [nscale + 1]: set of scale j (last: scaling part)
+  std::vector<int64_t> woff;   // [nscale + 1]: element offset of scale j in W (last: total)
   // host copies of the static descriptors (device copies live in `own`)
   std::vector<unsigned char> desc_w_host, desc_phi_host;
   std::vector<TileTask> tiles_w_host, tiles_phi_host;
@@ -357,25 +365,25 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
                                                          : kind;
   const bool direct_list = kind == CZT_ALPHA_ANA_DIRECT || kind == CZT_ALPHA_SYN_DIRECT;
   const bool fft_list = kind == CZT_BETA_ANA_FFT || kind == CZT_BETA_SYN_FFT;
-  const int L = p->L, n = 2 * L - 1;
-  const bool beta_fft = (4 * L == p->M);
-  if ((base_kind == CZT_BETA_ANA || base_kind == CZT_BETA_SYN) && beta_fft != fft_list) return;
-  const int64_t wscale = (int64_t)p->N * 2 * L * n;
-  const cx<T>* Hs = reinterpret_cast<const cx<T>*>(p->Hs);
   for (int j = 0; j <= p->nscale; ++j) {
     const bool phi = (j == p->nscale);
     const int Nj = phi ? 1 : p->N;
     const int Lj = p->Ycols[j];
+    const s2dw_plan_s::GridTables& G = p->gt[p->grid_of[j]];
+    const int L = G.L, n = 2 * L - 1;  // this scale's sampling grid
+    const bool beta_fft = (4 * L == G.M);
+    if ((base_kind == CZT_BETA_ANA || base_kind == CZT_BETA_SYN) && beta_fft != fft_list) continue;
+    const cx<T>* Hs = reinterpret_cast<const cx<T>*>(G.Hs);
     CztSeg<T> s;
     std::memset(&s, 0, sizeof(s));
     s.job = job;
     s.L = L;
     s.Lj = Lj;
     s.N = Nj;
-    s.logM = p->logM;
-    s.woff = phi ? 0 : (int64_t)j * wscale;
+    s.logM = G.logM;
+    s.woff = phi ? 0 : p->woff[j];
     s.is_phi = phi ? 1 : 0;
-    s.tw = reinterpret_cast<const cx<T>*>(p->tw);
+    s.tw = reinterpret_cast<const cx<T>*>(G.tw);
     s.scale = (T)(2.0 * 3.14159265358979323846 / n);
     const bool is_alpha = base_kind == CZT_ALPHA_ANA || base_kind == CZT_ALPHA_SYN;
     const bool direct = is_alpha && Lj <= kDirectMaxLj;
@@ -385,41 +393,41 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
         s.items = Nj * Lj;
         s.buf_in = reinterpret_cast<cx<T>*>(p->Y[j]);
         s.buf_out = reinterpret_cast<cx<T>*>(p->X[j]);
-        s.H = Hs + 0 * (size_t)p->M;
-        s.pre = reinterpret_cast<const cx<T>*>(p->pre_b);
-        s.post = reinterpret_cast<const cx<T>*>(p->post_b);
+        s.H = Hs + 0 * (size_t)G.M;
+        s.pre = reinterpret_cast<const cx<T>*>(G.pre_b);
+        s.post = reinterpret_cast<const cx<T>*>(G.post_b);
         break;
       case CZT_ALPHA_ANA:
         s.items = (Nj * L + alpha_czt_nt(sizeof(T) == 8) - 1) / alpha_czt_nt(sizeof(T) == 8);
         s.buf_in = reinterpret_cast<cx<T>*>(p->X[j]);
-        s.H = Hs + 1 * (size_t)p->M;
-        s.pre = reinterpret_cast<const cx<T>*>(p->chirp_a);
-        s.post = reinterpret_cast<const cx<T>*>(p->chirp_a);
+        s.H = Hs + 1 * (size_t)G.M;
+        s.pre = reinterpret_cast<const cx<T>*>(G.chirp_a);
+        s.post = reinterpret_cast<const cx<T>*>(G.chirp_a);
         break;
       case CZT_ALPHA_SYN:
         s.items = (Nj * L + alpha_czt_nt(sizeof(T) == 8) - 1) / alpha_czt_nt(sizeof(T) == 8);
         s.buf_out = reinterpret_cast<cx<T>*>(p->X[j]);
-        s.H = Hs + 2 * (size_t)p->M;
-        s.pre = reinterpret_cast<const cx<T>*>(p->chirp_a);
-        s.post = reinterpret_cast<const cx<T>*>(p->chirp_a);
+        s.H = Hs + 2 * (size_t)G.M;
+        s.pre = reinterpret_cast<const cx<T>*>(G.chirp_a);
+        s.post = reinterpret_cast<const cx<T>*>(G.chirp_a);
         break;
       case CZT_BETA_SYN:
         s.items = Nj * Lj;
         s.buf_in = reinterpret_cast<cx<T>*>(p->X[j]);
         s.buf_out = reinterpret_cast<cx<T>*>(p->Y[j]);
-        s.H = Hs + 3 * (size_t)p->M;
-        s.pre = reinterpret_cast<const cx<T>*>(p->preS_b);
-        s.post = reinterpret_cast<const cx<T>*>(p->postS_b);
+        s.H = Hs + 3 * (size_t)G.M;
+        s.pre = reinterpret_cast<const cx<T>*>(G.preS_b);
+        s.post = reinterpret_cast<const cx<T>*>(G.postS_b);
         break;
     }
     if (fft_list) {
-      s.pre = reinterpret_cast<const cx<T>*>(p->bfft);
-      s.post = reinterpret_cast<const cx<T>*>(p->bfft) + (2 * L - 1);
+      s.pre = reinterpret_cast<const cx<T>*>(G.bfft);
+      s.post = reinterpret_cast<const cx<T>*>(G.bfft) + (2 * L - 1);
     }
     if (direct) {
       const int rows = (base_kind == CZT_ALPHA_ANA) ? kDirectRowsAna : direct_rows_syn(sizeof(T) == 8);
       s.items = (Nj * 2 * L + rows - 1) / rows;
-      s.pre = reinterpret_cast<const cx<T>*>(p->root_a);
+      s.pre = reinterpret_cast<const cx<T>*>(G.root_a);
     }
     if (s.items <= 0) continue;
     s.start = start;
@@ -585,7 +593,7 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
 template <typename T>
 void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, const double* sabs_d,
                       const double* q_d, cudaStream_t st) {
-  const int L = p->L, N = p->N, n = 2 * L - 1, M = p->M;
+  const int L = p->L, N = p->N;
   // ---- workspace layout ----
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -600,19 +608,25 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     const int Nj = (j == p->nscale) ? 1 : N;
     const int Lj = p->Ycols[j];
     o_Y[j] = take((size_t)Nj * Lj * Lj * sizeof(cx<T>));
-    o_X[j] = take((size_t)Nj * 2 * L * Lj * sizeof(cx<T>));
+    o_X[j] = take((size_t)Nj * 2 * p->gt[p->grid_of[j]].L * Lj * sizeof(cx<T>));
   }
   const size_t o_P = take((size_t)p->nbr * L * p->Lp32 * sizeof(cx<T>));
   const size_t o_Pphi = take((size_t)p->nbr_phi * p->Lphi * p->Lphip32 * sizeof(cx<T>));
-  const size_t o_tw = take((size_t)M * sizeof(cx<T>));
-  const size_t o_ca = take((size_t)n * sizeof(cx<T>));
-  const size_t o_pb = take((size_t)(2 * L - 1) * sizeof(cx<T>));
-  const size_t o_qb = take((size_t)2 * L * sizeof(cx<T>));
-  const size_t o_pS = take((size_t)2 * L * sizeof(cx<T>));
-  const size_t o_qS = take((size_t)(2 * L - 1) * sizeof(cx<T>));
-  const size_t o_root = take((size_t)n * sizeof(cx<T>));
-  const size_t o_bf = take((size_t)(4 * L - 1) * sizeof(cx<T>));
-  const size_t o_H = take((size_t)4 * M * sizeof(cx<T>));
+  // per grid: twiddles, chirps, roots, beta phases and weights, spectra
+  struct GridOff { size_t tw, ca, pb, qb, pS, qS, root, bf, H; };
+  std::vector<GridOff> go(p->gt.size());
+  for (size_t g = 0; g < p->gt.size(); ++g) {
+    const int Lg = p->gt[g].L, ng = 2 * Lg - 1, Mg = p->gt[g].M;
+    go[g].tw = take((size_t)Mg * sizeof(cx<T>));
+    go[g].ca = take((size_t)ng * sizeof(cx<T>));
+    go[g].pb = take((size_t)(2 * Lg - 1) * sizeof(cx<T>));
+    go[g].qb = take((size_t)2 * Lg * sizeof(cx<T>));
+    go[g].pS = take((size_t)2 * Lg * sizeof(cx<T>));
+    go[g].qS = take((size_t)(2 * Lg - 1) * sizeof(cx<T>));
+    go[g].root = take((size_t)ng * sizeof(cx<T>));
+    go[g].bf = take((size_t)(4 * Lg - 1) * sizeof(cx<T>));
+    go[g].H = take((size_t)4 * Mg * sizeof(cx<T>));
+  }
   p->ws_bytes = off;
   amalloc(&p->ws, off, st);
   char* b = reinterpret_cast<char*>(p->ws);
@@ -626,15 +640,18 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   }
   p->P = b + o_P;
   p->Pphi = b + o_Pphi;
-  p->tw = b + o_tw;
-  p->chirp_a = b + o_ca;
-  p->pre_b = b + o_pb;
-  p->post_b = b + o_qb;
-  p->preS_b = b + o_pS;
-  p->postS_b = b + o_qS;
-  p->root_a = b + o_root;
-  p->bfft = b + o_bf;
-  p->Hs = b + o_H;
+  for (size_t g = 0; g < p->gt.size(); ++g) {
+    auto& G = p->gt[g];
+    G.tw = b + go[g].tw;
+    G.chirp_a = b + go[g].ca;
+    G.pre_b = b + go[g].pb;
+    G.post_b = b + go[g].qb;
+    G.preS_b = b + go[g].pS;
+    G.postS_b = b + go[g].qS;
+    G.root_a = b + go[g].root;
+    G.bfft = b + go[g].bf;
+    G.Hs = b + go[g].H;
+  }
 
   // ---- R tables ----
   std::vector<int> slot_w((size_t)L * 2, -1), slot_p(p->Lphi, 0);
@@ -649,41 +666,53 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   ck(launch_rtable<T>(reinterpret_cast<T*>(p->RS), p->tab->d64, kap_d, sabs_d, slot_d, L, p->Lp, N, 2, L, st));
   ck(launch_rtable<T>(reinterpret_cast<T*>(p->RSphi), p->tab->d64, phi_d, nullptr, slot_d + slot_w.size(), p->Lphi,
                       p->Lphip, 1, 1, L, st));
-  // ---- chirp tables (float64, then the working precision) ----
-  const size_t n64 = (size_t)M + n + (2 * L - 1) + 2 * L + 2 * L + (2 * L - 1) + n + (4 * L - 1) + 4 * (size_t)M;
+  // ---- chirp tables of every grid (float64, then the working precision) ----
   double2* t64 = nullptr;
-  amalloc(&t64, n64 * sizeof(double2), st);
-  double2* tw64 = t64;
-  double2* ca64 = tw64 + M;
-  double2* pb64 = ca64 + n;
-  double2* qb64 = pb64 + (2 * L - 1);
-  double2* pS64 = qb64 + 2 * L;
-  double2* qS64 = pS64 + 2 * L;
-  double2* rt64 = qS64 + (2 * L - 1);
-  double2* bf64 = rt64 + n;
-  double2* H64 = bf64 + (4 * L - 1);
-  ck(launch_chirp_build64(tw64, ca64, pb64, qb64, pS64, qS64, rt64, bf64, H64, q_d, L, p->logM, st));
-  if (sizeof(T) == sizeof(double)) {
-    ck(cudaMemcpyAsync(p->tw, tw64, (size_t)M * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    ck(cudaMemcpyAsync(p->chirp_a, ca64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    ck(cudaMemcpyAsync(p->pre_b, pb64, (size_t)(2 * L - 1) * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    ck(cudaMemcpyAsync(p->post_b, qb64, (size_t)2 * L * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    ck(cudaMemcpyAsync(p->preS_b, pS64, (size_t)2 * L * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    ck(cudaMemcpyAsync(p->postS_b, qS64, (size_t)(2 * L - 1) * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    ck(cudaMemcpyAsync(p->root_a, rt64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    ck(cudaMemcpyAsync(p->bfft, bf64, (size_t)(4 * L - 1) * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    ck(cudaMemcpyAsync(p->Hs, H64, (size_t)4 * M * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  } else {
-    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->tw), tw64, M, st));
-    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->chirp_a), ca64, n, st));
-    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->pre_b), pb64, 2 * L - 1, st));
-    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->post_b), qb64, 2 * L, st));
-    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->preS_b), pS64, 2 * L, st));
-    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->postS_b), qS64, 2 * L - 1, st));
-    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->root_a), rt64, n, st));
-    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->bfft), bf64, 4 * L - 1, st));
-    ck(launch_to_prec<float>(reinterpret_cast<float2*>(p->Hs), H64, (int64_t)4 * M, st));
+  double* qg = nullptr;
+  {
+    size_t need = 0;
+    for (const auto& G : p->gt) {
+      const size_t Lg = G.L, ng = 2 * Lg - 1;
+      need = std::max(need, (size_t)G.M + ng + (2 * Lg - 1) + 2 * Lg + 2 * Lg + (2 * Lg - 1) + ng + (4 * Lg - 1) +
+                                4 * (size_t)G.M);
+    }
+    amalloc(&t64, need * sizeof(double2), st);
+    amalloc(&qg, (size_t)2 * p->gt.back().L * sizeof(double), st);
   }
+  for (auto& G : p->gt) {
+    const int Lg = G.L, ng = 2 * Lg - 1, Mg = G.M;
+    double2* tw64 = t64;
+    double2* ca64 = tw64 + Mg;
+    double2* pb64 = ca64 + ng;
+    double2* qb64 = pb64 + (2 * Lg - 1);
+    double2* pS64 = qb64 + 2 * Lg;
+    double2* qS64 = pS64 + 2 * Lg;
+    double2* rt64 = qS64 + (2 * Lg - 1);
+    double2* bf64 = rt64 + ng;
+    double2* H64 = bf64 + (4 * Lg - 1);
+    const double* q_g = q_d;  // the plan's own grid reuses its weights
+    if (Lg != L) {
+      ck(launch_dh_weights(qg, Lg, st));
+      q_g = qg;
+    }
+    ck(launch_chirp_build64(tw64, ca64, pb64, qb64, pS64, qS64, rt64, bf64, H64, q_g, Lg, G.logM, st));
+    auto put = [&](void* dst, const double2* src, int64_t cnt) {
+      if (sizeof(T) == sizeof(double))
+        ck(cudaMemcpyAsync(dst, src, (size_t)cnt * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      else
+        ck(launch_to_prec<float>(reinterpret_cast<float2*>(dst), src, cnt, st));
+    };
+    put(G.tw, tw64, Mg);
+    put(G.chirp_a, ca64, ng);
+    put(G.pre_b, pb64, 2 * Lg - 1);
+    put(G.post_b, qb64, 2 * Lg);
+    put(G.preS_b, pS64, 2 * Lg);
+    put(G.postS_b, qS64, 2 * Lg - 1);
+    put(G.root_a, rt64, ng);
+    put(G.bfft, bf64, 4 * Lg - 1);
+    put(G.Hs, H64, (int64_t)4 * Mg);
+  }
+  afree(qg, st);
   afree(t64, st);
   afree(slot_d, st);
   ck(cudaStreamSynchronize(st));  // slot_w / slot_p host vectors are local
@@ -815,9 +844,37 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
     p->Lphip32 = round_up(p->Lphi, 32);
     p->nbr = (p->L0 + p->TMP - 1) / p->TMP;
     p->nbr_phi = (p->Lphi + p->TMP - 1) / p->TMP;
-    p->logM = 5;  // the radix-16 convolution engine needs M >= 32
-    while ((1 << p->logM) < 4 * L - 2) ++p->logM;
+    // sampling grid of every scale (last: the scaling part): the full grid of
+    // band-limit L, or with S2DW_MULTIRES the grid of the scale's own
+    // band-limit (1 + the last l with a nonzero kernel)
+    p->multires = (flags & S2DW_MULTIRES) != 0;
+    std::vector<int> Lg(p->nscale + 1);
+    for (int j = 0; j < p->nscale; ++j) Lg[j] = p->multires ? std::max(1, p->Lj[j]) : L;
+    Lg[p->nscale] = p->multires ? p->Lphi : L;
+    std::vector<int> uniq(Lg);
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    p->gt.resize(uniq.size());
+    p->logM = 0;
+    for (size_t g = 0; g < uniq.size(); ++g) {
+      auto& G = p->gt[g];
+      G.L = uniq[g];
+      G.logM = 5;  // the radix-16 convolution engine needs M >= 32
+      while ((1 << G.logM) < 4 * G.L - 2) ++G.logM;
+      G.M = 1 << G.logM;
+      p->logM = std::max(p->logM, G.logM);
+    }
     p->M = 1 << p->logM;
+    p->grid_of.resize(p->nscale + 1);
+    for (int j = 0; j <= p->nscale; ++j)
+      p->grid_of[j] = (int)(std::lower_bound(uniq.begin(), uniq.end(), Lg[j]) - uniq.begin());
+    p->woff.resize(p->nscale + 1);
+    int64_t wacc = 0;
+    for (int j = 0; j < p->nscale; ++j) {
+      p->woff[j] = wacc;
+      wacc += (int64_t)N * 2 * Lg[j] * (2 * Lg[j] - 1);
+    }
+    p->woff[p->nscale] = wacc;
     p->tab = delta_acquire(L, st);
     if (p->fp64) plan_build_typed<double>(p, kap, phi, sabs, q, st);
     else plan_build_typed<float>(p, kap, phi, sabs, q, st);
@@ -879,7 +936,7 @@ int s2dw_plan(s2dw_plan_t* out, int L, int N, double lambda, int J0, unsigned fl
   *out = nullptr;
   const unsigned prec = flags & (S2DW_FP64 | S2DW_MIXED);
   if (prec != S2DW_FP64 && prec != S2DW_MIXED) return S2DW_EINVAL;
-  if (flags & ~(unsigned)(S2DW_FP64 | S2DW_MIXED | S2DW_REAL_SIGNAL)) return S2DW_EINVAL;
+  if (flags & ~(unsigned)(S2DW_FP64 | S2DW_MIXED | S2DW_REAL_SIGNAL | S2DW_MULTIRES)) return S2DW_EINVAL;
   if (L < 2 || L > 2048) return S2DW_EINVAL;
   if (N < 1 || N > 8 || N > L) return S2DW_EINVAL;
   if (!(lambda > 1.0) || !std::isfinite(lambda)) return S2DW_EINVAL;
@@ -901,14 +958,15 @@ int s2dw_query(s2dw_plan_t p, int* J, int64_t* w_elems_per_scale, int64_t* wphi_
                int64_t* total_device_bytes) {
   if (!p) return S2DW_EINVAL;
   const int64_t L = p->L, n = 2 * L - 1;
-  const int64_t wps = (int64_t)p->N * 2 * L * n, wph = 2 * L * n;
+  const int64_t wps = p->multires ? 0 : (int64_t)p->N * 2 * L * n;
+  const int64_t Lp = p->gt[p->grid_of[p->nscale]].L, wph = 2 * Lp * (2 * Lp - 1);
   const int64_t el = p->fp64 ? 8 : 4;
   if (J) *J = p->J;
   if (w_elems_per_scale) *w_elems_per_scale = wps;
   if (wphi_elems) *wphi_elems = wph;
   if (workspace_bytes) *workspace_bytes = (int64_t)p->ws_bytes;
   if (total_device_bytes)
-    *total_device_bytes = (int64_t)p->ws_bytes + (wps * p->nscale + wph) * el + L * L * 2 * el;
+    *total_device_bytes = (int64_t)p->ws_bytes + (p->woff[p->nscale] + wph) * el + L * L * 2 * el;
   return S2DW_OK;
 }
 
@@ -924,10 +982,23 @@ int s2dw_steer(s2dw_plan_t p, const void* W, const double* gammas, int ngamma, v
       for (int k = 0; k < N; ++k) z += std::cos((-(N - 1) + 2 * k) * x);
       sw.w[t][g] = z / N;
     }
-  const int64_t per_scale = (int64_t)2 * p->L * (2 * p->L - 1);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = p->fp64 ? launch_steer<double>(W, out, sw, p->nscale, N, ngamma, per_scale, st)
-                          : launch_steer<float>(W, out, sw, p->nscale, N, ngamma, per_scale, st);
+  const size_t el = p->fp64 ? sizeof(double) : sizeof(float);
+  cudaError_t e = cudaSuccess;
+  if (!p->multires) {
+    const int64_t per_scale = (int64_t)2 * p->L * (2 * p->L - 1);
+    e = p->fp64 ? launch_steer<double>(W, out, sw, p->nscale, N, ngamma, per_scale, st)
+                : launch_steer<float>(W, out, sw, p->nscale, N, ngamma, per_scale, st);
+  } else {
+    // scales of different grids: out holds [ngamma][2Lg][2Lg-1] per scale, in order
+    for (int j = 0; j < p->nscale && e == cudaSuccess; ++j) {
+      const int64_t Lg = p->gt[p->grid_of[j]].L, per_scale = 2 * Lg * (2 * Lg - 1);
+      const char* Wj = reinterpret_cast<const char*>(W) + (size_t)p->woff[j] * el;
+      char* Oj = reinterpret_cast<char*>(out) + (size_t)(p->woff[j] / N) * ngamma * el;
+      e = p->fp64 ? launch_steer<double>(Wj, Oj, sw, 1, N, ngamma, per_scale, st)
+                  : launch_steer<float>(Wj, Oj, sw, 1, N, ngamma, per_scale, st);
+    }
+  }
   return err_of(e);
 }
 
@@ -983,6 +1054,16 @@ int s2dw_sht_forward(s2dw_plan_t p, const void* fpix, void* flm, void* stream) {
   else run_synthesis<float>(c->own, ptrs, rj, 1, st);
   mark_use(c, st);
   return err_of(cudaGetLastError());
+}
+
+int s2dw_scale_grid(s2dw_plan_t p, int j, int* Lgrid, int64_t* offset, int64_t* elems) {
+  if (!p || j < 0 || j > p->nscale) return S2DW_EINVAL;
+  const int64_t Lg = p->gt[p->grid_of[j]].L;
+  const int64_t per = (j == p->nscale ? 1 : p->N) * 2 * Lg * (2 * Lg - 1);
+  if (Lgrid) *Lgrid = (int)Lg;
+  if (offset) *offset = (j == p->nscale) ? 0 : p->woff[j];
+  if (elems) *elems = per;
+  return S2DW_OK;
 }
 
 int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {
@@ -1211,7 +1292,8 @@ int s2dw_stage(s2dw_plan_t p, int stage, int j, void* host_out, int64_t* nbytes)
   const int Nj = (j == p->nscale) ? 1 : p->N;
   const int Lj = p->Ycols[j];
   const int64_t el = p->fp64 ? 16 : 8;
-  const int64_t bytes = (stage == 0 ? (int64_t)Nj * Lj * Lj : (int64_t)Nj * 2 * p->L * Lj) * el;
+  const int64_t Lg = p->gt[p->grid_of[j]].L;  // the scale's beta grid
+  const int64_t bytes = (stage == 0 ? (int64_t)Nj * Lj * Lj : (int64_t)Nj * 2 * Lg * Lj) * el;
   if (nbytes) *nbytes = bytes;
   if (!host_out) return S2DW_OK;
   cudaError_t e = cudaDeviceSynchronize();

@@ -320,6 +320,11 @@ cudaError_t launch_kernel_values(double* kap, double* phi, double* sabs, double2
   return cudaGetLastError();
 }
 
+cudaError_t launch_dh_weights(double* q, int L, cudaStream_t st) {
+  k_dh_weights<<<nblk(2 * L, 128), 128, 0, st>>>(q, L);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_delta_build(double* d64, float* d32, double* em, int* ee, int Lmax, cudaStream_t st) {
   k_delta_edge<<<nblk(Lmax, 128), 128, 0, st>>>(em, ee, Lmax);
   cudaError_t err = cudaGetLastError();

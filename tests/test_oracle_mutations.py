@@ -98,6 +98,7 @@ PINS = [
     lambda: P.test_steer_reproduces_samples(3),
     lambda: P.test_sht_round_trip_exact(9),
     lambda: P.test_sht_textbook_harmonics(1, 1),
+    lambda: P.test_multires_round_trip_exact(16, 3, 2.0, 0),
 ]
 
 

@@ -388,3 +388,34 @@ def test_sht_round_trip_exact(L):
     pix = O.sht_inverse(f, L)
     assert np.abs(pix.imag).max() < 1e-13          # real signal -> real samples
     assert np.abs(O.sht_forward(pix.real, L) - f).max() < 1e-13
+
+
+# ---- multi-resolution sampling ----
+
+@pytest.mark.parametrize("L,N,lam,J0", [(16, 3, 2.0, 0), (24, 2, 2.0, 1), (20, 1, 3.0, 0), (12, 4, 2.0, 0)])
+def test_multires_round_trip_exact(L, N, lam, J0):
+    f = flm_gaussian(L, 31, "unit")
+    Ws, Wphi = O.analysis_multires(f, L, N, lam, J0)
+    Ls, Lp = O.band_limits(L, N, lam, J0)
+    assert all(W.shape == (N, 2 * Lj, 2 * Lj - 1) for W, Lj in zip(Ws, Ls)) and Wphi.shape == (2 * Lp, 2 * Lp - 1)
+    assert np.abs(O.synthesis_multires(Ws, Wphi, L, N, lam, J0) - f).max() < 1e-12
+
+
+def test_multires_matches_full_resolution_on_shared_samples():
+    """alpha = 0 is on every grid; beta_b of band-limit L_j equals beta_{3b+1} of
+    band-limit 3 L_j, so a scale with L = 3 L_j shares those samples."""
+    L, N, lam, J0 = 24, 3, 2.0, 0
+    f = flm_gaussian(L, 41, "cl")
+    Ws, Wphi = O.analysis_multires(f, L, N, lam, J0)
+    W, Wp = O.analysis(f, L, N, lam, J0)
+    Ls, Lp = O.band_limits(L, N, lam, J0)
+    checked = 0
+    for j, Lj in enumerate(Ls):
+        if 3 * Lj == L:
+            b = np.arange(2 * Lj)
+            assert np.abs(Ws[j][:, b, 0] - W[j][:, 3 * b + 1, 0]).max() < 1e-13
+            checked += 1
+        if Lj == L:
+            assert np.abs(Ws[j] - W[j]).max() < 1e-13
+            checked += 1
+    assert checked >= 2
