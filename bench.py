@@ -454,6 +454,45 @@ def run_multires_workload(args):
     return 0
 
 
+def run_sht_workload(args):
+    """Inverse then forward spherical harmonic transform of the L=1024 signal
+    on the DH sphere grid (mixed), timed with CUDA events; error of the round
+    trip."""
+    import torch
+    from paper_1308_5706_gb300 import binding as B
+    pm = B.Plan(L, N, LAM, J0, "mixed")
+    f = torch.from_numpy(flm_gaussian(L, SEED, "cl")).to(torch.complex64).cuda()
+    pix = pm.alloc_pix()
+    g = pm.alloc_flm()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pm.sht_inverse(f, pix)
+        pm.sht_forward(pix, g)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ti = tf = 0.0
+    for _ in range(args.steps):
+        ev[0].record(stream)
+        pm.sht_inverse(f, pix)
+        ev[1].record(stream)
+        pm.sht_forward(pix, g)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        ti += ev[0].elapsed_time(ev[1])
+        tf += ev[1].elapsed_time(ev[2])
+    f0 = f.to(torch.complex128)
+    eps = float((g.to(torch.complex128) - f0).abs().max() / f0.abs().max())
+    out = {"metric": "spherical harmonic transform pairs/s (L=1024, DH grid, mixed)",
+           "value": args.steps / ((ti + tf) / 1e3), "unit": "pairs/s",
+           "ms_per_step": (ti + tf) / args.steps, "ms_inverse": ti / args.steps, "ms_forward": tf / args.steps,
+           "steps": args.steps, "warmup": args.warmup,
+           "config": {"workload": "L=1024 real Gaussian f_lm C_l=1/(l(l+1)), seed 2; 2048 x 2047 samples"},
+           "round_trip_eps": eps}
+    print(json.dumps(out))
+    pm.close()
+    return 0
+
+
 def run_steer_workload(args):
     """Steering (Eq. (10)) of the L=1024, N=5 mixed W to one arbitrary
     orientation per step: one pass over W (read) and out (write)."""
@@ -499,7 +538,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="roundtrip", choices=["roundtrip", "batch", "serve", "steer", "multires"])
+    ap.add_argument("--workload", default="roundtrip", choices=["roundtrip", "batch", "serve", "steer", "multires", "sht"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=300.0)
     args = ap.parse_args()
@@ -514,6 +553,8 @@ def main():
         return run_steer_workload(args)
     if args.workload == "multires":
         return run_multires_workload(args)
+    if args.workload == "sht":
+        return run_sht_workload(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

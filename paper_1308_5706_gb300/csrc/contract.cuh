@@ -23,8 +23,10 @@
 //
 // Data movement: per l, the tile's Delta block (stored rows m' x columns m,
 // and for tiles below the diagonal the stored rows m x columns m'), the 32
-// values f_lm and the R rows are copied by cp.async into a STAGES-deep ring
-// in shared memory, issued STAGES-1 iterations ahead; one barrier per l.
+// values f_lm and the R rows are copied by cp.async into a ring of S stages
+// (up to 8, as two CTAs per SM allow) in shared memory, issued S-2 stages
+// ahead; one barrier per two l (the barrier round trip, not arithmetic,
+// bounded a loop with one barrier per l).
 // Thread layout: 256 threads, each owning E consecutive rows m' and one
 // column m of a (8E x 32) tile.  Tiles with every row above every column map
 // lanes along m' so that their reads of the transposed block stay conflict free.
@@ -36,7 +38,8 @@
 
 namespace s2dw {
 
-constexpr int STAGES = 4;
+constexpr int kMaxStages = 8;
+constexpr size_t kCtaSmemBudget = 112 * 1024;  // two CTAs per SM (228 KB, 1 KB reserved each)
 
 
 // E consecutive values from 16-byte aligned shared memory.
@@ -102,15 +105,27 @@ struct StageGeom {
   static constexpr size_t BYTES = (size_t)SIZE * sizeof(T);
 };
 
+template <typename T, bool SYN>
+__host__ __device__ constexpr size_t contract_red_bytes() {
+  return SYN ? 2 * LCH * 8 * TILE * sizeof(cx<T>) : 0;
+}
+// ring depth: as many stages as fit next to the reduction buffer (4..8, even)
 template <typename T, int N, int NSLOT, bool SYN, int E>
-constexpr size_t contract_smem_bytes() {
-  return STAGES * StageGeom<T, N, NSLOT, E>::BYTES + (SYN ? 2 * LCH * 8 * TILE * sizeof(cx<T>) : 0);
+__host__ __device__ constexpr int contract_stages() {
+  const size_t fit = (kCtaSmemBudget - contract_red_bytes<T, SYN>()) / StageGeom<T, N, NSLOT, E>::BYTES;
+  const int s = fit > (size_t)kMaxStages ? kMaxStages : (fit < 4 ? 4 : (int)fit);
+  return s & ~1;
+}
+template <typename T, int N, int NSLOT, bool SYN, int E>
+__host__ __device__ constexpr size_t contract_smem_bytes() {
+  return contract_stages<T, N, NSLOT, SYN, E>() * StageGeom<T, N, NSLOT, E>::BYTES + contract_red_bytes<T, SYN>();
 }
 
 template <typename T, int N, int NSLOT, bool SYN, int E>
 __global__ void __launch_bounds__(256)
 k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict__ tiles, CallPtrs ptrs) {
   using G = StageGeom<T, N, NSLOT, E>;
+  constexpr int STAGES = contract_stages<T, N, NSLOT, SYN, E>();
   constexpr int RG = 8;
   constexpr int TMP = G::TMP;
   constexpr int EPC = G::EPC;
@@ -216,7 +231,7 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   };
 
 #pragma unroll
-  for (int i = 0; i < STAGES - 1; ++i) issue(i);
+  for (int i = 0; i < STAGES - 2; ++i) issue(i);
 
   constexpr bool PACK = std::is_same<T, float>::value && E == 4;
   Acc<T, E, NSLOT, N, PACK> acc;
@@ -287,12 +302,9 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   };
 
   __syncthreads();  // cgk visible
-  for (int l = l_start; l <= l_end; ++l) {
-    const int it = l - l_start;
-    cp_async_wait<STAGES - 2>();
-    __syncthreads();
-    issue((it + STAGES - 1) % STAGES);
-    if (SYN && it > 0 && (it % LCH) == 0) reduce_chunk(rbuf ^ 1, l - LCH, LCH);
+  // Two l per barrier: stages it, it+1 are waited for together and stages
+  // it+S-2, it+S-1 are issued into the slots that l-2, l-1 have released.
+  auto process = [&](const int l, const int it) {
     // slot occupancy changes at segment boundaries
     if (l > seg_hi) {
       while (D->seg[sidx].hi < l) ++sidx;
@@ -417,6 +429,16 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
       red[((size_t)rbuf * LCH + lc) * RG * TILE + rg * TILE + c] = part;
       if (lc == LCH - 1) rbuf ^= 1;
     }
+  };
+  const int n_it = l_end - l_start + 1;
+  for (int it = 0; it < n_it; it += 2) {
+    cp_async_wait<STAGES - 4>();
+    __syncthreads();
+    issue((it + STAGES - 2) % STAGES);
+    issue((it + STAGES - 1) % STAGES);
+    if (SYN && it > 0 && (it % LCH) == 0) reduce_chunk(rbuf ^ 1, l_start + it - LCH, LCH);
+    process(l_start + it, it);
+    if (it + 1 < n_it) process(l_start + it + 1, it + 1);
   }
   cp_async_wait<0>();
   if (SYN) {
