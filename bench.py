@@ -266,10 +266,8 @@ def beta_flops(plan) -> float:
 # DRAM bytes per launch (read + write) of kernels captured with ncu on this
 # workload; None once the kernel has changed since the capture.
 NCU_TRAFFIC = {
-    "syn_alpha_czt": (0.503252e9 + 0.244352e9, "profiles/k_czt_alpha_L1024_N5.md"),
-    "ana_alpha_czt": (0.246607e9 + 0.465727e9, "profiles/k_czt_alpha_L1024_N5.md"),
-    "ana_contract": (1.089100e9 + 0.068842e9, "profiles/k_contract_L1024_N5.md"),
-    "syn_contract": (1.386839e9 + 0.092072e9, "profiles/k_contract_L1024_N5.md"),
+    "syn_alpha_czt": (0.503277e9 + 0.242538e9, "profiles/k_czt_alpha_L1024_N5.md"),
+    "ana_alpha_czt": (0.246671e9 + 0.459426e9, "profiles/k_czt_alpha_L1024_N5.md"),
 }
 
 
