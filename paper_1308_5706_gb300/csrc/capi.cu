@@ -421,6 +421,8 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
         break;
     }
     if (fft_list) {
+      const int ntb = beta_fft_nt(sizeof(T) == 8);
+      s.items = Nj * ((Lj + ntb - 1) / ntb);
       s.pre = reinterpret_cast<const cx<T>*>(G.bfft);
       s.post = reinterpret_cast<const cx<T>*>(G.bfft) + (2 * L - 1);
     }

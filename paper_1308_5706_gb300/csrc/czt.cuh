@@ -228,55 +228,95 @@ __global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restric
 // are one FFT each instead of a chirp-z convolution (two FFTs).
 // pre: e^{i pi m'/(4L)} at index m' + L - 1; post: q_b (real part), b < 2L.
 // ---------------------------------------------------------------------------
+// A CTA transforms NT adjacent columns m0.. of one gamma sample (FP32: two),
+// so the strided column reads and writes move NT complex values at a time.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_beta_ana_fft(const CztSeg<T>* __restrict__ segs, int nseg) {
+__global__ void __launch_bounds__(256, 2) k_beta_ana_fft(const CztSeg<T>* __restrict__ segs,
+                                                                              int nseg) {
+  constexpr int NT = beta_fft_nt(sizeof(T) == 8);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
   const int item = blockIdx.x - sg.start;
-  const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM;
-  const int g = item / Lj, m = item % Lj;
-  const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
-  for (int i = threadIdx.x; i < fft_smem_elems(M); i += blockDim.x) A[i] = mkc<T>(0, 0);
+  const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM, ST = fft_smem_elems(M);
+  const int per_g = (Lj + NT - 1) / NT;
+  const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
+  for (int i = threadIdx.x; i < NT * ST; i += blockDim.x) A[i] = mkc<T>(0, 0);
   __syncthreads();
-  const cx<T>* __restrict__ Y = sg.buf_in + ((size_t)g * Lj + m) * Lj;  // Y_g[m][.], m' fastest
   const cx<T>* __restrict__ tb = sg.pre + (L - 1);
-  for (int mp = threadIdx.x - (Lj - 1); mp < Lj; mp += blockDim.x) {
-    cx<T> y = Y[mp < 0 ? -mp : mp];
-    if (mp < 0) y = cscale<T>(y, sigma);
-    A[fpad(fft_pos(mp & (M - 1), logM))] = cmul<T>(y, __ldg(tb + mp));
+  for (int t = 0; t < nt; ++t) {
+    const int m = m0 + t;
+    const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
+    const cx<T>* __restrict__ Y = sg.buf_in + ((size_t)g * Lj + m) * Lj;  // Y_g[m][.], m' fastest
+    for (int mp = threadIdx.x - (Lj - 1); mp < Lj; mp += blockDim.x) {
+      cx<T> y = Y[mp < 0 ? -mp : mp];
+      if (mp < 0) y = cscale<T>(y, sigma);
+      A[t * ST + fpad(fft_pos(mp & (M - 1), logM))] = cmul<T>(y, __ldg(tb + mp));
+    }
   }
   __syncthreads();
-  cx<T>* __restrict__ X = sg.buf_out + (size_t)g * 2 * L * Lj + m;
-  fft_inverse_to<T>(A, logM, sg.tw, [&](int v, cx<T> val) {
-    if (v < 2 * L) X[(size_t)v * Lj] = val;
+  cx<T>* __restrict__ X = sg.buf_out + (size_t)g * 2 * L * Lj + m0;
+  const bool pair = (NT == 2) && (nt == 2) && (Lj % 2 == 0);  // 16-byte aligned column pairs
+  fft_inverse_to_n<T, NT>(A, ST, logM, sg.tw, [&](int v, const cx<T>* y) {
+    if (v < 2 * L) {
+      if (pair) {
+        *reinterpret_cast<float4*>(X + (size_t)v * Lj) = *reinterpret_cast<const float4*>(y);
+      } else {
+        for (int t = 0; t < nt; ++t) X[(size_t)v * Lj + t] = y[t];
+      }
+    }
   });
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_beta_syn_fft(const CztSeg<T>* __restrict__ segs, int nseg) {
+__global__ void __launch_bounds__(256, 2) k_beta_syn_fft(const CztSeg<T>* __restrict__ segs,
+                                                                              int nseg) {
+  constexpr int NT = beta_fft_nt(sizeof(T) == 8);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
   const int item = blockIdx.x - sg.start;
-  const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM;
-  const int g = item / Lj, m = item % Lj;
-  const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
-  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * 2 * L * Lj + m;  // column m of V_g[b][m]
+  const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM, ST = fft_smem_elems(M);
+  const int per_g = (Lj + NT - 1) / NT;
+  const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
+  const bool pair = (NT == 2) && (nt == 2) && (Lj % 2 == 0);
+  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * 2 * L * Lj + m0;  // columns m0.. of V_g[b][m]
   const cx<T>* __restrict__ q = sg.post;
-  fft_forward_from<T>(A, logM, sg.tw, [&](int v) -> cx<T> {
-    if (v >= 2 * L) return mkc<T>(0, 0);
-    return cscale<T>(V[(size_t)v * Lj], __ldg(q + v).x);
+  fft_forward_from_n<T, NT>(A, ST, logM, sg.tw, [&](int v, cx<T>* x) {
+    if (v >= 2 * L) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) x[t] = mkc<T>(0, 0);
+      return;
+    }
+    const T qv = __ldg(q + v).x;
+    if (pair) {
+      const float4 u = *reinterpret_cast<const float4*>(V + (size_t)v * Lj);
+      const cx<T>* uu = reinterpret_cast<const cx<T>*>(&u);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) x[t] = cscale<T>(uu[t], qv);
+    } else {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) x[t] = t < nt ? cscale<T>(V[(size_t)v * Lj + t], qv) : mkc<T>(0, 0);
+    }
   });
   const cx<T>* __restrict__ tb = sg.pre + (L - 1);
-  cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m;  // column m of Vhat_g[m'][m]
+  cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m0;  // columns m0.. of Vhat_g[m'][m]
   for (int mp = threadIdx.x; mp < Lj; mp += blockDim.x) {
-    cx<T> o = cmulc<T>(A[fpad(fft_pos(mp, logM))], __ldg(tb + mp));
-    if (mp > 0) {
-      const cx<T> tm = cmulc<T>(A[fpad(fft_pos(M - mp, logM))], __ldg(tb - mp));
-      o = mkc<T>(o.x + sigma * tm.x, o.y + sigma * tm.y);
+    cx<T> o[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const T sigma = ((m0 + t + sg.N - 1) & 1) ? T(-1) : T(1);
+      o[t] = cmulc<T>(A[t * ST + fpad(fft_pos(mp, logM))], __ldg(tb + mp));
+      if (mp > 0) {
+        const cx<T> tm = cmulc<T>(A[t * ST + fpad(fft_pos(M - mp, logM))], __ldg(tb - mp));
+        o[t] = mkc<T>(o[t].x + sigma * tm.x, o[t].y + sigma * tm.y);
+      }
     }
-    Vh[(size_t)mp * Lj] = o;
+    if (pair) {
+      *reinterpret_cast<float4*>(Vh + (size_t)mp * Lj) = *reinterpret_cast<const float4*>(o);
+    } else {
+      for (int t = 0; t < nt; ++t) Vh[(size_t)mp * Lj + t] = o[t];
+    }
   }
 }
 
@@ -507,8 +547,12 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
     case CZT_BETA_ANA: k_czt_beta_ana<T><<<grid, block, smem, st>>>(segs, nseg); break;
     case CZT_BETA_SYN: k_czt_beta_syn<T><<<grid, block, smem, st>>>(segs, nseg); break;
     case CZT_ALPHA_ANA_DIRECT: k_alpha_ana_direct<T><<<grid, block, 0, st>>>(segs, nseg, ptrs); break;
-    case CZT_BETA_ANA_FFT: k_beta_ana_fft<T><<<grid, block, smem, st>>>(segs, nseg); break;
-    case CZT_BETA_SYN_FFT: k_beta_syn_fft<T><<<grid, block, smem, st>>>(segs, nseg); break;
+    case CZT_BETA_ANA_FFT:
+      k_beta_ana_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
+      break;
+    case CZT_BETA_SYN_FFT:
+      k_beta_syn_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
+      break;
     case CZT_ALPHA_SYN_DIRECT:
       k_alpha_syn_direct<T><<<grid, block, alpha_syn_direct_smem<T>(1 << (maxlogM - 2)), st>>>(segs, nseg, ptrs);
       break;
@@ -528,9 +572,11 @@ cudaError_t czt_set_smem(int maxlogM) {
   e = cudaFuncSetAttribute(k_czt_alpha_syn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)alpha_czt_smem<T>(maxlogM, true));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_beta_ana_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(k_beta_ana_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem * beta_fft_nt(sizeof(T) == 8));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem * beta_fft_nt(sizeof(T) == 8));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_alpha_syn_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)alpha_syn_direct_smem<T>(2048));

@@ -513,6 +513,110 @@ __device__ __forceinline__ void fft_convolve_n(cx<T>* A, int ST, int logM, const
   if (WRITE_SMEM) __syncthreads();
 }
 
+// ---- NT transforms per CTA (buffers ST elements apart) ----
+template <typename T, int R, bool INV, int NT>
+__device__ __forceinline__ void fft_inner_stage_n(cx<T>* A, int M, int ST) {
+  for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
+    const int base = u * R;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      cx<T> v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = A[t * ST + fpad(base + r)];
+      DftR<T, R, INV>::run(v);
+#pragma unroll
+      for (int k = 0; k < R; ++k) A[t * ST + fpad(base + k)] = v[k];
+    }
+  }
+}
+
+template <typename T, bool INV, int NT>
+__device__ __forceinline__ void fft_inner_dispatch_n(cx<T>* A, int M, int Rl, int ST) {
+  switch (Rl) {
+    case 2: fft_inner_stage_n<T, 2, INV, NT>(A, M, ST); break;
+    case 4: fft_inner_stage_n<T, 4, INV, NT>(A, M, ST); break;
+    case 8: fft_inner_stage_n<T, 8, INV, NT>(A, M, ST); break;
+    default: fft_inner_stage_n<T, 16, INV, NT>(A, M, ST); break;
+  }
+}
+
+// fft_forward_from on NT transforms: input(v, x) fills x[t], t < NT, with
+// element v of transform t.  Ends with __syncthreads().
+template <typename T, int NT, typename In>
+__device__ __forceinline__ void fft_forward_from_n(cx<T>* A, int ST, int logM, const cx<T>* __restrict__ tw,
+                                                   In input) {
+  const int M = 1 << logM;
+  int Rl, nmid;
+  fft_schedule(logM, Rl, nmid);
+  {
+    const int Q = M / 16;
+    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+      cx<T> v[NT][16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        cx<T> x[NT];
+        input(j + Q * r, x);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) v[t][r] = x[t];
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        DftR<T, 16, false>::run(v[t]);
+#pragma unroll
+        for (int k = 1; k < 16; ++k) v[t][k] = cmul<T>(v[t][k], __ldg(tw + (k - 1) * Q + j));
+#pragma unroll
+        for (int k = 0; k < 16; ++k) A[t * ST + fpad(j + Q * k)] = v[t][k];
+      }
+    }
+  }
+  __syncthreads();
+  int S = M / 16;
+  for (int s = 0; s < nmid; ++s) {
+    fft_fwd_stage<T, 16, NT>(A, M, S, tw + fft_twiddle_level_offset(logM, s + 1), ST);
+    __syncthreads();
+    S /= 16;
+  }
+  fft_inner_dispatch_n<T, false, NT>(A, M, Rl, ST);
+  __syncthreads();
+}
+
+// fft_inverse_to on NT transforms: output(v, y) receives element v of every
+// transform (y[t]).  Expects A complete (call after a __syncthreads()).
+template <typename T, int NT, typename Out>
+__device__ __forceinline__ void fft_inverse_to_n(cx<T>* A, int ST, int logM, const cx<T>* __restrict__ tw,
+                                                 Out output) {
+  const int M = 1 << logM;
+  int Rl, nmid;
+  fft_schedule(logM, Rl, nmid);
+  fft_inner_dispatch_n<T, true, NT>(A, M, Rl, ST);
+  __syncthreads();
+  int S = M >> (4 * (nmid + 1));
+  for (int s = nmid - 1; s >= 0; --s) {
+    S *= 16;
+    fft_inv_stage<T, 16, NT>(A, M, S, tw + fft_twiddle_level_offset(logM, s + 1), ST);
+    __syncthreads();
+  }
+  const int Q = M / 16;
+  for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+    cx<T> v[NT][16];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[t][k] = A[t * ST + fpad(j + Q * k)];
+#pragma unroll
+      for (int k = 1; k < 16; ++k) v[t][k] = cmulc<T>(v[t][k], __ldg(tw + (k - 1) * Q + j));
+      DftR<T, 16, true>::run(v[t]);
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      cx<T> y[NT];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) y[t] = v[t][r];
+      output(j + Q * r, y);
+    }
+  }
+}
+
 // Forward transform only (smem in natural order -> smem in the engine's
 // order), values scaled by `scale`; used to build the kernel spectra.
 template <typename T>

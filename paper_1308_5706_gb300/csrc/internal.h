@@ -62,6 +62,8 @@ constexpr int kDirectMaxLj = 32;
 // row pairs (complex transforms) per CTA of the alpha chirp-z kernels: FP32
 // runs two so that each table value serves both (FP64 buffers would not fit)
 __host__ __device__ constexpr int alpha_czt_nt(bool fp64) { return fp64 ? 1 : 2; }
+// adjacent columns per CTA of the single-FFT beta kernels (FP32: a 16-byte pair)
+__host__ __device__ constexpr int beta_fft_nt(bool fp64) { return fp64 ? 1 : 2; }
 constexpr int kDirectRowsAna = 16;
 inline int direct_rows_syn(bool fp64) { return fp64 ? 4 : 8; }  // 32-byte line per alpha sample
 
