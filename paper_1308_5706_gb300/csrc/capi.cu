@@ -603,7 +603,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     off = align256(off + bytes);
     return o;
   };
-  const size_t o_RS = take((size_t)L * 2 * N * p->Lp * sizeof(T));
+  const size_t o_RS = take((size_t)L * 2 * ((N + 1) / 2) * p->Lp * sizeof(T));
   const size_t o_RSphi = take((size_t)p->Lphi * p->Lphip * sizeof(T));
   std::vector<size_t> o_Y(p->nscale + 1), o_X(p->nscale + 1);
   for (int j = 0; j <= p->nscale; ++j) {

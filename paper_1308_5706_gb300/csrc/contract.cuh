@@ -100,8 +100,8 @@ struct StageGeom {
   static constexpr int A_OFF = 0;
   static constexpr int B_OFF = A_OFF + TMP * APITCH;
   static constexpr int F_OFF = B_OFF + TILE * BPITCH;         // TILE complex = 2*TILE elements
-  static constexpr int R_OFF = F_OFF + 2 * TILE;              // [NSLOT][N][TMP]
-  static constexpr int SIZE = R_OFF + NSLOT * N * TMP;
+  static constexpr int R_OFF = F_OFF + 2 * TILE;              // [NSLOT][(N+1)/2][TMP], n_k >= 0
+  static constexpr int SIZE = R_OFF + NSLOT * ((N + 1) / 2) * TMP;
   static constexpr size_t BYTES = (size_t)SIZE * sizeof(T);
 };
 
@@ -126,6 +126,16 @@ __global__ void __launch_bounds__(256)
 k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict__ tiles, CallPtrs ptrs) {
   using G = StageGeom<T, N, NSLOT, E>;
   constexpr int STAGES = contract_stages<T, N, NSLOT, SYN, E>();
+  // Order parity: R_{l m' -n} = (-1)^{l+m'} R_{l m' n}, so only n >= 0 is
+  // staged (NH rows, row 0 is n = 0 when N is odd) and the sums over l of a
+  // pair +-n run as two banks, l of the parity of l_start (bank 0) and the
+  // other (bank 1): analysis G_{+n} = B0 + B1 and G_{-n} = (-1)^{m'+l_start}
+  // (B0 - B1); synthesis folds H_{+n} +- (-1)^{m'+l_start} H_{-n} into the
+  // bank of each parity.  Accumulator index q: bank 0 orders n > 0 in
+  // [0, NP), bank 1 in [NP, 2 NP), n = 0 at 2 NP.  Rows m' of a thread start
+  // at an even m', so (-1)^{m'} = (-1)^e.
+  constexpr int NH = (N + 1) / 2, ZH = N & 1, NP = N / 2;
+  static_assert(E % 2 == 0, "row parity of element e must be (-1)^e");
   constexpr int RG = 8;
   constexpr int TMP = G::TMP;
   constexpr int EPC = G::EPC;
@@ -185,7 +195,7 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   // for l_start, l_start+1, ... in order).
   const int t = threadIdx.x;
   constexpr int CPRA = TILE / EPC, CPRB = TMP / EPC, CPRR = TMP / EPC;
-  constexpr int FCH = 2 * TILE / EPC, CPC = EPC / 2, NRCH = NSLOT * N * CPRR;
+  constexpr int FCH = 2 * TILE / EPC, CPC = EPC / 2, NRCH = NSLOT * NH * CPRR;
   const bool do_a = need_a && t < TMP * CPRA;
   const bool do_b = need_b && t < TILE * CPRB;
   const int ra = mp0 + t / CPRA, rb = m0 + t / CPRB;
@@ -200,7 +210,7 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   const int r_dst = G::R_OFF + (t / CPRR) * TMP + (t % CPRR) * EPC;
   int64_t is_slab = delta_slab_offset(l_start);  // state of the next issue
   int64_t is_f = (int64_t)l_start * l_start + l_start;
-  const T* is_rs = RS + (size_t)l_start * (NSLOT * N) * Lp;
+  const T* is_rs = RS + (size_t)l_start * (NSLOT * NH) * Lp;
   int is_l = l_start;
   auto issue = [&](int st) {
     const int l = is_l;
@@ -224,7 +234,7 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
       if (do_r) cp_async16(S + r_dst, is_rs + r_src, 16);
       is_slab += 8 * (int64_t)cl * (cl + 1);
       is_f += 2 * (l + 1);
-      is_rs += (size_t)(NSLOT * N) * Lp;
+      is_rs += (size_t)(NSLOT * NH) * Lp;
       is_l = l + 1;
     }
     cp_async_commit();
@@ -256,11 +266,21 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
     for (int e = 0; e < E; ++e) {
       const int mp = mpb + e;
       if (mp < Lj && m < Lj) {
+        cx<T> gk[N];
+        if (ZH) gk[N / 2] = acc.get(e, s, 2 * NP);
+        const T sgn = ((l_start + e) & 1) ? T(-1) : T(1);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const cx<T> b0 = acc.get(e, s, p), b1 = acc.get(e, s, NP + p);
+          gk[(N + 1) / 2 + p] = cadd<T>(b0, b1);
+          const cx<T> d = csub<T>(b0, b1);
+          gk[N / 2 - 1 - p] = mkc<T>(sgn * d.x, sgn * d.y);
+        }
 #pragma unroll
         for (int g = 0; g < N; ++g) {
           cx<T> v = mkc<T>(0, 0);
 #pragma unroll
-          for (int k = 0; k < N; ++k) v = cadd<T>(v, cmul<T>(acc.get(e, s, k), cgk[k][g]));
+          for (int k = 0; k < N; ++k) v = cadd<T>(v, cmul<T>(gk[k], cgk[k][g]));
           Y[((size_t)g * Lj + m) * Lj + mp] = cmul_ipow<T>(v, (-m) & 3);
         }
       }
@@ -286,8 +306,15 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
 #pragma unroll
         for (int k = 0; k < N; ++k) h[k] = cmul_ipow<T>(h[k], m & 3);
       }
+      const T sgn = ((l_start + e) & 1) ? T(-1) : T(1);
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc.set(e, s, k, h[k]);
+      for (int p = 0; p < NP; ++p) {
+        const cx<T> hp = h[(N + 1) / 2 + p], hm = h[N / 2 - 1 - p];
+        const cx<T> t = mkc<T>(sgn * hm.x, sgn * hm.y);
+        acc.set(e, s, p, cadd<T>(hp, t));
+        acc.set(e, s, NP + p, csub<T>(hp, t));
+      }
+      if (ZH) acc.set(e, s, 2 * NP, h[N / 2]);
     }
   };
   auto reduce_chunk = [&](int buf, int lfirst, int count) {
@@ -304,7 +331,8 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   __syncthreads();  // cgk visible
   // Two l per barrier: stages it, it+1 are waited for together and stages
   // it+S-2, it+S-1 are issued into the slots that l-2, l-1 have released.
-  auto process = [&](const int l, const int it) {
+  auto process = [&](const int l, const int it, auto bank) {
+    constexpr int BQ = decltype(bank)::value * NP;  // first accumulator of this l's bank
     // slot occupancy changes at segment boundaries
     if (l > seg_hi) {
       while (D->seg[sidx].hi < l) ++sidx;
@@ -353,24 +381,26 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
 #pragma unroll
           for (int s = 0; s < NSLOT; ++s)
 #pragma unroll
-            for (int k = 0; k < N; ++k) {
-              const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(Rr + (s * N + k) * TMP);
-              acc.x[0][s][k] = fma2(tx0, r.x, acc.x[0][s][k]);
-              acc.y[0][s][k] = fma2(ty0, r.x, acc.y[0][s][k]);
-              acc.x[1][s][k] = fma2(tx1, r.y, acc.x[1][s][k]);
-              acc.y[1][s][k] = fma2(ty1, r.y, acc.y[1][s][k]);
+            for (int h = 0; h < NH; ++h) {
+              const int q = (ZH && h == 0) ? 2 * NP : BQ + h - ZH;
+              const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(Rr + (s * NH + h) * TMP);
+              acc.x[0][s][q] = fma2(tx0, r.x, acc.x[0][s][q]);
+              acc.y[0][s][q] = fma2(ty0, r.x, acc.y[0][s][q]);
+              acc.x[1][s][q] = fma2(tx1, r.y, acc.x[1][s][q]);
+              acc.y[1][s][q] = fma2(ty1, r.y, acc.y[1][s][q]);
             }
         } else {
           f2p px0 = 0, py0 = 0, px1 = 0, py1 = 0;
 #pragma unroll
           for (int s = 0; s < NSLOT; ++s)
 #pragma unroll
-            for (int k = 0; k < N; ++k) {
-              const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(Rr + (s * N + k) * TMP);
-              px0 = fma2(acc.x[0][s][k], r.x, px0);
-              py0 = fma2(acc.y[0][s][k], r.x, py0);
-              px1 = fma2(acc.x[1][s][k], r.y, px1);
-              py1 = fma2(acc.y[1][s][k], r.y, py1);
+            for (int h = 0; h < NH; ++h) {
+              const int q = (ZH && h == 0) ? 2 * NP : BQ + h - ZH;
+              const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(Rr + (s * NH + h) * TMP);
+              px0 = fma2(acc.x[0][s][q], r.x, px0);
+              py0 = fma2(acc.y[0][s][q], r.x, py0);
+              px1 = fma2(acc.x[1][s][q], r.y, px1);
+              py1 = fma2(acc.y[1][s][q], r.y, py1);
             }
           const f2p d01 = pk2(dv[0], dv[1]), d23 = pk2(dv[2], dv[3]);
           const f2p sx = fma2(d23, px1, mul2(d01, px0)), sy = fma2(d23, py1, mul2(d01, py0));
@@ -389,12 +419,13 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
 #pragma unroll
           for (int s = 0; s < NSLOT; ++s)
 #pragma unroll
-            for (int k = 0; k < N; ++k) {
+            for (int h = 0; h < NH; ++h) {
+              const int q = (ZH && h == 0) ? 2 * NP : BQ + h - ZH;
               T r[E];
-              VecLdS<T, E>::ld(Rr + (s * N + k) * TMP, r);
+              VecLdS<T, E>::ld(Rr + (s * NH + h) * TMP, r);
 #pragma unroll
               for (int e = 0; e < E; ++e) {
-                cx<T>& a = acc.v[e][s][k];
+                cx<T>& a = acc.v[e][s][q];
                 a.x = fma(tt[e].x, r[e], a.x);
                 a.y = fma(tt[e].y, r[e], a.y);
               }
@@ -406,12 +437,13 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
 #pragma unroll
           for (int s = 0; s < NSLOT; ++s)
 #pragma unroll
-            for (int k = 0; k < N; ++k) {
+            for (int h = 0; h < NH; ++h) {
+              const int q = (ZH && h == 0) ? 2 * NP : BQ + h - ZH;
               T r[E];
-              VecLdS<T, E>::ld(Rr + (s * N + k) * TMP, r);
+              VecLdS<T, E>::ld(Rr + (s * NH + h) * TMP, r);
 #pragma unroll
               for (int e = 0; e < E; ++e) {
-                const cx<T> a = acc.v[e][s][k];
+                const cx<T> a = acc.v[e][s][q];
                 p[e].x = fma(a.x, r[e], p[e].x);
                 p[e].y = fma(a.y, r[e], p[e].y);
               }
@@ -437,8 +469,8 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
     issue((it + STAGES - 2) % STAGES);
     issue((it + STAGES - 1) % STAGES);
     if (SYN && it > 0 && (it % LCH) == 0) reduce_chunk(rbuf ^ 1, l_start + it - LCH, LCH);
-    process(l_start + it, it);
-    if (it + 1 < n_it) process(l_start + it + 1, it + 1);
+    process(l_start + it, it, std::integral_constant<int, 0>());
+    if (it + 1 < n_it) process(l_start + it + 1, it + 1, std::integral_constant<int, 1>());
   }
   cp_async_wait<0>();
   if (SYN) {

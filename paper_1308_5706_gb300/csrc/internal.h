@@ -22,7 +22,7 @@ struct LSeg {
 template <typename T>
 struct ContractDesc {
   const T* delta;    // Delta table (padded eighth domain), working precision
-  const T* RS;       // [L][nslot][N][Lp]: Delta^l_{m',n_k} kappa^j(l) |s_{l,n_k}|
+  const T* RS;       // [L][nslot][(N+1)/2][Lp]: Delta^l_{m',n_k} kappa^j(l) |s_{l,n_k}|, n_k >= 0
   cx<T>* P;          // synthesis partials [nbr][L][Lp32]
   int L, Lp, Lp32, nbr;
   int nseg;

@@ -198,18 +198,22 @@ __device__ __forceinline__ double delta_lookup(const double* __restrict__ d64, i
   return s * d64[delta_slab_offset(l) + delta_entry(l, mp, m)];
 }
 
-// RS[l][s][k][m'] = Delta^l_{m', n_k} kap[js][l] sabs[l][k], js = slotj[l][s]
-// (zero if js < 0, m' > l or |n_k| > l).  sabs == nullptr means |s| = 1.
+// RS[l][s][h][m'] = Delta^l_{m', n_k} kap[js][l] sabs[l][k] for the orders
+// n_k >= 0 only, k = N/2 + h, h < (N+1)/2, js = slotj[l][s] (zero if js < 0,
+// m' > l or |n_k| > l).  sabs == nullptr means |s| = 1.  The rows of -n_k
+// follow from Delta^l_{m',-n} = (-1)^{l+m'} Delta^l_{m'n} and
+// |s_{l,-n}| = |s_{ln}| (Eq. (11) is symmetric in n), so they are not stored.
 template <typename T>
 __global__ void k_rtable(T* RS, const double* d64, const double* kap, const double* sabs, const int* slotj, int L,
                          int Lp, int N, int nslot, int kapL) {
+  const int NH = (N + 1) / 2;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)L * nslot * N * Lp;
+  const int64_t total = (int64_t)L * nslot * NH * Lp;
   if (idx >= total) return;
   const int mp = (int)(idx % Lp);
-  const int k = (int)((idx / Lp) % N);
-  const int s = (int)((idx / ((int64_t)Lp * N)) % nslot);
-  const int l = (int)(idx / ((int64_t)Lp * N * nslot));
+  const int k = N / 2 + (int)((idx / Lp) % NH);
+  const int s = (int)((idx / ((int64_t)Lp * NH)) % nslot);
+  const int l = (int)(idx / ((int64_t)Lp * NH * nslot));
   const int n = -(N - 1) + 2 * k;
   double v = 0.0;
   const int js = slotj[l * nslot + s];
@@ -344,7 +348,7 @@ cudaError_t launch_delta_build(double* d64, float* d32, double* em, int* ee, int
 template <typename T>
 cudaError_t launch_rtable(T* RS, const double* d64, const double* kap, const double* sabs, const int* slotj, int L,
                           int Lp, int N, int nslot, int kapL, cudaStream_t st) {
-  const int64_t total = (int64_t)L * nslot * N * Lp;
+  const int64_t total = (int64_t)L * nslot * ((N + 1) / 2) * Lp;
   if (total == 0) return cudaSuccess;
   k_rtable<T><<<nblk(total, 256), 256, 0, st>>>(RS, d64, kap, sabs, slotj, L, Lp, N, nslot, kapL);
   return cudaGetLastError();
