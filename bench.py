@@ -202,14 +202,16 @@ def aggregate_replicas(total_ms: float, steps: int, dist=None, device=None):
 def contraction_flops(plan) -> float:
     """Algorithmic flops of one contraction launch (analysis or synthesis):
     per scale j and l in its support, (l+1)^2 (m', m >= 0) triples, each
-    Delta * f (2 flops) plus N complex-by-real multiply-adds (4N flops)."""
+    Delta * f (2 flops) plus one complex-by-real multiply-add (4 flops) per
+    order n_k >= 0: the rows of -n_k equal those of n_k up to the sign
+    (-1)^{l+m'}, so a +-n pair costs one multiply-add per l."""
     tot = 0.0
     for j in range(plan.nscale):
         lo, hi = plan.support(j)
         if hi < 0:
             continue
         ls = np.arange(lo, hi + 1, dtype=np.float64)
-        tot += float(((ls + 1.0) ** 2).sum()) * (2 + 4 * plan.N)
+        tot += float(((ls + 1.0) ** 2).sum()) * (2 + 4 * ((plan.N + 1) // 2))
     return tot
 
 

@@ -116,7 +116,15 @@ DeltaTab* delta_acquire(int L, cudaStream_t st) {
     best->refs++;
     return best;
   }
-  const int Lmax = round_up(L, 64);
+  // Size classes (multiples of 64 up to 256, then of 256) keep the number of
+  // distinct tables small when plans of many band-limits come and go.  Slab l
+  // does not depend on Lmax, so the slabs of the largest existing table are
+  // copied and only the new ones are computed.
+  const int Lmax = L <= 256 ? round_up(L, 64) : round_up(L, 256);
+  DeltaTab* donor = nullptr;
+  for (DeltaTab* u : g_tabs)
+    if (u->device == dev && u->Lmax < Lmax && (!donor || u->Lmax > donor->Lmax)) donor = u;
+  const int l_first = donor ? donor->Lmax : 0;
   const int64_t entries = delta_table_entries(Lmax) + 64;  // + read-ahead pad
   DeltaTab* t = new DeltaTab{Lmax, dev, nullptr, nullptr, 1, 0};
   double* em = nullptr;
@@ -127,12 +135,17 @@ DeltaTab* delta_acquire(int L, cudaStream_t st) {
     amalloc(&t->d64, (entries + kDeltaPad) * sizeof(double), st);
     amalloc(&t->d32, (entries + kDeltaPad) * sizeof(float), st);
     t->bytes = entries * (sizeof(double) + sizeof(float));
-    ck(cudaMemsetAsync(t->d64, 0, (entries + kDeltaPad) * sizeof(double), st));
-    ck(cudaMemsetAsync(t->d32, 0, (entries + kDeltaPad) * sizeof(float), st));
+    const int64_t kept = delta_slab_offset(l_first);
+    if (donor) {
+      ck(cudaMemcpyAsync(t->d64, donor->d64, kept * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      ck(cudaMemcpyAsync(t->d32, donor->d32, kept * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    ck(cudaMemsetAsync(t->d64 + kept, 0, (entries + kDeltaPad - kept) * sizeof(double), st));
+    ck(cudaMemsetAsync(t->d32 + kept, 0, (entries + kDeltaPad - kept) * sizeof(float), st));
     const size_t ne = (size_t)Lmax * (Lmax + 1) / 2;
     amalloc(&em, ne * sizeof(double), st);
     amalloc(&ee, ne * sizeof(int), st);
-    ck(launch_delta_build(t->d64, t->d32, em, ee, Lmax, st));
+    ck(launch_delta_build(t->d64, t->d32, em, ee, Lmax, l_first, st));
     afree(em, st);
     afree(ee, st);
     ck(cudaStreamSynchronize(st));
@@ -261,18 +274,51 @@ struct s2dw_plan_s {
 
 namespace {
 
+// Launch lists of the plan sets seen by the batched entry points.  At most
+// kBatchCacheMax entries: beyond that the least recently used one is freed
+// once its last launch has completed, unless it was used while its stream was
+// being captured into a CUDA graph (the graph keeps reading it, so it lives
+// until one of its plans is destroyed).
+struct BatchEnt {
+  Lists* ls = nullptr;
+  uint64_t tick = 0;
+  cudaEvent_t done = nullptr;  // recorded after the entry's latest launches
+  bool pinned = false;
+};
+constexpr size_t kBatchCacheMax = 64;
 std::mutex g_batch_mu;
-std::map<std::vector<s2dw_plan_t>, Lists*> g_batch_cache;
+std::map<std::vector<s2dw_plan_t>, BatchEnt> g_batch_cache;
+uint64_t g_batch_tick = 0;
+
+void free_batch_ent(BatchEnt& e) {
+  if (e.done) {
+    cudaEventSynchronize(e.done);  // only this entry's launches
+    cudaEventDestroy(e.done);
+  }
+  delete e.ls;
+}
 
 void drop_batches_with(s2dw_plan_t p) {
   std::lock_guard<std::mutex> lk(g_batch_mu);
   for (auto it = g_batch_cache.begin(); it != g_batch_cache.end();) {
     if (std::find(it->first.begin(), it->first.end(), p) != it->first.end()) {
-      delete it->second;
+      free_batch_ent(it->second);
       it = g_batch_cache.erase(it);
     } else {
       ++it;
     }
+  }
+}
+
+void evict_batches() {  // g_batch_mu held; called before an insertion
+  while (g_batch_cache.size() >= kBatchCacheMax) {  // room for one more
+    auto victim = g_batch_cache.end();
+    for (auto it = g_batch_cache.begin(); it != g_batch_cache.end(); ++it)
+      if (!it->second.pinned && (victim == g_batch_cache.end() || it->second.tick < victim->second.tick))
+        victim = it;
+    if (victim == g_batch_cache.end()) return;
+    free_batch_ent(victim->second);
+    g_batch_cache.erase(victim);
   }
 }
 
@@ -790,7 +836,7 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
     std::vector<double> glx, glw;
     const int Q = 16, PAN = 32;
     gauss_legendre(Q, glx, glw);
-    amalloc(&gl, 2 * Q * sizeof(double), st);
+    amalloc(&gl, (2 * Q + 1) * sizeof(double), st);  // nodes, weights, the kappa normalisation
     ck(cudaMemcpyAsync(gl, glx.data(), Q * sizeof(double), cudaMemcpyHostToDevice, st));
     ck(cudaMemcpyAsync(gl + Q, glw.data(), Q * sizeof(double), cudaMemcpyHostToDevice, st));
     amalloc(&kap, (size_t)(J + 1) * L * sizeof(double), st);
@@ -798,7 +844,7 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
     amalloc(&sabs, (size_t)L * N * sizeof(double), st);
     amalloc(&psi, (size_t)(J + 1) * L * N * sizeof(double2), st);
     amalloc(&q, (size_t)2 * L * sizeof(double), st);
-    ck(launch_kernel_values(kap, phi, sabs, psi, q, L, N, J, lam, gl, gl + Q, Q, PAN, st));
+    ck(launch_kernel_values(kap, phi, sabs, psi, q, L, N, J, lam, gl, gl + Q, Q, PAN, gl + 2 * Q, st));
     std::vector<double> kap_h((size_t)(J + 1) * L);
     p->phi_host.resize(L);
     p->psi_host.resize((size_t)(J + 1) * L * N * 2);
@@ -1179,7 +1225,9 @@ int s2dw_profile_read(s2dw_plan_t p, double* ms, int* ncalls) {
   return S2DW_OK;
 }
 
-static int batch_lists(const s2dw_plan_t* plans, int njobs, Lists** out, bool* fp64) {
+// Looks up (or builds) the launch lists of a plan set; g_batch_mu must be held
+// by the caller until the launches using the entry are queued and recorded.
+static int batch_lists(const s2dw_plan_t* plans, int njobs, BatchEnt** out, bool* fp64) {
   if (!plans || njobs < 1 || njobs > MAXB) return S2DW_EINVAL;
   std::vector<s2dw_plan_t> key(plans, plans + njobs);
   for (int i = 0; i < njobs; ++i) {
@@ -1189,31 +1237,42 @@ static int batch_lists(const s2dw_plan_t* plans, int njobs, Lists** out, bool* f
     if (key[i]->fp64 != key[0]->fp64) return S2DW_ENOTSUP;
   }
   *fp64 = key[0]->fp64;
-  std::lock_guard<std::mutex> lk(g_batch_mu);
   auto it = g_batch_cache.find(key);
-  if (it != g_batch_cache.end()) {
-    *out = it->second;
-    return S2DW_OK;
+  if (it == g_batch_cache.end()) {
+    evict_batches();
+    BatchEnt e;
+    try {
+      e.ls = *fp64 ? build_lists<double>(key) : build_lists<float>(key);
+    } catch (const CudaFail& err) {
+      return err_of(err.err);
+    } catch (...) {
+      return S2DW_ENOMEM;
+    }
+    if (cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming) != cudaSuccess) {
+      delete e.ls;
+      return S2DW_ECUDA;
+    }
+    it = g_batch_cache.emplace(key, e).first;
   }
-  try {
-    Lists* ls = *fp64 ? build_lists<double>(key) : build_lists<float>(key);
-    g_batch_cache[key] = ls;
-    *out = ls;
-  } catch (const CudaFail& e) {
-    return err_of(e.err);
-  } catch (...) {
-    return S2DW_ENOMEM;
-  }
+  it->second.tick = ++g_batch_tick;
+  *out = &it->second;
   return S2DW_OK;
+}
+
+static void batch_used(BatchEnt* e, cudaStream_t st) {
+  if (capturing(st)) e->pinned = true;
+  else cudaEventRecord(e->done, st);
 }
 
 int s2dw_analysis_batch(const s2dw_plan_t* plans, const void* const* flm, void* const* W, void* const* Wphi,
                         int njobs, void* stream) {
   if (!flm || !W || !Wphi) return S2DW_EINVAL;
-  Lists* ls = nullptr;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchEnt* be = nullptr;
   bool fp64 = false;
-  int rc = batch_lists(plans, njobs, &ls, &fp64);
+  int rc = batch_lists(plans, njobs, &be, &fp64);
   if (rc != S2DW_OK) return rc;
+  const Lists* ls = be->ls;
   CallPtrs ptrs;
   std::memset(&ptrs, 0, sizeof(ptrs));
   for (int i = 0; i < njobs; ++i) {
@@ -1225,6 +1284,7 @@ int s2dw_analysis_batch(const s2dw_plan_t* plans, const void* const* flm, void* 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (fp64) run_analysis<double>(*ls, ptrs, st);
   else run_analysis<float>(*ls, ptrs, st);
+  batch_used(be, st);
   for (int i = 0; i < njobs; ++i) mark_use(plans[i], st);
   return err_of(cudaGetLastError());
 }
@@ -1232,10 +1292,12 @@ int s2dw_analysis_batch(const s2dw_plan_t* plans, const void* const* flm, void* 
 int s2dw_synthesis_batch(const s2dw_plan_t* plans, const void* const* W, const void* const* Wphi, void* const* flm,
                          int njobs, void* stream) {
   if (!flm || !W || !Wphi) return S2DW_EINVAL;
-  Lists* ls = nullptr;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchEnt* be = nullptr;
   bool fp64 = false;
-  int rc = batch_lists(plans, njobs, &ls, &fp64);
+  int rc = batch_lists(plans, njobs, &be, &fp64);
   if (rc != S2DW_OK) return rc;
+  const Lists* ls = be->ls;
   CallPtrs ptrs;
   std::memset(&ptrs, 0, sizeof(ptrs));
   ReduceJobs rj;
@@ -1256,6 +1318,7 @@ int s2dw_synthesis_batch(const s2dw_plan_t* plans, const void* const* W, const v
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (fp64) run_synthesis<double>(*ls, ptrs, rj, njobs, st);
   else run_synthesis<float>(*ls, ptrs, rj, njobs, st);
+  batch_used(be, st);
   for (int i = 0; i < njobs; ++i) mark_use(plans[i], st);
   return err_of(cudaGetLastError());
 }

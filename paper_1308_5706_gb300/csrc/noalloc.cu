@@ -59,6 +59,6 @@ extern "C" int s2dw_delta_table_noalloc(int Lmax, double* table64, float* table3
   // padded entries of the output must be zero; every edge entry used is rewritten
   if (cudaMemsetAsync(table64, 0, (size_t)n * sizeof(double), st) != cudaSuccess) return S2DW_ECUDA;
   if (table32 && cudaMemsetAsync(table32, 0, (size_t)n * sizeof(float), st) != cudaSuccess) return S2DW_ECUDA;
-  if (s2dw::launch_delta_build(table64, table32, em, ee, Lmax, st) != cudaSuccess) return S2DW_ECUDA;
+  if (s2dw::launch_delta_build(table64, table32, em, ee, Lmax, 0, st) != cudaSuccess) return S2DW_ECUDA;
   return S2DW_OK;
 }

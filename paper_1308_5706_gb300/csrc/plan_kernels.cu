@@ -19,7 +19,9 @@ __device__ double integrand(double u, double lam) {
   return exp(-2.0 / d) / u;  // s_lam(u)^2 / u, s(x) = exp(-1/(1-x^2)) (Eq. (12))
 }
 
-// int_lo^hi s_lam(u)^2/u du, limits clipped to the support [1/lam, 1].
+// int_lo^hi s_lam(u)^2/u du, limits clipped to the support [1/lam, 1], by a
+// whole warp: lane i takes panels i, i + 32, ..., then a butterfly sum (every
+// lane ends with the same, order-fixed total).  Called with warp-uniform arguments.
 __device__ double I_gl(double lo, double hi, double lam, const double* __restrict__ glx,
                        const double* __restrict__ glw, int Q, int P) {
   lo = fmax(lo, 1.0 / lam);
@@ -27,13 +29,15 @@ __device__ double I_gl(double lo, double hi, double lam, const double* __restric
   if (lo >= hi) return 0.0;
   const double h = (hi - lo) / P;
   double tot = 0.0;
-  for (int p = 0; p < P; ++p) {
+  for (int p = threadIdx.x & 31; p < P; p += 32) {
     const double a = lo + p * h, b = (p + 1 == P) ? hi : lo + (p + 1) * h;
     const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
     double s = 0.0;
     for (int q = 0; q < Q; ++q) s += glw[q] * integrand(mid + half * glx[q], lam);
     tot += half * s;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
   return tot;
 }
 
@@ -43,22 +47,34 @@ __device__ double k_lambda(double t, double lam, double I0, const double* glx, c
   return I_gl(t, 1.0, lam, glx, glw, Q, P) / I0;
 }
 
+// The normalisation I(1/lam) = int_{1/lam}^1 s_lam(u)^2/u du of Eq. (13), once.
+__global__ void k_kappa_norm(double* I0, double lam, const double* glx, const double* glw, int Q, int P) {
+  const double v = I_gl(1.0 / lam, 1.0, lam, glx, glw, Q, P);  // one warp
+  if (threadIdx.x == 0) *I0 = v;
+}
+
 // kap[j][l] = kappa^j(l) = sqrt(k(t/lam) - k(t)), t = lam^j l / L (Eqs. (14)-(15)),
 // with the difference evaluated as the single integral
 //   k(t/lam) - k(t) = int_{t/lam}^{t} s_lam(u)^2/u du / I(1/lam)   (Eq. (13)),
 // free of cancellation near the support edges; phi[l] = sqrt(k(lam^J l / L)) (Eq. (16)).
+// Entries whose interval misses the support [1/lam, 1] are exact 0 (or 1) and
+// need no quadrature; about (lam + 1) L of the (J + 2) L entries do.  One warp per entry.
 __global__ void k_kernel_values(double* kap, double* phi, int L, int J, double lam, const double* glx,
-                                const double* glw, int Q, int P) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (J + 2) * L) return;
+                                const double* glw, int Q, int P, const double* I0p) {
+  const int idx = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (idx >= (J + 2) * L) return;  // warp-uniform
+  const bool lead = (threadIdx.x & 31) == 0;
   const int j = idx / L, l = idx % L;
-  const double I0 = I_gl(1.0 / lam, 1.0, lam, glx, glw, Q, P);
   if (j <= J) {
     const double t = pow(lam, (double)j) * l / L;
-    kap[(size_t)j * L + l] = sqrt(I_gl(t / lam, t, lam, glx, glw, Q, P) / I0);
+    const bool empty = fmax(t / lam, 1.0 / lam) >= fmin(t, 1.0);
+    const double v = empty ? 0.0 : sqrt(I_gl(t / lam, t, lam, glx, glw, Q, P) / *I0p);
+    if (lead) kap[(size_t)j * L + l] = v;
   } else {
     const double t = pow(lam, (double)J) * l / L;
-    phi[l] = sqrt(k_lambda(t, lam, I0, glx, glw, Q, P));
+    const double v = (t <= 1.0 / lam || t >= 1.0) ? sqrt(k_lambda(t, lam, 1.0, glx, glw, Q, P))
+                                                  : sqrt(k_lambda(t, lam, *I0p, glx, glw, Q, P));
+    if (lead) phi[l] = v;
   }
 }
 
@@ -91,16 +107,20 @@ __global__ void k_psi(double2* psi, const double* kap, const double* sabs, int L
 }
 
 // q(theta_t) = (2/L) sin(theta_t) sum_{k<L} sin((2k+1) theta_t)/(2k+1), theta_t = pi(2t+1)/(4L).
+// One warp per t: lane i sums k = i, i + 32, ..., then a fixed shuffle tree.
 __global__ void k_dh_weights(double* q, int L) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * L) return;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= 2 * L) return;  // warp-uniform
   const long long period = 8LL * L;
   double s = 0.0;
-  for (int k = 0; k < L; ++k) {
+  for (int k = lane; k < L; k += 32) {
     const long long p = ((long long)(2 * k + 1) * (2 * t + 1)) % period;
     s += sinpi((double)p / (4.0 * L)) / (2 * k + 1);
   }
-  q[t] = 2.0 / L * sinpi((double)(2 * t + 1) / (4.0 * L)) * s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) q[t] = 2.0 / L * sinpi((double)(2 * t + 1) / (4.0 * L)) * s;
 }
 
 // ---------------------------------------------------------------------------
@@ -316,26 +336,27 @@ static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / 
 
 cudaError_t launch_kernel_values(double* kap, double* phi, double* sabs, double2* psi, double* q, int L, int N,
                                  int J, double lam, const double* glx, const double* glw, int Q, int P,
-                                 cudaStream_t st) {
-  k_kernel_values<<<nblk((int64_t)(J + 2) * L, 128), 128, 0, st>>>(kap, phi, L, J, lam, glx, glw, Q, P);
+                                 double* I0, cudaStream_t st) {
+  k_kappa_norm<<<1, 32, 0, st>>>(I0, lam, glx, glw, Q, P);
+  k_kernel_values<<<nblk((int64_t)(J + 2) * L * 32, 128), 128, 0, st>>>(kap, phi, L, J, lam, glx, glw, Q, P, I0);
   k_sabs<<<nblk((int64_t)L * N, 128), 128, 0, st>>>(sabs, L, N);
   k_psi<<<nblk((int64_t)(J + 1) * L * N, 128), 128, 0, st>>>(psi, kap, sabs, L, N, J);
-  k_dh_weights<<<nblk(2 * L, 128), 128, 0, st>>>(q, L);
-  return cudaGetLastError();
+  return launch_dh_weights(q, L, st);
 }
 
 cudaError_t launch_dh_weights(double* q, int L, cudaStream_t st) {
-  k_dh_weights<<<nblk(2 * L, 128), 128, 0, st>>>(q, L);
+  k_dh_weights<<<nblk(2 * (int64_t)L * 32, 128), 128, 0, st>>>(q, L);
   return cudaGetLastError();
 }
 
-cudaError_t launch_delta_build(double* d64, float* d32, double* em, int* ee, int Lmax, cudaStream_t st) {
+cudaError_t launch_delta_build(double* d64, float* d32, double* em, int* ee, int Lmax, int l_first,
+                               cudaStream_t st) {
   k_delta_edge<<<nblk(Lmax, 128), 128, 0, st>>>(em, ee, Lmax);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  // slabs in chunks of l so that a single launch stays short
+  // slabs l_first .. Lmax-1 in chunks of l so that a single launch stays short
   const int chunk = 256;
-  for (int l0 = 0; l0 < Lmax; l0 += chunk) {
+  for (int l0 = l_first; l0 < Lmax; l0 += chunk) {
     const int nl = (Lmax - l0 < chunk) ? Lmax - l0 : chunk;
     dim3 grid(nblk(l0 + nl, 128), nl);
     k_delta_slab<<<grid, 128, 0, st>>>(d64, d32, em, ee, l0);

@@ -7,9 +7,11 @@ namespace s2dw {
 
 cudaError_t launch_kernel_values(double* kap, double* phi, double* sabs, double2* psi, double* q, int L, int N,
                                  int J, double lam, const double* glx, const double* glw, int Q, int P,
-                                 cudaStream_t st);
+                                 double* I0, cudaStream_t st);
 cudaError_t launch_dh_weights(double* q, int L, cudaStream_t st);  // Eq. (18), 2L weights
-cudaError_t launch_delta_build(double* d64, float* d32, double* em, int* ee, int Lmax, cudaStream_t st);
+// slabs l_first .. Lmax-1 (the edge arrays em/ee always cover l < Lmax)
+cudaError_t launch_delta_build(double* d64, float* d32, double* em, int* ee, int Lmax, int l_first,
+                               cudaStream_t st);
 template <typename T>
 cudaError_t launch_rtable(T* RS, const double* d64, const double* kap, const double* sabs, const int* slotj, int L,
                           int Lp, int N, int nslot, int kapL, cudaStream_t st);

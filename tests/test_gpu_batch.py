@@ -103,3 +103,30 @@ def test_batch_in_cuda_graph_then_destroy():
     torch.cuda.synchronize()
     for p in plans:
         p.close()  # raises on a non-zero status
+
+
+def test_batch_cache_eviction():
+    """More distinct plan sets than the launch-list cache holds (64): every
+    batch, including ones whose lists were evicted and rebuilt, equals the
+    single runs."""
+    import itertools
+    import torch
+    specs = [(16, 1 + i % 4, 2.0, 0) for i in range(12)]
+    plans = [B.Plan(*s, "mixed") for s in specs]
+    cd, _ = plans[0].torch_dtypes()
+    fs = [torch.from_numpy(flm_gaussian(p.L, 60 + i, "cl")).to(cd).cuda() for i, p in enumerate(plans)]
+    ref = []
+    for p, f in zip(plans, fs):
+        W, Wp = p.alloc_w()
+        p.analysis(f, W, Wp)
+        ref.append(W)
+    pairs = list(itertools.combinations(range(12), 2))   # 66 distinct sets
+    for pair in pairs + pairs[:3]:                       # the first three again, after eviction
+        Wb = [plans[i].alloc_w() for i in pair]
+        B.s2dw_analysis_batch([plans[i].handle for i in pair], [fs[i] for i in pair],
+                              [w[0] for w in Wb], [w[1] for w in Wb])
+        torch.cuda.synchronize()
+        for i, w in zip(pair, Wb):
+            assert torch.equal(w[0], ref[i]), pair
+    for p in plans:
+        p.close()
