@@ -97,10 +97,12 @@ inline void afree(void* p, cudaStream_t st) {
 struct DeltaTab {
   int Lmax;
   int device;
-  double* d64;
+  double* d64;  // entry 0 of the table (kDeltaFront zero entries precede it)
   float* d32;
   int refs;
   size_t bytes;
+  double* raw64 = nullptr;  // the allocations
+  float* raw32 = nullptr;
 };
 std::mutex g_mu;
 std::vector<DeltaTab*> g_tabs;
@@ -132,8 +134,12 @@ DeltaTab* delta_acquire(int L, cudaStream_t st) {
   try {
     // kDeltaPad spare entries: the contraction copies 16-byte chunks of row
     // segments that may run past the last row of the last slab
-    amalloc(&t->d64, (entries + kDeltaPad) * sizeof(double), st);
-    amalloc(&t->d32, (entries + kDeltaPad) * sizeof(float), st);
+    amalloc(&t->raw64, (kDeltaFront + entries + kDeltaPad) * sizeof(double), st);
+    amalloc(&t->raw32, (kDeltaFront + entries + kDeltaPad) * sizeof(float), st);
+    ck(cudaMemsetAsync(t->raw64, 0, kDeltaFront * sizeof(double), st));
+    ck(cudaMemsetAsync(t->raw32, 0, kDeltaFront * sizeof(float), st));
+    t->d64 = t->raw64 + kDeltaFront;
+    t->d32 = t->raw32 + kDeltaFront;
     t->bytes = entries * (sizeof(double) + sizeof(float));
     const int64_t kept = delta_slab_offset(l_first);
     if (donor) {
@@ -153,8 +159,8 @@ DeltaTab* delta_acquire(int L, cudaStream_t st) {
     cudaStreamSynchronize(st);
     afree(em, st);
     afree(ee, st);
-    afree(t->d64, st);
-    afree(t->d32, st);
+    afree(t->raw64, st);
+    afree(t->raw32, st);
     delete t;
     throw;
   }
@@ -167,8 +173,8 @@ void delta_release(DeltaTab* t) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (--t->refs == 0) {
     cudaStream_t st = setup_stream();
-    afree(t->d64, st);
-    afree(t->d32, st);
+    afree(t->raw64, st);
+    afree(t->raw32, st);
     g_tabs.erase(std::remove(g_tabs.begin(), g_tabs.end(), t), g_tabs.end());
     delete t;
   }

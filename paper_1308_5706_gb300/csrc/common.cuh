@@ -70,6 +70,14 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
 }
+// 16 bytes to a 32-bit shared-memory address: whole (no size operand) or
+// the first src_bytes with the rest zero-filled
+__device__ __forceinline__ void cp_async16_s(uint32_t saddr, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16_s(uint32_t saddr, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(gmem), "r"(src_bytes) : "memory");
+}
 // one element of 4, 8 or 16 bytes, cached in L1 (.ca allows the small sizes)
 template <int BYTES>
 __device__ __forceinline__ void cp_async_ca(void* smem, const void* gmem) {

@@ -121,8 +121,9 @@ __host__ __device__ constexpr size_t contract_smem_bytes() {
   return contract_stages<T, N, NSLOT, SYN, E>() * StageGeom<T, N, NSLOT, E>::BYTES + contract_red_bytes<T, SYN>();
 }
 
+// Two CTAs per SM (128 registers) where the accumulators allow it (FP32, N <= 5).
 template <typename T, int N, int NSLOT, bool SYN, int E>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && N <= 5 ? 2 : 1))
 k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict__ tiles, CallPtrs ptrs) {
   using G = StageGeom<T, N, NSLOT, E>;
   constexpr int STAGES = contract_stages<T, N, NSLOT, SYN, E>();
@@ -192,7 +193,12 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   // ---- producer: stage the operands of iteration l into ring slot st ----
   // Per-thread copy roles are fixed for the whole tile; only the slab, f and
   // R offsets move with l, and they advance incrementally (issue() is called
-  // for l_start, l_start+1, ... in order).
+  // for l_start, l_start+1, ... in order).  Offsets are 32-bit element
+  // offsets (a table of L = 2048 has 1.44e9 entries) and destinations 32-bit
+  // shared addresses.  Rows of the Delta block past the slab (m' or m > l)
+  // are copied unguarded: they read neighbouring table entries (finite; the
+  // table has a zero front pad for the rows of small l that start before it)
+  // and meet zero R rows (m' > l) or zero f (m > l).
   const int t = threadIdx.x;
   constexpr int CPRA = TILE / EPC, CPRB = TMP / EPC, CPRR = TMP / EPC;
   constexpr int FCH = 2 * TILE / EPC, CPC = EPC / 2, NRCH = NSLOT * NH * CPRR;
@@ -201,47 +207,43 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   const int ra = mp0 + t / CPRA, rb = m0 + t / CPRB;
   const int a_A = delta_row_A(ra, m0 + (t % CPRA) * EPC), a_B = delta_row_B(ra);
   const int b_A = delta_row_A(rb, mp0 + (t % CPRB) * EPC), b_B = delta_row_B(rb);
-  const int a_dst = G::A_OFF + (t / CPRA) * G::APITCH + (t % CPRA) * EPC;
-  const int b_dst = G::B_OFF + (t / CPRB) * G::BPITCH + (t % CPRB) * EPC;
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+  const uint32_t a_dst = ring_s + (uint32_t)(G::A_OFF + (t / CPRA) * G::APITCH + (t % CPRA) * EPC) * sizeof(T);
+  const uint32_t b_dst = ring_s + (uint32_t)(G::B_OFF + (t / CPRB) * G::BPITCH + (t % CPRB) * EPC) * sizeof(T);
   const int fq = t - 256 + FCH;
   const int f_mm = m0 + fq * CPC;
+  const uint32_t f_dst = ring_s + (uint32_t)(G::F_OFF + fq * EPC) * sizeof(T);
   const bool do_r = t < NRCH;
-  const int r_src = (t / CPRR) * Lp + mp0 + (t % CPRR) * EPC;
-  const int r_dst = G::R_OFF + (t / CPRR) * TMP + (t % CPRR) * EPC;
-  int64_t is_slab = delta_slab_offset(l_start);  // state of the next issue
-  int64_t is_f = (int64_t)l_start * l_start + l_start;
-  const T* is_rs = RS + (size_t)l_start * (NSLOT * NH) * Lp;
+  const uint32_t r_dst = ring_s + (uint32_t)(G::R_OFF + (t / CPRR) * TMP + (t % CPRR) * EPC) * sizeof(T);
+  int is_slab = (int)delta_slab_offset(l_start);  // state of the next issue
+  int is_f = l_start * l_start + l_start + f_mm;
+  int is_rs = l_start * (NSLOT * NH) * Lp + (t / CPRR) * Lp + mp0 + (t % CPRR) * EPC;
   int is_l = l_start;
-  auto issue = [&](int st) {
+  int wr = 0;  // ring slot of the next issue
+  auto issue = [&]() {
     const int l = is_l;
     if (l <= l_end) {
-      T* S = ring + st * G::SIZE;
-      const int cl = (l >> 2) + 1, rows_in_slab = 4 * cl;
-      const T* __restrict__ slab = delta + is_slab;
-      if (do_a) {
-        const bool ok = ra < rows_in_slab;
-        cp_async16(S + a_dst, ok ? slab + a_A + a_B * cl : slab, ok ? 16 : 0);
-      }
-      if (do_b) {
-        const bool ok = rb < rows_in_slab;
-        cp_async16(S + b_dst, ok ? slab + b_A + b_B * cl : slab, ok ? 16 : 0);
-      }
+      const uint32_t so = (uint32_t)wr * (uint32_t)G::BYTES;
+      const int cl = (l >> 2) + 1;
+      if (do_a) cp_async16_s(a_dst + so, delta + (is_slab + a_A + a_B * cl));
+      if (do_b) cp_async16_s(b_dst + so, delta + (is_slab + b_A + b_B * cl));
       if (!SYN && fq >= 0) {
         // f_lm for m in [m0, m0 + TILE), zero beyond m = l (the array ends at l = L-1)
         const int nvalid = min(CPC, max(0, l + 1 - f_mm));
-        cp_async16(S + G::F_OFF + fq * EPC, f + (nvalid > 0 ? is_f + f_mm : 0), nvalid * (int)sizeof(cx<T>));
+        cp_async16_s(f_dst + so, f + (nvalid > 0 ? is_f : 0), nvalid * (int)sizeof(cx<T>));
       }
-      if (do_r) cp_async16(S + r_dst, is_rs + r_src, 16);
-      is_slab += 8 * (int64_t)cl * (cl + 1);
+      if (do_r) cp_async16_s(r_dst + so, RS + is_rs);
+      is_slab += 8 * cl * (cl + 1);
       is_f += 2 * (l + 1);
-      is_rs += (size_t)(NSLOT * NH) * Lp;
+      is_rs += (NSLOT * NH) * Lp;
       is_l = l + 1;
     }
+    wr = (wr + 1 == STAGES) ? 0 : wr + 1;
     cp_async_commit();
   };
 
 #pragma unroll
-  for (int i = 0; i < STAGES - 2; ++i) issue(i);
+  for (int i = 0; i < STAGES - 2; ++i) issue();
 
   constexpr bool PACK = std::is_same<T, float>::value && E == 4;
   Acc<T, E, NSLOT, N, PACK> acc;
@@ -331,6 +333,7 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   __syncthreads();  // cgk visible
   // Two l per barrier: stages it, it+1 are waited for together and stages
   // it+S-2, it+S-1 are issued into the slots that l-2, l-1 have released.
+  int rd = 0;  // ring slot of the next iteration processed
   auto process = [&](const int l, const int it, auto bank) {
     constexpr int BQ = decltype(bank)::value * NP;  // first accumulator of this l's bank
     // slot occupancy changes at segment boundaries
@@ -354,7 +357,8 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
         }
       }
     }
-    const T* S = ring + (it % STAGES) * G::SIZE;
+    const T* S = ring + rd * G::SIZE;
+    rd = (rd + 1 == STAGES) ? 0 : rd + 1;
     // Every element computes: out-of-range rows and columns contribute exact
     // zeros (zero R rows for m' > l or inactive slots, zero-filled f for
     // m > l, zero H outside a scale's band), and synthesis partials of
@@ -466,8 +470,8 @@ k_contract(const ContractDesc<T>* __restrict__ descs, const TileTask* __restrict
   for (int it = 0; it < n_it; it += 2) {
     cp_async_wait<STAGES - 4>();
     __syncthreads();
-    issue((it + STAGES - 2) % STAGES);
-    issue((it + STAGES - 1) % STAGES);
+    issue();
+    issue();
     if (SYN && it > 0 && (it % LCH) == 0) reduce_chunk(rbuf ^ 1, l_start + it - LCH, LCH);
     process(l_start + it, it, std::integral_constant<int, 0>());
     if (it + 1 < n_it) process(l_start + it + 1, it + 1, std::integral_constant<int, 1>());

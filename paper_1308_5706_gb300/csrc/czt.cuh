@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256) k_alpha_ana_direct(const CztSeg<T>* __res
         st[q] = __ldg(root + aq[q]);
         w[q] = st[q];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) acc[q][r] = Xs[rg + r][0].x;
+        for (int r = 0; r < 8; ++r) acc[q][r] = Lj > 0 ? Xs[rg + r][0].x : T(0);  // empty scale: W = 0
       }
       for (int m = 1; m < Lj; ++m) {
         if ((m & 15) == 0) {

@@ -117,6 +117,8 @@ template <> void launch_syn_reduce<double>(const ReduceJobs&, int, int, cudaStre
 cudaError_t czt_prepare_f32(int maxlogM);
 cudaError_t czt_prepare_f64(int maxlogM);
 int contract_rows_per_thread(bool fp64);
-constexpr int kDeltaPad = 64;  // spare entries after a Delta table (row-segment copies)
+constexpr int kDeltaPad = 64;     // spare entries after a Delta table (row-segment copies)
+constexpr int kDeltaFront = 512;  // zero entries before it: the contraction's unguarded row
+                                  // copies start up to 324 entries early (small l)
 
 }  // namespace s2dw

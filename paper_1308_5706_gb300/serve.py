@@ -16,13 +16,17 @@ Scheduling (host thread, non-blocking):
     (s2dw_analysis_batch / s2dw_synthesis_batch) on its own CUDA stream, so
     work that arrives while other batches are on the GPU overlaps with them;
   * completion is observed with CUDA events; latency = completion - arrival.
-Plans are pooled per (L, N, lambda, J0, precision) and reused.  Results are
-deterministic (no atomics in the kernels), so a request gives bit-identical
-output alone and in the mix.
+Plans are pooled per (L, N, lambda, J0, precision) and reused.  A request
+whose configuration has no free plan waits while one is created on a worker
+thread (plan creation runs device kernels and blocks its thread for
+milliseconds; the library call releases the GIL), so the scheduler keeps
+launching other work meanwhile.  Results are deterministic (no atomics in the
+kernels), so a request gives bit-identical output alone and in the mix.
 """
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
 import math
 import time
@@ -84,7 +88,8 @@ def poisson_workload(rate: float, duration: float, seed: int, L_range=(32, 2048)
 
 class Server:
     def __init__(self, precision: str = "mixed", slots: int = 4, max_batch: int = 16,
-                 hbm_budget: Optional[int] = None, max_pool_bytes: Optional[int] = None):
+                 hbm_budget: Optional[int] = None, max_pool_bytes: Optional[int] = None,
+                 plan_workers: int = 2):
         import torch
         self.torch = torch
         self.precision = precision
@@ -98,20 +103,40 @@ class Server:
         self.in_use = 0            # bytes of f/W buffers alive
         self.rejected = 0          # admission deferrals (budget or slots)
         self.stats = collections.Counter()
+        self.workers = concurrent.futures.ThreadPoolExecutor(max_workers=max(1, plan_workers))
+        self.creating: Dict[tuple, List[concurrent.futures.Future]] = collections.defaultdict(list)
 
     # ---- plans -------------------------------------------------------------
     def _key(self, r: Request):
         return (r.L, r.N, r.lam, r.J0, self.precision)
 
-    def _take_plan(self, r: Request) -> B.Plan:
-        lst = self.pool[self._key(r)]
+    def _take_plan(self, r: Request) -> Optional[B.Plan]:
+        """A free plan of r's configuration, or None (one is then being made)."""
+        key = self._key(r)
+        lst = self.pool[key]
         if lst:
-            self.stats["plan_reuse"] += 1
+            self.stats["plan_take"] += 1
             p = lst.pop()
             self.pool_bytes -= p.info["workspace_bytes"]
             return p
-        self.stats["plan_create"] += 1
-        return B.Plan(r.L, r.N, r.lam, r.J0, self.precision)
+        if not self.creating[key]:
+            self.stats["plan_create"] += 1
+            self.creating[key].append(self.workers.submit(self._make_plan, r.L, r.N, r.lam, r.J0))
+        return None
+
+    def _make_plan(self, L, N, lam, J0):
+        t0 = time.perf_counter()
+        p = B.Plan(L, N, lam, J0, self.precision)
+        return p, time.perf_counter() - t0
+
+    def _collect_plans(self):
+        for key, futs in self.creating.items():
+            for fu in [f for f in futs if f.done()]:
+                futs.remove(fu)
+                p, dt = fu.result()
+                self.stats["plan_create_s"] += dt
+                self.pool[key].append(p)
+                self.pool_bytes += p.info["workspace_bytes"]
 
     def prewarm(self, reqs: List[Request], per_key: int = 1) -> float:
         """Create `per_key` plans for every configuration in `reqs` ahead of
@@ -180,6 +205,7 @@ class Server:
                                 self.in_use -= _nbytes(r.f)
                                 r.f = None
                     busy[s] = None
+            self._collect_plans()
             # arrivals -> ready (synthesis waits for its analysis)
             while pending and pending[0].arrival <= now:
                 ready.append(pending.popleft())
@@ -189,26 +215,29 @@ class Server:
                     continue
                 kind = None
                 batch: List[Request] = []
+                plans: List[B.Plan] = []
                 budget_left = self.budget - self.in_use - self.pool_bytes
                 for r in list(ready):
                     if r.kind == "synthesis" and not (by_id[r.parent].t_done <= now):
                         continue
-                    if kind is None:
-                        kind = r.kind
-                    if r.kind != kind or len(batch) >= self.max_batch:
+                    if (kind is not None and r.kind != kind) or len(batch) >= self.max_batch:
                         continue
                     fp = self._footprint(r)
                     if fp > budget_left and (batch or self.in_use > 0):
                         self.rejected += 1
                         continue
+                    p = self._take_plan(r)
+                    if p is None:
+                        continue
+                    kind = r.kind
                     batch.append(r)
+                    plans.append(p)
                     budget_left -= fp
                 if not batch:
                     continue
                 for r in batch:
                     ready.remove(r)
                 stream = self.streams[s]
-                plans = [self._take_plan(r) for r in batch]
                 with torch.cuda.stream(stream):
                     if kind == "analysis":
                         for r, p in zip(batch, plans):
@@ -255,9 +284,12 @@ class Server:
                                "mean": float(lat.mean()), "max": float(lat.max())},
                 "admission_deferrals": self.rejected, "batches": self.stats["batches"],
                 "mean_batch": self.stats["batched_jobs"] / max(1, self.stats["batches"]),
-                "plans_created": self.stats["plan_create"], "plans_reused": self.stats["plan_reuse"]}
+                "plans_created": self.stats["plan_create"], "plans_taken_from_pool": self.stats["plan_take"],
+                "plan_create_s": round(self.stats["plan_create_s"], 3)}
 
     def close(self):
+        self.workers.shutdown(wait=True)
+        self._collect_plans()
         for lst in self.pool.values():
             for p in lst:
                 p.close()
