@@ -212,8 +212,9 @@ __device__ __forceinline__ void fft_inv_stage(cx<T>* A, int M, int S, const cx<T
   }
 }
 
-// Innermost stage (Q = 1): forward DFT, product with the spectrum (same
-// order), inverse DFT.  H == nullptr: forward only (used to build spectra).
+// Innermost stage (Q = 1): forward DFT, product with the spectrum (entry k
+// of block u stored at H[k (M/R) + u]), inverse DFT.  H == nullptr: forward
+// only (used to build spectra).
 template <typename T, int R, int NT = 1>
 __device__ __forceinline__ void fft_mid_stage(cx<T>* A, int M, const cx<T>* __restrict__ H, T scale, int ST = 0) {
   for (int u = threadIdx.x; u < M / R; u += blockDim.x) {
@@ -228,7 +229,7 @@ __device__ __forceinline__ void fft_mid_stage(cx<T>* A, int M, const cx<T>* __re
         DftR<T, R, false>::run(v);
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-          if (t == 0) h[k] = __ldg(H + base + k);
+          if (t == 0) h[k] = __ldg(H + k * (M / R) + u);
           v[k] = cmul<T>(v[k], h[k]);
         }
         DftR<T, R, true>::run(v);

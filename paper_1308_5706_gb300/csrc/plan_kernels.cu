@@ -311,7 +311,9 @@ __global__ void k_chirp_kernels(double2* H, int L, int M) {
 }
 
 // Spectrum of each chirp kernel: the forward stages of the convolution engine
-// (its digit-reversed order), scaled by 1/M.
+// (its digit-reversed order), scaled by 1/M, stored for the innermost stage:
+// entry k of block u (position u R + k, R its radix) at k (M/R) + u, so that
+// the R loads of a thread are each coalesced across the warp.
 __global__ void __launch_bounds__(256) k_chirp_spectra(double2* H, const double2* tw, int logM) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* A = reinterpret_cast<double2*>(smem_raw);
@@ -320,7 +322,10 @@ __global__ void __launch_bounds__(256) k_chirp_spectra(double2* H, const double2
   for (int v = threadIdx.x; v < M; v += blockDim.x) A[fpad(v)] = h[v];
   __syncthreads();
   fft_forward_inplace<double>(A, logM, tw, 1.0 / M);
-  for (int v = threadIdx.x; v < M; v += blockDim.x) h[v] = A[fpad(v)];
+  int R, nmid;
+  fft_schedule(logM, R, nmid);
+  const int nb = M / R;
+  for (int v = threadIdx.x; v < M; v += blockDim.x) h[(v % R) * nb + v / R] = A[fpad(v)];
 }
 
 template <typename T>
