@@ -35,7 +35,8 @@ METRIC = "wavelet analysis+synthesis transforms/s at L=1024,N=5 (mixed vs FP64, 
 UNIT = "transforms/s"
 WORKLOAD = "L=1024, N=5, lambda=2, J0=0 (11 scales), real Gaussian f_lm C_l=1/(l(l+1)), seed 2"
 FP32_LANES_PER_SM, N_SM = 128, 152
-DIRECT_MAX_LJ = 32  # scales with L_j <= 32 take the direct alpha sums
+# scales with L_j up to these take the direct alpha sums (analysis, synthesis)
+DIRECT_MAX_LJ = {"ana": 32, "syn": 32}
 
 
 def peaks():
@@ -215,17 +216,17 @@ def contraction_flops(plan) -> float:
     return tot
 
 
-def alpha_bytes(plan, elem: int, direct: bool) -> float:
+def alpha_bytes(plan, elem: int, direct: bool, side: str) -> float:
     """Algorithmic bytes of one alpha launch over the scales it handles
-    (direct: L_j <= 32, else chirp-z): W written (or read) once plus the
-    [N][2L][L_j] complex rows read (or written) once."""
+    (direct: L_j <= DIRECT_MAX_LJ[side], else chirp-z): W written (or read)
+    once plus the [N][2L][L_j] complex rows read (or written) once."""
     n = 2 * L - 1
     tot = 0.0
     for j in range(plan.nscale + 1):
         phi = j == plan.nscale
         lo, hi = plan.support(j)
         Lj = hi + 1
-        if Lj <= 0 or (Lj <= DIRECT_MAX_LJ) != direct:
+        if Lj <= 0 or (Lj <= DIRECT_MAX_LJ[side]) != direct:
             continue
         rows = (1 if phi else N) * 2 * L
         tot += rows * n * elem + rows * Lj * 2 * elem
@@ -245,13 +246,13 @@ def fft_flops(M: int) -> float:
     return 5.0 * M * math.log2(M)
 
 
-def alpha_czt_flops(plan) -> float:
+def alpha_czt_flops(plan, side: str) -> float:
     """Algorithmic flops of one chirp-z alpha launch: per complex transform
     (two real rows) two length-M FFTs and the spectrum product (6M)."""
     M, pairs = fft_len(plan.L), 0
     for j in range(plan.nscale + 1):
         Lj = plan.support(j)[1] + 1
-        if Lj > DIRECT_MAX_LJ:
+        if Lj > DIRECT_MAX_LJ[side]:
             pairs += (1 if j == plan.nscale else N) * L
     return pairs * (2 * fft_flops(M) + 6.0 * M)
 
@@ -267,10 +268,7 @@ def beta_flops(plan) -> float:
 
 # DRAM bytes per launch (read + write) of kernels captured with ncu on this
 # workload; None once the kernel has changed since the capture.
-NCU_TRAFFIC = {
-    "syn_alpha_czt": (0.503277e9 + 0.242538e9, "profiles/k_czt_alpha_L1024_N5.md"),
-    "ana_alpha_czt": (0.246671e9 + 0.459426e9, "profiles/k_czt_alpha_L1024_N5.md"),
-}
+NCU_TRAFFIC = {}
 
 
 def roofline(pm, mean_stage):
@@ -281,9 +279,10 @@ def roofline(pm, mean_stage):
     alu_src = f"derived FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz"
     work = {
         "ana_contract": ("alu", contraction_flops(pm)), "syn_contract": ("alu", contraction_flops(pm)),
-        "ana_alpha_czt": ("alu", alpha_czt_flops(pm)), "syn_alpha_czt": ("alu", alpha_czt_flops(pm)),
+        "ana_alpha_czt": ("alu", alpha_czt_flops(pm, "ana")), "syn_alpha_czt": ("alu", alpha_czt_flops(pm, "syn")),
         "ana_beta": ("alu", beta_flops(pm)), "syn_beta": ("alu", beta_flops(pm)),
-        "ana_alpha_direct": ("hbm", alpha_bytes(pm, 4, True)), "syn_alpha_direct": ("hbm", alpha_bytes(pm, 4, True)),
+        "ana_alpha_direct": ("hbm", alpha_bytes(pm, 4, True, "ana")),
+        "syn_alpha_direct": ("hbm", alpha_bytes(pm, 4, True, "syn")),
     }
     per = {}
     for k, (bound, w) in work.items():

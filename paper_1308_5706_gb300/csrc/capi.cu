@@ -408,7 +408,8 @@ void sort_tiles(std::vector<TileTask>& t) {
 
 template <typename T>
 void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, int& start) {
-  // kinds 4 / 5 collect the alpha segments of scales with Lj <= kDirectMaxLj,
+  // kinds 4 / 5 collect the alpha segments of scales with Lj <= kDirectMaxLjAna
+  // (analysis) or kDirectMaxLj (synthesis),
   // kinds 6 / 7 the beta segments of plans whose FFT length M is 4L
   const int base_kind = (kind == CZT_ALPHA_ANA_DIRECT) ? CZT_ALPHA_ANA
                         : (kind == CZT_ALPHA_SYN_DIRECT) ? CZT_ALPHA_SYN
@@ -438,7 +439,7 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     s.tw = reinterpret_cast<const cx<T>*>(G.tw);
     s.scale = (T)(2.0 * 3.14159265358979323846 / n);
     const bool is_alpha = base_kind == CZT_ALPHA_ANA || base_kind == CZT_ALPHA_SYN;
-    const bool direct = is_alpha && Lj <= kDirectMaxLj;
+    const bool direct = is_alpha && Lj <= (base_kind == CZT_ALPHA_ANA ? kDirectMaxLjAna : kDirectMaxLj);
     if (direct != direct_list) continue;
     switch (base_kind) {
       case CZT_BETA_ANA:
@@ -479,8 +480,10 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
       s.post = reinterpret_cast<const cx<T>*>(G.bfft) + (2 * L - 1);
     }
     if (direct) {
-      const int rows = (base_kind == CZT_ALPHA_ANA) ? kDirectRowsAna : direct_rows_syn(sizeof(T) == 8);
-      s.items = (Nj * 2 * L + rows - 1) / rows;
+      if (base_kind == CZT_ALPHA_ANA)
+        s.items = ((n + kAgCols - 1) / kAgCols) * ((Nj * 2 * L + kAgChunk - 1) / kAgChunk);
+      else
+        s.items = (Nj * 2 * L + direct_rows_syn(sizeof(T) == 8) - 1) / direct_rows_syn(sizeof(T) == 8);
       s.pre = reinterpret_cast<const cx<T>*>(G.root_a);
     }
     if (s.items <= 0) continue;

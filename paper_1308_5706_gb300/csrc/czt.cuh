@@ -328,58 +328,135 @@ __global__ void __launch_bounds__(256, 2) k_beta_syn_fft(const CztSeg<T>* __rest
 // of m (or a) and are re-read exactly from the root table every 16 steps.
 // ---------------------------------------------------------------------------
 constexpr int kDirectMax = kDirectMaxLj;
-constexpr int kDRowsAna = kDirectRowsAna;
 
 // W[row][a] = X_0 + 2 sum_{m=1}^{Lj-1} Re(X_m e^{2 pi i m a / n})   (Eq. (30), Hermitian in m)
+// as a small matrix product W = A B over k < K = 2 Lj - 1 with
+//   A[row] = (X_0.x, X_1.x, X_1.y, X_2.x, ...),
+//   B[.][a] = (1, 2 cos(2 pi a/n), -2 sin(2 pi a/n), 2 cos(4 pi a/n), ...).
+// A CTA owns kAgCols consecutive samples a and kAgChunk rows: it builds its
+// B tile once in shared memory from the exact root table (index m a mod n
+// advanced by additions), then per pass of kAgRows rows stages A and
+// accumulates a register tile of 8 rows x 4 samples per thread, samples
+// lane + 32 i so that every store of a warp is one 128-byte line.  Layouts:
+// B[k][lane][i] (one 16-byte load per k), A[k][row] (FP32: each value
+// duplicated, so that 16-byte loads give the (A, A) operand pairs of the
+// packed f32x2 multiply-adds).
 template <typename T>
 __global__ void __launch_bounds__(256) k_alpha_ana_direct(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
-  __shared__ cx<T> Xs[kDRowsAna][kDirectMax];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool PACK = sizeof(T) == 4;
+  constexpr int KMAX = 2 * kDirectMaxLjAna - 1;
+  constexpr int AW = PACK ? 2 : 1;          // stored copies of each A value
+  T* Bs = reinterpret_cast<T*>(smem_raw);  // [KMAX][32][4]
+  T* As = Bs + KMAX * kAgCols;              // [KMAX][kAgRows][AW]
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
   const int item = blockIdx.x - sg.start;
-  const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1;
-  const int nrows = sg.N * 2 * L, row0 = item * kDRowsAna, nr = min(kDRowsAna, nrows - row0);
-  const cx<T>* __restrict__ root = sg.pre;  // e^{2 pi i t / n}, t < n
-  for (int i = threadIdx.x; i < kDRowsAna * Lj; i += blockDim.x) {
-    const int r = i / Lj, m = i % Lj;
-    Xs[r][m] = r < nr ? sg.buf_in[(size_t)(row0 + r) * Lj + m] : mkc<T>(0, 0);
-  }
-  __syncthreads();
+  const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1, K = 2 * Lj - 1;
+  const int ntile = (n + kAgCols - 1) / kAgCols;
+  const int a0 = (item % ntile) * kAgCols;
+  const int nrows = sg.N * 2 * L, rbeg = (item / ntile) * kAgChunk, rend = min(nrows, rbeg + kAgChunk);
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const cx<T>* __restrict__ root = sg.pre;  // e^{2 pi i u / n}, u < n
   T* __restrict__ Wb = reinterpret_cast<T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff;
-  for (int a0 = threadIdx.x; a0 < n; a0 += 4 * blockDim.x) {
-    int aq[4];
+  if (K <= 0) {  // empty scale: W = 0
+    for (int r = rbeg; r < rend; ++r)
+      for (int c = t; c < kAgCols; c += blockDim.x)
+        if (a0 + c < n) Wb[(size_t)r * n + a0 + c] = T(0);
+    return;
+  }
+  // B tile: thread t fills sample c = t % kAgCols for m = 1 + t / kAgCols, step 256 / kAgCols
+  {
+    constexpr int MS = 256 / kAgCols;
+    const int c = t % kAgCols, a = a0 + c;
+    const int pos = (c & 31) * 4 + (c >> 5);  // [lane][i] of sample c = lane + 32 i
+    const bool ok = a < n;
+    if (t < kAgCols) Bs[pos] = ok ? T(1) : T(0);
+    int m = 1 + t / kAgCols;
+    int u = ok ? (int)(((long long)m * a) % n) : 0;
+    const int du = ok ? (int)(((long long)MS * a) % n) : 0;
+#pragma unroll 8
+    for (; m < Lj; m += MS) {  // unrolled: the root loads of 8 steps are in flight together
+      const cx<T> e = ok ? __ldg(root + u) : mkc<T>(0, 0);
+      Bs[(2 * m - 1) * kAgCols + pos] = T(2) * e.x;
+      Bs[(2 * m) * kAgCols + pos] = T(-2) * e.y;
+      u += du;
+      if (u >= n) u -= n;
+    }
+  }
+  for (int r0 = rbeg; r0 < rend; r0 += kAgRows) {
+    const int nr = min(kAgRows, rend - r0);
+    __syncthreads();  // B tile written / previous pass done with As
+#pragma unroll 4
+    for (int i = t; i < kAgRows * Lj; i += blockDim.x) {
+      const int m = i / kAgRows, r = i % kAgRows;  // consecutive threads: consecutive rows (no bank conflicts)
+      const cx<T> x = r < nr ? sg.buf_in[(size_t)(r0 + r) * Lj + m] : mkc<T>(0, 0);
+      const int k1 = m == 0 ? 0 : 2 * m - 1;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) aq[q] = min(a0 + q * (int)blockDim.x, n - 1);
-    for (int rg = 0; rg < kDRowsAna; rg += 8) {
-      T acc[4][8];
-      cx<T> w[4], st[4];
+      for (int d = 0; d < AW; ++d) As[(k1 * kAgRows + r) * AW + d] = x.x;
+      if (m > 0) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        st[q] = __ldg(root + aq[q]);
-        w[q] = st[q];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) acc[q][r] = Lj > 0 ? Xs[rg + r][0].x : T(0);  // empty scale: W = 0
+        for (int d = 0; d < AW; ++d) As[((k1 + 1) * kAgRows + r) * AW + d] = x.y;
       }
-      for (int m = 1; m < Lj; ++m) {
-        if ((m & 15) == 0) {
+    }
+    __syncthreads();
+    T out[8][4];
+    if constexpr (PACK) {
+      f2p acc[8][2];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) w[q] = __ldg(root + (int)(((long long)m * aq[q]) % n));
+      for (int r = 0; r < 8; ++r) acc[r][0] = acc[r][1] = 0;
+      const float4* __restrict__ ap = reinterpret_cast<const float4*>(As) + 4 * w;  // rows 8w.. as (A, A) pairs
+      const float4* __restrict__ bp = reinterpret_cast<const float4*>(Bs) + lane;
+#pragma unroll 2
+      for (int k = 0; k < K; ++k) {
+        const float4 bq = bp[0];
+        const f2p b01 = pk2(bq.x, bq.y), b23 = pk2(bq.z, bq.w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 aq = ap[q];
+          const f2p ar0 = pk2(aq.x, aq.y), ar1 = pk2(aq.z, aq.w);
+          acc[2 * q][0] = fma2(ar0, b01, acc[2 * q][0]);
+          acc[2 * q][1] = fma2(ar0, b23, acc[2 * q][1]);
+          acc[2 * q + 1][0] = fma2(ar1, b01, acc[2 * q + 1][0]);
+          acc[2 * q + 1][1] = fma2(ar1, b23, acc[2 * q + 1][1]);
         }
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const cx<T> x = Xs[rg + r][m];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q][r] += T(2) * (x.x * w[q].x - x.y * w[q].y);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = cmul<T>(w[q], st[q]);
+        ap += kAgRows / 2;
+        bp += kAgCols / 4;
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int a = a0 + q * (int)blockDim.x;
-        if (a < n) {
+      for (int r = 0; r < 8; ++r) {
+        upk2(acc[r][0], out[r][0], out[r][1]);
+        upk2(acc[r][1], out[r][2], out[r][3]);
+      }
+    } else {
 #pragma unroll
-          for (int r = 0; r < 8; ++r)
-            if (rg + r < nr) Wb[(size_t)(row0 + rg + r) * n + a] = acc[q][r];
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[r][i] = T(0);
+      const T* __restrict__ ap = As + 8 * w;
+      const T* __restrict__ bp = Bs + 4 * lane;
+#pragma unroll 2
+      for (int k = 0; k < K; ++k) {
+        T av[8], bv[4];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) av[r] = ap[r];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) bv[i] = bp[i];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) out[r][i] = fma(av[r], bv[i], out[r][i]);
+        ap += kAgRows;
+        bp += kAgCols;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int row = 8 * w + r;
+      if (row < nr) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int a = a0 + lane + 32 * i;
+          if (a < n) Wb[(size_t)(r0 + row) * n + a] = out[r][i];
         }
       }
     }
@@ -546,7 +623,9 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
   switch (kind) {
     case CZT_BETA_ANA: k_czt_beta_ana<T><<<grid, block, smem, st>>>(segs, nseg); break;
     case CZT_BETA_SYN: k_czt_beta_syn<T><<<grid, block, smem, st>>>(segs, nseg); break;
-    case CZT_ALPHA_ANA_DIRECT: k_alpha_ana_direct<T><<<grid, block, 0, st>>>(segs, nseg, ptrs); break;
+    case CZT_ALPHA_ANA_DIRECT:
+      k_alpha_ana_direct<T><<<grid, block, alpha_ana_direct_smem<T>(), st>>>(segs, nseg, ptrs);
+      break;
     case CZT_BETA_ANA_FFT:
       k_beta_ana_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
       break;
@@ -577,6 +656,9 @@ cudaError_t czt_set_smem(int maxlogM) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            smem * beta_fft_nt(sizeof(T) == 8));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_alpha_ana_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)alpha_ana_direct_smem<T>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_alpha_syn_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)alpha_syn_direct_smem<T>(2048));

@@ -58,13 +58,19 @@ enum CztKind {
   CZT_BETA_ANA_FFT = 6,      // beta sums as one FFT of length 4L (L a power of two)
   CZT_BETA_SYN_FFT = 7
 };
-constexpr int kDirectMaxLj = 32;
+constexpr int kDirectMaxLj = 32;     // synthesis: direct alpha sums for L_j <= 32
+constexpr int kDirectMaxLjAna = 32;  // analysis: direct (matrix-product) alpha sums for L_j <= 32
+// tile of the direct analysis kernel: samples per CTA, rows per pass, rows per CTA
+constexpr int kAgCols = 128, kAgRows = 64, kAgChunk = 512;
+template <typename T>  // B tile + A tile (FP32 stores each A value twice)
+constexpr size_t alpha_ana_direct_smem() {
+  return (size_t)(2 * kDirectMaxLjAna - 1) * (kAgCols + kAgRows * (sizeof(T) == 4 ? 2 : 1)) * sizeof(T);
+}
 // row pairs (complex transforms) per CTA of the alpha chirp-z kernels: FP32
 // runs two so that each table value serves both (FP64 buffers would not fit)
 __host__ __device__ constexpr int alpha_czt_nt(bool fp64) { return fp64 ? 1 : 2; }
 // adjacent columns per CTA of the single-FFT beta kernels (FP32: a 16-byte pair)
 __host__ __device__ constexpr int beta_fft_nt(bool fp64) { return fp64 ? 1 : 2; }
-constexpr int kDirectRowsAna = 16;
 inline int direct_rows_syn(bool fp64) { return fp64 ? 4 : 8; }  // 32-byte line per alpha sample
 
 // One segment of a chirp-z launch: all columns / row pairs of one scale of
