@@ -268,7 +268,12 @@ def beta_flops(plan) -> float:
 
 # DRAM bytes per launch (read + write) of kernels captured with ncu on this
 # workload; None once the kernel has changed since the capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "ana_alpha_czt": (0.246710e9 + 0.458258e9, "profiles/k_czt_alpha_L1024_N5.md"),
+    "syn_alpha_czt": (0.503261e9 + 0.243395e9, "profiles/k_czt_alpha_L1024_N5.md"),
+    "ana_contract": (1.218407e9 + 0.070254e9, "profiles/k_contract_L1024_N5.md"),
+    "syn_contract": (1.575094e9 + 0.091380e9, "profiles/k_contract_L1024_N5.md"),
+}
 
 
 def roofline(pm, mean_stage):
