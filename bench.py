@@ -35,8 +35,7 @@ METRIC = "wavelet analysis+synthesis transforms/s at L=1024,N=5 (mixed vs FP64, 
 UNIT = "transforms/s"
 WORKLOAD = "L=1024, N=5, lambda=2, J0=0 (11 scales), real Gaussian f_lm C_l=1/(l(l+1)), seed 2"
 FP32_LANES_PER_SM, N_SM = 128, 152
-# scales with L_j up to these take the direct alpha sums (analysis, synthesis)
-DIRECT_MAX_LJ = {"ana": 32, "syn": 32}
+SIDE = {"ana": 0, "syn": 1}  # direction index of s2dw_alpha_method
 
 
 def peaks():
@@ -218,15 +217,15 @@ def contraction_flops(plan) -> float:
 
 def alpha_bytes(plan, elem: int, direct: bool, side: str) -> float:
     """Algorithmic bytes of one alpha launch over the scales it handles
-    (direct: L_j <= DIRECT_MAX_LJ[side], else chirp-z): W written (or read)
-    once plus the [N][2L][L_j] complex rows read (or written) once."""
+    (direct sums, or chirp-z of either form, as the plan reports): W written
+    (or read) once plus the [N][2L][L_j] complex rows read (or written) once."""
     n = 2 * L - 1
     tot = 0.0
     for j in range(plan.nscale + 1):
         phi = j == plan.nscale
         lo, hi = plan.support(j)
         Lj = hi + 1
-        if Lj <= 0 or (Lj <= DIRECT_MAX_LJ[side]) != direct:
+        if Lj <= 0 or (plan.alpha_method(j, SIDE[side])[0] == 0) != direct:
             continue
         rows = (1 if phi else N) * 2 * L
         tot += rows * n * elem + rows * Lj * 2 * elem
@@ -247,14 +246,18 @@ def fft_flops(M: int) -> float:
 
 
 def alpha_czt_flops(plan, side: str) -> float:
-    """Algorithmic flops of one chirp-z alpha launch: per complex transform
-    (two real rows) two length-M FFTs and the spectrum product (6M)."""
-    M, pairs = fft_len(plan.L), 0
+    """Algorithmic flops of the chirp-z alpha launches of one direction: per
+    complex transform (two real rows) two length-M FFTs and the spectrum
+    product (6M); segmented: S + 1 FFTs of length M' and S products."""
+    tot = 0.0
     for j in range(plan.nscale + 1):
-        Lj = plan.support(j)[1] + 1
-        if Lj > DIRECT_MAX_LJ[side]:
-            pairs += (1 if j == plan.nscale else N) * L
-    return pairs * (2 * fft_flops(M) + 6.0 * M)
+        method, Mf, S, _ = plan.alpha_method(j, SIDE[side])
+        pairs = (1 if j == plan.nscale else N) * L
+        if method == 1:
+            tot += pairs * (2 * fft_flops(Mf) + 6.0 * Mf)
+        elif method == 2:
+            tot += pairs * ((S + 1) * fft_flops(Mf) + S * 6.0 * Mf)
+    return tot
 
 
 def beta_flops(plan) -> float:

@@ -113,6 +113,20 @@ int s2dw_query(s2dw_plan_t plan, int* J, int64_t* w_elems_per_scale, int64_t* wp
 int s2dw_scale_grid(s2dw_plan_t plan, int j, int* Lgrid, int64_t* offset, int64_t* elems);
 
 /*
+ * s2dw_alpha_method: how the alpha sums of scale j (0 <= j <= J, or J+1 for
+ * the scaling part) are evaluated (Eqs. (30), (37)), per direction
+ * (dir 0 analysis, 1 synthesis):
+ *   *method = 0: direct sums (small band L_j);
+ *             1: one chirp-z convolution of length *fft_len over all 2Lg-1
+ *                samples (*segments = 1);
+ *             2: segmented chirp-z: *segments convolutions of length
+ *                *fft_len, each covering *seg_len samples, sharing one
+ *                forward FFT (analysis) or one inverse FFT (synthesis).
+ * Host only; any output may be NULL.  S2DW_EINVAL for a bad j or dir.
+ */
+int s2dw_alpha_method(s2dw_plan_t plan, int j, int dir, int* method, int* fft_len, int* segments, int* seg_len);
+
+/*
  * s2dw_launch_counts: number of kernel launches one s2dw_analysis and one
  * s2dw_synthesis call of this plan issue (stages with no work launch
  * nothing).  Either pointer may be NULL.  Host only; no counterpart in the

@@ -32,6 +32,7 @@ _SIGNATURES = {
     "s2dw_query": (_c_i, [_c_p, _c_ip, _c_i64p, _c_i64p, _c_i64p, _c_i64p]),
     "s2dw_launch_counts": (_c_i, [_c_p, _c_ip, _c_ip]),
     "s2dw_scale_grid": (_c_i, [_c_p, _c_i, _c_ip, _c_i64p, _c_i64p]),
+    "s2dw_alpha_method": (_c_i, [_c_p, _c_i, _c_i, _c_ip, _c_ip, _c_ip, _c_ip]),
     "s2dw_steer": (_c_i, [_c_p, _c_p, _c_dp, _c_i, _c_p, _c_p]),
     "s2dw_sht_inverse": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
     "s2dw_sht_forward": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
@@ -147,6 +148,15 @@ def s2dw_scale_grid(plan: int, j: int):
     Lg, off, n = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
     _check(lib().s2dw_scale_grid(plan, j, ctypes.byref(Lg), ctypes.byref(off), ctypes.byref(n)), "s2dw_scale_grid")
     return Lg.value, off.value, n.value
+
+
+def s2dw_alpha_method(plan: int, j: int, direction: int):
+    """(method, fft_len, segments, seg_len) of the alpha sums of scale j;
+    direction 0 analysis, 1 synthesis; method 0 direct, 1 chirp-z,
+    2 segmented chirp-z."""
+    vals = [ctypes.c_int() for _ in range(4)]
+    _check(lib().s2dw_alpha_method(plan, j, direction, *[ctypes.byref(v) for v in vals]), "s2dw_alpha_method")
+    return tuple(v.value for v in vals)
 
 
 def s2dw_launch_counts(plan: int):
@@ -334,6 +344,10 @@ class Plan:
 
     def synthesis(self, W, Wphi, flm, stream=None):
         s2dw_synthesis(self.handle, W, Wphi, flm, stream)
+
+    def alpha_method(self, j: int, direction: int):
+        """(method, fft_len, segments, seg_len) of scale j's alpha sums (see s2dw_alpha_method)."""
+        return s2dw_alpha_method(self.handle, j, direction)
 
     def support(self, j):
         return s2dw_scale_support(self.handle, j)

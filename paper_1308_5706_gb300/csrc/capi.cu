@@ -26,6 +26,30 @@ inline void ck(cudaError_t e) {
   if (e != cudaSuccess) throw CudaFail{e};
 }
 
+// Segmented chirp-z choice for a band Lj on a grid of band L whose chirp-z
+// length is 2^logM: the length M' = 2^logMs (512 <= M' <= min(M/2, 4096)) and
+// S = ceil(n / P) segments of P = M' - 2 Lj + 2 samples (n = 2L - 1) that
+// minimise the FFT work (S + 1) M' log2 M', used where that is below 0.85 of
+// the two FFTs of length M of one convolution (else S = 0).
+void seg_choice(int L, int Lj, int logM, int& logMs, int& P, int& S) {
+  const int n = 2 * L - 1;
+  double best = 0.85 * 2.0 * (double)(1 << logM) * logM;
+  logMs = P = S = 0;
+  for (int lm = 9; lm <= std::min(logM - 1, 12); ++lm) {
+    const int Mp = 1 << lm, p = Mp - 2 * Lj + 2;
+    if (p <= 0) continue;
+    const int s = (n + p - 1) / p;
+    if (s > 64) continue;
+    const double c = (double)(s + 1) * Mp * lm;
+    if (c < best) {
+      best = c;
+      logMs = lm;
+      P = p;
+      S = s;
+    }
+  }
+}
+
 int jmax_of(int L, double lam) {
   int J = 0;
   double p = 1.0;
@@ -188,7 +212,7 @@ struct Lists {
   std::vector<std::pair<int, std::pair<void*, int>>> tiles_w;  // (N, (tiles, count))
   void* tiles_phi = nullptr;
   int ntiles_phi = 0;
-  static constexpr int NK = 8;  // chirp-z kinds 0..3, direct alpha 4..5, single-FFT beta 6..7
+  static constexpr int NK = 10;  // chirp-z 0..3, direct alpha 4..5, single-FFT beta 6..7, segmented alpha 8..9
   void* segs[NK] = {};
   int nseg[NK] = {};
   int items[NK] = {};
@@ -249,6 +273,14 @@ struct s2dw_plan_s {
   std::vector<GridTables> gt;  // one set per distinct grid band-limit
   std::vector<int> grid_of;    // [nscale + 1]: set of scale j (last: scaling part)
   std::vector<int64_t> woff;   // [nscale + 1]: element offset of scale j in W (last: total)
+  // segmented chirp-z of scale j (S == 0: one convolution of the grid's length M)
+  struct SegTables {
+    int logM = 0, P = 0, S = 0;
+    void* tw = nullptr;  // twiddles of length 2^logM
+    void* Ha = nullptr;  // S analysis spectra of length 2^logM
+    void* Hs = nullptr;  // S synthesis spectra
+  };
+  std::vector<SegTables> seg;  // [nscale + 1]
   // host copies of the static descriptors (device copies live in `own`)
   std::vector<unsigned char> desc_w_host, desc_phi_host;
   std::vector<TileTask> tiles_w_host, tiles_phi_host;
@@ -411,12 +443,14 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
   // kinds 4 / 5 collect the alpha segments of scales with Lj <= kDirectMaxLjAna
   // (analysis) or kDirectMaxLj (synthesis),
   // kinds 6 / 7 the beta segments of plans whose FFT length M is 4L
-  const int base_kind = (kind == CZT_ALPHA_ANA_DIRECT) ? CZT_ALPHA_ANA
-                        : (kind == CZT_ALPHA_SYN_DIRECT) ? CZT_ALPHA_SYN
+  // kinds 8 / 9 the alpha segments of scales with a segmented chirp-z
+  const int base_kind = (kind == CZT_ALPHA_ANA_DIRECT || kind == CZT_ALPHA_ANA_SEG) ? CZT_ALPHA_ANA
+                        : (kind == CZT_ALPHA_SYN_DIRECT || kind == CZT_ALPHA_SYN_SEG) ? CZT_ALPHA_SYN
                         : (kind == CZT_BETA_ANA_FFT)     ? CZT_BETA_ANA
                         : (kind == CZT_BETA_SYN_FFT)     ? CZT_BETA_SYN
                                                          : kind;
   const bool direct_list = kind == CZT_ALPHA_ANA_DIRECT || kind == CZT_ALPHA_SYN_DIRECT;
+  const bool seg_list = kind == CZT_ALPHA_ANA_SEG || kind == CZT_ALPHA_SYN_SEG;
   const bool fft_list = kind == CZT_BETA_ANA_FFT || kind == CZT_BETA_SYN_FFT;
   for (int j = 0; j <= p->nscale; ++j) {
     const bool phi = (j == p->nscale);
@@ -441,6 +475,7 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     const bool is_alpha = base_kind == CZT_ALPHA_ANA || base_kind == CZT_ALPHA_SYN;
     const bool direct = is_alpha && Lj <= (base_kind == CZT_ALPHA_ANA ? kDirectMaxLjAna : kDirectMaxLj);
     if (direct != direct_list) continue;
+    if (is_alpha && !direct && (p->seg[j].S > 0) != seg_list) continue;
     switch (base_kind) {
       case CZT_BETA_ANA:
         s.items = Nj * Lj;
@@ -478,6 +513,16 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
       s.items = Nj * ((Lj + ntb - 1) / ntb);
       s.pre = reinterpret_cast<const cx<T>*>(G.bfft);
       s.post = reinterpret_cast<const cx<T>*>(G.bfft) + (2 * L - 1);
+    }
+    if (seg_list) {
+      const auto& sgt = p->seg[j];
+      const int groups = 1 << (12 - sgt.logM);  // row pairs per CTA (one per group of M'/16 threads)
+      s.items = (Nj * L + groups - 1) / groups;
+      s.logM = sgt.logM;
+      s.tw = reinterpret_cast<const cx<T>*>(sgt.tw);
+      s.H = reinterpret_cast<const cx<T>*>(base_kind == CZT_ALPHA_ANA ? sgt.Ha : sgt.Hs);
+      s.P = sgt.P;
+      s.nsegs = sgt.S;
     }
     if (direct) {
       if (base_kind == CZT_ALPHA_ANA)
@@ -613,6 +658,8 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
   rec(ev, 3, st);
   launch_czt<T>(CZT_ALPHA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1], ls.maxlogM,
                 ptrs, st);
+  launch_czt<T>(CZT_ALPHA_ANA_SEG, reinterpret_cast<const CztSeg<T>*>(ls.segs[8]), ls.nseg[8], ls.items[8],
+                ls.maxlogM, ptrs, st);
   rec(ev, 4, st);
   launch_czt<T>(CZT_ALPHA_ANA_DIRECT, reinterpret_cast<const CztSeg<T>*>(ls.segs[4]), ls.nseg[4], ls.items[4],
                 ls.maxlogM, ptrs, st);
@@ -631,6 +678,8 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
   rec(ev, 1, st);
   launch_czt<T>(CZT_ALPHA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[2]), ls.nseg[2], ls.items[2], ls.maxlogM,
                 ptrs, st);
+  launch_czt<T>(CZT_ALPHA_SYN_SEG, reinterpret_cast<const CztSeg<T>*>(ls.segs[9]), ls.nseg[9], ls.items[9],
+                ls.maxlogM, ptrs, st);
   rec(ev, 2, st);
   launch_czt<T>(CZT_BETA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[3]), ls.nseg[3], ls.items[3], ls.maxlogM,
                 ptrs, st);
@@ -684,6 +733,22 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     go[g].bf = take((size_t)(4 * Lg - 1) * sizeof(cx<T>));
     go[g].H = take((size_t)4 * Mg * sizeof(cx<T>));
   }
+  // segmented chirp-z tables of the scales that use it (chirp-z bands only)
+  p->seg.assign(p->nscale + 1, s2dw_plan_s::SegTables());
+  struct SegOff { size_t tw, Ha, Hs; };
+  std::vector<SegOff> so(p->nscale + 1);
+  for (int j = 0; j <= p->nscale; ++j) {
+    const auto& G = p->gt[p->grid_of[j]];
+    const int Lj = p->Ycols[j];
+    if (Lj <= kDirectMaxLj) continue;  // direct sums
+    auto& sgt = p->seg[j];
+    seg_choice(G.L, Lj, G.logM, sgt.logM, sgt.P, sgt.S);
+    if (sgt.S == 0) continue;
+    const size_t Ms = (size_t)1 << sgt.logM;
+    so[j].tw = take((size_t)twiddle_entries(sgt.logM) * sizeof(cx<T>));
+    so[j].Ha = take((size_t)sgt.S * Ms * sizeof(cx<T>));
+    so[j].Hs = take((size_t)sgt.S * Ms * sizeof(cx<T>));
+  }
   p->ws_bytes = off;
   amalloc(&p->ws, off, st);
   char* b = reinterpret_cast<char*>(p->ws);
@@ -708,6 +773,13 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     G.root_a = b + go[g].root;
     G.bfft = b + go[g].bf;
     G.Hs = b + go[g].H;
+  }
+  for (int j = 0; j <= p->nscale; ++j) {
+    auto& sgt = p->seg[j];
+    if (sgt.S == 0) continue;
+    sgt.tw = b + so[j].tw;
+    sgt.Ha = b + so[j].Ha;
+    sgt.Hs = b + so[j].Hs;
   }
 
   // ---- R tables ----
@@ -768,6 +840,34 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     put(G.root_a, rt64, ng);
     put(G.bfft, bf64, 4 * Lg - 1);
     put(G.Hs, H64, (int64_t)4 * Mg);
+  }
+  {
+    size_t need = 0;
+    for (const auto& sgt : p->seg)
+      if (sgt.S)
+        need = std::max(need, (size_t)twiddle_entries(sgt.logM) + 2 * (size_t)sgt.S * ((size_t)1 << sgt.logM));
+    double2* s64 = nullptr;
+    if (need) amalloc(&s64, need * sizeof(double2), st);
+    for (int j = 0; j <= p->nscale; ++j) {
+      const auto& sgt = p->seg[j];
+      if (sgt.S == 0) continue;
+      const auto& G = p->gt[p->grid_of[j]];
+      const int64_t Ms = (int64_t)1 << sgt.logM, ntw = twiddle_entries(sgt.logM);
+      double2* tw64 = s64;
+      double2* ha64 = tw64 + ntw;
+      double2* hs64 = ha64 + sgt.S * Ms;
+      ck(launch_seg_build64(tw64, ha64, hs64, G.L, p->Ycols[j], sgt.logM, sgt.P, sgt.S, st));
+      auto put = [&](void* dst, const double2* src, int64_t cnt) {
+        if (sizeof(T) == sizeof(double))
+          ck(cudaMemcpyAsync(dst, src, (size_t)cnt * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        else
+          ck(launch_to_prec<float>(reinterpret_cast<float2*>(dst), src, cnt, st));
+      };
+      put(sgt.tw, tw64, ntw);
+      put(sgt.Ha, ha64, sgt.S * Ms);
+      put(sgt.Hs, hs64, sgt.S * Ms);
+    }
+    afree(s64, st);
   }
   afree(qg, st);
   afree(t64, st);
@@ -1123,14 +1223,36 @@ int s2dw_scale_grid(s2dw_plan_t p, int j, int* Lgrid, int64_t* offset, int64_t* 
   return S2DW_OK;
 }
 
+int s2dw_alpha_method(s2dw_plan_t p, int j, int dir, int* method, int* fft_len, int* segments, int* seg_len) {
+  if (!p || j < 0 || j > p->nscale || dir < 0 || dir > 1) return S2DW_EINVAL;
+  const int Lj = p->Ycols[j];
+  const auto& G = p->gt[p->grid_of[j]];
+  const auto& sgt = p->seg[j];
+  int m = 1, len = G.M, ns = 1, sl = 2 * G.L - 1;
+  if (Lj <= (dir == 0 ? kDirectMaxLjAna : kDirectMaxLj)) {
+    m = 0;
+    len = ns = sl = 0;
+  } else if (sgt.S > 0) {
+    m = 2;
+    len = 1 << sgt.logM;
+    ns = sgt.S;
+    sl = sgt.P;
+  }
+  if (method) *method = m;
+  if (fft_len) *fft_len = len;
+  if (segments) *segments = ns;
+  if (seg_len) *seg_len = sl;
+  return S2DW_OK;
+}
+
 int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {
   if (!p) return S2DW_EINVAL;
   const Lists& ls = p->own;
   int contract = ls.ntiles_phi > 0 ? 1 : 0;
   for (auto& t : ls.tiles_w) contract += t.second.second > 0 ? 1 : 0;
   auto has = [&](int k) { return ls.items[k] > 0 ? 1 : 0; };
-  if (analysis) *analysis = contract + has(0) + has(1) + has(4) + has(6);
-  if (synthesis) *synthesis = contract + has(2) + has(3) + has(5) + has(7) + 1;
+  if (analysis) *analysis = contract + has(0) + has(1) + has(4) + has(6) + has(8);
+  if (synthesis) *synthesis = contract + has(2) + has(3) + has(5) + has(7) + has(9) + 1;
   return S2DW_OK;
 }
 

@@ -192,6 +192,125 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------
+// Segmented chirp-z for the alpha sums of scales whose band L_j is small next
+// to L (Eqs. (30), (37)).  A chirp-z convolution of length M covers the n =
+// 2L-1 outputs at once and costs two FFTs of M >= n + 2 L_j - 2; here the n
+// outputs (analysis) or inputs (synthesis) are cut into S segments of P =
+// M' - 2 L_j + 2 samples, each a circular convolution of a shorter length M'
+// with its own kernel spectrum (the chirp shifted by the segment's first
+// sample a_s = s P).  Analysis: one forward FFT of the pre-chirped row, then
+// per segment the product with its spectrum and an inverse FFT that yields P
+// outputs.  Synthesis (the adjoint): per segment a forward FFT of the
+// segment's inputs, products accumulated over the segments in the frequency
+// domain, then one inverse FFT.  S + 1 FFTs of M' replace two of M.  A CTA
+// runs G = 4096 / M' row pairs side by side, one per group of M'/16 threads.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
+  const int logM = sg.logM, M = 1 << logM, nthr = M / 16, G = 256 / nthr;
+  const int g = threadIdx.x / nthr, tid = threadIdx.x % nthr, ST = fft_smem_elems(M);
+  cx<T>* Y = sm + g * ST;
+  cx<T>* Z = sm + (G + g) * ST;
+  const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1, P = sg.P, S = sg.nsegs;
+  const int pidx = (blockIdx.x - sg.start) * G + g;  // row pair (complex transform) of this group
+  const bool valid = pidx < sg.N * L;
+  int Rl, nmid;
+  fft_schedule(logM, Rl, nmid);  // nmid == 1 for 9 <= logM <= 12
+  const cx<T>* __restrict__ X = sg.buf_in + (size_t)(2 * (valid ? pidx : 0)) * Lj;
+  const cx<T>* __restrict__ tw1 = sg.tw + fft_twiddle_level_offset(logM, 1);
+  // y_m = (X1 + i X2)_m e^{i pi m^2/n} at position m mod M
+  fftg_first_fwd<T>(Y, M, tid, sg.tw, [&](int v) -> cx<T> {
+    if (!valid) return mkc<T>(0, 0);
+    if (v < Lj) {
+      const cx<T> x1 = X[v], x2 = X[Lj + v];
+      return cmul<T>(mkc<T>(x1.x - x2.y, x1.y + x2.x), __ldg(sg.pre + v));
+    }
+    if (v > M - Lj) {
+      const int mm = M - v;
+      const cx<T> x1 = X[mm], x2 = X[Lj + mm];
+      return cmul<T>(mkc<T>(x1.x + x2.y, x2.x - x1.y), __ldg(sg.pre + mm));  // conj(X1) + i conj(X2)
+    }
+    return mkc<T>(0, 0);
+  });
+  __syncthreads();
+  fftg_stage16<T, false>(Y, M, M / 16, tid, nthr, tw1);
+  __syncthreads();
+  fftg_inner<T, 0>(Y, Y, M, Rl, tid, nthr, nullptr);
+  __syncthreads();
+  T* __restrict__ Wb = reinterpret_cast<T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff +
+                       (size_t)(2 * (valid ? pidx : 0)) * n;
+  for (int s = 0; s < S; ++s) {
+    fftg_inner<T, 1>(Y, Z, M, Rl, tid, nthr, sg.H + (size_t)s * M);
+    __syncthreads();
+    fftg_stage16<T, true>(Z, M, M / 16, tid, nthr, tw1);
+    __syncthreads();
+    const int as = s * P;
+    fftg_last_inv<T>(Z, M, tid, sg.tw, [&](int v, cx<T> y) {
+      const int a = as + v;
+      if (valid && v < P && a < n) {
+        const cx<T> w = cmul<T>(y, __ldg(sg.post + a));
+        Wb[a] = w.x;
+        Wb[n + a] = w.y;
+      }
+    });
+    __syncthreads();  // Z is rewritten by the next segment
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
+  const int logM = sg.logM, M = 1 << logM, nthr = M / 16, G = 256 / nthr;
+  const int g = threadIdx.x / nthr, tid = threadIdx.x % nthr, ST = fft_smem_elems(M);
+  cx<T>* ACC = sm + g * ST;
+  cx<T>* B = sm + (G + g) * ST;
+  const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1, P = sg.P, S = sg.nsegs;
+  const int pidx = (blockIdx.x - sg.start) * G + g;
+  const bool valid = pidx < sg.N * L;
+  int Rl, nmid;
+  fft_schedule(logM, Rl, nmid);
+  const cx<T>* __restrict__ tw1 = sg.tw + fft_twiddle_level_offset(logM, 1);
+  const T* __restrict__ Wr = reinterpret_cast<const T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) +
+                             sg.woff + (size_t)(2 * (valid ? pidx : 0)) * n;
+  for (int s = 0; s < S; ++s) {
+    const int as = s * P;
+    // u_p = (W1 + i W2)_{a_s + p} e^{-i pi a^2/n}, p < P
+    fftg_first_fwd<T>(B, M, tid, sg.tw, [&](int v) -> cx<T> {
+      const int a = as + v;
+      if (!valid || v >= P || a >= n) return mkc<T>(0, 0);
+      return cmulc<T>(mkc<T>(Wr[a], Wr[n + a]), __ldg(sg.pre + a));
+    });
+    __syncthreads();
+    fftg_stage16<T, false>(B, M, M / 16, tid, nthr, tw1);
+    __syncthreads();
+    fftg_inner<T, 2>(B, ACC, M, Rl, tid, nthr, sg.H + (size_t)s * M, s == 0);
+    __syncthreads();
+  }
+  fftg_inner<T, 3>(ACC, ACC, M, Rl, tid, nthr, nullptr);
+  __syncthreads();
+  fftg_stage16<T, true>(ACC, M, M / 16, tid, nthr, tw1);
+  __syncthreads();
+  fftg_last_inv<T>(ACC, M, tid, sg.tw, [&](int v, cx<T> y) { ACC[fpad(v)] = y; });
+  __syncthreads();
+  if (!valid) return;
+  const T h = sg.scale * T(0.5);
+  cx<T>* __restrict__ V1 = sg.buf_out + (size_t)(2 * pidx) * Lj;  // V_g[b][m] rows, m fastest
+  for (int mm = tid; mm < Lj; mm += nthr) {
+    const cx<T> ch = __ldg(sg.post + mm);
+    const cx<T> zp = cmulc<T>(ACC[fpad(mm)], ch);
+    const cx<T> zm = cmulc<T>(ACC[fpad((M - mm) & (M - 1))], ch);
+    // V1 = (Zp + conj(Zm))/2, V2 = (Zp - conj(Zm))/(2i)
+    V1[mm] = mkc<T>((zp.x + zm.x) * h, (zp.y - zm.y) * h);
+    V1[Lj + mm] = mkc<T>((zp.y + zm.y) * h, (zm.x - zp.x) * h);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restrict__ segs, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -612,6 +731,14 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
     k_czt_alpha_ana<T><<<total_items, 256, alpha_czt_smem<T>(maxlogM, false), st>>>(segs, nseg, maxlogM, ptrs);
     return;
   }
+  if (kind == CZT_ALPHA_ANA_SEG) {
+    k_czt_alpha_ana_seg<T><<<total_items, 256, alpha_seg_smem<T>(), st>>>(segs, nseg, ptrs);
+    return;
+  }
+  if (kind == CZT_ALPHA_SYN_SEG) {
+    k_czt_alpha_syn_seg<T><<<total_items, 256, alpha_seg_smem<T>(), st>>>(segs, nseg, ptrs);
+    return;
+  }
   if (kind == CZT_ALPHA_SYN) {
     const size_t sm = alpha_czt_smem<T>(maxlogM, true);
     const int g = std::min(total_items, alpha_czt_grid<T>(k_czt_alpha_syn<T>, sm));
@@ -656,6 +783,12 @@ cudaError_t czt_set_smem(int maxlogM) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            smem * beta_fft_nt(sizeof(T) == 8));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_czt_alpha_ana_seg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)alpha_seg_smem<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_czt_alpha_syn_seg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)alpha_seg_smem<T>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_alpha_ana_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)alpha_ana_direct_smem<T>());

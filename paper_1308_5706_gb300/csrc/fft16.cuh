@@ -618,6 +618,113 @@ __device__ __forceinline__ void fft_inverse_to_n(cx<T>* A, int ST, int logM, con
   }
 }
 
+// ---------------------------------------------------------------------------
+// Thread-group transforms: a CTA runs several transforms of length M side by
+// side, each on its own group of nthr = M/16 threads (thread tid of the
+// group) and its own shared-memory buffer, so that lengths below 4096 keep
+// every thread busy.  The stage sequence is the one above (first radix-16
+// stage, radix-16 stages, innermost R_last); callers put a __syncthreads()
+// between stages (all groups run the same schedule).
+// ---------------------------------------------------------------------------
+
+// First forward stage fused with the input functor (in(v) gives element v).
+template <typename T, typename In>
+__device__ __forceinline__ void fftg_first_fwd(cx<T>* A, int M, int tid, const cx<T>* __restrict__ tw, In in) {
+  const int Q = M / 16, j = tid;
+  cx<T> v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = in(j + Q * r);
+  DftR<T, 16, false>::run(v);
+#pragma unroll
+  for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+#pragma unroll
+  for (int k = 0; k < 16; ++k) A[fpad(j + Q * k)] = v[k];
+}
+
+// Radix-16 stage of block size S, forward (DIF) or inverse (DIT), smem -> smem.
+template <typename T, bool INV>
+__device__ __forceinline__ void fftg_stage16(cx<T>* A, int M, int S, int tid, int nthr, const cx<T>* __restrict__ tw) {
+  const int Q = S / 16;
+  for (int u = tid; u < M / 16; u += nthr) {
+    const int j = u & (Q - 1), base = (u - j) * 16 + j;
+    cx<T> v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = A[fpad(base + Q * r)];
+    if (!INV) {
+      DftR<T, 16, false>::run(v);
+#pragma unroll
+      for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+    } else {
+#pragma unroll
+      for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+      DftR<T, 16, true>::run(v);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) A[fpad(base + Q * k)] = v[k];
+  }
+}
+
+// Innermost stage (blocks of R consecutive entries), three forms:
+//   MODE 0: forward DFT in place (Src == Dst);
+//   MODE 1: Dst = inverse DFT of (Src .* H)   (spectrum entry k of block u at H[k (M/R) + u]);
+//   MODE 2: Dst (+)= (forward DFT of Src) .* H   (accumulate unless first);
+//   MODE 3: inverse DFT in place (Src == Dst).
+template <typename T, int R, int MODE>
+__device__ __forceinline__ void fftg_inner_r(const cx<T>* Src, cx<T>* Dst, int M, int tid, int nthr,
+                                             const cx<T>* __restrict__ H, bool first) {
+  for (int u = tid; u < M / R; u += nthr) {
+    const int base = u * R;
+    cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = Src[fpad(base + r)];
+    if (MODE == 1 || MODE == 3) {
+      if (MODE == 1) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = cmul<T>(v[k], __ldg(H + k * (M / R) + u));
+      }
+      DftR<T, R, true>::run(v);
+#pragma unroll
+      for (int k = 0; k < R; ++k) Dst[fpad(base + k)] = v[k];
+    } else {
+      DftR<T, R, false>::run(v);
+      if (MODE == 0) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) Dst[fpad(base + k)] = v[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          const cx<T> p = cmul<T>(v[k], __ldg(H + k * (M / R) + u));
+          Dst[fpad(base + k)] = first ? p : cadd<T>(Dst[fpad(base + k)], p);
+        }
+      }
+    }
+  }
+}
+template <typename T, int MODE>
+__device__ __forceinline__ void fftg_inner(const cx<T>* Src, cx<T>* Dst, int M, int Rl, int tid, int nthr,
+                                           const cx<T>* __restrict__ H, bool first = true) {
+  switch (Rl) {
+    case 2: fftg_inner_r<T, 2, MODE>(Src, Dst, M, tid, nthr, H, first); break;
+    case 4: fftg_inner_r<T, 4, MODE>(Src, Dst, M, tid, nthr, H, first); break;
+    case 8: fftg_inner_r<T, 8, MODE>(Src, Dst, M, tid, nthr, H, first); break;
+    default: fftg_inner_r<T, 16, MODE>(Src, Dst, M, tid, nthr, H, first); break;
+  }
+}
+
+// Last inverse stage fused with the output functor (out(v, value) for every v < M).
+template <typename T, typename Out>
+__device__ __forceinline__ void fftg_last_inv(const cx<T>* A, int M, int tid, const cx<T>* __restrict__ tw, Out out) {
+  const int Q = M / 16, j = tid;
+  cx<T> v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = A[fpad(j + Q * k)];
+#pragma unroll
+  for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+  DftR<T, 16, true>::run(v);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) out(j + Q * r, v[r]);
+}
+
 // Forward transform only (smem in natural order -> smem in the engine's
 // order), values scaled by `scale`; used to build the kernel spectra.
 template <typename T>

@@ -56,8 +56,14 @@ enum CztKind {
   CZT_ALPHA_ANA_DIRECT = 4,  // small-band scales, direct sums
   CZT_ALPHA_SYN_DIRECT = 5,
   CZT_BETA_ANA_FFT = 6,      // beta sums as one FFT of length 4L (L a power of two)
-  CZT_BETA_SYN_FFT = 7
+  CZT_BETA_SYN_FFT = 7,
+  CZT_ALPHA_ANA_SEG = 8,     // segmented chirp-z (bands small next to L)
+  CZT_ALPHA_SYN_SEG = 9
 };
+// shared memory of the segmented chirp-z kernels: two buffers of M' (+ padding)
+// for each of the 4096 / M' row pairs of a CTA
+template <typename T>
+constexpr size_t alpha_seg_smem() { return 2 * (size_t)(4096 + 4096 / 16) * 2 * sizeof(T); }
 constexpr int kDirectMaxLj = 32;     // synthesis: direct alpha sums for L_j <= 32
 constexpr int kDirectMaxLjAna = 32;  // analysis: direct (matrix-product) alpha sums for L_j <= 32
 // tile of the direct analysis kernel: samples per CTA, rows per pass, rows per CTA
@@ -90,6 +96,7 @@ struct CztSeg {
   const cx<T>* pre;
   const cx<T>* post;
   T scale;
+  int P, nsegs;   // segmented chirp-z: samples per segment, segments
 };
 
 // Per-job parameters of the batched final synthesis reduction.

@@ -245,6 +245,57 @@ __global__ void k_rtable(T* RS, const double* d64, const double* kap, const doub
   RS[idx] = (T)v;
 }
 
+// Entry i of the twiddle table of length 2^logM: locate level d, then (k, j)
+// in it: e^{-2 pi i j k / S_d}.
+template <typename T>
+__device__ __forceinline__ cx<T> twiddle_entry(int i, int logM) {
+  const int M = 1 << logM;
+  int d = 0, off = 0;
+  while (i >= off + 15 * (M >> (4 * (d + 1)))) {
+    off += 15 * (M >> (4 * (d + 1)));
+    ++d;
+  }
+  const int Q = M >> (4 * (d + 1)), S = 16 * Q;
+  const int k = (i - off) / Q + 1, j = (i - off) % Q;
+  const long long p = ((long long)j * k) % S;
+  double s, c;
+  sincospi(-2.0 * (double)p / S, &s, &c);
+  return mkc<T>((T)c, (T)s);
+}
+
+__global__ void k_twiddles(double2* tw, int logM) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < fft_twiddle_entries(logM)) tw[i] = twiddle_entry<double>(i, logM);
+}
+
+// Kernels of the segmented chirp-z (segment s = blockIdx.y starts at sample
+// a_s = s P), natural order mod M, float64:
+//   analysis  h_s[d] = e^{-i pi (d + a_s)^2 / n}, d in [-(Lj-1), M - Lj];
+//   synthesis g_s[d] = e^{+i pi (d - a_s)^2 / n}, d in [-(Lj+P-2), M - Lj - P + 1].
+__global__ void k_seg_kernels(double2* Ha, double2* Hs, int L, int Lj, int M, int P) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (v >= M) return;
+  const long long n = 2LL * L - 1, as = (long long)s * P;
+  double sn, cs;
+  {
+    const long long u0 = -(long long)(Lj - 1);
+    const long long d = u0 + ((((long long)v - u0) % M) + M) % M;
+    const long long e = d + as, p = ((e % (2 * n)) * (e % (2 * n))) % (2 * n);
+    sincospi((double)p / (double)n, &sn, &cs);
+    Ha[(size_t)s * M + v] = make_double2(cs, -sn);
+  }
+  {
+    const long long u0 = -(long long)(Lj + P - 2);
+    const long long d = u0 + ((((long long)v - u0) % M) + M) % M;
+    long long e = (d - as) % (2 * n);
+    if (e < 0) e += 2 * n;
+    const long long p = (e * e) % (2 * n);
+    sincospi((double)p / (double)n, &sn, &cs);
+    Hs[(size_t)s * M + v] = make_double2(cs, sn);
+  }
+}
+
 // Chirp tables (angles reduced exactly in integers before sincospi).
 template <typename T>
 __global__ void k_chirp_tables(cx<T>* tw, cx<T>* chirp_a, cx<T>* pre_b, cx<T>* post_b, cx<T>* preS_b,
@@ -253,19 +304,7 @@ __global__ void k_chirp_tables(cx<T>* tw, cx<T>* chirp_a, cx<T>* pre_b, cx<T>* p
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = 2 * L - 1;
   double s, c;
-  if (i < fft_twiddle_entries(logM)) {
-    // locate level d, then (k, j) in it: e^{-2 pi i j k / S_d}
-    int d = 0, off = 0;
-    while (i >= off + 15 * (M >> (4 * (d + 1)))) {
-      off += 15 * (M >> (4 * (d + 1)));
-      ++d;
-    }
-    const int Q = M >> (4 * (d + 1)), S = 16 * Q;
-    const int k = (i - off) / Q + 1, j = (i - off) % Q;
-    const long long p = ((long long)j * k) % S;
-    sincospi(-2.0 * (double)p / S, &s, &c);
-    tw[i] = mkc<T>((T)c, (T)s);
-  }
+  if (i < fft_twiddle_entries(logM)) tw[i] = twiddle_entry<T>(i, logM);
   if (i < n) {
     const long long p = ((long long)i * i) % (2LL * n);
     sincospi((double)p / n, &s, &c);
@@ -395,6 +434,23 @@ cudaError_t launch_chirp_build64(double2* tw, double2* chirp_a, double2* pre_b, 
   err = cudaFuncSetAttribute(k_chirp_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
   k_chirp_spectra<<<4, 256, smem, st>>>(H, tw, logM);
+  return cudaGetLastError();
+}
+
+int twiddle_entries(int logM) { return fft_twiddle_entries(logM); }
+
+cudaError_t launch_seg_build64(double2* tw, double2* Ha, double2* Hs, int L, int Lj, int logM, int P, int S,
+                               cudaStream_t st) {
+  const int M = 1 << logM;
+  k_twiddles<<<nblk(fft_twiddle_entries(logM), 256), 256, 0, st>>>(tw, logM);
+  k_seg_kernels<<<dim3(nblk(M, 256), S), 256, 0, st>>>(Ha, Hs, L, Lj, M, P);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int smem = (int)sizeof(double2) * fft_smem_elems(M);
+  err = cudaFuncSetAttribute(k_chirp_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (err != cudaSuccess) return err;
+  k_chirp_spectra<<<S, 256, smem, st>>>(Ha, tw, logM);
+  k_chirp_spectra<<<S, 256, smem, st>>>(Hs, tw, logM);
   return cudaGetLastError();
 }
 

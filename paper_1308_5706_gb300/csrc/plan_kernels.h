@@ -8,6 +8,11 @@ namespace s2dw {
 cudaError_t launch_kernel_values(double* kap, double* phi, double* sabs, double2* psi, double* q, int L, int N,
                                  int J, double lam, const double* glx, const double* glw, int Q, int P,
                                  double* I0, cudaStream_t st);
+int twiddle_entries(int logM);  // entries of the FFT twiddle table of length 2^logM
+// Segmented chirp-z tables (float64): twiddles of length 2^logM and the S
+// analysis / synthesis kernel spectra (S x 2^logM each) of a band Lj.
+cudaError_t launch_seg_build64(double2* tw, double2* Ha, double2* Hs, int L, int Lj, int logM, int P, int S,
+                               cudaStream_t st);
 cudaError_t launch_dh_weights(double* q, int L, cudaStream_t st);  // Eq. (18), 2L weights
 // slabs l_first .. Lmax-1 (the edge arrays em/ee always cover l < Lmax)
 cudaError_t launch_delta_build(double* d64, float* d32, double* em, int* ee, int Lmax, int l_first,
