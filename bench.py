@@ -272,8 +272,9 @@ def beta_flops(plan) -> float:
 # DRAM bytes per launch (read + write) of kernels captured with ncu on this
 # workload; None once the kernel has changed since the capture.
 NCU_TRAFFIC = {
-    "ana_alpha_czt": (0.246710e9 + 0.458258e9, "profiles/k_czt_alpha_L1024_N5.md"),
-    "syn_alpha_czt": (0.503261e9 + 0.243395e9, "profiles/k_czt_alpha_L1024_N5.md"),
+    # the alpha chirp-z stage is two launches (full-band and segmented): their sum
+    "ana_alpha_czt": (0.167998e9 + 0.122535e9 + 0.079100e9 + 0.275988e9, "profiles/k_czt_alpha_L1024_N5.md"),
+    "syn_alpha_czt": (0.167881e9 + 0.119082e9 + 0.335626e9 + 0.076106e9, "profiles/k_czt_alpha_L1024_N5.md"),
     "ana_contract": (1.218407e9 + 0.070254e9, "profiles/k_contract_L1024_N5.md"),
     "syn_contract": (1.575094e9 + 0.091380e9, "profiles/k_contract_L1024_N5.md"),
 }
