@@ -13,6 +13,7 @@ Index conventions (shared with the C ABI, by specification only):
   * n_k = -(N-1) + 2k, k = 0..N-1: the azimuthal orders with s_ln != 0.
   * W has shape [J+1][N][2L][2L-1] = [scale j][gamma g][beta b][alpha a].
   * W^Phi has shape [2L][2L-1] = [theta t][phi p].
+  * On the grid of mw_betas (L beta samples) the beta axes have L entries.
 """
 from __future__ import annotations
 
@@ -30,6 +31,7 @@ __all__ = [
     "analysis_rows", "synthesis", "synthesis_modes", "fourier_cube",
     "support", "steer", "sht_inverse", "sht_forward",
     "band_limits", "analysis_multires", "synthesis_multires",
+    "mw_betas", "analysis_mw", "resample_mw_to_dh", "synthesis_mw",
 ]
 
 # How each function is pinned to something other than itself (tests named in
@@ -48,6 +50,10 @@ PARITY = {
     "sht_forward": "textbook Y_lm maps give unit coefficients; exact round trip with sht_inverse",
     "analysis_multires": "equals the full-resolution W at the samples the two grids share; exact round trip",
     "synthesis_multires": "exact round trip with analysis_multires (Sec. 3.4 metric)",
+    "mw_betas": "closed values (last sample beta = pi)",
+    "analysis_mw": "closed-form D^l_mn at the MW beta samples (l <= 2)",
+    "resample_mw_to_dh": "equals the DH analysis of the same signal (exact resampling)",
+    "synthesis_mw": "exact round trip with analysis_mw (Sec. 3.4 metric)",
 }
 
 
@@ -322,7 +328,7 @@ def grid_to_flm(F: np.ndarray, L: int) -> np.ndarray:
 # Analysis (Sec. 3.2)
 # ---------------------------------------------------------------------------
 
-def analysis_rows(flm, L: int, N: int, lam: float, J0: int, b_list, kern=None):
+def analysis_rows(flm, L: int, N: int, lam: float, J0: int, b_list, kern=None, betas=None):
     """Wavelet and scaling coefficients on the rows beta_b, b in b_list.
 
     W^j(alpha_a, beta_b, gamma_g) = sum_{l<L} sum_{|m|<=l} sum_{n=n_k}
@@ -331,11 +337,14 @@ def analysis_rows(flm, L: int, N: int, lam: float, J0: int, b_list, kern=None):
     W^Phi(theta_t, phi_p) = sum_lm f_lm Phi_l0 e^{i m phi_p} d^l_m0(theta_t)
     is Eq. (3) with (R_omega Phi)_lm = D^l_m0(phi, theta, 0) Phi_l0.
 
+    `betas` replaces the DH beta samples (b_list then indexes into it).
     Returns (W [J+1][N][len(b_list)][2L-1], Wphi [len(b_list)][2L-1],
     max |imag part| seen)."""
     psi, phi = kern if kern is not None else kernels(L, N, lam, J0)
     J1 = psi.shape[0]
     alpha, beta, gamma = grids(L, N)
+    if betas is not None:
+        beta = np.asarray(betas, np.float64)
     ns = n_orders(N)
     ms = np.arange(-(L - 1), L)
     F = flm_to_grid(np.asarray(flm, np.complex128), L)
@@ -575,3 +584,75 @@ def synthesis_multires(Ws, Wphi, L: int, N: int, lam: float, J0: int, kern=None)
     fs = synthesis(np.zeros((0, N, 2 * Lp, 2 * Lp - 1)), Wphi, Lp, N, lam, J0, (psi[:0, :Lp], phi[:Lp]))
     out[:Lp * Lp] += fs
     return out
+
+
+# ---------------------------------------------------------------------------
+# Sampling with L beta samples (the McEwen-Wiaux grid the paper's Sec. 5
+# names as the replacement of the DH grid): beta_b = pi(2b+1)/(2L-1), b < L
+# (the last sample is beta = pi), alpha and gamma as in Sec. 3.1.
+# ---------------------------------------------------------------------------
+
+def mw_betas(L: int) -> np.ndarray:
+    """beta_b = pi (2b+1)/(2L-1), b < L: half of the 2L-1 equispaced points
+    of the beta torus [0, 2 pi), the other half being their reflections
+    2 pi - beta."""
+    return np.pi * (2 * np.arange(L) + 1) / (2 * L - 1)
+
+
+def analysis_mw(flm, L: int, N: int, lam: float, J0: int, kern=None):
+    """Eq. (20) / Eq. (3) sampled at the L beta values of mw_betas (the sums
+    of analysis_rows at those beta).  Returns (W [J+1][N][L][2L-1],
+    W^Phi [L][2L-1])."""
+    W, Wphi, _ = analysis_rows(flm, L, N, lam, J0, range(L), kern, betas=mw_betas(L))
+    return W, Wphi
+
+
+def _mw_beta_to_dh(U, L: int, sigma):
+    """Band-limited resampling in beta of U [..., L samples at mw_betas, ...]
+    (axis -2) to the 2L DH samples: U is a trigonometric polynomial of degree
+    < L in beta with U(2 pi - beta) = sigma U(beta) (sigma broadcast over the
+    other axes), so its L samples and their reflections are 2L-1 equispaced
+    samples on the torus, whose discrete Fourier coefficients give it
+    exactly."""
+    n = 2 * L - 1
+    bet = np.pi * (2 * np.arange(n) + 1) / n                       # the whole torus
+    ext = np.concatenate([U, sigma * U[..., L - 2::-1, :]], axis=-2)  # b >= L: reflection of n-1-b
+    p = np.arange(-(L - 1), L)
+    c = np.einsum("...bm,pb->...pm", ext, np.exp(-1j * np.outer(p, bet))) / n
+    _, bdh, _ = grids(L, 1)
+    return np.einsum("...pm,tp->...tm", c, np.exp(1j * np.outer(bdh, p)))
+
+
+def resample_mw_to_dh(W, Wphi, L: int, N: int):
+    """Coefficients on the grid of mw_betas -> the same band-limited functions
+    on the DH grid of Sec. 3.1 (exact): per (m, n) Fourier component in
+    (alpha, gamma) the beta dependence sum_l c_l d^l_mn(beta) is a
+    trigonometric polynomial of degree < L with U(2 pi - beta) =
+    (-1)^{m-n} U(beta) (d^l_mn(-beta) = (-1)^{m-n} d^l_mn(beta)); the scaling
+    part has n = 0."""
+    alpha, _, gamma = grids(L, N)
+    n = 2 * L - 1
+    ms = np.arange(-(L - 1), L)
+    ns = n_orders(N)
+    Ea = np.exp(-1j * np.outer(alpha, ms)) / n                     # [a][m]: alpha Fourier coefficients
+    Eg = np.exp(-1j * np.outer(gamma, ns)) / N                     # [g][k]: gamma coefficients (z_n = 1/N)
+    W = np.asarray(W, np.float64)
+    out = np.zeros(W.shape[:2] + (2 * L, n))
+    sig = (-1.0) ** (ms[None, :] - ns[:, None])                    # [k][m]
+    for j in range(W.shape[0]):
+        A = np.einsum("gba,am,gk->kbm", W[j], Ea, Eg)                # [k][b][m]
+        Ad = _mw_beta_to_dh(A, L, sig[:, None, :])                  # [k][t][m]
+        out[j] = np.einsum("ktm,am,gk->gta", Ad, np.exp(1j * np.outer(alpha, ms)),
+                           np.exp(1j * np.outer(gamma, ns))).real
+    A0 = np.asarray(Wphi, np.float64) @ Ea                         # [b][m]
+    A0d = _mw_beta_to_dh(A0, L, ((-1.0) ** ms)[None, :])
+    Wphi_dh = (A0d @ np.exp(1j * np.outer(ms, alpha))).real
+    return out, Wphi_dh
+
+
+def synthesis_mw(W, Wphi, L: int, N: int, lam: float, J0: int, kern=None):
+    """f_lm from coefficients on the grid of mw_betas: the synthesis of
+    Eqs. (32)-(33), (41) (exact on the DH grid) applied to the exact DH
+    resampling of the coefficients (resample_mw_to_dh)."""
+    Wd, Wpd = resample_mw_to_dh(W, Wphi, L, N)
+    return synthesis(Wd, Wpd, L, N, lam, J0, kern)

@@ -28,9 +28,9 @@ _orig_rows = OS.analysis_rows
 _orig_synth = OS.synthesis
 
 
-def _analysis_noconj(flm, L, N, lam, J0, b_list, kern=None):
+def _analysis_noconj(flm, L, N, lam, J0, b_list, kern=None, **kw):
     psi, phi = kern if kern is not None else _orig_kernels(L, N, lam, J0)
-    return _orig_rows(flm, L, N, lam, J0, b_list, (np.conj(psi), phi))
+    return _orig_rows(flm, L, N, lam, J0, b_list, (np.conj(psi), phi), **kw)
 
 
 def _synthesis_conj(W, Wphi, L, N, lam, J0, kern=None):
@@ -84,6 +84,18 @@ def _steer_no_norm(W, N, gammas):
     return _orig_steer(W, N, gammas) * N
 
 
+_orig_mw_to_dh = OS._mw_beta_to_dh
+
+
+def _mw_reflection_unsigned(U, L, sigma):
+    # reflection 2 pi - beta taken without the (-1)^{m-n} sign
+    return _orig_mw_to_dh(U, L, np.ones_like(sigma))
+
+
+def _mw_betas_2L(L):
+    return np.pi * (2 * np.arange(L) + 1) / (2 * L)
+
+
 PINS = [
     lambda: P.test_single_mode_analysis_closed_form(3, 2.0, 0),
     lambda: P.test_single_mode_analysis_closed_form(2, 2.0, 1),
@@ -99,6 +111,8 @@ PINS = [
     lambda: P.test_sht_round_trip_exact(9),
     lambda: P.test_sht_textbook_harmonics(1, 1),
     lambda: P.test_multires_round_trip_exact(16, 3, 2.0, 0),
+    lambda: P.test_mw_single_mode_analysis_closed_form(3),
+    lambda: P.test_mw_resampling_and_round_trip_exact(8, 3, 2.0, 0),
 ]
 
 
@@ -113,10 +127,12 @@ PINS = [
     ("sign of n in d", "wigner_d", _wigner_sign),
     ("steering samples on [0, 2pi)", "steer", _steer_2pi_spacing),
     ("steering without z_n = 1/N", "steer", _steer_no_norm),
+    ("MW reflection without its sign", "_mw_beta_to_dh", _mw_reflection_unsigned),
+    ("MW beta grid of spacing pi/L", "mw_betas", _mw_betas_2L),
 ])
 def test_planted_mistake_is_caught(monkeypatch, name, attr, bad):
     monkeypatch.setattr(OS, attr, bad)
-    monkeypatch.setattr(O, attr, bad)
+    monkeypatch.setattr(O, attr, bad, raising=False)
     OS._I.cache_clear()
     caught = 0
     for pin in PINS:

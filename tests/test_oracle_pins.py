@@ -419,3 +419,56 @@ def test_multires_matches_full_resolution_on_shared_samples():
             assert np.abs(Ws[j] - W[j]).max() < 1e-13
             checked += 1
     assert checked >= 2
+
+
+# ---- sampling with L beta samples (the grid named in Sec. 5 as the DH replacement) ----
+
+def test_mw_betas_values():
+    b = O.mw_betas(5)
+    assert b.shape == (5,)
+    assert np.allclose(b, np.pi * np.array([1, 3, 5, 7, 9]) / 9)
+    assert abs(b[-1] - np.pi) < 1e-15          # the last sample is the pole beta = pi
+
+
+@pytest.mark.parametrize("N", [1, 3, 4])
+def test_mw_single_mode_analysis_closed_form(N):
+    """Eq. (20) at the MW beta samples against closed-form D (l <= 2)."""
+    L, lam, J0 = 6, 2.0, 1
+    psi, phi = O.kernels(L, N, lam, J0)
+    alpha, _, gamma = O.grids(L, N)
+    beta = O.mw_betas(L)
+    ns = O.n_orders(N)
+    for (l0, m0, c) in ((1, 1, 0.3 - 0.7j), (2, 2, -0.4 + 0.9j), (2, 0, -1.3 + 0j)):
+        f = _single_mode_f(L, l0, m0, c)
+        W, Wphi = O.analysis_mw(f, L, N, lam, J0)
+        assert W.shape == (psi.shape[0], N, L, 2 * L - 1) and Wphi.shape == (L, 2 * L - 1)
+        for j in range(psi.shape[0]):
+            for (g, b, a) in ((0, 0, 2), (N - 1, L - 1, 10), (N // 2, 3, 0)):
+                ref = 0.0
+                for k, n in enumerate(ns):
+                    if abs(n) > l0:
+                        continue
+                    for mm, cc in ((m0, f[l0 * l0 + l0 + m0]), (-m0, f[l0 * l0 + l0 - m0])) if m0 else ((0, f[l0 * l0 + l0]),):
+                        ref += cc * np.conj(psi[j, l0, k]) * np.conj(D_closed(l0, mm, n, alpha[a], beta[b], gamma[g]))
+                assert abs(W[j, g, b, a] - ref.real) < 1e-14
+        for (b, a) in ((0, 0), (L - 1, 3)):
+            ref = 0.0
+            for mm in ((m0, -m0) if m0 else (0,)):
+                ref += f[l0 * l0 + l0 + mm] * phi[l0] * np.conj(D_closed(l0, mm, 0, alpha[a], beta[b], 0.0))
+            assert abs(Wphi[b, a] - ref.real) < 1e-14
+
+
+@pytest.mark.parametrize("L,N,lam,J0", [(8, 3, 2.0, 0), (9, 2, 2.0, 1), (12, 4, 3.0, 0), (7, 1, 2.0, 1)])
+def test_mw_resampling_and_round_trip_exact(L, N, lam, J0):
+    """The L-sample coefficients hold the same band-limited functions: resampled
+    to the DH grid they equal the DH analysis, and the synthesis from them is
+    exact (Sec. 3.4 metric)."""
+    f = flm_gaussian(L, 13, "unit")
+    kern = O.kernels(L, N, lam, J0)
+    Wm, Wpm = O.analysis_mw(f, L, N, lam, J0, kern)
+    Wd, Wpd = O.analysis(f, L, N, lam, J0, kern)
+    Wr, Wpr = O.resample_mw_to_dh(Wm, Wpm, L, N)
+    assert np.abs(Wr - Wd).max() < 1e-13 * np.abs(Wd).max()
+    assert np.abs(Wpr - Wpd).max() < 1e-13 * max(1.0, np.abs(Wpd).max())
+    fr = O.synthesis_mw(Wm, Wpm, L, N, lam, J0, kern)
+    assert np.abs(fr - f).max() < 1e-12 * np.abs(f).max()
