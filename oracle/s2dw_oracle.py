@@ -587,7 +587,7 @@ def synthesis_multires(Ws, Wphi, L: int, N: int, lam: float, J0: int, kern=None)
 
 
 # ---------------------------------------------------------------------------
-# Sampling with L beta samples (the McEwen-Wiaux grid the paper's Sec. 5
+# Sampling with L beta samples (the McEwen-Wiaux grid that Sec. 4
 # names as the replacement of the DH grid): beta_b = pi(2b+1)/(2L-1), b < L
 # (the last sample is beta = pi), alpha and gamma as in Sec. 3.1.
 # ---------------------------------------------------------------------------
@@ -607,29 +607,37 @@ def analysis_mw(flm, L: int, N: int, lam: float, J0: int, kern=None):
     return W, Wphi
 
 
-def _mw_beta_to_dh(U, L: int, sigma):
+def _mw_beta_to_dh(U, L: int, sigma, band=None):
     """Band-limited resampling in beta of U [..., L samples at mw_betas, ...]
     (axis -2) to the 2L DH samples: U is a trigonometric polynomial of degree
-    < L in beta with U(2 pi - beta) = sigma U(beta) (sigma broadcast over the
-    other axes), so its L samples and their reflections are 2L-1 equispaced
-    samples on the torus, whose discrete Fourier coefficients give it
-    exactly."""
+    < band (<= L) in beta with U(2 pi - beta) = sigma U(beta) (sigma
+    broadcast over the other axes), so its L samples and their reflections
+    are 2L-1 equispaced samples on the torus, whose discrete Fourier
+    coefficients |p| < band give it exactly.  The last sample is its own
+    reflection (beta = pi): where sigma = -1 a symmetric U vanishes there, and
+    the sample is weighted by (1 + sigma)/2 (it is 0 for coefficients of a
+    band-limited signal; for arbitrary ones this keeps the extension
+    symmetric, i.e. c_{-p} = sigma c_p)."""
     n = 2 * L - 1
+    band = L if band is None else band
     bet = np.pi * (2 * np.arange(n) + 1) / n                       # the whole torus
+    U = np.array(U, dtype=np.complex128)
+    U[..., L - 1, :] *= (1.0 + sigma[..., 0, :] if np.ndim(sigma) >= 2 else 1.0 + sigma) / 2.0
     ext = np.concatenate([U, sigma * U[..., L - 2::-1, :]], axis=-2)  # b >= L: reflection of n-1-b
-    p = np.arange(-(L - 1), L)
+    p = np.arange(-(band - 1), band)
     c = np.einsum("...bm,pb->...pm", ext, np.exp(-1j * np.outer(p, bet))) / n
     _, bdh, _ = grids(L, 1)
     return np.einsum("...pm,tp->...tm", c, np.exp(1j * np.outer(bdh, p)))
 
 
-def resample_mw_to_dh(W, Wphi, L: int, N: int):
+def resample_mw_to_dh(W, Wphi, L: int, N: int, bands=None):
     """Coefficients on the grid of mw_betas -> the same band-limited functions
     on the DH grid of Sec. 3.1 (exact): per (m, n) Fourier component in
     (alpha, gamma) the beta dependence sum_l c_l d^l_mn(beta) is a
-    trigonometric polynomial of degree < L with U(2 pi - beta) =
-    (-1)^{m-n} U(beta) (d^l_mn(-beta) = (-1)^{m-n} d^l_mn(beta)); the scaling
-    part has n = 0."""
+    trigonometric polynomial of degree < L_j (the scale's band, l < L_j) with
+    U(2 pi - beta) = (-1)^{m-n} U(beta) (d^l_mn(-beta) = (-1)^{m-n}
+    d^l_mn(beta)); the scaling part has n = 0.  bands = ([L_j], L_Phi)
+    (default: L for every part)."""
     alpha, _, gamma = grids(L, N)
     n = 2 * L - 1
     ms = np.arange(-(L - 1), L)
@@ -639,13 +647,14 @@ def resample_mw_to_dh(W, Wphi, L: int, N: int):
     W = np.asarray(W, np.float64)
     out = np.zeros(W.shape[:2] + (2 * L, n))
     sig = (-1.0) ** (ms[None, :] - ns[:, None])                    # [k][m]
+    Ls, Lp = bands if bands is not None else ([L] * W.shape[0], L)
     for j in range(W.shape[0]):
         A = np.einsum("gba,am,gk->kbm", W[j], Ea, Eg)                # [k][b][m]
-        Ad = _mw_beta_to_dh(A, L, sig[:, None, :])                  # [k][t][m]
+        Ad = _mw_beta_to_dh(A, L, sig[:, None, :], max(1, Ls[j]))   # [k][t][m]
         out[j] = np.einsum("ktm,am,gk->gta", Ad, np.exp(1j * np.outer(alpha, ms)),
                            np.exp(1j * np.outer(gamma, ns))).real
     A0 = np.asarray(Wphi, np.float64) @ Ea                         # [b][m]
-    A0d = _mw_beta_to_dh(A0, L, ((-1.0) ** ms)[None, :])
+    A0d = _mw_beta_to_dh(A0, L, ((-1.0) ** ms)[None, :], max(1, Lp))
     Wphi_dh = (A0d @ np.exp(1j * np.outer(ms, alpha))).real
     return out, Wphi_dh
 
@@ -653,6 +662,9 @@ def resample_mw_to_dh(W, Wphi, L: int, N: int):
 def synthesis_mw(W, Wphi, L: int, N: int, lam: float, J0: int, kern=None):
     """f_lm from coefficients on the grid of mw_betas: the synthesis of
     Eqs. (32)-(33), (41) (exact on the DH grid) applied to the exact DH
-    resampling of the coefficients (resample_mw_to_dh)."""
-    Wd, Wpd = resample_mw_to_dh(W, Wphi, L, N)
-    return synthesis(Wd, Wpd, L, N, lam, J0, kern)
+    resampling of the coefficients (resample_mw_to_dh, each part within its
+    band L_j; for coefficients that are not band-limited this is the
+    projection onto the band)."""
+    psi, phi = kern if kern is not None else kernels(L, N, lam, J0)
+    Wd, Wpd = resample_mw_to_dh(W, Wphi, L, N, band_limits(L, N, lam, J0, (psi, phi)))
+    return synthesis(Wd, Wpd, L, N, lam, J0, (psi, phi))

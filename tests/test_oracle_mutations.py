@@ -87,9 +87,9 @@ def _steer_no_norm(W, N, gammas):
 _orig_mw_to_dh = OS._mw_beta_to_dh
 
 
-def _mw_reflection_unsigned(U, L, sigma):
+def _mw_reflection_unsigned(U, L, sigma, band=None):
     # reflection 2 pi - beta taken without the (-1)^{m-n} sign
-    return _orig_mw_to_dh(U, L, np.ones_like(sigma))
+    return _orig_mw_to_dh(U, L, np.ones_like(sigma), band)
 
 
 def _mw_betas_2L(L):

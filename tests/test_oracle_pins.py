@@ -421,7 +421,7 @@ def test_multires_matches_full_resolution_on_shared_samples():
     assert checked >= 2
 
 
-# ---- sampling with L beta samples (the grid named in Sec. 5 as the DH replacement) ----
+# ---- sampling with L beta samples (the grid named in Sec. 4 as the DH replacement) ----
 
 def test_mw_betas_values():
     b = O.mw_betas(5)
