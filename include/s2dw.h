@@ -18,6 +18,8 @@
  *         alpha_a = 2 pi a/(2L-1), beta_b = pi (2b+1)/(4L), gamma_g = pi g/N
  *         (Sec. 3.1).  Scale j = 0 is the finest.
  *   - Wphi: real array [2L][2L-1] = [theta_t][phi_p] on the same grid.
+ *   - S2DW_MW plans sample beta at the L values beta_b = pi (2b+1)/(2L-1),
+ *     b < L (the McEwen-Wiaux grid, Sec. 4): every 2L above is then L.
  *   - Precision: S2DW_FP64 plans take complex128 f and double W / Wphi;
  *     S2DW_MIXED plans take complex64 f and float W / Wphi (FP32 arithmetic,
  *     Wigner Delta generated in FP64 and stored in FP32).
@@ -55,7 +57,8 @@ enum {
   S2DW_FP64 = 1,        /* plain float64 path                              */
   S2DW_MIXED = 2,       /* float32 arithmetic, FP64-generated Delta        */
   S2DW_REAL_SIGNAL = 4, /* real signals (required; set implicitly)         */
-  S2DW_MULTIRES = 8     /* each scale on the grid of its own band-limit     */
+  S2DW_MULTIRES = 8,    /* each scale on the grid of its own band-limit     */
+  S2DW_MW = 16          /* L beta samples (McEwen-Wiaux grid), not 2L       */
 };
 
 typedef struct s2dw_plan_s* s2dw_plan_t;
@@ -68,7 +71,8 @@ typedef struct s2dw_plan_s* s2dw_plan_t;
  *   Kernels: Psi^j_ln = kappa^j(l) s_ln (Eqs. (7), (11)-(15)).
  * Valid ranges: 2 <= L <= 2048, 1 <= N <= min(8, L), lambda > 1 (at most 64
  * scales), 0 <= J0 <= J_max; flags = exactly one of S2DW_FP64 / S2DW_MIXED,
- * optionally | S2DW_REAL_SIGNAL and | S2DW_MULTIRES.  Otherwise S2DW_EINVAL.
+ * optionally | S2DW_REAL_SIGNAL and | one of S2DW_MULTIRES / S2DW_MW.
+ * Otherwise S2DW_EINVAL.
  * S2DW_MULTIRES samples each W^j on the DH SO(3) grid of its own band-limit
  * L_j = 1 + the largest l with kappa^j(l) > 0 (and W^Phi on the sphere grid
  * of L_Phi): W^j is band-limited there, so the samples are exact and the
@@ -76,6 +80,17 @@ typedef struct s2dw_plan_s* s2dw_plan_t;
  * that not every scale needs the full band-limit, Sec. 3.2).  W is then one
  * array holding the scales one after the other (s2dw_scale_grid gives each
  * scale's band-limit, offset and size).
+ * S2DW_MW samples beta at beta_b = pi (2b+1)/(2L-1), b < L, the grid whose
+ * sampling theorem Sec. 4 names as the replacement of the DH grid: half the
+ * beta samples (the last is beta = pi), alpha and gamma as in Sec. 3.1.
+ * Analysis evaluates Eq. (20) / Eq. (3) there.  Synthesis is exact for the
+ * coefficients of a band-limited signal: per Fourier component (m, n) the
+ * beta dependence is a trigonometric polynomial of degree < L_j with
+ * U(2 pi - beta) = (-1)^{m-n} U(beta), so the L samples and their
+ * reflections are 2L-1 equispaced torus samples; its coefficients are taken
+ * from them (the self-reflected sample beta = pi weighted (1 + (-1)^{m-n})/2),
+ * evaluated on the DH beta grid and the DH synthesis of Sec. 3.3 follows.
+ * For arbitrary arrays this synthesises their projection onto that space.
  * Work: evaluates the kernels, the DH weights (Eq. (18)) and the Delta table
  * on the device (FP64 recursion, grown to cover l < L on first need) and
  * allocates the workspace (stream-ordered, on a private stream; other
@@ -93,9 +108,9 @@ int s2dw_plan_destroy(s2dw_plan_t plan);
 /*
  * s2dw_query: sizes of a plan, any pointer may be NULL.
  *   J: largest scale index (scales 0..J);
- *   w_elems_per_scale: N * 2L * (2L-1) (0 for S2DW_MULTIRES plans, whose
- *   scales differ in size); wphi_elems: 2L_Phi * (2L_Phi-1), L_Phi = L unless
- *   S2DW_MULTIRES;
+ *   w_elems_per_scale: N * nb * (2L-1), nb = 2L (L for S2DW_MW plans; 0 for
+ *   S2DW_MULTIRES plans, whose scales differ in size); wphi_elems:
+ *   nb_Phi * (2L_Phi-1), L_Phi = L and nb_Phi = nb unless S2DW_MULTIRES;
  *   workspace_bytes: device bytes owned by the plan (intermediates, tables);
  *   total_device_bytes: workspace_bytes + the caller's f, W, Wphi bytes for
  *   one transform (used for admission by HBM footprint).
@@ -105,9 +120,10 @@ int s2dw_query(s2dw_plan_t plan, int* J, int64_t* w_elems_per_scale, int64_t* wp
 
 /*
  * s2dw_scale_grid: sampling grid of scale j (0 <= j <= J) or, for j = J+1,
- * of the scaling part: its band-limit Lg (2Lg beta and 2Lg-1 alpha samples),
- * the element offset of W^j in W (0 for j = J+1: W^Phi is its own array) and
- * the element count (N 2Lg (2Lg-1), or 2Lg (2Lg-1)).  Any output may be NULL.
+ * of the scaling part: its band-limit Lg (nb = 2Lg beta samples, Lg for
+ * S2DW_MW, and 2Lg-1 alpha samples), the element offset of W^j in W (0 for
+ * j = J+1: W^Phi is its own array) and the element count (N nb (2Lg-1), or
+ * nb (2Lg-1)).  Any output may be NULL.
  * S2DW_EINVAL for j outside [0, J+1].
  */
 int s2dw_scale_grid(s2dw_plan_t plan, int j, int* Lgrid, int64_t* offset, int64_t* elems);
@@ -219,8 +235,9 @@ const char* s2dw_strerror(int status);
  *   s2dw_stage: copy intermediate `stage` of scale j from the last call on
  *     this plan into host memory: 0 = analysis Fourier cube after the gamma
  *     step, complex [N][Lj (m >= 0)][Lj (m' >= 0)]; 1 = after the beta step,
- *     complex [N][2L (beta_b)][Lj (m)]; *nbytes gets the size; host may be
- *     NULL to query only.  Scale j = J+1 is the scaling part (N = 1).
+ *     complex [N][2L (beta_b)][Lj (m)] (an S2DW_MW analysis fills its
+ *     leading [N][L][Lj]); *nbytes gets the size; host may be NULL to query
+ *     only.  Scale j = J+1 is the scaling part (N = 1).
  */
 int s2dw_scale_support(s2dw_plan_t plan, int j, int* lo, int* hi);
 int s2dw_delta_slab(s2dw_plan_t plan, int l, double* host_out);

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libs2dw.so")
 
 S2DW_OK, S2DW_EINVAL, S2DW_ENOMEM, S2DW_ECUDA, S2DW_ETIMEOUT, S2DW_EBUSY, S2DW_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-S2DW_FP64, S2DW_MIXED, S2DW_REAL_SIGNAL, S2DW_MULTIRES = 1, 2, 4, 8
+S2DW_FP64, S2DW_MIXED, S2DW_REAL_SIGNAL, S2DW_MULTIRES, S2DW_MW = 1, 2, 4, 8, 16
 
 _lib = None
 
@@ -252,14 +252,18 @@ class Plan:
     """
 
     def __init__(self, L: int, N: int, lam: float = 2.0, J0: int = 0, precision: str = "mixed",
-                 multires: bool = False):
+                 multires: bool = False, mw: bool = False):
         flags = (S2DW_FP64 if precision == "fp64" else S2DW_MIXED) | S2DW_REAL_SIGNAL
         if multires:
             flags |= S2DW_MULTIRES
+        if mw:
+            flags |= S2DW_MW
         if precision not in ("fp64", "mixed"):
             raise ValueError(precision)
         self.L, self.N, self.lam, self.J0, self.precision = L, N, float(lam), J0, precision
         self.multires = bool(multires)
+        self.mw = bool(mw)
+        self.nb = L if mw else 2 * L  # beta samples
         self.handle = s2dw_plan(L, N, lam, J0, flags)
         q = s2dw_query(self.handle)
         self.J = q["J"]
@@ -285,12 +289,12 @@ class Plan:
         if self.multires:  # the scales one after the other, each [N][2Lg][2Lg-1]
             Lg, off, n = self.grids[self.nscale - 1]
             return (off + n,)
-        return (self.nscale, self.N, 2 * self.L, 2 * self.L - 1)
+        return (self.nscale, self.N, self.nb, 2 * self.L - 1)
 
     @property
     def wphi_shape(self):
         Lg = self.grids[self.nscale][0]
-        return (2 * Lg, 2 * Lg - 1)
+        return (Lg if self.mw else 2 * Lg, 2 * Lg - 1)
 
     def w_scale(self, W, j):
         """View of scale j of W as [N][2Lg][2Lg-1]."""

@@ -212,12 +212,14 @@ struct Lists {
   std::vector<std::pair<int, std::pair<void*, int>>> tiles_w;  // (N, (tiles, count))
   void* tiles_phi = nullptr;
   int ntiles_phi = 0;
-  static constexpr int NK = 10;  // chirp-z 0..3, direct alpha 4..5, single-FFT beta 6..7, segmented alpha 8..9
+  static constexpr int NK = 13;  // chirp-z 0..3, direct alpha 4..5, single-FFT beta 6..7, segmented alpha 8..9,
+                                 // MW-grid synthesis beta 10..12
   void* segs[NK] = {};
   int nseg[NK] = {};
   int items[NK] = {};
   int maxlogM = 0;
   int Lmax = 0;
+  int odd = 0;  // CZT_ODD_ROWS when a plan of the list samples the MW grid
   ~Lists() {
     if (mem) {
       try {
@@ -259,6 +261,7 @@ struct s2dw_plan_s {
   // Tables of one sampling grid (band-limit Lg: 2Lg beta, 2Lg-1 alpha samples).
   struct GridTables {
     int L = 0, logM = 0, M = 0;
+    int nb = 0;              // beta samples: 2L (DH), or L (MW grid)
     void* tw = nullptr;
     void* chirp_a = nullptr;
     void* pre_b = nullptr;
@@ -266,10 +269,12 @@ struct s2dw_plan_s {
     void* preS_b = nullptr;
     void* postS_b = nullptr;
     void* root_a = nullptr;  // e^{2 pi i t/(2Lg-1)}
+    void* pre_mw = nullptr;  // MW beta chirp e^{i pi (m'^2 + m')/(2Lg-1)}, |m'| < Lg
     void* bfft = nullptr;    // e^{i pi m'/(4Lg)} (|m'| < Lg), then q_b (b < 2Lg): single-FFT beta
     void* Hs = nullptr;      // 4 x M spectra
   };
   bool multires = false;       // every scale on the grid of its own band-limit
+  bool mw = false;             // L beta samples per grid (McEwen-Wiaux), not 2L
   std::vector<GridTables> gt;  // one set per distinct grid band-limit
   std::vector<int> grid_of;    // [nscale + 1]: set of scale j (last: scaling part)
   std::vector<int64_t> woff;   // [nscale + 1]: element offset of scale j in W (last: total)
@@ -443,23 +448,33 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
   // kinds 4 / 5 collect the alpha segments of scales with Lj <= kDirectMaxLjAna
   // (analysis) or kDirectMaxLj (synthesis),
   // kinds 6 / 7 the beta segments of plans whose FFT length M is 4L
-  // kinds 8 / 9 the alpha segments of scales with a segmented chirp-z
+  // kinds 8 / 9 the alpha segments of scales with a segmented chirp-z;
+  // kinds 10..12 (MW grid only) the synthesis-side resampling of V from the L
+  // MW beta samples to the DH beta grid (torus coefficients, then their
+  // evaluation on the DH grid by the analysis beta kernels)
+  if ((kind == CZT_BETA_MW_DFT || kind == CZT_BETA_RS_FFT || kind == CZT_BETA_RS) && !p->mw) return;
   const int base_kind = (kind == CZT_ALPHA_ANA_DIRECT || kind == CZT_ALPHA_ANA_SEG) ? CZT_ALPHA_ANA
                         : (kind == CZT_ALPHA_SYN_DIRECT || kind == CZT_ALPHA_SYN_SEG) ? CZT_ALPHA_SYN
-                        : (kind == CZT_BETA_ANA_FFT)     ? CZT_BETA_ANA
+                        : (kind == CZT_BETA_ANA_FFT || kind == CZT_BETA_RS_FFT || kind == CZT_BETA_RS ||
+                           kind == CZT_BETA_MW_DFT) ? CZT_BETA_ANA
                         : (kind == CZT_BETA_SYN_FFT)     ? CZT_BETA_SYN
                                                          : kind;
+  const bool rs_list = kind == CZT_BETA_RS_FFT || kind == CZT_BETA_RS;
   const bool direct_list = kind == CZT_ALPHA_ANA_DIRECT || kind == CZT_ALPHA_SYN_DIRECT;
   const bool seg_list = kind == CZT_ALPHA_ANA_SEG || kind == CZT_ALPHA_SYN_SEG;
-  const bool fft_list = kind == CZT_BETA_ANA_FFT || kind == CZT_BETA_SYN_FFT;
+  const bool fft_list = kind == CZT_BETA_ANA_FFT || kind == CZT_BETA_SYN_FFT || kind == CZT_BETA_RS_FFT;
   for (int j = 0; j <= p->nscale; ++j) {
     const bool phi = (j == p->nscale);
     const int Nj = phi ? 1 : p->N;
     const int Lj = p->Ycols[j];
     const s2dw_plan_s::GridTables& G = p->gt[p->grid_of[j]];
     const int L = G.L, n = 2 * L - 1;  // this scale's sampling grid
-    const bool beta_fft = (4 * L == G.M);
-    if ((base_kind == CZT_BETA_ANA || base_kind == CZT_BETA_SYN) && beta_fft != fft_list) continue;
+    // the analysis beta step of an MW plan evaluates at the MW samples (chirp-z only);
+    // the DH-grid beta kernels (FFT for power-of-two L) serve DH plans and the MW resampling
+    const bool mw_ana_beta = p->mw && base_kind == CZT_BETA_ANA && !rs_list && kind != CZT_BETA_MW_DFT;
+    const bool beta_fft = (4 * L == G.M) && !mw_ana_beta;
+    if ((base_kind == CZT_BETA_ANA || base_kind == CZT_BETA_SYN) && kind != CZT_BETA_MW_DFT && beta_fft != fft_list)
+      continue;
     const cx<T>* Hs = reinterpret_cast<const cx<T>*>(G.Hs);
     CztSeg<T> s;
     std::memset(&s, 0, sizeof(s));
@@ -472,6 +487,7 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     s.is_phi = phi ? 1 : 0;
     s.tw = reinterpret_cast<const cx<T>*>(G.tw);
     s.scale = (T)(2.0 * 3.14159265358979323846 / n);
+    s.nb = G.nb;
     const bool is_alpha = base_kind == CZT_ALPHA_ANA || base_kind == CZT_ALPHA_SYN;
     const bool direct = is_alpha && Lj <= (base_kind == CZT_ALPHA_ANA ? kDirectMaxLjAna : kDirectMaxLj);
     if (direct != direct_list) continue;
@@ -484,16 +500,29 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
         s.H = Hs + 0 * (size_t)G.M;
         s.pre = reinterpret_cast<const cx<T>*>(G.pre_b);
         s.post = reinterpret_cast<const cx<T>*>(G.post_b);
+        if (kind == CZT_BETA_MW_DFT) {  // V [g][b < L][m] -> torus coefficients [g][m][p]
+          s.buf_in = reinterpret_cast<cx<T>*>(p->X[j]);
+          s.buf_out = reinterpret_cast<cx<T>*>(p->Y[j]);
+          s.H = Hs + 2 * (size_t)G.M;   // the alpha synthesis kernel e^{+i pi u^2/n}
+          s.pre = reinterpret_cast<const cx<T>*>(G.chirp_a);
+          s.post = reinterpret_cast<const cx<T>*>(G.pre_mw);
+        } else if (rs_list) {           // coefficients -> the 2L DH samples
+          s.nb = 2 * L;
+        } else if (p->mw) {             // analysis: the L MW samples beta_b = (2b+1) pi / n
+          s.H = Hs + 1 * (size_t)G.M;   // the alpha analysis kernel e^{-i pi u^2/n}
+          s.pre = reinterpret_cast<const cx<T>*>(G.pre_mw);
+          s.post = reinterpret_cast<const cx<T>*>(G.chirp_a);
+        }
         break;
       case CZT_ALPHA_ANA:
-        s.items = (Nj * L + alpha_czt_nt(sizeof(T) == 8) - 1) / alpha_czt_nt(sizeof(T) == 8);
+        s.items = ((Nj * G.nb + 1) / 2 + alpha_czt_nt(sizeof(T) == 8) - 1) / alpha_czt_nt(sizeof(T) == 8);
         s.buf_in = reinterpret_cast<cx<T>*>(p->X[j]);
         s.H = Hs + 1 * (size_t)G.M;
         s.pre = reinterpret_cast<const cx<T>*>(G.chirp_a);
         s.post = reinterpret_cast<const cx<T>*>(G.chirp_a);
         break;
       case CZT_ALPHA_SYN:
-        s.items = (Nj * L + alpha_czt_nt(sizeof(T) == 8) - 1) / alpha_czt_nt(sizeof(T) == 8);
+        s.items = ((Nj * G.nb + 1) / 2 + alpha_czt_nt(sizeof(T) == 8) - 1) / alpha_czt_nt(sizeof(T) == 8);
         s.buf_out = reinterpret_cast<cx<T>*>(p->X[j]);
         s.H = Hs + 2 * (size_t)G.M;
         s.pre = reinterpret_cast<const cx<T>*>(G.chirp_a);
@@ -501,6 +530,7 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
         break;
       case CZT_BETA_SYN:
         s.items = Nj * Lj;
+        s.nb = 2 * L;  // DH quadrature (an MW plan resamples V to the DH grid first)
         s.buf_in = reinterpret_cast<cx<T>*>(p->X[j]);
         s.buf_out = reinterpret_cast<cx<T>*>(p->Y[j]);
         s.H = Hs + 3 * (size_t)G.M;
@@ -517,7 +547,7 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     if (seg_list) {
       const auto& sgt = p->seg[j];
       const int groups = 1 << (12 - sgt.logM);  // row pairs per CTA (one per group of M'/16 threads)
-      s.items = (Nj * L + groups - 1) / groups;
+      s.items = ((Nj * G.nb + 1) / 2 + groups - 1) / groups;
       s.logM = sgt.logM;
       s.tw = reinterpret_cast<const cx<T>*>(sgt.tw);
       s.H = reinterpret_cast<const cx<T>*>(base_kind == CZT_ALPHA_ANA ? sgt.Ha : sgt.Hs);
@@ -526,9 +556,9 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     }
     if (direct) {
       if (base_kind == CZT_ALPHA_ANA)
-        s.items = ((n + kAgCols - 1) / kAgCols) * ((Nj * 2 * L + kAgChunk - 1) / kAgChunk);
+        s.items = ((n + kAgCols - 1) / kAgCols) * ((Nj * G.nb + kAgChunk - 1) / kAgChunk);
       else
-        s.items = (Nj * 2 * L + direct_rows_syn(sizeof(T) == 8) - 1) / direct_rows_syn(sizeof(T) == 8);
+        s.items = (Nj * G.nb + direct_rows_syn(sizeof(T) == 8) - 1) / direct_rows_syn(sizeof(T) == 8);
       s.pre = reinterpret_cast<const cx<T>*>(G.root_a);
     }
     if (s.items <= 0) continue;
@@ -563,6 +593,7 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
     for (int k = 0; k < Lists::NK; ++k) build_segs<T>(p, i, k, segs[k], start[k]);
     ls->maxlogM = std::max(ls->maxlogM, p->logM);
     ls->Lmax = std::max(ls->Lmax, p->L);
+    if (p->mw) ls->odd = CZT_ODD_ROWS;
   }
   for (auto& kv : tw_byN) sort_tiles(kv.second);
   sort_tiles(tphi);
@@ -656,9 +687,9 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
   launch_czt<T>(CZT_BETA_ANA_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[6]), ls.nseg[6], ls.items[6],
                 ls.maxlogM, ptrs, st);
   rec(ev, 3, st);
-  launch_czt<T>(CZT_ALPHA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1], ls.maxlogM,
-                ptrs, st);
-  launch_czt<T>(CZT_ALPHA_ANA_SEG, reinterpret_cast<const CztSeg<T>*>(ls.segs[8]), ls.nseg[8], ls.items[8],
+  launch_czt<T>(CZT_ALPHA_ANA | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1],
+                ls.maxlogM, ptrs, st);
+  launch_czt<T>(CZT_ALPHA_ANA_SEG | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[8]), ls.nseg[8], ls.items[8],
                 ls.maxlogM, ptrs, st);
   rec(ev, 4, st);
   launch_czt<T>(CZT_ALPHA_ANA_DIRECT, reinterpret_cast<const CztSeg<T>*>(ls.segs[4]), ls.nseg[4], ls.items[4],
@@ -678,9 +709,16 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
   rec(ev, 1, st);
   launch_czt<T>(CZT_ALPHA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[2]), ls.nseg[2], ls.items[2], ls.maxlogM,
                 ptrs, st);
-  launch_czt<T>(CZT_ALPHA_SYN_SEG, reinterpret_cast<const CztSeg<T>*>(ls.segs[9]), ls.nseg[9], ls.items[9],
+  launch_czt<T>(CZT_ALPHA_SYN_SEG | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[9]), ls.nseg[9], ls.items[9],
                 ls.maxlogM, ptrs, st);
   rec(ev, 2, st);
+  // MW grid: V from its L beta samples to the DH grid (torus coefficients, then the DH samples)
+  launch_czt<T>(CZT_BETA_MW_DFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[10]), ls.nseg[10], ls.items[10],
+                ls.maxlogM, ptrs, st);
+  launch_czt<T>(CZT_BETA_RS_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[11]), ls.nseg[11], ls.items[11],
+                ls.maxlogM, ptrs, st);
+  launch_czt<T>(CZT_BETA_RS, reinterpret_cast<const CztSeg<T>*>(ls.segs[12]), ls.nseg[12], ls.items[12],
+                ls.maxlogM, ptrs, st);
   launch_czt<T>(CZT_BETA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[3]), ls.nseg[3], ls.items[3], ls.maxlogM,
                 ptrs, st);
   launch_czt<T>(CZT_BETA_SYN_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[7]), ls.nseg[7], ls.items[7],
@@ -719,7 +757,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   const size_t o_P = take((size_t)p->nbr * L * p->Lp32 * sizeof(cx<T>));
   const size_t o_Pphi = take((size_t)p->nbr_phi * p->Lphi * p->Lphip32 * sizeof(cx<T>));
   // per grid: twiddles, chirps, roots, beta phases and weights, spectra
-  struct GridOff { size_t tw, ca, pb, qb, pS, qS, root, bf, H; };
+  struct GridOff { size_t tw, ca, pb, qb, pS, qS, root, bf, H, pm; };
   std::vector<GridOff> go(p->gt.size());
   for (size_t g = 0; g < p->gt.size(); ++g) {
     const int Lg = p->gt[g].L, ng = 2 * Lg - 1, Mg = p->gt[g].M;
@@ -732,6 +770,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     go[g].root = take((size_t)ng * sizeof(cx<T>));
     go[g].bf = take((size_t)(4 * Lg - 1) * sizeof(cx<T>));
     go[g].H = take((size_t)4 * Mg * sizeof(cx<T>));
+    go[g].pm = take((size_t)ng * sizeof(cx<T>));
   }
   // segmented chirp-z tables of the scales that use it (chirp-z bands only)
   p->seg.assign(p->nscale + 1, s2dw_plan_s::SegTables());
@@ -773,6 +812,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     G.root_a = b + go[g].root;
     G.bfft = b + go[g].bf;
     G.Hs = b + go[g].H;
+    G.pre_mw = b + go[g].pm;
   }
   for (int j = 0; j <= p->nscale; ++j) {
     auto& sgt = p->seg[j];
@@ -840,6 +880,8 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     put(G.root_a, rt64, ng);
     put(G.bfft, bf64, 4 * Lg - 1);
     put(G.Hs, H64, (int64_t)4 * Mg);
+    ck(launch_mw_pre64(tw64, Lg, st));  // reuse the scratch: the grid's tables are converted above
+    put(G.pre_mw, tw64, ng);
   }
   {
     size_t need = 0;
@@ -902,6 +944,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   }
   p->own.maxlogM = ls->maxlogM;
   p->own.Lmax = ls->Lmax;
+  p->own.odd = ls->odd;
   delete ls;
   // the cap covers every plan size (M <= 8192 for L <= 2048), so plans of
   // different sizes can share a batched launch
@@ -1005,6 +1048,8 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
     // band-limit L, or with S2DW_MULTIRES the grid of the scale's own
     // band-limit (1 + the last l with a nonzero kernel)
     p->multires = (flags & S2DW_MULTIRES) != 0;
+    p->mw = (flags & S2DW_MW) != 0;
+    if (p->mw && p->multires) throw CudaFail{cudaErrorInvalidValue};
     std::vector<int> Lg(p->nscale + 1);
     for (int j = 0; j < p->nscale; ++j) Lg[j] = p->multires ? std::max(1, p->Lj[j]) : L;
     Lg[p->nscale] = p->multires ? p->Lphi : L;
@@ -1019,6 +1064,7 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
       G.logM = 5;  // the radix-16 convolution engine needs M >= 32
       while ((1 << G.logM) < 4 * G.L - 2) ++G.logM;
       G.M = 1 << G.logM;
+      G.nb = p->mw ? G.L : 2 * G.L;
       p->logM = std::max(p->logM, G.logM);
     }
     p->M = 1 << p->logM;
@@ -1029,7 +1075,7 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
     int64_t wacc = 0;
     for (int j = 0; j < p->nscale; ++j) {
       p->woff[j] = wacc;
-      wacc += (int64_t)N * 2 * Lg[j] * (2 * Lg[j] - 1);
+      wacc += (int64_t)N * p->gt[p->grid_of[j]].nb * (2 * Lg[j] - 1);
     }
     p->woff[p->nscale] = wacc;
     p->tab = delta_acquire(L, st);
@@ -1093,7 +1139,8 @@ int s2dw_plan(s2dw_plan_t* out, int L, int N, double lambda, int J0, unsigned fl
   *out = nullptr;
   const unsigned prec = flags & (S2DW_FP64 | S2DW_MIXED);
   if (prec != S2DW_FP64 && prec != S2DW_MIXED) return S2DW_EINVAL;
-  if (flags & ~(unsigned)(S2DW_FP64 | S2DW_MIXED | S2DW_REAL_SIGNAL | S2DW_MULTIRES)) return S2DW_EINVAL;
+  if (flags & ~(unsigned)(S2DW_FP64 | S2DW_MIXED | S2DW_REAL_SIGNAL | S2DW_MULTIRES | S2DW_MW)) return S2DW_EINVAL;
+  if ((flags & S2DW_MW) && (flags & S2DW_MULTIRES)) return S2DW_EINVAL;
   if (L < 2 || L > 2048) return S2DW_EINVAL;
   if (N < 1 || N > 8 || N > L) return S2DW_EINVAL;
   if (!(lambda > 1.0) || !std::isfinite(lambda)) return S2DW_EINVAL;
@@ -1115,8 +1162,9 @@ int s2dw_query(s2dw_plan_t p, int* J, int64_t* w_elems_per_scale, int64_t* wphi_
                int64_t* total_device_bytes) {
   if (!p) return S2DW_EINVAL;
   const int64_t L = p->L, n = 2 * L - 1;
-  const int64_t wps = p->multires ? 0 : (int64_t)p->N * 2 * L * n;
-  const int64_t Lp = p->gt[p->grid_of[p->nscale]].L, wph = 2 * Lp * (2 * Lp - 1);
+  const int64_t wps = p->multires ? 0 : (int64_t)p->N * p->gt[0].nb * n;
+  const auto& Gp = p->gt[p->grid_of[p->nscale]];
+  const int64_t Lp = Gp.L, wph = (int64_t)Gp.nb * (2 * Lp - 1);
   const int64_t el = p->fp64 ? 8 : 4;
   if (J) *J = p->J;
   if (w_elems_per_scale) *w_elems_per_scale = wps;
@@ -1143,7 +1191,7 @@ int s2dw_steer(s2dw_plan_t p, const void* W, const double* gammas, int ngamma, v
   const size_t el = p->fp64 ? sizeof(double) : sizeof(float);
   cudaError_t e = cudaSuccess;
   if (!p->multires) {
-    const int64_t per_scale = (int64_t)2 * p->L * (2 * p->L - 1);
+    const int64_t per_scale = (int64_t)p->gt[0].nb * (2 * p->L - 1);
     e = p->fp64 ? launch_steer<double>(W, out, sw, p->nscale, N, ngamma, per_scale, st)
                 : launch_steer<float>(W, out, sw, p->nscale, N, ngamma, per_scale, st);
   } else {
@@ -1215,8 +1263,8 @@ int s2dw_sht_forward(s2dw_plan_t p, const void* fpix, void* flm, void* stream) {
 
 int s2dw_scale_grid(s2dw_plan_t p, int j, int* Lgrid, int64_t* offset, int64_t* elems) {
   if (!p || j < 0 || j > p->nscale) return S2DW_EINVAL;
-  const int64_t Lg = p->gt[p->grid_of[j]].L;
-  const int64_t per = (j == p->nscale ? 1 : p->N) * 2 * Lg * (2 * Lg - 1);
+  const int64_t Lg = p->gt[p->grid_of[j]].L, nb = p->gt[p->grid_of[j]].nb;
+  const int64_t per = (j == p->nscale ? 1 : p->N) * nb * (2 * Lg - 1);
   if (Lgrid) *Lgrid = (int)Lg;
   if (offset) *offset = (j == p->nscale) ? 0 : p->woff[j];
   if (elems) *elems = per;
@@ -1252,7 +1300,7 @@ int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {
   for (auto& t : ls.tiles_w) contract += t.second.second > 0 ? 1 : 0;
   auto has = [&](int k) { return ls.items[k] > 0 ? 1 : 0; };
   if (analysis) *analysis = contract + has(0) + has(1) + has(4) + has(6) + has(8);
-  if (synthesis) *synthesis = contract + has(2) + has(3) + has(5) + has(7) + has(9) + 1;
+  if (synthesis) *synthesis = contract + has(2) + has(3) + has(5) + has(7) + has(9) + has(10) + has(11) + has(12) + 1;
   return S2DW_OK;
 }
 

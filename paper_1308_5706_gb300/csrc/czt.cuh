@@ -66,9 +66,47 @@ __global__ void __launch_bounds__(256) k_czt_beta_ana(const CztSeg<T>* __restric
     if (mp < 0) y = cscale<T>(y, sigma);
     return cmul<T>(y, __ldg(pre + mp));
   };
-  cx<T>* __restrict__ X = sg.buf_out + (size_t)g * 2 * L * Lj + m;
+  cx<T>* __restrict__ X = sg.buf_out + (size_t)g * sg.nb * Lj + m;
   auto out = [&](int v, cx<T> val) {
-    if (v < 2 * L) X[(size_t)v * Lj] = cmul<T>(val, __ldg(sg.post + v));
+    if (v < sg.nb) X[(size_t)v * Lj] = cmul<T>(val, __ldg(sg.post + v));
+  };
+  // An odd row count N nb (MW grid) pairs the last row with row N nb of the
+  // buffer (which holds 2L rows per gamma sample) in the alpha analysis: zero it.
+  if (g == sg.N - 1 && ((sg.N * sg.nb) & 1) && threadIdx.x == 0) X[(size_t)sg.nb * Lj] = mkc<T>(0, 0);
+  fft_convolve<T, false>(A, sg.logM, sg.H, sg.tw, in, out);
+}
+
+// MW grid, synthesis: the beta dependence of a (g, m) column of V is a
+// trigonometric polynomial of degree < L_j with V(2 pi - beta) = sigma
+// V(beta), sigma = (-1)^{m+n} (d^l_mn(-beta) = (-1)^{m-n} d^l_mn(beta); all
+// orders n have the parity of N-1).  Its L samples beta_b = (2b+1) pi / n and
+// their reflections are the n = 2L-1 equispaced points of the torus, so
+//   c_p = (1/n) sum_{b<n} V(beta_b) e^{-i p beta_b},  0 <= p < L_j
+// are its Fourier coefficients exactly (c_{-p} = sigma c_p).  Chirp-z of
+// length M: c_p = (1/n) e^{-i pi (p^2 + p)/n} sum_b [V_b e^{-i pi b^2/n}]
+// e^{+i pi (p - b)^2/n}.  Output in the Y layout [g][m][p] that the beta
+// evaluation kernels read, which then give the column on the DH grid.
+template <typename T>
+__global__ void __launch_bounds__(256) k_beta_mw_dft(const CztSeg<T>* __restrict__ segs, int nseg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
+  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
+  const int item = blockIdx.x - sg.start;
+  const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1;
+  const int g = item / Lj, m = item % Lj;
+  const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
+  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * sg.nb * Lj + m;  // column m of V_g[b][m], b < L
+  auto in = [&](int v) -> cx<T> {
+    if (v >= n) return mkc<T>(0, 0);
+    // beta = pi (v = L - 1) is its own reflection: a sigma = -1 column vanishes there
+    const cx<T> x = v < L ? cscale<T>(V[(size_t)v * Lj], (v == L - 1 && sigma < T(0)) ? T(0) : T(1))
+                          : cscale<T>(V[(size_t)(n - 1 - v) * Lj], sigma);
+    return cmulc<T>(x, __ldg(sg.pre + v));  // sg.pre: e^{i pi b^2/n}
+  };
+  cx<T>* __restrict__ C = sg.buf_out + ((size_t)g * Lj + m) * Lj;  // c_p, p < Lj
+  const T inv_n = T(1) / T(n);
+  auto out = [&](int v, cx<T> val) {
+    if (v < Lj) C[v] = cscale<T>(cmulc<T>(val, __ldg(sg.post + (L - 1) + v)), inv_n);  // sg.post: MW chirp
   };
   fft_convolve<T, false>(A, sg.logM, sg.H, sg.tw, in, out);
 }
@@ -90,7 +128,9 @@ __host__ __device__ constexpr size_t alpha_czt_smem(int maxlogM, bool staging) {
 // The analysis form is not persistent: its inputs (the X rows the beta step
 // has just written) are mostly L2-resident and few, so one CTA per item with
 // direct loads measured faster than staging them ahead.
-template <typename T>
+// ODD: some segment may have an odd row count (MW grid); the DH grid's even
+// counts compile without the guards.
+template <typename T, bool ODD>
 __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __restrict__ segs, int nseg, int maxlogM,
                                                           CallPtrs ptrs) {
   constexpr int NT = alpha_czt_nt(sizeof(T) == 8);
@@ -100,7 +140,8 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __res
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
   const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM, n = 2 * L - 1;
   const int p0 = (blockIdx.x - sg.start) * NT;
-  const int nt = min(NT, sg.N * L - p0);  // transforms present in this CTA
+  const int rows = sg.N * sg.nb;           // rows (g, b); row pair p = rows 2p, 2p+1
+  const int nt = min(NT, (ODD ? rows + 1 : rows) / 2 - p0);  // transforms present in this CTA
   const cx<T>* __restrict__ X = sg.buf_in + (size_t)(2 * p0) * Lj;
   // input position v holds m = v (v < Lj) or m = v - M (v > M - Lj)
   auto pre = [&](int v) -> cx<T> {
@@ -108,6 +149,9 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __res
     if (v > M - Lj) return __ldg(sg.pre + (M - v));
     return mkc<T>(0, 0);
   };
+  // an odd row count (MW grid) leaves the last pair one row; its partner is
+  // the zero row that the beta analysis writes after the last row
+  auto two = [&](int t) { return !ODD || 2 * (p0 + t) + 1 < rows; };
   auto in = [&](int v, int t, cx<T> c) -> cx<T> {
     if (t >= nt) return mkc<T>(0, 0);
     if (v < Lj) {
@@ -128,7 +172,7 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __res
     if (v < n && t < nt) {
       const cx<T> w = cmul<T>(y, c);
       Wb[(size_t)(2 * t) * n + v] = w.x;
-      Wb[(size_t)(2 * t + 1) * n + v] = w.y;
+      if (two(t)) Wb[(size_t)(2 * t + 1) * n + v] = w.y;
     }
   };
   fft_convolve_n<T, NT, false>(A, ST, sg.logM, sg.H, sg.tw, pre, in, post, out, []() {});
@@ -146,12 +190,15 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
   auto prefetch = [&](int it) {
     if (it < total) {
       const CztSeg<T> sp = segs[czt_find_seg<T>(segs, nseg, it)];
-      const int p0 = (it - sp.start) * NT, nr = 2 * min(NT, sp.N * sp.L - p0), n = 2 * sp.L - 1;
+      const int p0 = (it - sp.start) * NT, n = 2 * sp.L - 1;
+      const int nr = min(2 * NT, sp.N * sp.nb - 2 * p0);  // rows of this item (the last pair may have one)
       const T* __restrict__ Wr = reinterpret_cast<const T*>(sp.is_phi ? ptrs.Wphi[sp.job] : ptrs.W[sp.job]) +
                                  sp.woff + (size_t)(2 * p0) * n;
       for (int r = 0; r < nr; ++r)
         for (int a = threadIdx.x; a < n; a += blockDim.x)
           cp_async_ca<sizeof(T)>(stg + r * P + a, Wr + (size_t)r * n + a);
+      if (nr & 1)  // the missing second row of the last pair (MW grid, odd row count): zeros
+        for (int a = threadIdx.x; a < n; a += blockDim.x) stg[nr * P + a] = T(0);
     }
     cp_async_commit();
   };
@@ -161,7 +208,8 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
     const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg, it)];
     const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM, n = 2 * L - 1;
     const int p0 = (it - sg.start) * NT;
-    const int nt = min(NT, sg.N * L - p0);
+    const int rows = sg.N * sg.nb;
+    const int nt = min(NT, (rows + 1) / 2 - p0);
     cp_async_wait<0>();
     __syncthreads();
     auto pre = [&](int v) -> cx<T> { return v < n ? __ldg(sg.pre + v) : mkc<T>(0, 0); };
@@ -184,7 +232,7 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
         // V1 = (Zp + conj(Zm))/2, V2 = (Zp - conj(Zm))/(2i), rows 2(p0 + t), 2(p0 + t) + 1
         cx<T>* __restrict__ V1 = sg.buf_out + (size_t)(2 * (p0 + t)) * Lj;  // V_g[b][m] rows, m fastest
         V1[mm] = mkc<T>((zp.x + zm.x) * h, (zp.y - zm.y) * h);
-        V1[Lj + mm] = mkc<T>((zp.y + zm.y) * h, (zm.x - zp.x) * h);
+        if (2 * (p0 + t) + 1 < rows) V1[Lj + mm] = mkc<T>((zp.y + zm.y) * h, (zm.x - zp.x) * h);
       }
     }
     __syncthreads();  // A is rewritten by the next item
@@ -206,7 +254,7 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
 // domain, then one inverse FFT.  S + 1 FFTs of M' replace two of M.  A CTA
 // runs G = 4096 / M' row pairs side by side, one per group of M'/16 threads.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool ODD>
 __global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
@@ -217,7 +265,8 @@ __global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __re
   cx<T>* Z = sm + (G + g) * ST;
   const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1, P = sg.P, S = sg.nsegs;
   const int pidx = (blockIdx.x - sg.start) * G + g;  // row pair (complex transform) of this group
-  const bool valid = pidx < sg.N * L;
+  const int rows = sg.N * sg.nb;
+  const bool valid = pidx < (ODD ? rows + 1 : rows) / 2, two = !ODD || 2 * pidx + 1 < rows;
   int Rl, nmid;
   fft_schedule(logM, Rl, nmid);  // nmid == 1 for 9 <= logM <= 12
   const cx<T>* __restrict__ X = sg.buf_in + (size_t)(2 * (valid ? pidx : 0)) * Lj;
@@ -226,7 +275,7 @@ __global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __re
   fftg_first_fwd<T>(Y, M, tid, sg.tw, [&](int v) -> cx<T> {
     if (!valid) return mkc<T>(0, 0);
     if (v < Lj) {
-      const cx<T> x1 = X[v], x2 = X[Lj + v];
+      const cx<T> x1 = X[v], x2 = X[Lj + v];  // a missing partner: the zero row after the last
       return cmul<T>(mkc<T>(x1.x - x2.y, x1.y + x2.x), __ldg(sg.pre + v));
     }
     if (v > M - Lj) {
@@ -254,14 +303,14 @@ __global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __re
       if (valid && v < P && a < n) {
         const cx<T> w = cmul<T>(y, __ldg(sg.post + a));
         Wb[a] = w.x;
-        Wb[n + a] = w.y;
+        if (two) Wb[n + a] = w.y;
       }
     });
     __syncthreads();  // Z is rewritten by the next segment
   }
 }
 
-template <typename T>
+template <typename T, bool ODD>
 __global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
@@ -272,19 +321,25 @@ __global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __re
   cx<T>* B = sm + (G + g) * ST;
   const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1, P = sg.P, S = sg.nsegs;
   const int pidx = (blockIdx.x - sg.start) * G + g;
-  const bool valid = pidx < sg.N * L;
+  const int rows = sg.N * sg.nb;
+  const bool valid = pidx < (ODD ? rows + 1 : rows) / 2, two = !ODD || 2 * pidx + 1 < rows;
   int Rl, nmid;
   fft_schedule(logM, Rl, nmid);
   const cx<T>* __restrict__ tw1 = sg.tw + fft_twiddle_level_offset(logM, 1);
   const T* __restrict__ Wr = reinterpret_cast<const T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) +
                              sg.woff + (size_t)(2 * (valid ? pidx : 0)) * n;
+  // A missing second row (odd row count, MW grid) re-reads the first: the
+  // split below recovers the first row's transform whatever its finite
+  // partner, and the second is not stored.  (A guarded load here costs a
+  // quarter of the kernel's time.)
+  const int o2 = two ? n : 0;
   for (int s = 0; s < S; ++s) {
     const int as = s * P;
     // u_p = (W1 + i W2)_{a_s + p} e^{-i pi a^2/n}, p < P
     fftg_first_fwd<T>(B, M, tid, sg.tw, [&](int v) -> cx<T> {
       const int a = as + v;
       if (!valid || v >= P || a >= n) return mkc<T>(0, 0);
-      return cmulc<T>(mkc<T>(Wr[a], Wr[n + a]), __ldg(sg.pre + a));
+      return cmulc<T>(mkc<T>(Wr[a], Wr[o2 + a]), __ldg(sg.pre + a));
     });
     __syncthreads();
     fftg_stage16<T, false>(B, M, M / 16, tid, nthr, tw1);
@@ -307,7 +362,7 @@ __global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __re
     const cx<T> zm = cmulc<T>(ACC[fpad((M - mm) & (M - 1))], ch);
     // V1 = (Zp + conj(Zm))/2, V2 = (Zp - conj(Zm))/(2i)
     V1[mm] = mkc<T>((zp.x + zm.x) * h, (zp.y - zm.y) * h);
-    V1[Lj + mm] = mkc<T>((zp.y + zm.y) * h, (zm.x - zp.x) * h);
+    if (two) V1[Lj + mm] = mkc<T>((zp.y + zm.y) * h, (zm.x - zp.x) * h);
   }
 }
 
@@ -320,9 +375,9 @@ __global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restric
   const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM;
   const int g = item / Lj, m = item % Lj;
   const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
-  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * 2 * L * Lj + m;  // column m of V_g[b][m]
+  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * sg.nb * Lj + m;  // column m of V_g[b][m]
   auto in = [&](int v) -> cx<T> {
-    if (v >= 2 * L) return mkc<T>(0, 0);
+    if (v >= sg.nb) return mkc<T>(0, 0);
     return cmul<T>(V[(size_t)v * Lj], __ldg(sg.pre + v));
   };
   auto none = [](int, cx<T>) {};
@@ -374,10 +429,10 @@ __global__ void __launch_bounds__(256, 2) k_beta_ana_fft(const CztSeg<T>* __rest
     }
   }
   __syncthreads();
-  cx<T>* __restrict__ X = sg.buf_out + (size_t)g * 2 * L * Lj + m0;
+  cx<T>* __restrict__ X = sg.buf_out + (size_t)g * sg.nb * Lj + m0;
   const bool pair = (NT == 2) && (nt == 2) && (Lj % 2 == 0);  // 16-byte aligned column pairs
   fft_inverse_to_n<T, NT>(A, ST, logM, sg.tw, [&](int v, const cx<T>* y) {
-    if (v < 2 * L) {
+    if (v < sg.nb) {
       if (pair) {
         *reinterpret_cast<float4*>(X + (size_t)v * Lj) = *reinterpret_cast<const float4*>(y);
       } else {
@@ -399,10 +454,10 @@ __global__ void __launch_bounds__(256, 2) k_beta_syn_fft(const CztSeg<T>* __rest
   const int per_g = (Lj + NT - 1) / NT;
   const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
   const bool pair = (NT == 2) && (nt == 2) && (Lj % 2 == 0);
-  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * 2 * L * Lj + m0;  // columns m0.. of V_g[b][m]
+  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * sg.nb * Lj + m0;  // columns m0.. of V_g[b][m]
   const cx<T>* __restrict__ q = sg.post;
   fft_forward_from_n<T, NT>(A, ST, logM, sg.tw, [&](int v, cx<T>* x) {
-    if (v >= 2 * L) {
+    if (v >= sg.nb) {
 #pragma unroll
       for (int t = 0; t < NT; ++t) x[t] = mkc<T>(0, 0);
       return;
@@ -473,7 +528,7 @@ __global__ void __launch_bounds__(256) k_alpha_ana_direct(const CztSeg<T>* __res
   const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1, K = 2 * Lj - 1;
   const int ntile = (n + kAgCols - 1) / kAgCols;
   const int a0 = (item % ntile) * kAgCols;
-  const int nrows = sg.N * 2 * L, rbeg = (item / ntile) * kAgChunk, rend = min(nrows, rbeg + kAgChunk);
+  const int nrows = sg.N * sg.nb, rbeg = (item / ntile) * kAgChunk, rend = min(nrows, rbeg + kAgChunk);
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const cx<T>* __restrict__ root = sg.pre;  // e^{2 pi i u / n}, u < n
   T* __restrict__ Wb = reinterpret_cast<T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff;
@@ -611,7 +666,7 @@ __global__ void __launch_bounds__(256) k_alpha_syn_direct(const CztSeg<T>* __res
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
   const int item = blockIdx.x - sg.start;
   const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1;
-  const int nrows = sg.N * 2 * L, row0 = item * R, nr = min(R, nrows - row0);
+  const int nrows = sg.N * sg.nb, row0 = item * R, nr = min(R, nrows - row0);
   T* Ws = reinterpret_cast<T*>(smem_raw);  // [n][R], later the partials
   const T* __restrict__ Wb = reinterpret_cast<const T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff +
                              (size_t)row0 * n;
@@ -727,16 +782,21 @@ template <typename T>
 void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items, int maxlogM,
                      const CallPtrs& ptrs, cudaStream_t st) {
   if (total_items <= 0) return;
+  const bool odd = (kind & CZT_ODD_ROWS) != 0;
+  kind &= ~CZT_ODD_ROWS;
   if (kind == CZT_ALPHA_ANA) {
-    k_czt_alpha_ana<T><<<total_items, 256, alpha_czt_smem<T>(maxlogM, false), st>>>(segs, nseg, maxlogM, ptrs);
+    auto k = odd ? k_czt_alpha_ana<T, true> : k_czt_alpha_ana<T, false>;
+    k<<<total_items, 256, alpha_czt_smem<T>(maxlogM, false), st>>>(segs, nseg, maxlogM, ptrs);
     return;
   }
   if (kind == CZT_ALPHA_ANA_SEG) {
-    k_czt_alpha_ana_seg<T><<<total_items, 256, alpha_seg_smem<T>(), st>>>(segs, nseg, ptrs);
+    auto k = odd ? k_czt_alpha_ana_seg<T, true> : k_czt_alpha_ana_seg<T, false>;
+    k<<<total_items, 256, alpha_seg_smem<T>(), st>>>(segs, nseg, ptrs);
     return;
   }
   if (kind == CZT_ALPHA_SYN_SEG) {
-    k_czt_alpha_syn_seg<T><<<total_items, 256, alpha_seg_smem<T>(), st>>>(segs, nseg, ptrs);
+    auto k = odd ? k_czt_alpha_syn_seg<T, true> : k_czt_alpha_syn_seg<T, false>;
+    k<<<total_items, 256, alpha_seg_smem<T>(), st>>>(segs, nseg, ptrs);
     return;
   }
   if (kind == CZT_ALPHA_SYN) {
@@ -750,6 +810,11 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
   switch (kind) {
     case CZT_BETA_ANA: k_czt_beta_ana<T><<<grid, block, smem, st>>>(segs, nseg); break;
     case CZT_BETA_SYN: k_czt_beta_syn<T><<<grid, block, smem, st>>>(segs, nseg); break;
+    case CZT_BETA_MW_DFT: k_beta_mw_dft<T><<<grid, block, smem, st>>>(segs, nseg); break;
+    case CZT_BETA_RS: k_czt_beta_ana<T><<<grid, block, smem, st>>>(segs, nseg); break;
+    case CZT_BETA_RS_FFT:
+      k_beta_ana_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
+      break;
     case CZT_ALPHA_ANA_DIRECT:
       k_alpha_ana_direct<T><<<grid, block, alpha_ana_direct_smem<T>(), st>>>(segs, nseg, ptrs);
       break;
@@ -770,11 +835,14 @@ template <typename T>
 cudaError_t czt_set_smem(int maxlogM) {
   const int smem = (int)(sizeof(cx<T>) * (size_t)fft_smem_elems(1 << maxlogM));
   cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(k_beta_mw_dft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_czt_beta_ana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_czt_alpha_ana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)alpha_czt_smem<T>(maxlogM, false));
-  if (e != cudaSuccess) return e;
+  for (auto k : {k_czt_alpha_ana<T, false>, k_czt_alpha_ana<T, true>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)alpha_czt_smem<T>(maxlogM, false));
+    if (e != cudaSuccess) return e;
+  }
   e = cudaFuncSetAttribute(k_czt_alpha_syn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)alpha_czt_smem<T>(maxlogM, true));
   if (e != cudaSuccess) return e;
@@ -784,12 +852,11 @@ cudaError_t czt_set_smem(int maxlogM) {
   e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            smem * beta_fft_nt(sizeof(T) == 8));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_czt_alpha_ana_seg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)alpha_seg_smem<T>());
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_czt_alpha_syn_seg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)alpha_seg_smem<T>());
-  if (e != cudaSuccess) return e;
+  for (auto k : {k_czt_alpha_ana_seg<T, false>, k_czt_alpha_ana_seg<T, true>, k_czt_alpha_syn_seg<T, false>,
+                 k_czt_alpha_syn_seg<T, true>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)alpha_seg_smem<T>());
+    if (e != cudaSuccess) return e;
+  }
   e = cudaFuncSetAttribute(k_alpha_ana_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)alpha_ana_direct_smem<T>());
   if (e != cudaSuccess) return e;

@@ -58,8 +58,14 @@ enum CztKind {
   CZT_BETA_ANA_FFT = 6,      // beta sums as one FFT of length 4L (L a power of two)
   CZT_BETA_SYN_FFT = 7,
   CZT_ALPHA_ANA_SEG = 8,     // segmented chirp-z (bands small next to L)
-  CZT_ALPHA_SYN_SEG = 9
+  CZT_ALPHA_SYN_SEG = 9,
+  CZT_BETA_MW_DFT = 10,      // MW grid, synthesis: torus coefficients from the L beta samples
+  CZT_BETA_RS_FFT = 11,      // MW grid, synthesis: those coefficients evaluated on the DH beta grid
+  CZT_BETA_RS = 12           //   (single FFT, or chirp-z for non-power-of-two L)
 };
+// Or-ed into an alpha chirp-z kind: the list may hold segments with an odd row
+// count N nb (MW grid), whose last row pair has one row.
+constexpr int CZT_ODD_ROWS = 0x100;
 // shared memory of the segmented chirp-z kernels: two buffers of M' (+ padding)
 // for each of the 4096 / M' row pairs of a CTA
 template <typename T>
@@ -97,6 +103,7 @@ struct CztSeg {
   const cx<T>* post;
   T scale;
   int P, nsegs;   // segmented chirp-z: samples per segment, segments
+  int nb;         // beta samples per gamma sample (rows of X, V and W per g): 2L, or L on the MW grid
 };
 
 // Per-job parameters of the batched final synthesis reduction.

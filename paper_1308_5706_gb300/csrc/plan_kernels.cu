@@ -439,6 +439,25 @@ cudaError_t launch_chirp_build64(double2* tw, double2* chirp_a, double2* pre_b, 
 
 int twiddle_entries(int logM) { return fft_twiddle_entries(logM); }
 
+// MW beta chirp: pre_mw[m' + L - 1] = e^{i pi (m'^2 + m')/n}, |m'| < L, n = 2L-1
+// (the linear term is the grid's offset beta_b = (2b+1) pi / n).
+__global__ void k_mw_pre(double2* pre, int L) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = 2LL * L - 1;
+  if (i >= n) return;
+  const long long mp = (long long)i - (L - 1);
+  long long p = (mp * (mp + 1)) % (2 * n);
+  if (p < 0) p += 2 * n;
+  double s, c;
+  sincospi((double)p / (double)n, &s, &c);
+  pre[i] = make_double2(c, s);
+}
+
+cudaError_t launch_mw_pre64(double2* pre, int L, cudaStream_t st) {
+  k_mw_pre<<<nblk(2 * (int64_t)L - 1, 256), 256, 0, st>>>(pre, L);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_seg_build64(double2* tw, double2* Ha, double2* Hs, int L, int Lj, int logM, int P, int S,
                                cudaStream_t st) {
   const int M = 1 << logM;

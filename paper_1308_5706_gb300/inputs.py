@@ -63,12 +63,14 @@ def flm_uniform(L: int, seed: int) -> np.ndarray:
     return f
 
 
-def w_random(L: int, N: int, n_scale: int, seed: int):
-    """Arbitrary real wavelet coefficients [n_scale][N][2L][2L-1] and scaling
-    coefficients [2L][2L-1], standard normal; inputs for synthesis-only checks."""
+def w_random(L: int, N: int, n_scale: int, seed: int, nb: int = None):
+    """Arbitrary real wavelet coefficients [n_scale][N][nb][2L-1] and scaling
+    coefficients [nb][2L-1] (nb beta samples, default 2L), standard normal;
+    inputs for synthesis-only checks."""
+    nb = 2 * L if nb is None else nb
     rng = np.random.Generator(np.random.PCG64(seed))
-    W = rng.standard_normal((n_scale, N, 2 * L, 2 * L - 1))
-    Wphi = rng.standard_normal((2 * L, 2 * L - 1))
+    W = rng.standard_normal((n_scale, N, nb, 2 * L - 1))
+    Wphi = rng.standard_normal((nb, 2 * L - 1))
     return W, Wphi
 
 
