@@ -226,6 +226,17 @@ int s2dw_steer(s2dw_plan_t plan, const void* W, const double* gammas, int ngamma
 const char* s2dw_strerror(int status);
 
 /*
+ * s2dw_wait_timeouts: number of bounded waits in the library's kernels that
+ * gave up since the last call (0 in normal operation).  The tensor-core
+ * kernels of the small-band alpha sums (FP32 plans) wait on an mbarrier for
+ * their matrix products, about one second at most; one that gives up skips
+ * the rest of its work and releases its tensor memory, so the output of that
+ * call is invalid.  Synchronous (waits for the device); reads and resets the
+ * count.  S2DW_EINVAL for NULL.
+ */
+int s2dw_wait_timeouts(int* count);
+
+/*
  * Introspection used by the tests (synchronous, host outputs).
  *   s2dw_scale_support: l-range [lo, hi] on which kappa^j(l) > 0 (j = J+1
  *     gives Phi's range, lo = 0).

@@ -50,6 +50,7 @@ _SIGNATURES = {
     "s2dw_profile": (_c_i, [_c_p, _c_i]),
     "s2dw_profile_read": (_c_i, [_c_p, _c_dp, _c_ip]),
     "s2dw_delta_table_noalloc": (_c_i, [_c_i, _c_p, _c_p, _c_i64p, _c_p]),
+    "s2dw_wait_timeouts": (_c_i, [_c_ip]),
 }
 
 STAGES = ["ana_contract", "ana_contract_phi", "ana_beta", "ana_alpha_czt", "ana_alpha_direct",
@@ -164,6 +165,14 @@ def s2dw_launch_counts(plan: int):
     a, s = ctypes.c_int(), ctypes.c_int()
     _check(lib().s2dw_launch_counts(plan, ctypes.byref(a), ctypes.byref(s)), "s2dw_launch_counts")
     return a.value, s.value
+
+
+def s2dw_wait_timeouts() -> int:
+    """Bounded waits in the library's kernels that gave up since the last
+    call (0 in normal operation); synchronises the device."""
+    c = ctypes.c_int()
+    _check(lib().s2dw_wait_timeouts(ctypes.byref(c)), "s2dw_wait_timeouts")
+    return c.value
 
 
 def s2dw_kernels(plan: int, J: int, L: int, N: int):

@@ -1,6 +1,7 @@
 // C ABI: plans, the shared Delta table, launch lists, analysis and synthesis.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -286,6 +287,8 @@ struct s2dw_plan_s {
     void* Hs = nullptr;  // S synthesis spectra
   };
   std::vector<SegTables> seg;  // [nscale + 1]
+  // [nscale + 1]: tensor-core basis images of the direct alpha sums (FP32 plans)
+  std::vector<void*> tc_ana, tc_syn;
   // host copies of the static descriptors (device copies live in `own`)
   std::vector<unsigned char> desc_w_host, desc_phi_host;
   std::vector<TileTask> tiles_w_host, tiles_phi_host;
@@ -555,10 +558,15 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
       s.nsegs = sgt.S;
     }
     if (direct) {
-      if (base_kind == CZT_ALPHA_ANA)
+      const bool syn = base_kind == CZT_ALPHA_SYN;
+      if (sizeof(T) == sizeof(float)) {  // tensor cores: the plan's basis image of this scale
+        s.items = alpha_tc_items(L, Nj * G.nb, syn);
+        s.H = reinterpret_cast<const cx<T>*>(syn ? p->tc_syn[j] : p->tc_ana[j]);
+      } else if (!syn) {
         s.items = ((n + kAgCols - 1) / kAgCols) * ((Nj * G.nb + kAgChunk - 1) / kAgChunk);
-      else
+      } else {
         s.items = (Nj * G.nb + direct_rows_syn(sizeof(T) == 8) - 1) / direct_rows_syn(sizeof(T) == 8);
+      }
       s.pre = reinterpret_cast<const cx<T>*>(G.root_a);
     }
     if (s.items <= 0) continue;
@@ -788,6 +796,16 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     so[j].Ha = take((size_t)sgt.S * Ms * sizeof(cx<T>));
     so[j].Hs = take((size_t)sgt.S * Ms * sizeof(cx<T>));
   }
+  // tensor-core basis images of the direct alpha sums (FP32 plans)
+  std::vector<size_t> o_ta(p->nscale + 1, SIZE_MAX), o_ts(p->nscale + 1, SIZE_MAX);
+  if (sizeof(T) == sizeof(float)) {
+    for (int j = 0; j <= p->nscale; ++j) {
+      const int Lj = p->Ycols[j], Lg = p->gt[p->grid_of[j]].L;
+      if (Lj <= 0) continue;
+      if (Lj <= kDirectMaxLjAna) o_ta[j] = take(alpha_tc_table_floats(Lg, Lj, false) * sizeof(float));
+      if (Lj <= kDirectMaxLj) o_ts[j] = take(alpha_tc_table_floats(Lg, Lj, true) * sizeof(float));
+    }
+  }
   p->ws_bytes = off;
   amalloc(&p->ws, off, st);
   char* b = reinterpret_cast<char*>(p->ws);
@@ -820,6 +838,19 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     sgt.tw = b + so[j].tw;
     sgt.Ha = b + so[j].Ha;
     sgt.Hs = b + so[j].Hs;
+  }
+  p->tc_ana.assign(p->nscale + 1, nullptr);
+  p->tc_syn.assign(p->nscale + 1, nullptr);
+  for (int j = 0; j <= p->nscale; ++j) {
+    const int Lj = p->Ycols[j], Lg = p->gt[p->grid_of[j]].L;
+    if (o_ta[j] != SIZE_MAX) {
+      p->tc_ana[j] = b + o_ta[j];
+      ck(alpha_tc_build_table(reinterpret_cast<float*>(p->tc_ana[j]), Lg, Lj, false, st));
+    }
+    if (o_ts[j] != SIZE_MAX) {
+      p->tc_syn[j] = b + o_ts[j];
+      ck(alpha_tc_build_table(reinterpret_cast<float*>(p->tc_syn[j]), Lg, Lj, true, st));
+    }
   }
 
   // ---- R tables ----
@@ -1291,6 +1322,13 @@ int s2dw_alpha_method(s2dw_plan_t p, int j, int dir, int* method, int* fft_len, 
   if (segments) *segments = ns;
   if (seg_len) *seg_len = sl;
   return S2DW_OK;
+}
+
+int s2dw_wait_timeouts(int* count) {
+  if (!count) return S2DW_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return err_of(e);
+  return err_of(alpha_tc_timeouts(count));
 }
 
 int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {

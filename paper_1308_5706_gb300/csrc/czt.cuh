@@ -816,7 +816,10 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
       k_beta_ana_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
       break;
     case CZT_ALPHA_ANA_DIRECT:
-      k_alpha_ana_direct<T><<<grid, block, alpha_ana_direct_smem<T>(), st>>>(segs, nseg, ptrs);
+      if constexpr (sizeof(T) == sizeof(float))
+        launch_alpha_tc(false, segs, nseg, total_items, ptrs, st);  // tensor cores
+      else
+        k_alpha_ana_direct<T><<<grid, block, alpha_ana_direct_smem<T>(), st>>>(segs, nseg, ptrs);
       break;
     case CZT_BETA_ANA_FFT:
       k_beta_ana_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
@@ -825,7 +828,10 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
       k_beta_syn_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
       break;
     case CZT_ALPHA_SYN_DIRECT:
-      k_alpha_syn_direct<T><<<grid, block, alpha_syn_direct_smem<T>(1 << (maxlogM - 2)), st>>>(segs, nseg, ptrs);
+      if constexpr (sizeof(T) == sizeof(float))
+        launch_alpha_tc(true, segs, nseg, total_items, ptrs, st);  // tensor cores
+      else
+        k_alpha_syn_direct<T><<<grid, block, alpha_syn_direct_smem<T>(1 << (maxlogM - 2)), st>>>(segs, nseg, ptrs);
       break;
     default: break;
   }
@@ -857,12 +863,17 @@ cudaError_t czt_set_smem(int maxlogM) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)alpha_seg_smem<T>());
     if (e != cudaSuccess) return e;
   }
-  e = cudaFuncSetAttribute(k_alpha_ana_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)alpha_ana_direct_smem<T>());
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_alpha_syn_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)alpha_syn_direct_smem<T>(2048));
-  if (e != cudaSuccess) return e;
+  if constexpr (sizeof(T) == sizeof(double)) {  // FP32 plans take the tensor-core kernels
+    e = cudaFuncSetAttribute(k_alpha_ana_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)alpha_ana_direct_smem<T>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_alpha_syn_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)alpha_syn_direct_smem<T>(2048));
+    if (e != cudaSuccess) return e;
+  } else {
+    e = alpha_tc_prepare();
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(k_czt_beta_syn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 

@@ -106,6 +106,16 @@ struct CztSeg {
   int nb;         // beta samples per gamma sample (rows of X, V and W per g): 2L, or L on the MW grid
 };
 
+// Direct alpha sums on the tensor cores (FP32 plans, scales with L_j <= 32;
+// alpha_tc.cu).  Basis tables: one per scale and direction, built per plan.
+size_t alpha_tc_table_floats(int L, int Lj, bool syn);
+cudaError_t alpha_tc_build_table(float* out, int L, int Lj, bool syn, cudaStream_t st);
+int alpha_tc_items(int L, int rows, bool syn);
+void launch_alpha_tc(bool syn, const CztSeg<float>* segs, int nseg, int total_items, const CallPtrs& ptrs,
+                     cudaStream_t st);
+cudaError_t alpha_tc_prepare();
+cudaError_t alpha_tc_timeouts(int* count);  // reads and resets the device count
+
 // Per-job parameters of the batched final synthesis reduction.
 struct ReduceJobs {
   const void* dw[MAXB];

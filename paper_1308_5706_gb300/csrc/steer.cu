@@ -32,7 +32,11 @@ template <typename T, bool VEC>
 __global__ void __launch_bounds__(256) k_steer(const T* __restrict__ W, T* __restrict__ out, SteerWeights sw,
                                                int N, int ngamma, int64_t per_scale) {
   __shared__ T wt[kSteerMaxGamma][kSteerMaxN];
-  for (int i = threadIdx.x; i < ngamma * N; i += blockDim.x) wt[i / N][i % N] = (T)sw.w[i / N][i % N];
+  // every entry: the scalar path below multiplies the unused ones (g >= N) by zero
+  for (int i = threadIdx.x; i < kSteerMaxGamma * kSteerMaxN; i += blockDim.x) {
+    const int t = i / kSteerMaxN, g = i % kSteerMaxN;
+    wt[t][g] = (t < ngamma && g < N) ? (T)sw.w[t][g] : T(0);
+  }
   __syncthreads();
   const int j = blockIdx.y;
   const T* __restrict__ Wj = W + (size_t)j * N * per_scale;
