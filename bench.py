@@ -464,6 +464,43 @@ def run_multires_workload(args):
     return 0
 
 
+def run_mw_workload(args):
+    """The L=1024, N=5, lambda=2 round trip sampled on the McEwen-Wiaux grid
+    (S2DW_MW: L beta samples instead of 2L): mixed timed with CUDA events,
+    checked against the FP64 MW plan and by the round trip."""
+    import torch
+    from paper_1308_5706_gb300 import binding as B
+    pm = B.Plan(L, N, LAM, J0, "mixed", mw=True)
+    f = torch.from_numpy(flm_gaussian(L, SEED, "cl")).to(torch.complex64).cuda()
+    stream = torch.cuda.Stream()
+    per, total, Wm, Wpm, frm, prof = time_path(torch, pm, f, args.steps, args.warmup, stream, profile=True)
+    stage_ms, nana, nsyn = prof
+    mean_stage = {k: round(v / (nana if k.startswith("ana") else nsyn), 4) for k, v in stage_ms.items()}
+    p64 = B.Plan(L, N, LAM, J0, "fp64", mw=True)
+    W64, Wp64 = p64.alloc_w()
+    p64.analysis(f.to(torch.complex128), W64, Wp64)
+    f64r = p64.alloc_flm()
+    p64.synthesis(W64, Wp64, f64r)
+    torch.cuda.synchronize()
+    err = max(float((Wm[j].double() - W64[j]).abs().max() / W64[j].abs().max().clamp_min(1e-300))
+              for j in range(pm.nscale))
+    f0 = f.to(torch.complex128)
+    eps_m = float((frm.to(torch.complex128) - f0).abs().max() / f0.abs().max())
+    eps_64 = float((f64r - f0).abs().max() / f0.abs().max())
+    out = {"metric": "MW-grid wavelet analysis+synthesis transforms/s (L=1024, N=5, mixed)",
+           "value": args.steps / (total / 1e3), "unit": "transforms/s", "ms_per_step": total / args.steps,
+           "steps": args.steps, "warmup": args.warmup,
+           "config": {"workload": WORKLOAD + "; beta sampled at pi(2b+1)/(2L-1), b < L",
+                      "samples": int(Wm.numel()), "samples_dh": int(pm.nscale * N * 2 * L * (2 * L - 1))},
+           "max_rel_err": {"mixed_vs_fp64_W_max_rel_per_scale": err, "round_trip_eps_mixed": eps_m,
+                           "round_trip_eps_fp64": eps_64},
+           "stage_ms": mean_stage}
+    print(json.dumps(out))
+    pm.close()
+    p64.close()
+    return 0
+
+
 def run_sht_workload(args):
     """Inverse then forward spherical harmonic transform of the L=1024 signal
     on the DH sphere grid (mixed), timed with CUDA events; error of the round
@@ -548,7 +585,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="roundtrip", choices=["roundtrip", "batch", "serve", "steer", "multires", "sht"])
+    ap.add_argument("--workload", default="roundtrip",
+                    choices=["roundtrip", "batch", "serve", "steer", "multires", "sht", "mw"])
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
@@ -565,6 +603,8 @@ def main():
         return run_multires_workload(args)
     if args.workload == "sht":
         return run_sht_workload(args)
+    if args.workload == "mw":
+        return run_mw_workload(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

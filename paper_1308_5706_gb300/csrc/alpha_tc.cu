@@ -99,15 +99,14 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
   const bool kin = k < K, kst = k < K8;
   const int o0 = kst ? tc::img_off(rl0, k, K8) : 0, oq = (RS / 8) * (K8 / 4) * tc::kLboF;
   const float* __restrict__ X = reinterpret_cast<const float*>(sg.buf_in);
-  float xr[16];  // NQ <= 16
-  auto load = [&](int i) {
+  auto load = [&](int i, float (&xr)[16]) {  // NQ <= 16
     const int r = rbeg + i * kTcRows + rl0;
     const float* src = X + (size_t)r * K + k;
 #pragma unroll
     for (int q = 0; q < 16; ++q)
       if (q < NQ) xr[q] = (kin && r + q * RS < rend) ? __ldg(src + (size_t)q * RS * K) : 0.f;
   };
-  auto store = [&](int stg) {
+  auto store = [&](int stg, const float (&xr)[16]) {
     float* hi = Bimg + (size_t)stg * 2 * img + o0;
     float* lo = hi + img;
     if (kst) {
@@ -135,8 +134,12 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
       tc::mma_tf32(tmem_d + kTcRows, aL + o, bH + o, idesc, 1);
     }
   };
-  load(0);
-  store(0);
+  // row tiles in registers one tile ahead of their store, two buffers used
+  // by name (the loop is unrolled by two), so no copy waits on loads in flight
+  float xa[16], xb[16];
+  load(0, xa);
+  if (ntr > 1) load(1, xb);
+  store(0, xa);
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   tc::fence_async_smem();
   tc::fence_before();
@@ -150,17 +153,18 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
   int last = 0;  // last row tile whose MMAs were issued
   // epilogue map: warp w holds samples a0 + 32 (w % 4) + lane and rows 32 (w / 4) .. + 31 of a tile
   const int a = a0 + 32 * (w & 3) + lane, cg = 32 * (w >> 2);
-  for (int i = 0; i < ntr; ++i) {
+  // tile i: fill = the buffer of tile i (stored), reloaded with tile i + 2; use = tile i + 1
+  auto step = [&](int i, float (&use)[16], float (&fill)[16]) -> bool {
     const int s = i & 1;
-    if (i + 1 < ntr) load(i + 1);
-    if (i + 1 < ntr) store(s ^ 1);  // stage s ^ 1: tile i - 1 was waited for
+    if (i + 2 < ntr) load(i + 2, fill);
+    if (i + 1 < ntr) store(s ^ 1, use);  // stage s ^ 1: tile i - 1 was waited for
     // one thread waits for tile i's MMAs; the barrier below passes it on
     if (t == 0 && !tc::mbar_wait(s ? mb1 : mb0, (i >> 1) & 1, tc::kWaitCycles)) fail = 1;
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (fail) break;  // read after the barrier: the same decision in every thread
+    if (fail) return false;  // read after the barrier: the same decision in every thread
     if (i + 1 < ntr) {
       if (t == 0) {
         issue(s ^ 1, tmem + (uint32_t)((s ^ 1) * 2 * kTcRows));
@@ -182,6 +186,11 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
       }
     }
     tc::fence_before();
+    return true;
+  };
+  for (int i = 0; i < ntr; i += 2) {
+    if (!step(i, xb, xa)) break;
+    if (i + 1 < ntr && !step(i + 1, xa, xb)) break;
   }
   if (fail && t == 0) {
     atomicAdd(&g_tc_timeouts, 1);
@@ -193,19 +202,21 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
 }
 
 // Synthesis, warp-specialised (one CTA of 128 rows per SM):
-//   warps 0-7   producers: W chunk c (registers, one chunk ahead) split into
+//   warps 0-7   producers: W chunk c (registers, two chunks ahead) split into
 //               the A image of ring stage c % 3, the basis chunk copied into
 //               its B image (cp.async, one chunk ahead); arrive on full[stage]
-//   warp  12    MMA issuer (one thread): waits full[stage] and tempty[buffer],
+//   warp  16    MMA issuer (one thread): waits full[stage] and tempty[buffer],
 //               12 MMAs into TMEM buffer c % 2, commits to empty[stage] and
 //               tfull[buffer]
-//   warps 8-11  accumulators: wait tfull[buffer], add the chunk's sums (TMEM
-//               lanes = rows) to FP32 registers, arrive on tempty[buffer];
-//               finally write V
+//   warps 8-15  accumulators: wait tfull[buffer], add the chunk's sums (TMEM
+//               lanes = rows, half the columns per warp, one TMEM wait per
+//               chunk) to FP32 registers, arrive on tempty[buffer]; finally
+//               write V
 // No CTA-wide barrier inside the K loop; every wait is bounded and a timeout
 // in any role stops all of them.
 constexpr int kSynProd = 8;                          // producer warps
-constexpr int kSynThreads = (kSynProd + 4 + 1) * 32;  // + 4 accumulator warps + the MMA warp
+constexpr int kSynAcc = 8;                            // accumulator warps
+constexpr int kSynThreads = (kSynProd + kSynAcc + 1) * 32;  // + the MMA warp
 
 __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<float>* __restrict__ segs, int nseg,
                                                                  CallPtrs ptrs) {
@@ -239,7 +250,7 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(tfull(b), 1);
-      tc::mbar_init(tempty(b), 128);
+      tc::mbar_init(tempty(b), kSynAcc * 32);
     }
     fail = 0;
   }
@@ -266,19 +277,18 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
       for (int i = 4 * t; i < 2 * imgB; i += 4 * kSynProd * 32) cp16(Bhi + i, src + i);
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    float cur[16], nxt[16];
-    load(0, cur);
-    fetch_basis(0);
-    for (int c = 0; c < nchunk; ++c) {
-      if (fail) break;
+    // W registers two chunks ahead in a ring of three buffers used by name
+    // (the loop is unrolled by three), so no copy waits on loads in flight
+    auto step = [&](int c, float (&use)[16], float (&fill)[16]) -> bool {
+      if (fail) return false;
       const int st = c % kSynStages;
+      if (c + 2 < nchunk) load(c + 2, fill);
       if (c + 1 < nchunk) {
-        load(c + 1, nxt);
         const int c1 = c + 1;
         if (c1 >= kSynStages &&
             !tc::mbar_wait(empty(c1 % kSynStages), (c1 / kSynStages - 1) & 1, tc::kWaitCycles)) {
           fail = 1;
-          break;
+          return false;
         }
         fetch_basis(c1);  // stage of chunk c + 1 is free: its previous chunk's MMAs completed
       }
@@ -288,7 +298,7 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
       for (int q = 0; q < 16; ++q) {
         const int o = tc::img_off(w + 8 * q, lane, kTcKc);
         float h, l;
-        tc::split_tf32(cur[q], h, l);
+        tc::split_tf32(use[q], h, l);
         Ahi[o] = h;
         Alo[o] = l;
       }
@@ -298,16 +308,25 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
         asm volatile("cp.async.wait_group 0;" ::: "memory");
       tc::fence_async_smem();
       tc::mbar_arrive(full(st));
-#pragma unroll
-      for (int q = 0; q < 16; ++q) cur[q] = nxt[q];
+      return true;
+    };
+    float b0[16], b1[16], b2[16];
+    load(0, b0);
+    if (nchunk > 1) load(1, b1);
+    fetch_basis(0);
+    for (int c = 0; c < nchunk; c += 3) {
+      if (!step(c, b0, b2)) break;
+      if (c + 1 < nchunk && !step(c + 1, b1, b0)) break;
+      if (c + 2 < nchunk && !step(c + 2, b2, b1)) break;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-  } else if (w < kSynProd + 4) {
-    // ---- accumulators: TMEM lanes 32 (w % 4) .. = rows; all NP columns of both halves ----
-    const int lrow = 32 * (w & 3);
-    float acc[64];
+  } else if (w < kSynProd + kSynAcc) {
+    // ---- accumulators: TMEM lanes 32 (w % 4) .. = rows, columns HC h .. + HC of both
+    //      halves (h = 0, 1; HC = NP / 2 = 8, 16, 24 or 32) ----
+    const int lrow = 32 * (w & 3), h = (w - kSynProd) >> 2, HC = NP / 2;
+    float acc[32];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
     bool ok = true;
     for (int c = 0; c < nchunk; ++c) {
       if (fail) {
@@ -322,14 +341,21 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
         break;
       }
       tc::fence_after();
-      const uint32_t ta = tmem + ((uint32_t)lrow << 16) + (uint32_t)(2 * NP * b);
+      const uint32_t ta = tmem + ((uint32_t)lrow << 16) + (uint32_t)(2 * NP * b + HC * h);
+      if (HC == 32) {
+        float vm[32], vc[32];
+        tc::tmem_ld32x2(ta, ta + NP, vm, vc);
 #pragma unroll
-      for (int g = 0; g < 8; ++g) {
-        if (8 * g < NP) {
-          float vm[8], vc[8];
-          tc::tmem_ld8x2(ta + 8 * g, ta + NP + 8 * g, vm, vc);
+        for (int j = 0; j < 32; ++j) acc[j] += vm[j] + vc[j];
+      } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[8 * g + j] += vm[j] + vc[j];
+        for (int g = 0; g < 3; ++g) {
+          if (8 * g < HC) {
+            float vm[8], vc[8];
+            tc::tmem_ld8x2(ta + 8 * g, ta + NP + 8 * g, vm, vc);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[8 * g + j] += vm[j] + vc[j];
+          }
         }
       }
       tc::fence_before();
@@ -338,8 +364,10 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
     const int r = lrow + lane;
     if (ok && r < nr) {
 #pragma unroll
-      for (int j = 0; j < 64; j += 2)
-        if ((j >> 1) < Lj) V[(size_t)r * Lj + (j >> 1)] = mkc<float>(acc[j], acc[j + 1]);
+      for (int j = 0; j < 32; j += 2) {
+        const int m = (HC * h + j) >> 1;
+        if (j < HC && m < Lj) V[(size_t)r * Lj + m] = mkc<float>(acc[j], acc[j + 1]);
+      }
     }
   } else if (lane == 0) {
     // ---- MMA issuer ----
