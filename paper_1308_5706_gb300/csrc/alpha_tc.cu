@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
     tc::mbar_init(mb1, 1);
     fail = 0;
   }
-  // TMEM: stage s holds the hi*hi sums at column 256 s, the cross terms at 256 s + 128
-  if (w == 0) tc::tmem_alloc(&tbase, 4 * kTcRows);
+  // TMEM: the sums of stage s at column 128 s
+  if (w == 0) tc::tmem_alloc(&tbase, 2 * kTcRows);
   // basis image of this sample tile (built per plan, already split)
   {
     const float* src = reinterpret_cast<const float*>(sg.H) + (size_t)ta * 2 * img;
@@ -123,15 +123,18 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
   };
   const uint32_t idesc = tc::idesc_tf32(kTcA, kTcRows);
   const uint64_t kstep = (uint64_t)(tc::img_kstep_bytes(1) >> 4);  // start-address field per K-step
-  auto issue = [&](int stg, uint32_t tmem_d) {  // D = A_hi B_hi, D' = A_hi B_lo + A_lo B_hi
+  auto issue = [&](int stg, uint32_t tmem_d) {  // D = (A_hi B_lo + A_lo B_hi) + A_hi B_hi, cross terms first
     const uint64_t aH = tc::smem_desc(tc::smem_u32(Ahi), K8), aL = tc::smem_desc(tc::smem_u32(Alo), K8);
     const uint64_t bH = tc::smem_desc(tc::smem_u32(Bimg + (size_t)stg * 2 * img), K8);
     const uint64_t bL = tc::smem_desc(tc::smem_u32(Bimg + (size_t)stg * 2 * img + img), K8);
     for (int s = 0; s < K8 / 8; ++s) {
       const uint64_t o = kstep * s;
-      tc::mma_tf32(tmem_d, aH + o, bH + o, idesc, s > 0);
-      tc::mma_tf32(tmem_d + kTcRows, aH + o, bL + o, idesc, s > 0);
-      tc::mma_tf32(tmem_d + kTcRows, aL + o, bH + o, idesc, 1);
+      tc::mma_tf32(tmem_d, aH + o, bL + o, idesc, s > 0);
+      tc::mma_tf32(tmem_d, aL + o, bH + o, idesc, 1);
+    }
+    for (int s = 0; s < K8 / 8; ++s) {
+      const uint64_t o = kstep * s;
+      tc::mma_tf32(tmem_d, aH + o, bH + o, idesc, 1);
     }
   };
   // row tiles in registers one tile ahead of their store, two buffers used
@@ -167,22 +170,21 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
     if (fail) return false;  // read after the barrier: the same decision in every thread
     if (i + 1 < ntr) {
       if (t == 0) {
-        issue(s ^ 1, tmem + (uint32_t)((s ^ 1) * 2 * kTcRows));
+        issue(s ^ 1, tmem + (uint32_t)((s ^ 1) * kTcRows));
         tc::mma_commit(s ^ 1 ? mb1 : mb0);
       }
       last = i + 1;
     }
     const int r0 = rbeg + i * kTcRows + cg;
-    const uint32_t te = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(s * 2 * kTcRows + cg);
+    const uint32_t te = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(s * kTcRows + cg);
     float* pw = Wb + (size_t)r0 * n + a;
-#pragma unroll
-    for (int c = 0; c < 32; c += 8) {
-      float v[8], vc[8];
-      tc::tmem_ld8x2(te + c, te + kTcRows + c, v, vc);
+    {
+      float v[32];
+      tc::tmem_ld32(te, v);
       if (a < n) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (r0 + c + j < rend) pw[(size_t)(c + j) * n] = v[j] + vc[j];
+        for (int j = 0; j < 32; ++j)
+          if (r0 + j < rend) pw[(size_t)j * n] = v[j];
       }
     }
     tc::fence_before();
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
     tc::mbar_wait(last & 1 ? mb1 : mb0, (last >> 1) & 1, tc::kWaitCycles);
   }
   __syncthreads();
-  if (w == 0) tc::tmem_free(tmem, 4 * kTcRows);
+  if (w == 0) tc::tmem_free(tmem, 2 * kTcRows);
 }
 
 // Synthesis, warp-specialised (one CTA of 128 rows per SM):
@@ -237,8 +239,8 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
   const int imgA = tc::img_floats(kTcM, kTcKc), imgB = tc::img_floats(NP, kTcKc);
   const int stage = 2 * (imgA + imgB);  // floats: A hi, A lo, B hi, B lo
   float* base = reinterpret_cast<float*>(smem_raw);
-  // TMEM buffer b (chunk parity): hi*hi sums at column 2 NP b, cross terms at 2 NP b + NP
-  const int ncols = 4 * NP <= 64 ? 64 : (4 * NP <= 128 ? 128 : 256);
+  // TMEM buffer b (chunk parity): the chunk's sums at column NP b
+  const int ncols = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : 128);
   auto full = [&](int i) { return tc::smem_u32(&bar[i]); };
   auto empty = [&](int i) { return tc::smem_u32(&bar[kSynStages + i]); };
   auto tfull = [&](int b) { return tc::smem_u32(&bar[2 * kSynStages + b]); };
@@ -341,20 +343,28 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
         break;
       }
       tc::fence_after();
-      const uint32_t ta = tmem + ((uint32_t)lrow << 16) + (uint32_t)(2 * NP * b + HC * h);
+      const uint32_t ta = tmem + ((uint32_t)lrow << 16) + (uint32_t)(NP * b + HC * h);
       if (HC == 32) {
-        float vm[32], vc[32];
-        tc::tmem_ld32x2(ta, ta + NP, vm, vc);
+        float v[32];
+        tc::tmem_ld32(ta, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] += vm[j] + vc[j];
+        for (int j = 0; j < 32; ++j) acc[j] += v[j];
+      } else if (HC == 16) {
+        float va[8], vb[8];
+        tc::tmem_ld8x2(ta, ta + 8, va, vb);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          acc[j] += va[j];
+          acc[8 + j] += vb[j];
+        }
       } else {
 #pragma unroll
         for (int g = 0; g < 3; ++g) {
           if (8 * g < HC) {
-            float vm[8], vc[8];
-            tc::tmem_ld8x2(ta + 8 * g, ta + NP + 8 * g, vm, vc);
+            float v[8];
+            tc::tmem_ld8(ta + 8 * g, v);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[8 * g + j] += vm[j] + vc[j];
+            for (int j = 0; j < 8; ++j) acc[8 * g + j] += v[j];
           }
         }
       }
@@ -384,15 +394,19 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
       tc::fence_after();
       const uint32_t aH = tc::smem_u32(base + (size_t)st * stage), aL = aH + imgA * 4, bH = aL + imgA * 4,
                      bL = bH + imgB * 4;
-      const uint32_t dm = tmem + (uint32_t)(2 * NP * b), dc = dm + (uint32_t)NP;
+      const uint32_t dm = tmem + (uint32_t)(NP * b);
       const uint64_t dAH = tc::smem_desc(aH, kTcKc), dAL = tc::smem_desc(aL, kTcKc);
       const uint64_t dBH = tc::smem_desc(bH, kTcKc), dBL = tc::smem_desc(bL, kTcKc);
 #pragma unroll
+      for (int k = 0; k < kTcKc / 8; ++k) {  // cross terms first, then hi*hi
+        const uint64_t o = kstep * k;
+        tc::mma_tf32(dm, dAH + o, dBL + o, idesc, k > 0);
+        tc::mma_tf32(dm, dAL + o, dBH + o, idesc, 1);
+      }
+#pragma unroll
       for (int k = 0; k < kTcKc / 8; ++k) {
         const uint64_t o = kstep * k;
-        tc::mma_tf32(dm, dAH + o, dBH + o, idesc, k > 0);
-        tc::mma_tf32(dc, dAH + o, dBL + o, idesc, k > 0);
-        tc::mma_tf32(dc, dAL + o, dBH + o, idesc, 1);
+        tc::mma_tf32(dm, dAH + o, dBH + o, idesc, 1);
       }
       tc::mma_commit(empty(st));
       tc::mma_commit(tfull(b));

@@ -9,9 +9,11 @@
 // three MMAs accumulating in FP32 give FP32-level sums.  The tensor cores'
 // FP32 accumulation loses up to about one unit in the last place of the
 // accumulator per MMA (measured: the error grows with the number of MMAs
-// accumulated), so the kernels keep the hi*hi products and the two small
-// cross products in separate TMEM accumulators, and long sums are moved to
-// registers chunk by chunk and added there with rounding to nearest.
+// accumulated), so the kernels issue all cross products (about 2^-11 of the
+// sum) first, while the accumulator is still small, and the hi*hi products
+// after them: the large sum then takes one truncation per K-step, as if the
+// cross terms were kept apart.  Long sums are moved to registers chunk by
+// chunk and added there with rounding to nearest.
 #pragma once
 
 #include <cstdint>
@@ -70,12 +72,14 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// The thread may be suspended in the wait (up to the hint, 0.1 ms) instead of
+// spinning, so waiting warps do not take issue slots from working ones.
 __device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(mbar), "r"(parity)
+      : "r"(mbar), "r"(parity), "r"(100000u)
       : "memory");
   return ok != 0;
 }
@@ -117,6 +121,33 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 #define S2DW_R8(b) "=r"(r[b]), "=r"(r[b + 1]), "=r"(r[b + 2]), "=r"(r[b + 3]), "=r"(r[b + 4]), "=r"(r[b + 5]), \
                    "=r"(r[b + 6]), "=r"(r[b + 7])
 
+// one load of 8 columns
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : S2DW_R8(0)
+      : "r"(ta)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// one load of 32 columns
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : S2DW_R8(0), S2DW_R8(8), S2DW_R8(16), S2DW_R8(24)
+      : "r"(ta)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 // two loads of 8 columns (at ta and tb)
 __device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float (&va)[8], float (&vb)[8]) {
   uint32_t r[16];
@@ -134,24 +165,6 @@ __device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float (&va)
   }
 }
 
-// two loads of 32 columns (at ta and tb)
-__device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float (&va)[32], float (&vb)[32]) {
-  uint32_t r[64];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : S2DW_R8(0), S2DW_R8(8), S2DW_R8(16), S2DW_R8(24), S2DW_R8(32), S2DW_R8(40), S2DW_R8(48), S2DW_R8(56)
-      : "r"(ta), "r"(tb)
-      : "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    va[j] = __uint_as_float(r[j]);
-    vb[j] = __uint_as_float(r[32 + j]);
-  }
-}
 #undef S2DW_R8
 
 __device__ __forceinline__ float to_tf32(float x) {
