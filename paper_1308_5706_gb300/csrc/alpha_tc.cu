@@ -33,14 +33,14 @@ constexpr int kTcM = 128;       // synthesis: rows per CTA (MMA M)
 constexpr int kTcKc = 32;       // synthesis: samples per K chunk
 constexpr int kSynStages = 3;   // synthesis: shared-memory ring stages
 
+// The shared-memory and TMEM budgets below hold for K8 <= 64 and NP <= 64.
+static_assert(kDirectMaxLjAna <= 32 && kDirectMaxLj <= 32, "tensor-core direct alpha sums sized for L_j <= 32");
+
 __host__ __device__ constexpr int ana_k8(int Lj) { return (2 * Lj + 7) & ~7; }
 __host__ __device__ constexpr int syn_npad(int Lj) { return 2 * Lj <= 16 ? 16 : (2 * Lj + 15) & ~15; }
 
 __device__ __forceinline__ void cp16(float* sdst, const float* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(sdst)), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_commit_wait() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
 // smem bytes of the analysis kernel for K8 = 64: basis image (hi, lo) and two
