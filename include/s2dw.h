@@ -232,9 +232,19 @@ const char* s2dw_strerror(int status);
  * their matrix products, about one second at most; one that gives up skips
  * the rest of its work and releases its tensor memory, so the output of that
  * call is invalid.  Synchronous (waits for the device); reads and resets the
- * count.  S2DW_EINVAL for NULL.
+ * count.  Returns S2DW_ETIMEOUT when the count is nonzero (the count is
+ * written either way), S2DW_EINVAL for NULL.
  */
 int s2dw_wait_timeouts(int* count);
+
+/*
+ * s2dw_wait_probe: the failure path of those waits, on demand.  Launches one
+ * warp on `stream` that waits on an mbarrier nothing arrives on, for at most
+ * limit_cycles SM cycles (clamped to [1e3, 2e9]), gives up and counts it like
+ * any bounded wait of the library: the next s2dw_wait_timeouts reports it.
+ * No fault, trap or hang is involved; the context stays usable.
+ */
+int s2dw_wait_probe(long long limit_cycles, void* stream);
 
 /*
  * Introspection used by the tests (synchronous, host outputs).

@@ -51,6 +51,7 @@ _SIGNATURES = {
     "s2dw_profile_read": (_c_i, [_c_p, _c_dp, _c_ip]),
     "s2dw_delta_table_noalloc": (_c_i, [_c_i, _c_p, _c_p, _c_i64p, _c_p]),
     "s2dw_wait_timeouts": (_c_i, [_c_ip]),
+    "s2dw_wait_probe": (_c_i, [ctypes.c_longlong, _c_p]),
 }
 
 STAGES = ["ana_contract", "ana_contract_phi", "ana_beta", "ana_alpha_czt", "ana_alpha_direct",
@@ -169,10 +170,20 @@ def s2dw_launch_counts(plan: int):
 
 def s2dw_wait_timeouts() -> int:
     """Bounded waits in the library's kernels that gave up since the last
-    call (0 in normal operation); synchronises the device."""
+    call (0 in normal operation); synchronises the device.  The status
+    S2DW_ETIMEOUT that accompanies a nonzero count is not raised: the count
+    is the result."""
     c = ctypes.c_int()
-    _check(lib().s2dw_wait_timeouts(ctypes.byref(c)), "s2dw_wait_timeouts")
+    st = lib().s2dw_wait_timeouts(ctypes.byref(c))
+    if st not in (0, -4):
+        _check(st, "s2dw_wait_timeouts")
     return c.value
+
+
+def s2dw_wait_probe(limit_cycles: int, stream=None) -> None:
+    """One warp waits, at most limit_cycles SM cycles, on an mbarrier nothing
+    arrives on and counts the give-up (the failure path of the bounded waits)."""
+    _check(lib().s2dw_wait_probe(int(limit_cycles), _stream(stream)), "s2dw_wait_probe")
 
 
 def s2dw_kernels(plan: int, J: int, L: int, N: int):

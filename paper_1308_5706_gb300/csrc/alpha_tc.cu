@@ -473,7 +473,23 @@ __global__ void k_tc_basis_syn(float* out, int n, int Lj, double scale) {
   }
 }
 
+// One warp waits, bounded, on an mbarrier that nothing arrives on: the
+// failure path of every bounded wait above (give up, count it), on demand.
+__global__ void k_wait_probe(long long limit) {
+  __shared__ __align__(8) uint64_t mbar;
+  const uint32_t mb = tc::smem_u32(&mbar);
+  if (threadIdx.x == 0) tc::mbar_init(mb, 1);
+  __syncwarp();
+  const bool ok = tc::mbar_wait(mb, 0, limit);
+  if (!__any_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicAdd(&g_tc_timeouts, 1);
+}
+
 }  // namespace
+
+cudaError_t alpha_tc_wait_probe(long long limit, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(limit);
+  return cudaGetLastError();
+}
 
 size_t alpha_tc_table_floats(int L, int Lj, bool syn) {
   if (Lj <= 0) return 0;

@@ -1328,7 +1328,14 @@ int s2dw_wait_timeouts(int* count) {
   if (!count) return S2DW_EINVAL;
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return err_of(e);
-  return err_of(alpha_tc_timeouts(count));
+  e = alpha_tc_timeouts(count);
+  if (e != cudaSuccess) return err_of(e);
+  return *count > 0 ? S2DW_ETIMEOUT : S2DW_OK;
+}
+
+int s2dw_wait_probe(long long limit_cycles, void* stream) {
+  const long long lim = std::min(std::max(limit_cycles, 1000LL), 2000000000LL);
+  return err_of(alpha_tc_wait_probe(lim, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {

@@ -115,6 +115,7 @@ void launch_alpha_tc(bool syn, const CztSeg<float>* segs, int nseg, int total_it
                      cudaStream_t st);
 cudaError_t alpha_tc_prepare();
 cudaError_t alpha_tc_timeouts(int* count);  // reads and resets the device count
+cudaError_t alpha_tc_wait_probe(long long limit, cudaStream_t st);  // a wait that runs out
 
 // Per-job parameters of the batched final synthesis reduction.
 struct ReduceJobs {
