@@ -442,56 +442,103 @@ __global__ void __launch_bounds__(256, 2) k_beta_ana_fft(const CztSeg<T>* __rest
   });
 }
 
+// Persistent (items it = blockIdx.x, + gridDim.x, ...): the strided column
+// rows of the next item (16 bytes per row b: the NT complex values of
+// columns m0..) are staged in shared memory by cp.async while the current
+// one is transformed, issued as soon as the current item's first FFT stage
+// has read its inputs.  Items whose rows are not 16-byte aligned (odd L_j,
+// a last single column) read them directly.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_beta_syn_fft(const CztSeg<T>* __restrict__ segs,
-                                                                              int nseg) {
+__device__ __forceinline__ bool beta_syn_staged(int Lj, int nt) {
+  constexpr int NT = beta_fft_nt(sizeof(T) == 8);
+  return NT * sizeof(cx<T>) == 16 && nt == NT && (sizeof(T) == 8 || Lj % 2 == 0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_beta_syn_fft(const CztSeg<T>* __restrict__ segs, int nseg, int total,
+                                                         int maxlogM) {
   constexpr int NT = beta_fft_nt(sizeof(T) == 8);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
-  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
-  const int item = blockIdx.x - sg.start;
-  const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM, ST = fft_smem_elems(M);
-  const int per_g = (Lj + NT - 1) / NT;
-  const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
-  const bool pair = (NT == 2) && (nt == 2) && (Lj % 2 == 0);
-  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * sg.nb * Lj + m0;  // columns m0.. of V_g[b][m]
-  const cx<T>* __restrict__ q = sg.post;
-  fft_forward_from_n<T, NT>(A, ST, logM, sg.tw, [&](int v, cx<T>* x) {
-    if (v >= sg.nb) {
-#pragma unroll
-      for (int t = 0; t < NT; ++t) x[t] = mkc<T>(0, 0);
-      return;
-    }
-    const T qv = __ldg(q + v).x;
-    if (pair) {
-      const float4 u = *reinterpret_cast<const float4*>(V + (size_t)v * Lj);
-      const cx<T>* uu = reinterpret_cast<const cx<T>*>(&u);
-#pragma unroll
-      for (int t = 0; t < NT; ++t) x[t] = cscale<T>(uu[t], qv);
-    } else {
-#pragma unroll
-      for (int t = 0; t < NT; ++t) x[t] = t < nt ? cscale<T>(V[(size_t)v * Lj + t], qv) : mkc<T>(0, 0);
-    }
-  });
-  const cx<T>* __restrict__ tb = sg.pre + (L - 1);
-  cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m0;  // columns m0.. of Vhat_g[m'][m]
-  for (int mp = threadIdx.x; mp < Lj; mp += blockDim.x) {
-    cx<T> o[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const T sigma = ((m0 + t + sg.N - 1) & 1) ? T(-1) : T(1);
-      o[t] = cmulc<T>(A[t * ST + fpad(fft_pos(mp, logM))], __ldg(tb + mp));
-      if (mp > 0) {
-        const cx<T> tm = cmulc<T>(A[t * ST + fpad(fft_pos(M - mp, logM))], __ldg(tb - mp));
-        o[t] = mkc<T>(o[t].x + sigma * tm.x, o[t].y + sigma * tm.y);
+  const int STmax = fft_smem_elems(1 << maxlogM);
+  cx<T>* stg = A + NT * STmax;  // [b][NT] rows of the next item
+  auto prefetch = [&](int it) {
+    if (it < total) {
+      const CztSeg<T> sp = segs[czt_find_seg<T>(segs, nseg, it)];
+      const int item = it - sp.start, per_g = (sp.Lj + NT - 1) / NT;
+      const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, sp.Lj - m0);
+      if (beta_syn_staged<T>(sp.Lj, nt)) {
+        const cx<T>* V = sp.buf_in + (size_t)g * sp.nb * sp.Lj + m0;
+        for (int v = threadIdx.x; v < sp.nb; v += blockDim.x) cp_async16(stg + v * NT, V + (size_t)v * sp.Lj, 16);
       }
     }
-    if (pair) {
-      *reinterpret_cast<float4*>(Vh + (size_t)mp * Lj) = *reinterpret_cast<const float4*>(o);
-    } else {
-      for (int t = 0; t < nt; ++t) Vh[(size_t)mp * Lj + t] = o[t];
+    cp_async_commit();
+  };
+  prefetch(blockIdx.x);
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg, it)];
+    const int item = it - sg.start;
+    const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM, ST = fft_smem_elems(M);
+    const int per_g = (Lj + NT - 1) / NT;
+    const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
+    const bool staged = beta_syn_staged<T>(Lj, nt);
+    const bool pair = (NT == 2) && (nt == 2) && (Lj % 2 == 0);
+    const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * sg.nb * Lj + m0;  // columns m0.. of V_g[b][m]
+    const cx<T>* __restrict__ q = sg.post;
+    cp_async_wait<0>();
+    __syncthreads();  // staged rows visible; A free
+    fft_forward_from_n<T, NT>(
+        A, ST, logM, sg.tw,
+        [&](int v, cx<T>* x) {
+          if (v >= sg.nb) {
+#pragma unroll
+            for (int t = 0; t < NT; ++t) x[t] = mkc<T>(0, 0);
+            return;
+          }
+          const T qv = __ldg(q + v).x;
+          if (staged) {
+#pragma unroll
+            for (int t = 0; t < NT; ++t) x[t] = cscale<T>(stg[v * NT + t], qv);
+          } else if (pair) {
+            const float4 u = *reinterpret_cast<const float4*>(V + (size_t)v * Lj);
+            const cx<T>* uu = reinterpret_cast<const cx<T>*>(&u);
+#pragma unroll
+            for (int t = 0; t < NT; ++t) x[t] = cscale<T>(uu[t], qv);
+          } else {
+#pragma unroll
+            for (int t = 0; t < NT; ++t) x[t] = t < nt ? cscale<T>(V[(size_t)v * Lj + t], qv) : mkc<T>(0, 0);
+          }
+        },
+        [&]() { prefetch(it + gridDim.x); });  // stg has been read by every thread
+    const cx<T>* __restrict__ tb = sg.pre + (L - 1);
+    cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m0;  // columns m0.. of Vhat_g[m'][m]
+    for (int mp = threadIdx.x; mp < Lj; mp += blockDim.x) {
+      cx<T> o[NT];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const T sigma = ((m0 + t + sg.N - 1) & 1) ? T(-1) : T(1);
+        o[t] = cmulc<T>(A[t * ST + fpad(fft_pos(mp, logM))], __ldg(tb + mp));
+        if (mp > 0) {
+          const cx<T> tm = cmulc<T>(A[t * ST + fpad(fft_pos(M - mp, logM))], __ldg(tb - mp));
+          o[t] = mkc<T>(o[t].x + sigma * tm.x, o[t].y + sigma * tm.y);
+        }
+      }
+      if (pair) {
+        *reinterpret_cast<float4*>(Vh + (size_t)mp * Lj) = *reinterpret_cast<const float4*>(o);
+      } else {
+        for (int t = 0; t < nt; ++t) Vh[(size_t)mp * Lj + t] = o[t];
+      }
     }
   }
+  cp_async_wait<0>();
+}
+
+// shared memory of k_beta_syn_fft: NT transforms of the largest length and
+// the staged rows (2L = M/2 rows of 16 bytes)
+template <typename T>
+size_t beta_syn_fft_smem(int maxlogM) {
+  return (size_t)beta_fft_nt(sizeof(T) == 8) * fft_smem_elems(1 << maxlogM) * sizeof(cx<T>) +
+         ((size_t)1 << (maxlogM - 1)) * 16;
 }
 
 // ---------------------------------------------------------------------------
@@ -824,9 +871,12 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
     case CZT_BETA_ANA_FFT:
       k_beta_ana_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
       break;
-    case CZT_BETA_SYN_FFT:
-      k_beta_syn_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
+    case CZT_BETA_SYN_FFT: {  // persistent
+      const size_t sm = beta_syn_fft_smem<T>(maxlogM);
+      const int g = std::min(total_items, alpha_czt_grid<T>(k_beta_syn_fft<T>, sm));
+      k_beta_syn_fft<T><<<g, block, sm, st>>>(segs, nseg, total_items, maxlogM);
       break;
+    }
     case CZT_ALPHA_SYN_DIRECT:
       if constexpr (sizeof(T) == sizeof(float))
         launch_alpha_tc(true, segs, nseg, total_items, ptrs, st);  // tensor cores
@@ -856,7 +906,7 @@ cudaError_t czt_set_smem(int maxlogM) {
                            smem * beta_fft_nt(sizeof(T) == 8));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem * beta_fft_nt(sizeof(T) == 8));
+                           (int)beta_syn_fft_smem<T>(maxlogM));
   if (e != cudaSuccess) return e;
   for (auto k : {k_czt_alpha_ana_seg<T, false>, k_czt_alpha_ana_seg<T, true>, k_czt_alpha_syn_seg<T, false>,
                  k_czt_alpha_syn_seg<T, true>}) {

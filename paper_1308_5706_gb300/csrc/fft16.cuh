@@ -542,10 +542,11 @@ __device__ __forceinline__ void fft_inner_dispatch_n(cx<T>* A, int M, int Rl, in
 }
 
 // fft_forward_from on NT transforms: input(v, x) fills x[t], t < NT, with
-// element v of transform t.  Ends with __syncthreads().
-template <typename T, int NT, typename In>
+// element v of transform t.  after_input() runs once every input has been
+// read (after the first stage's barrier).  Ends with __syncthreads().
+template <typename T, int NT, typename In, typename AfterInput>
 __device__ __forceinline__ void fft_forward_from_n(cx<T>* A, int ST, int logM, const cx<T>* __restrict__ tw,
-                                                   In input) {
+                                                   In input, AfterInput after_input) {
   const int M = 1 << logM;
   int Rl, nmid;
   fft_schedule(logM, Rl, nmid);
@@ -571,6 +572,7 @@ __device__ __forceinline__ void fft_forward_from_n(cx<T>* A, int ST, int logM, c
     }
   }
   __syncthreads();
+  after_input();
   int S = M / 16;
   for (int s = 0; s < nmid; ++s) {
     fft_fwd_stage<T, 16, NT>(A, M, S, tw + fft_twiddle_level_offset(logM, s + 1), ST);
