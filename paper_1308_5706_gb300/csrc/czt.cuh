@@ -404,42 +404,85 @@ __global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restric
 // ---------------------------------------------------------------------------
 // A CTA transforms NT adjacent columns m0.. of one gamma sample (FP32: two),
 // so the strided column reads and writes move NT complex values at a time.
+// Persistent (items it = blockIdx.x, + gridDim.x, ...): the next item's
+// input rows Y_g[m0 + t][.] (contiguous) are staged in shared memory by
+// cp.async while the current one is transformed, issued once the current
+// item's rows have been scattered into the FFT buffer.  Odd L_j in FP32
+// (rows not 16-byte aligned) reads them directly.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_beta_ana_fft(const CztSeg<T>* __restrict__ segs,
-                                                                              int nseg) {
+__device__ __forceinline__ bool beta_ana_staged(int Lj) {
+  return sizeof(T) == 8 || Lj % 2 == 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_beta_ana_fft(const CztSeg<T>* __restrict__ segs, int nseg, int total,
+                                                         int maxlogM) {
   constexpr int NT = beta_fft_nt(sizeof(T) == 8);
+  constexpr int EPC = 16 / (int)sizeof(cx<T>);  // complex values per 16-byte copy
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
-  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
-  const int item = blockIdx.x - sg.start;
-  const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM, ST = fft_smem_elems(M);
-  const int per_g = (Lj + NT - 1) / NT;
-  const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
-  for (int i = threadIdx.x; i < NT * ST; i += blockDim.x) A[i] = mkc<T>(0, 0);
-  __syncthreads();
-  const cx<T>* __restrict__ tb = sg.pre + (L - 1);
-  for (int t = 0; t < nt; ++t) {
-    const int m = m0 + t;
-    const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
-    const cx<T>* __restrict__ Y = sg.buf_in + ((size_t)g * Lj + m) * Lj;  // Y_g[m][.], m' fastest
-    for (int mp = threadIdx.x - (Lj - 1); mp < Lj; mp += blockDim.x) {
-      cx<T> y = Y[mp < 0 ? -mp : mp];
-      if (mp < 0) y = cscale<T>(y, sigma);
-      A[t * ST + fpad(fft_pos(mp & (M - 1), logM))] = cmul<T>(y, __ldg(tb + mp));
-    }
-  }
-  __syncthreads();
-  cx<T>* __restrict__ X = sg.buf_out + (size_t)g * sg.nb * Lj + m0;
-  const bool pair = (NT == 2) && (nt == 2) && (Lj % 2 == 0);  // 16-byte aligned column pairs
-  fft_inverse_to_n<T, NT>(A, ST, logM, sg.tw, [&](int v, const cx<T>* y) {
-    if (v < sg.nb) {
-      if (pair) {
-        *reinterpret_cast<float4*>(X + (size_t)v * Lj) = *reinterpret_cast<const float4*>(y);
-      } else {
-        for (int t = 0; t < nt; ++t) X[(size_t)v * Lj + t] = y[t];
+  const int STmax = fft_smem_elems(1 << maxlogM);
+  cx<T>* stg = A + NT * STmax;  // [t][m'] rows of the next item, L_j <= M/4
+  auto prefetch = [&](int it) {
+    if (it < total) {
+      const CztSeg<T> sp = segs[czt_find_seg<T>(segs, nseg, it)];
+      const int item = it - sp.start, per_g = (sp.Lj + NT - 1) / NT;
+      const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, sp.Lj - m0);
+      if (beta_ana_staged<T>(sp.Lj)) {
+        const cx<T>* Y = sp.buf_in + ((size_t)g * sp.Lj + m0) * sp.Lj;  // nt consecutive rows
+        const int nchunk = nt * sp.Lj / EPC;
+        for (int i = threadIdx.x; i < nchunk; i += blockDim.x) cp_async16(stg + i * EPC, Y + i * EPC, 16);
       }
     }
-  });
+    cp_async_commit();
+  };
+  prefetch(blockIdx.x);
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg, it)];
+    const int item = it - sg.start;
+    const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM, ST = fft_smem_elems(M);
+    const int per_g = (Lj + NT - 1) / NT;
+    const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
+    const bool staged = beta_ana_staged<T>(Lj);
+    cp_async_wait<0>();
+    __syncthreads();  // staged rows visible; A free
+    for (int i = threadIdx.x; i < NT * ST; i += blockDim.x) A[i] = mkc<T>(0, 0);
+    __syncthreads();
+    const cx<T>* __restrict__ tb = sg.pre + (L - 1);
+    for (int t = 0; t < nt; ++t) {
+      const int m = m0 + t;
+      const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
+      const cx<T>* __restrict__ Y = sg.buf_in + ((size_t)g * Lj + m) * Lj;  // Y_g[m][.], m' fastest
+      for (int mp = threadIdx.x - (Lj - 1); mp < Lj; mp += blockDim.x) {
+        const int am = mp < 0 ? -mp : mp;
+        cx<T> y = staged ? stg[t * Lj + am] : Y[am];
+        if (mp < 0) y = cscale<T>(y, sigma);
+        A[t * ST + fpad(fft_pos(mp & (M - 1), logM))] = cmul<T>(y, __ldg(tb + mp));
+      }
+    }
+    __syncthreads();
+    prefetch(it + gridDim.x);  // stg has been read by every thread
+    cx<T>* __restrict__ X = sg.buf_out + (size_t)g * sg.nb * Lj + m0;
+    const bool pair = (NT == 2) && (nt == 2) && (Lj % 2 == 0);  // 16-byte aligned column pairs
+    fft_inverse_to_n<T, NT>(A, ST, logM, sg.tw, [&](int v, const cx<T>* y) {
+      if (v < sg.nb) {
+        if (pair) {
+          *reinterpret_cast<float4*>(X + (size_t)v * Lj) = *reinterpret_cast<const float4*>(y);
+        } else {
+          for (int t = 0; t < nt; ++t) X[(size_t)v * Lj + t] = y[t];
+        }
+      }
+    });
+  }
+  cp_async_wait<0>();
+}
+
+// shared memory of k_beta_ana_fft: NT transforms of the largest length and
+// the staged input rows (NT rows of at most L = M/4 values)
+template <typename T>
+size_t beta_ana_fft_smem(int maxlogM) {
+  constexpr int NT = beta_fft_nt(sizeof(T) == 8);
+  return (size_t)NT * (fft_smem_elems(1 << maxlogM) + ((size_t)1 << (maxlogM - 2))) * sizeof(cx<T>);
 }
 
 // Persistent (items it = blockIdx.x, + gridDim.x, ...): the strided column
@@ -860,17 +903,19 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
     case CZT_BETA_MW_DFT: k_beta_mw_dft<T><<<grid, block, smem, st>>>(segs, nseg); break;
     case CZT_BETA_RS: k_czt_beta_ana<T><<<grid, block, smem, st>>>(segs, nseg); break;
     case CZT_BETA_RS_FFT:
-      k_beta_ana_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
+    case CZT_BETA_ANA_FFT: {  // persistent
+      const size_t sm = beta_ana_fft_smem<T>(maxlogM);
+      const int g = std::min(total_items, alpha_czt_grid<T>(k_beta_ana_fft<T>, sm));
+      k_beta_ana_fft<T><<<g, block, sm, st>>>(segs, nseg, total_items, maxlogM);
       break;
+    }
     case CZT_ALPHA_ANA_DIRECT:
       if constexpr (sizeof(T) == sizeof(float))
         launch_alpha_tc(false, segs, nseg, total_items, ptrs, st);  // tensor cores
       else
         k_alpha_ana_direct<T><<<grid, block, alpha_ana_direct_smem<T>(), st>>>(segs, nseg, ptrs);
       break;
-    case CZT_BETA_ANA_FFT:
-      k_beta_ana_fft<T><<<grid, block, smem * beta_fft_nt(sizeof(T) == 8), st>>>(segs, nseg);
-      break;
+
     case CZT_BETA_SYN_FFT: {  // persistent
       const size_t sm = beta_syn_fft_smem<T>(maxlogM);
       const int g = std::min(total_items, alpha_czt_grid<T>(k_beta_syn_fft<T>, sm));
@@ -903,7 +948,7 @@ cudaError_t czt_set_smem(int maxlogM) {
                            (int)alpha_czt_smem<T>(maxlogM, true));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_beta_ana_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem * beta_fft_nt(sizeof(T) == 8));
+                           (int)beta_ana_fft_smem<T>(maxlogM));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)beta_syn_fft_smem<T>(maxlogM));
