@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -141,7 +142,9 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}.csv")
+        # the raw samples go to $S2DW_CLOCKS_DIR when set (to keep them), else a temporary folder
+        out_dir = os.environ.get("S2DW_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_bench_{index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
