@@ -130,3 +130,39 @@ def test_batch_cache_eviction():
             assert torch.equal(w[0], ref[i]), pair
     for p in plans:
         p.close()
+
+
+def test_batch_mixes_grids_and_plan_kinds():
+    """DH, MW (odd and even row counts N L) and multi-resolution plans in one
+    batched launch set: the same bits as each plan alone, exact round trips.
+    The odd-row alpha variants then serve the DH jobs too."""
+    import torch
+    specs = [((64, 3, 2.0, 0), {}), ((33, 5, 2.0, 0), {"mw": True}), ((32, 4, 2.0, 1), {"mw": True}),
+             ((64, 3, 2.0, 0), {"multires": True}), ((33, 1, 2.0, 1), {})]
+    for prec in ("mixed", "fp64"):
+        plans = [B.Plan(*s, prec, **kw) for s, kw in specs]
+        try:
+            cd, _ = plans[0].torch_dtypes()
+            fs = [torch.from_numpy(flm_gaussian(p.L, 60 + i, "cl")).to(cd).cuda() for i, p in enumerate(plans)]
+            Wb = [p.alloc_w() for p in plans]
+            Ws = [p.alloc_w() for p in plans]
+            B.s2dw_analysis_batch([p.handle for p in plans], fs, [w[0] for w in Wb], [w[1] for w in Wb])
+            for p, f, w in zip(plans, fs, Ws):
+                p.analysis(f, w[0], w[1])
+            torch.cuda.synchronize()
+            for wb, ws in zip(Wb, Ws):
+                assert torch.equal(wb[0], ws[0]) and torch.equal(wb[1], ws[1])
+            fb = [p.alloc_flm() for p in plans]
+            fsn = [p.alloc_flm() for p in plans]
+            B.s2dw_synthesis_batch([p.handle for p in plans], [w[0] for w in Wb], [w[1] for w in Wb], fb)
+            for p, w, f in zip(plans, Ws, fsn):
+                p.synthesis(w[0], w[1], f)
+            torch.cuda.synchronize()
+            for i, (a, b, f0) in enumerate(zip(fb, fsn, fs)):
+                assert torch.equal(a, b), i
+                eps = (a.to(torch.complex128) - f0.to(torch.complex128)).abs().max().item()
+                assert eps < (1e-12 if prec == "fp64" else 1e-5) * f0.abs().max().item(), (prec, i, eps)
+        finally:
+            for p in plans:
+                p.close()
+    assert B.s2dw_wait_timeouts() == 0
