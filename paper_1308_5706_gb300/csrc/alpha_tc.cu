@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int r = w + 8 * q;
-        x[q] = (r < nr && a < n) ? __ldg(Wb + (size_t)r * n + a) : 0.f;
+        x[q] = (r < nr && a < n) ? __ldcs(Wb + (size_t)r * n + a) : 0.f;  // read once: streaming
       }
     };
     auto fetch_basis = [&](int c) {  // basis chunk c into the B images of stage c % S

@@ -85,8 +85,7 @@ __device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  uint64_t state;
-  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(mbar) : "memory");
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
 }
 
 // Wait for the phase of the given parity to complete; false after `limit` SM cycles.
