@@ -602,15 +602,14 @@ constexpr int kDirectMax = kDirectMaxLj;
 // advanced by additions), then per pass of kAgRows rows stages A and
 // accumulates a register tile of 8 rows x 4 samples per thread, samples
 // lane + 32 i so that every store of a warp is one 128-byte line.  Layouts:
-// B[k][lane][i] (one 16-byte load per k), A[k][row] (FP32: each value
-// duplicated, so that 16-byte loads give the (A, A) operand pairs of the
-// packed f32x2 multiply-adds).
+// B[k][lane][i] (one 16-byte load per k), A[k][row].  FP64 plans only (FP32
+// plans run the tensor-core kernels of alpha_tc.cu).
 template <typename T>
 __global__ void __launch_bounds__(256) k_alpha_ana_direct(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+  static_assert(sizeof(T) == sizeof(double), "FP32 plans use the tensor-core kernels");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr bool PACK = sizeof(T) == 4;
   constexpr int KMAX = 2 * kDirectMaxLjAna - 1;
-  constexpr int AW = PACK ? 2 : 1;          // stored copies of each A value
+  constexpr int AW = 1;                     // stored copies of each A value
   T* Bs = reinterpret_cast<T*>(smem_raw);  // [KMAX][32][4]
   T* As = Bs + KMAX * kAgCols;              // [KMAX][kAgRows][AW]
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
@@ -664,34 +663,7 @@ __global__ void __launch_bounds__(256) k_alpha_ana_direct(const CztSeg<T>* __res
     }
     __syncthreads();
     T out[8][4];
-    if constexpr (PACK) {
-      f2p acc[8][2];
-#pragma unroll
-      for (int r = 0; r < 8; ++r) acc[r][0] = acc[r][1] = 0;
-      const float4* __restrict__ ap = reinterpret_cast<const float4*>(As) + 4 * w;  // rows 8w.. as (A, A) pairs
-      const float4* __restrict__ bp = reinterpret_cast<const float4*>(Bs) + lane;
-#pragma unroll 2
-      for (int k = 0; k < K; ++k) {
-        const float4 bq = bp[0];
-        const f2p b01 = pk2(bq.x, bq.y), b23 = pk2(bq.z, bq.w);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 aq = ap[q];
-          const f2p ar0 = pk2(aq.x, aq.y), ar1 = pk2(aq.z, aq.w);
-          acc[2 * q][0] = fma2(ar0, b01, acc[2 * q][0]);
-          acc[2 * q][1] = fma2(ar0, b23, acc[2 * q][1]);
-          acc[2 * q + 1][0] = fma2(ar1, b01, acc[2 * q + 1][0]);
-          acc[2 * q + 1][1] = fma2(ar1, b23, acc[2 * q + 1][1]);
-        }
-        ap += kAgRows / 2;
-        bp += kAgCols / 4;
-      }
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        upk2(acc[r][0], out[r][0], out[r][1]);
-        upk2(acc[r][1], out[r][2], out[r][3]);
-      }
-    } else {
+    {
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -735,21 +707,16 @@ __global__ void __launch_bounds__(256) k_alpha_ana_direct(const CztSeg<T>* __res
 // chunk w; its lanes are (sub, m) with P = 32 / Lj lanes per m splitting the
 // chunk further.  Partials are reduced over sub by shuffles when Lj divides
 // 32, then over the chunks in shared memory.
+// FP64 plans only (FP32 plans run the tensor-core kernels of alpha_tc.cu).
 template <typename T>
 __device__ __forceinline__ void syn_direct_line(const T* p, T (&x)[32 / sizeof(T)]) {
-  const float4 u = reinterpret_cast<const float4*>(p)[0];
-  const float4 v = reinterpret_cast<const float4*>(p)[1];
-  if constexpr (sizeof(T) == 4) {
-    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
-    x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
-  } else {
-    const double2 a = *reinterpret_cast<const double2*>(&u), b = *reinterpret_cast<const double2*>(&v);
-    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
-  }
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_alpha_syn_direct(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+  static_assert(sizeof(T) == sizeof(double), "FP32 plans use the tensor-core kernels");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int R = 32 / sizeof(T);
   constexpr int U = 4;  // samples per thread per load batch (R * U loads in flight)
@@ -773,14 +740,9 @@ __global__ void __launch_bounds__(256) k_alpha_syn_direct(const CztSeg<T>* __res
     for (int u = 0; u < U; ++u) {
       const int a = a0 + u * 256 + tid;
       if (a < n) {
-        float4* d = reinterpret_cast<float4*>(Ws + (size_t)a * R);
-        if constexpr (sizeof(T) == 4) {
-          d[0] = make_float4(x[u][0], x[u][1], x[u][2], x[u][3]);
-          d[1] = make_float4(x[u][4], x[u][5], x[u][6], x[u][7]);
-        } else {
-          reinterpret_cast<double2*>(d)[0] = make_double2(x[u][0], x[u][1]);
-          reinterpret_cast<double2*>(d)[1] = make_double2(x[u][2], x[u][3]);
-        }
+        double2* d = reinterpret_cast<double2*>(Ws + (size_t)a * R);
+        d[0] = make_double2(x[u][0], x[u][1]);
+        d[1] = make_double2(x[u][2], x[u][3]);
       }
     }
   }
