@@ -92,6 +92,19 @@ def _mw_reflection_unsigned(U, L, sigma, band=None):
     return _orig_mw_to_dh(U, L, np.ones_like(sigma), band)
 
 
+def _mw_pole_unweighted(U, L, sigma, band=None):
+    # the pole sample beta = pi counted as an ordinary sample (no (1 + sigma)/2 weight)
+    n = 2 * L - 1
+    band = L if band is None else band
+    bet = np.pi * (2 * np.arange(n) + 1) / n
+    U = np.array(U, dtype=np.complex128)
+    ext = np.concatenate([U, sigma * U[..., L - 2::-1, :]], axis=-2)
+    p = np.arange(-(band - 1), band)
+    c = np.einsum("...bm,pb->...pm", ext, np.exp(-1j * np.outer(p, bet))) / n
+    _, bdh, _ = OS.grids(L, 1)
+    return np.einsum("...pm,tp->...tm", c, np.exp(1j * np.outer(bdh, p)))
+
+
 def _mw_betas_2L(L):
     return np.pi * (2 * np.arange(L) + 1) / (2 * L)
 
@@ -113,6 +126,7 @@ PINS = [
     lambda: P.test_multires_round_trip_exact(16, 3, 2.0, 0),
     lambda: P.test_mw_single_mode_analysis_closed_form(3),
     lambda: P.test_mw_resampling_and_round_trip_exact(8, 3, 2.0, 0),
+    lambda: P.test_mw_pole_only_component(1, True),
 ]
 
 
@@ -129,6 +143,7 @@ PINS = [
     ("steering without z_n = 1/N", "steer", _steer_no_norm),
     ("MW reflection without its sign", "_mw_beta_to_dh", _mw_reflection_unsigned),
     ("MW beta grid of spacing pi/L", "mw_betas", _mw_betas_2L),
+    ("MW pole sample without the (1 + sigma)/2 weight", "_mw_beta_to_dh", _mw_pole_unweighted),
 ])
 def test_planted_mistake_is_caught(monkeypatch, name, attr, bad):
     monkeypatch.setattr(OS, attr, bad)

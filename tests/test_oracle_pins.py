@@ -472,3 +472,27 @@ def test_mw_resampling_and_round_trip_exact(L, N, lam, J0):
     assert np.abs(Wpr - Wpd).max() < 1e-13 * max(1.0, np.abs(Wpd).max())
     fr = O.synthesis_mw(Wm, Wpm, L, N, lam, J0, kern)
     assert np.abs(fr - f).max() < 1e-12 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("m,vanishes", [(1, True), (3, True), (2, False)])
+def test_mw_pole_only_component(m, vanishes):
+    """The pole sample beta = pi is its own reflection on the beta torus.
+    Take coefficients nonzero only there, and constant in gamma, so that for
+    the wavelets only the order n = 0 of S_N (N = 3) survives the gamma sum.
+    In a Fourier component with sigma = (-1)^{m-n} = -1 (odd m) they
+    describe no band-limited function, because such a component vanishes at
+    the pole.  Their synthesis (the projection onto band-limited signals)
+    is then exactly zero.  With sigma = +1 (even m) it is not."""
+    L, N, lam, J0 = 6, 3, 2.0, 1
+    kern = O.kernels(L, N, lam, J0)
+    alpha, _, _ = O.grids(L, N)
+    nj = kern[0].shape[0]
+    W = np.zeros((nj, N, L, 2 * L - 1))
+    W[:, :, L - 1, :] = np.cos(m * alpha)[None, None, :]
+    Wphi = np.zeros((L, 2 * L - 1))
+    Wphi[L - 1, :] = np.cos(m * alpha)
+    f = O.synthesis_mw(W, Wphi, L, N, lam, J0, kern)
+    if vanishes:
+        assert np.abs(f).max() < 1e-13
+    else:
+        assert np.abs(f).max() > 1e-3
