@@ -358,7 +358,7 @@ class Plan:
         ng = len(np.atleast_1d(gammas))
         if out is None:
             shape = ((self.w_shape[0] // self.N) * ng,) if self.multires else \
-                (self.J + 1, ng, 2 * self.L, 2 * self.L - 1)
+                (self.J + 1, ng, self.nb, 2 * self.L - 1)
             out = torch.empty(shape, dtype=W.dtype, device=W.device)
         s2dw_steer(self.handle, W, gammas, out, stream)
         return out
