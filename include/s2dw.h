@@ -69,10 +69,11 @@ typedef struct s2dw_plan_s* s2dw_plan_t;
  *   Scales: J_max = ceil(log_lambda L) (Sec. 2.2), J = J_max - J0, wavelet
  *   scales j = 0..J; the scaling function Phi covers the rest (Eq. (16)).
  *   Kernels: Psi^j_ln = kappa^j(l) s_ln (Eqs. (7), (11)-(15)).
- * Valid ranges: 2 <= L <= 2048, 1 <= N <= min(8, L), lambda > 1 (at most 64
- * scales), 0 <= J0 <= J_max; flags = exactly one of S2DW_FP64 / S2DW_MIXED,
- * optionally | S2DW_REAL_SIGNAL and | one of S2DW_MULTIRES / S2DW_MW.
- * Otherwise S2DW_EINVAL.
+ * Valid requests: L >= 2, 1 <= N <= L, lambda > 1 (finite), 0 <= J0 <= J_max;
+ * flags = exactly one of S2DW_FP64 / S2DW_MIXED, optionally | S2DW_REAL_SIGNAL
+ * and | one of S2DW_MULTIRES / S2DW_MW.  Otherwise S2DW_EINVAL.
+ * Limits of this build: L <= 2048, N <= 8 and at most 64 scales (J + 1);
+ * a valid request beyond them returns S2DW_ENOTSUP.
  * S2DW_MULTIRES samples each W^j on the DH SO(3) grid of its own band-limit
  * L_j = 1 + the largest l with kappa^j(l) > 0 (and W^Phi on the sphere grid
  * of L_Phi): W^j is band-limited there, so the samples are exact and the
@@ -189,7 +190,6 @@ int s2dw_analysis_batch(const s2dw_plan_t* plans, const void* const* flm, void* 
 int s2dw_synthesis_batch(const s2dw_plan_t* plans, const void* const* W, const void* const* Wphi,
                          void* const* flm, int njobs, void* stream);
 
-/* Static text for a status code. */
 /*
  * Spherical harmonic transforms of a real signal on the DH sphere grid of
  * Sec. 3.1 (theta_t = pi(2t+1)/(4L), t < 2L; phi_p = 2 pi p/(2L-1)), with
@@ -223,6 +223,7 @@ int s2dw_sht_forward(s2dw_plan_t plan, const void* fpix, void* flm, void* stream
  */
 int s2dw_steer(s2dw_plan_t plan, const void* W, const double* gammas, int ngamma, void* out, void* stream);
 
+/* Static text for a status code (never NULL, never freed by the caller). */
 const char* s2dw_strerror(int status);
 
 /*
@@ -299,7 +300,10 @@ int s2dw_profile_read(s2dw_plan_t plan, double* ms, int* ncalls);
  *   table64: device array of that many doubles (NULL: only report the size,
  *     no device work); table32: NULL or a device array of that many floats
  *     that receives the float32 copy.
- *   Layout (the plans use the same one): slab l starts at entry
+ *   Layout (the eighth-domain layout of the plans' FP64 table, without the
+ *   zero front pad and read-ahead pad that the plans' copies carry, so this
+ *   table is for the caller's own use and cannot stand in for a plan's):
+ *     slab l starts at entry
  *     32 C(C+1)(C+2)/3 + (l mod 4) * 8 c(c+1), C = floor(l/4), c = C+1; in it,
  *     Delta^l_{m'm} with m >= 4 floor(m'/4) sits at
  *     16 q c - 8 q (q-1) + 4 r (c-q) + m - 4q, q = floor(m'/4), r = m' mod 4;

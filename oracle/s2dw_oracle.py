@@ -34,10 +34,27 @@ __all__ = [
     "mw_betas", "analysis_mw", "resample_mw_to_dh", "synthesis_mw",
 ]
 
-# How each function is pinned to something other than itself (tests named in
-# tests/test_oracle_pins.py).  No function is "parity unpinned".
+# How each public function is pinned to something other than itself (tests
+# named in tests/test_oracle_pins.py; planted mistakes in
+# tests/test_oracle_mutations.py).  No function is "parity unpinned".
 PARITY = {
-    "j_max": "closed values from the definition in Sec. 2.2 (L=1024, lam=2 -> 10)",
+    "j_max": "closed values from the definition in Sec. 2.2 (L=1024, lam=2 -> 10; L=1000, lam=3 -> 7)",
+    "n_scales": "closed values J = J_max - J0 and the J0 > J_max error",
+    "n_orders": "closed order lists of Eq. (11) for N = 1, 4, 5",
+    "bump": "admissibility Eq. (6) and the k_lambda derivative pin (s^2 enters both)",
+    "s_lambda": "k_lambda derivative -s_lam^2/t/I(1/lam) by finite differences; support ends of kappa",
+    "kappa_lambda": "peak of unity at t = 1 (kappa^j(lam^-j L) = 1); admissibility Eq. (6)",
+    "kappa": "hand-typed supports of Sec. 2.2 (tests/golden/supports_*.txt): zero at and outside the ends",
+    "phi_l": "admissibility Eq. (6); band-limit of Phi derived by hand",
+    "s_dir": "explicit s_ln values and sum_n |s_ln|^2 = 1 (Eq. (8))",
+    "grids": "single-mode closed-form D at the grid samples (planted 2L-point alpha / 2pi gamma grids caught)",
+    "flm_to_grid": "index placement of a single mode; inverse of grid_to_flm",
+    "grid_to_flm": "inverse of flm_to_grid",
+    "analysis_rows": "the rows of analysis (same pins: closed-form D, realness, steerability)",
+    "synthesis_modes": "exact round trip at every (l, m) with the scaling term live; equals synthesis on arbitrary arrays",
+    "fourier_cube": "Eq. (26) applied to the cube reproduces the (pinned) analysis",
+    "support": "hand-typed values of the Sec. 2.2 formula at L=1024, lam=2 and L=100, lam=3",
+    "band_limits": "closed values derived by hand at L=1024, lam=2 and L=100, lam=3 (J0 = 0, 1)",
     "k_lambda": "limits k=1 below 1/lam, 0 above 1; derivative vs -s^2/t/I by finite differences",
     "kernels": "admissibility Eq. (6); sum_n |s_ln|^2 = 1 (Eq. (8)); support edges (Sec. 2.2)",
     "dh_weights": "sum q = 2; exact integration of sin(t)cos(kt), k < 2L (Eq. (17))",

@@ -254,10 +254,33 @@ def s2dw_profile_read(plan: int):
 
 def s2dw_delta_table_noalloc(Lmax: int, table64=None, table32=None, stream=None) -> int:
     """Number of table entries; with table64 given, builds the table into the
-    caller's device buffers (no allocation by the library)."""
+    caller's device buffers (no allocation by the library).
+
+    The buffers are checked here before the C call (the library cannot see
+    their sizes or types): table64 a contiguous float64 CUDA tensor of at
+    least that many entries on the current device, table32 None or the same
+    in float32.  ValueError otherwise."""
     n = ctypes.c_int64()
-    st = _stream(stream) if table64 is not None else 0
-    _check(lib().s2dw_delta_table_noalloc(Lmax, _ptr(table64), _ptr(table32), ctypes.byref(n), st),
+    if table64 is None:
+        _check(lib().s2dw_delta_table_noalloc(Lmax, None, None, ctypes.byref(n), None), "s2dw_delta_table_noalloc")
+        return n.value
+    _check(lib().s2dw_delta_table_noalloc(Lmax, None, None, ctypes.byref(n), None), "s2dw_delta_table_noalloc")
+    import torch
+    dev = torch.cuda.current_device()
+    for name, t, dt in (("table64", table64, torch.float64), ("table32", table32, torch.float32)):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() < n.value:
+            raise ValueError(f"{name} holds {t.numel()} entries, the table needs {n.value}")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+    _check(lib().s2dw_delta_table_noalloc(Lmax, _ptr(table64), _ptr(table32), ctypes.byref(n), _stream(stream)),
            "s2dw_delta_table_noalloc")
     return n.value
 

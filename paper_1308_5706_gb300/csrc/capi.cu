@@ -51,12 +51,16 @@ void seg_choice(int L, int Lj, int logM, int& logMs, int& P, int& S) {
   }
 }
 
+// J_max = ceil(log_lam L) by an integer loop (Sec. 2.2); -1 when it exceeds
+// kJmaxCap (lambda so close to 1 that the loop would not end in reasonable
+// time; such a plan would exceed the 64-scale limit anyway unless J0 were huge).
+constexpr int kJmaxCap = 1 << 20;
 int jmax_of(int L, double lam) {
   int J = 0;
   double p = 1.0;
   while (p < L) {
     p *= lam;
-    ++J;
+    if (++J > kJmaxCap) return -1;
   }
   return J;
 }
@@ -994,7 +998,7 @@ int plan_create(s2dw_plan_t* out, int L, int N, double lam, int J0, unsigned fla
   const int Jm = jmax_of(L, lam);
   if (J0 < 0 || J0 > Jm) return S2DW_EINVAL;
   const int J = Jm - J0;
-  if (J + 1 > 64) return S2DW_EINVAL;
+  if (J + 1 > 64) return S2DW_ENOTSUP;
   s2dw_plan_s* p = new s2dw_plan_s();
   p->L = L;
   p->N = N;
@@ -1172,9 +1176,13 @@ int s2dw_plan(s2dw_plan_t* out, int L, int N, double lambda, int J0, unsigned fl
   if (prec != S2DW_FP64 && prec != S2DW_MIXED) return S2DW_EINVAL;
   if (flags & ~(unsigned)(S2DW_FP64 | S2DW_MIXED | S2DW_REAL_SIGNAL | S2DW_MULTIRES | S2DW_MW)) return S2DW_EINVAL;
   if ((flags & S2DW_MW) && (flags & S2DW_MULTIRES)) return S2DW_EINVAL;
-  if (L < 2 || L > 2048) return S2DW_EINVAL;
-  if (N < 1 || N > 8 || N > L) return S2DW_EINVAL;
+  // invalid requests (no transform exists) before limits of this build
+  if (L < 2 || N < 1 || N > L) return S2DW_EINVAL;
   if (!(lambda > 1.0) || !std::isfinite(lambda)) return S2DW_EINVAL;
+  const int jm = jmax_of(L, lambda);
+  if (jm < 0) return S2DW_ENOTSUP;  // over a million scales
+  if (J0 < 0 || J0 > jm) return S2DW_EINVAL;
+  if (L > 2048 || N > 8) return S2DW_ENOTSUP;
   try {
     return plan_create(out, L, N, lambda, J0, flags);
   } catch (...) {

@@ -38,9 +38,16 @@ def test_strerror_and_argument_validation_without_gpu():
     assert B.s2dw_strerror(B.S2DW_OK) == "ok"
     assert B.s2dw_strerror(B.S2DW_EINVAL) == "invalid argument"
     # argument checks happen before any CUDA call
-    for args in ((1, 1, 2.0, 0, B.S2DW_FP64), (32, 0, 2.0, 0, B.S2DW_FP64), (32, 9, 2.0, 0, B.S2DW_FP64),
+    # invalid requests: no transform exists for them
+    for args in ((1, 1, 2.0, 0, B.S2DW_FP64), (32, 0, 2.0, 0, B.S2DW_FP64), (4, 5, 2.0, 0, B.S2DW_FP64),
                  (32, 3, 1.0, 0, B.S2DW_FP64), (32, 3, 2.0, 0, 0), (32, 3, 2.0, 0, B.S2DW_FP64 | B.S2DW_MIXED),
-                 (4096, 3, 2.0, 0, B.S2DW_MIXED), (32, 3, float("nan"), 0, B.S2DW_FP64)):
+                 (32, 3, float("nan"), 0, B.S2DW_FP64), (32, 3, 2.0, 6, B.S2DW_FP64),
+                 (32, 3, 2.0, -1, B.S2DW_FP64)):
         with pytest.raises(B.S2dwError) as ei:
             B.s2dw_plan(*args)
-        assert ei.value.status == B.S2DW_EINVAL
+        assert ei.value.status == B.S2DW_EINVAL, args
+    # valid requests beyond this build's limits (L <= 2048, N <= 8)
+    for args in ((4096, 3, 2.0, 0, B.S2DW_MIXED), (32, 9, 2.0, 0, B.S2DW_FP64)):
+        with pytest.raises(B.S2dwError) as ei:
+            B.s2dw_plan(*args)
+        assert ei.value.status == B.S2DW_ENOTSUP, args

@@ -105,6 +105,26 @@ def _mw_pole_unweighted(U, L, sigma, band=None):
     return np.einsum("...pm,tp->...tm", c, np.exp(1j * np.outer(bdh, p)))
 
 
+_orig_modes = OS.synthesis_modes
+
+
+def _modes_no_phi(W, Wphi, L, N, lam, J0, lm_list, kern=None):
+    # the scaling term of Eq. (41) dropped
+    return _orig_modes(W, np.zeros_like(Wphi), L, N, lam, J0, lm_list, kern)
+
+
+def _modes_q_shifted(W, Wphi, L, N, lam, J0, lm_list, kern=None):
+    # each beta row paired with the quadrature weight of its neighbour
+    return _orig_modes(np.roll(W, 1, axis=2), np.roll(Wphi, 1, axis=0), L, N, lam, J0, lm_list, kern)
+
+
+def _modes_wrong_2l1(W, Wphi, L, N, lam, J0, lm_list, kern=None):
+    # the wavelet part scaled by (2l+1)/(4 pi) instead of (2l+1)/(8 pi^2)
+    out = _orig_modes(W, np.zeros_like(Wphi), L, N, lam, J0, lm_list, kern)
+    ph = _orig_modes(np.zeros_like(W), Wphi, L, N, lam, J0, lm_list, kern)
+    return {k: v * 2 * np.pi + ph[k] for k, v in out.items()}
+
+
 def _mw_betas_2L(L):
     return np.pi * (2 * np.arange(L) + 1) / (2 * L)
 
@@ -127,6 +147,7 @@ PINS = [
     lambda: P.test_mw_single_mode_analysis_closed_form(3),
     lambda: P.test_mw_resampling_and_round_trip_exact(8, 3, 2.0, 0),
     lambda: P.test_mw_pole_only_component(1, True),
+    lambda: P.test_synthesis_modes_round_trip_exact(8, 3, 2.0, 1),
 ]
 
 
@@ -144,6 +165,9 @@ PINS = [
     ("MW reflection without its sign", "_mw_beta_to_dh", _mw_reflection_unsigned),
     ("MW beta grid of spacing pi/L", "mw_betas", _mw_betas_2L),
     ("MW pole sample without the (1 + sigma)/2 weight", "_mw_beta_to_dh", _mw_pole_unweighted),
+    ("per-mode synthesis without the scaling term", "synthesis_modes", _modes_no_phi),
+    ("per-mode synthesis with q_b of the next row", "synthesis_modes", _modes_q_shifted),
+    ("per-mode synthesis with (2l+1)/(4 pi) on the wavelet part", "synthesis_modes", _modes_wrong_2l1),
 ])
 def test_planted_mistake_is_caught(monkeypatch, name, attr, bad):
     monkeypatch.setattr(OS, attr, bad)

@@ -50,25 +50,63 @@ def test_jmax_values():
     assert O.j_max(2, 2.0) == 1
 
 
-def test_support_golden_and_kernel_zeros():
-    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "supports_L1024_lam2.txt"))
-            if not ln.startswith("#")]
-    assert rows[0] == ["Jmax", "10"]
-    L, lam = 1024, 2.0
+@pytest.mark.parametrize("fname", ["supports_L1024_lam2.txt", "supports_L100_lam3.txt"])
+def test_support_golden_and_kernel_zeros(fname):
+    """Supports typed by hand from the Sec. 2.2 formulas (fixture headers show
+    the arithmetic); kappa^j must vanish at the ends and peak at lam^-j L."""
+    lines = open(os.path.join(GOLDEN, fname)).read().splitlines()
+    L, lam = [(int(a.split("=")[1]), float(b.split("=")[1]))
+              for a, b in (ln[2:].split() for ln in lines if ln.startswith("# L="))][0]
+    rows = [ln.split() for ln in lines if ln and not ln.startswith("#")]
+    assert rows[0][0] == "Jmax"
+    assert O.j_max(L, lam) == int(rows[0][1])
+    assert len(rows) - 1 == O.j_max(L, lam) + 1
     for j, lo, hi in ((int(a), int(b), int(c)) for a, b, c in rows[1:]):
         assert O.support(j, L, lam) == (lo, hi)
         # kappa^j vanishes at and outside the support ends, is positive inside
         for l in (lo, min(hi, L - 1) if hi < L else None):
             if l is not None and l < L:
                 assert O.kappa(j, l, L, lam) == 0.0
-        mid = int(round(lam ** (-j) * L))
-        if 0 < mid < L:
-            assert abs(O.kappa(j, mid, L, lam) - 1.0) < 1e-14     # peak of unity at lam^-j L
+        if lo > 0:
+            assert O.kappa(j, lo - 1, L, lam) == 0.0
+        mid = lam ** (-j) * L
+        if 0 < mid < L and float(mid).is_integer():
+            assert abs(O.kappa(j, int(mid), L, lam) - 1.0) < 1e-14     # peak of unity at lam^-j L
         # strictly inside the support kappa^j > 0 (checked a tenth of the way in;
         # right at the ends exp(-1/(1-x^2)) underflows in float64)
         inner = lo + max(1, (min(hi, L - 1) - lo) // 10)
         if inner < min(hi, L):
             assert O.kappa(j, inner, L, lam) > 0.0
+
+
+def test_scale_counts_orders_and_band_limits():
+    """Closed values derived by hand from Sec. 2.2: J = J_max - J0; the orders
+    n with beta_(N,n) = 1, |n| < N (Eq. (11)); the band-limit of scale j is the
+    upper support end ceil(lam^(1-j) L) clipped at L (kappa^j vanishes there and
+    is positive just below), that of Phi the largest l with lam^J l / L < 1,
+    plus one."""
+    assert O.n_scales(1024, 2.0, 0) == 10 and O.n_scales(1024, 2.0, 3) == 7
+    with pytest.raises(ValueError):
+        O.n_scales(1024, 2.0, 11)
+    assert list(O.n_orders(5)) == [-4, -2, 0, 2, 4]
+    assert list(O.n_orders(4)) == [-3, -1, 1, 3]
+    assert list(O.n_orders(1)) == [0]
+    assert O.band_limits(1024, 5, 2.0, 0) == ([1024, 1024, 512, 256, 128, 64, 32, 16, 8, 4, 2], 1)
+    # L = 100, lam = 3: hi = 300, 100, 34, 12, 4, 2 (supports_L100_lam3.txt);
+    # Phi: 3^5 l / 100 < 1 -> l = 0 (J0 = 0); 3^4 l / 100 < 1 -> l <= 1 (J0 = 1)
+    assert O.band_limits(100, 3, 3.0, 0) == ([100, 100, 34, 12, 4, 2], 1)
+    assert O.band_limits(100, 3, 3.0, 1) == ([100, 100, 34, 12, 4], 2)
+
+
+def test_flm_grid_layout():
+    """f_lm sits at flat index l*l + l + m and at grid cell [l, m + L - 1]."""
+    L = 5
+    f = np.zeros(L * L, complex)
+    f[3 * 3 + 3 - 2] = 1.0 + 2.0j                  # (l, m) = (3, -2)
+    F = O.flm_to_grid(f, L)
+    assert F[3, -2 + L - 1] == 1.0 + 2.0j and np.count_nonzero(F) == 1
+    g = flm_gaussian(L, 1)
+    assert np.array_equal(O.grid_to_flm(O.flm_to_grid(g, L), L), g)
 
 
 def test_k_lambda_limits_and_derivative():
@@ -338,6 +376,38 @@ def test_round_trip_exact(L, N, lam, J0, kind):
     assert np.abs(fr - f).max() < 1e-12
 
 
+@pytest.mark.parametrize("L,N,lam,J0", [(8, 3, 2.0, 1), (12, 1, 2.0, 2), (12, 4, 3.0, 1), (10, 2, 2.0, 0)])
+def test_synthesis_modes_round_trip_exact(L, N, lam, J0):
+    """synthesis_modes (the per-(l, m) form of Eqs. (32)-(33), (41)) must
+    return every f_lm exactly, negative m included, from the analysis of a
+    real signal, with J0 > 0 so that the scaling term of Eq. (41) carries
+    signal (Sec. 3.4 exactness, eps to 1e-12)."""
+    f = flm_gaussian(L, 5)
+    W, Wphi = O.analysis(f, L, N, lam, J0)
+    if J0 > 0:
+        assert np.abs(Wphi).max() > 1e-3          # the Phi term is live
+    lm = [(l, m) for l in range(L) for m in range(-l, l + 1)]
+    got = O.synthesis_modes(W, Wphi, L, N, lam, J0, lm)
+    err = max(abs(got[(l, m)] - f[l * l + l + m]) for (l, m) in lm)
+    assert err < 1e-12, err
+
+
+@pytest.mark.parametrize("L,N,lam,J0", [(8, 3, 2.0, 1), (9, 2, 2.0, 1)])
+def test_synthesis_modes_equals_synthesis_on_arbitrary_arrays(L, N, lam, J0):
+    """On arrays that are not the analysis of any signal (so nothing cancels),
+    synthesis_modes must equal the full synthesis at every (l, m)."""
+    rng = np.random.default_rng(7)
+    J1 = O.n_scales(L, lam, J0) + 1
+    W = rng.standard_normal((J1, N, 2 * L, 2 * L - 1))
+    Wphi = rng.standard_normal((2 * L, 2 * L - 1))
+    full = O.synthesis(W, Wphi, L, N, lam, J0)
+    lm = [(l, m) for l in range(L) for m in range(-l, l + 1)]
+    got = O.synthesis_modes(W, Wphi, L, N, lam, J0, lm)
+    scale = np.abs(full).max()
+    err = max(abs(got[(l, m)] - full[l * l + l + m]) for (l, m) in lm)
+    assert err < 1e-12 * max(1.0, scale), err
+
+
 def test_fourier_cube_reproduces_analysis():
     """Eq. (26): W = sum_{m m' n} U_{m m' n} e^{i(m alpha + m' beta + n gamma)}."""
     L, N, lam, J0 = 8, 3, 2.0, 0
@@ -496,3 +566,10 @@ def test_mw_pole_only_component(m, vanishes):
         assert np.abs(f).max() < 1e-13
     else:
         assert np.abs(f).max() > 1e-3
+
+
+def test_parity_table_names_every_public_function():
+    """Every public oracle function states how it is pinned."""
+    import oracle.s2dw_oracle as OS
+    missing = [n for n in OS.__all__ if n != "PARITY" and n not in OS.PARITY]
+    assert not missing, missing
