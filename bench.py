@@ -592,8 +592,15 @@ def main():
                     choices=["roundtrip", "batch", "serve", "steer", "multires", "sht", "mw"])
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--L", type=int, default=1024,
+                    help="band-limit of the roundtrip workload; values other than 1024 are for profiling "
+                         "captures at a smaller size and give no bench line of the metric")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    global L, WORKLOAD
+    if args.L != L:
+        L = args.L
+        WORKLOAD = WORKLOAD.replace("L=1024", f"L={L}") + " (profiling size, not the metric's workload)"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

@@ -230,9 +230,10 @@ const char* s2dw_strerror(int status);
  * s2dw_wait_timeouts: number of bounded waits in the library's kernels that
  * gave up since the last call (0 in normal operation).  The tensor-core
  * kernels of the small-band alpha sums (FP32 plans) wait on an mbarrier for
- * their matrix products, about one second at most; one that gives up skips
- * the rest of its work and releases its tensor memory, so the output of that
- * call is invalid.  Synchronous (waits for the device); reads and resets the
+ * their matrix products, and the FP32 contraction for the bulk copies of its
+ * operands, about one second at most; one that gives up skips the rest of
+ * its work (and releases its tensor memory, or waits for its copies in
+ * flight), so the output of that call is invalid.  Synchronous (waits for the device); reads and resets the
  * count.  Returns S2DW_ETIMEOUT when the count is nonzero (the count is
  * written either way), S2DW_EINVAL for NULL.
  */

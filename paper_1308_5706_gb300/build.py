@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libs2dw.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
-SOURCES = ["contract_f32.cu", "contract_f64.cu", "czt_f32.cu", "czt_f64.cu", "plan_kernels.cu", "capi.cu",
+SOURCES = ["contract_f32.cu", "contract_f64.cu", "contract_pair.cu", "czt_f32.cu", "czt_f64.cu", "plan_kernels.cu", "capi.cu",
            "noalloc.cu", "steer.cu", "alpha_tc.cu"]
 
 

@@ -132,6 +132,7 @@ struct DeltaTab {
   size_t bytes;
   double* raw64 = nullptr;  // the allocations
   float* raw32 = nullptr;
+  float* pair32 = nullptr;  // pair table of the FP32 tile-pair contraction (built for the first FP32 plan)
 };
 std::mutex g_mu;
 std::vector<DeltaTab*> g_tabs;
@@ -197,6 +198,22 @@ DeltaTab* delta_acquire(int L, cudaStream_t st) {
   return t;
 }
 
+// The FP32 pair table of a shared table (built from its FP64 slabs on first need).
+void delta_pair_ensure(DeltaTab* t, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (t->pair32) return;
+  float* pt = nullptr;
+  amalloc(&pt, (size_t)pair_table_entries(t->Lmax) * sizeof(float), st);
+  cudaError_t e = launch_pair_table(pt, t->d64, t->Lmax, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    afree(pt, st);
+    throw CudaFail{e};
+  }
+  t->pair32 = pt;
+  t->bytes += (size_t)pair_table_entries(t->Lmax) * sizeof(float);
+}
+
 void delta_release(DeltaTab* t) {
   if (!t) return;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -204,6 +221,7 @@ void delta_release(DeltaTab* t) {
     cudaStream_t st = setup_stream();
     afree(t->raw64, st);
     afree(t->raw32, st);
+    afree(t->pair32, st);
     g_tabs.erase(std::remove(g_tabs.begin(), g_tabs.end(), t), g_tabs.end());
     delete t;
   }
@@ -225,6 +243,7 @@ struct Lists {
   int maxlogM = 0;
   int Lmax = 0;
   int odd = 0;  // CZT_ODD_ROWS when a plan of the list samples the MW grid
+  int njobs = 0, nbmax = 0, Lrmax = 0;  // f packing of the FP32 contraction (jobs, 32-blocks, rows)
   ~Lists() {
     if (mem) {
       try {
@@ -293,9 +312,15 @@ struct s2dw_plan_s {
   std::vector<SegTables> seg;  // [nscale + 1]
   // [nscale + 1]: tensor-core basis images of the direct alpha sums (FP32 plans)
   std::vector<void*> tc_ana, tc_syn;
+  // FP32 plans: R rows and packed f of the tile-pair contraction
+  void* RSp = nullptr;
+  void* RSphi_p = nullptr;
+  void* fP = nullptr;
+  int Lr = 0, Lrphi = 0, Lrf = 0;
   // host copies of the static descriptors (device copies live in `own`)
   std::vector<unsigned char> desc_w_host, desc_phi_host;
-  std::vector<TileTask> tiles_w_host, tiles_phi_host;
+  std::vector<TileTask> tiles_w_host, tiles_phi_host;  // FP64 plans
+  std::vector<PairTask> ptasks_w_host, ptasks_phi_host;  // FP32 plans
   Lists own;
   // stage timing (s2dw_profile): one set of events per call, up to kProfCalls
   static constexpr int kProfCalls = 256;
@@ -377,6 +402,11 @@ void fill_desc(s2dw_plan_s* p, ContractDesc<T>& dw, ContractDesc<T>& dp, const T
   std::memset(&dw, 0, sizeof(dw));
   std::memset(&dp, 0, sizeof(dp));
   dw.delta = delta;
+  dw.dpair = p->tab->pair32;
+  dw.RSp = reinterpret_cast<const float*>(p->RSp);
+  dw.fP = reinterpret_cast<const cx<T>*>(p->fP);
+  dw.Lr = p->Lr;
+  dw.Lrf = p->Lrf;
   dw.RS = reinterpret_cast<const T*>(p->RS);
   dw.P = reinterpret_cast<cx<T>*>(p->P);
   dw.L = p->L;
@@ -415,6 +445,11 @@ void fill_desc(s2dw_plan_s* p, ContractDesc<T>& dw, ContractDesc<T>& dp, const T
   dw.nseg = ns;
   // scaling part: one N = 1 "scale" with kernel Phi on [0, lphi]
   dp.delta = delta;
+  dp.dpair = p->tab->pair32;
+  dp.RSp = reinterpret_cast<const float*>(p->RSphi_p);
+  dp.fP = reinterpret_cast<const cx<T>*>(p->fP);
+  dp.Lr = p->Lrphi;
+  dp.Lrf = p->Lrf;
   dp.RS = reinterpret_cast<const T*>(p->RSphi);
   dp.P = reinterpret_cast<cx<T>*>(p->Pphi);
   dp.L = p->Lphi;
@@ -442,6 +477,29 @@ void build_tiles(int Lband, int lend, int TMP, int prob, std::vector<TileTask>& 
       if (ls > lend) continue;
       out.push_back(TileTask{prob, bp, bm, ls, lend});
     }
+}
+
+// Tile pairs (p <= q) of a band Lband with l in [32 q, lend]; a pair whose
+// tiles run on separate CTAs (N > 5) becomes two tasks.  Sorted by decreasing
+// work (two tiles count double) so that the long ones start first.
+void build_pair_tasks(int Lband, int lend, int N, int table_Lmax, std::vector<PairTask>& out) {
+  if (Lband <= 0 || lend < 0) return;
+  const int nb = (Lband + 31) / 32;
+  const bool two = pair_two_tiles(N);
+  for (int q = 0; q < nb; ++q)
+    for (int p = 0; p <= q; ++p) {
+      const int ls = 32 * q;
+      if (ls > lend) continue;
+      const long long base = pair_run_base(p, q, table_Lmax);
+      if (two || p == q) {
+        out.push_back(PairTask{0, p, q, ls, lend, 0, base});
+      } else {
+        out.push_back(PairTask{0, p, q, ls, lend, 0, base});
+        out.push_back(PairTask{0, p, q, ls, lend, 1, base});
+      }
+    }
+  auto work = [two](const PairTask& t) { return (long long)(t.lend - t.lstart + 1) * (two && t.p != t.q ? 2 : 1); };
+  std::stable_sort(out.begin(), out.end(), [&](const PairTask& a, const PairTask& b) { return work(a) > work(b); });
 }
 
 void sort_tiles(std::vector<TileTask>& t) {
@@ -583,32 +641,60 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
 // Build the device launch lists for a set of plans (same precision).
 template <typename T>
 Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
+  // FP32 plans run the tile-pair contraction (PairTask), FP64 plans the
+  // eighth-domain one (TileTask)
+  using Task = typename std::conditional<sizeof(T) == sizeof(float), PairTask, TileTask>::type;
   const int nj = (int)plans.size();
   std::vector<ContractDesc<T>> dw(nj), dp(nj);
-  std::map<int, std::vector<TileTask>> tw_byN;
-  std::vector<TileTask> tphi;
+  std::map<int, std::vector<Task>> tw_byN;
+  std::vector<Task> tphi;
   std::vector<CztSeg<T>> segs[Lists::NK];
   int start[Lists::NK] = {};
   Lists* ls = new Lists();
+  ls->njobs = nj;
   for (int i = 0; i < nj; ++i) {
     s2dw_plan_s* p = plans[i];
     std::memcpy(&dw[i], p->desc_w_host.data(), sizeof(ContractDesc<T>));
     std::memcpy(&dp[i], p->desc_phi_host.data(), sizeof(ContractDesc<T>));
-    for (TileTask t : p->tiles_w_host) {
+    const std::vector<Task>* tws;
+    const std::vector<Task>* tps;
+    if constexpr (sizeof(T) == sizeof(float)) {
+      tws = &p->ptasks_w_host;
+      tps = &p->ptasks_phi_host;
+    } else {
+      tws = &p->tiles_w_host;
+      tps = &p->tiles_phi_host;
+    }
+    for (Task t : *tws) {
       t.prob = i;
       tw_byN[p->N].push_back(t);
     }
-    for (TileTask t : p->tiles_phi_host) {
+    for (Task t : *tps) {
       t.prob = i;
       tphi.push_back(t);
     }
     for (int k = 0; k < Lists::NK; ++k) build_segs<T>(p, i, k, segs[k], start[k]);
     ls->maxlogM = std::max(ls->maxlogM, p->logM);
     ls->Lmax = std::max(ls->Lmax, p->L);
+    ls->nbmax = std::max(ls->nbmax, (p->L + 31) / 32);
+    ls->Lrmax = std::max(ls->Lrmax, p->Lrf);
     if (p->mw) ls->odd = CZT_ODD_ROWS;
   }
-  for (auto& kv : tw_byN) sort_tiles(kv.second);
-  sort_tiles(tphi);
+  // longest tasks first (a CTA computing both tiles of a pair counts double)
+  auto by_work = [](std::vector<Task>& v, int N) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+      const bool two = pair_two_tiles(N);
+      auto work = [two](const PairTask& t) {
+        return (long long)(t.lend - t.lstart + 1) * (two && t.p != t.q ? 2 : 1);
+      };
+      std::stable_sort(v.begin(), v.end(), [&](const PairTask& a, const PairTask& b) { return work(a) > work(b); });
+    } else {
+      (void)N;
+      sort_tiles(v);
+    }
+  };
+  for (auto& kv : tw_byN) by_work(kv.second, kv.first);
+  by_work(tphi, 1);
   // one allocation for everything
   size_t off = 0;
   const size_t o_dw = off;
@@ -618,10 +704,10 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
   std::vector<size_t> o_tw;
   for (auto& kv : tw_byN) {
     o_tw.push_back(off);
-    off = align256(off + kv.second.size() * sizeof(TileTask));
+    off = align256(off + kv.second.size() * sizeof(Task));
   }
   const size_t o_tp = off;
-  off = align256(off + tphi.size() * sizeof(TileTask));
+  off = align256(off + tphi.size() * sizeof(Task));
   size_t o_sg[Lists::NK];
   for (int k = 0; k < Lists::NK; ++k) {
     o_sg[k] = off;
@@ -632,10 +718,10 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
   std::memcpy(host.data() + o_dp, dp.data(), nj * sizeof(ContractDesc<T>));
   int q = 0;
   for (auto& kv : tw_byN) {
-    std::memcpy(host.data() + o_tw[q], kv.second.data(), kv.second.size() * sizeof(TileTask));
+    std::memcpy(host.data() + o_tw[q], kv.second.data(), kv.second.size() * sizeof(Task));
     ++q;
   }
-  if (!tphi.empty()) std::memcpy(host.data() + o_tp, tphi.data(), tphi.size() * sizeof(TileTask));
+  if (!tphi.empty()) std::memcpy(host.data() + o_tp, tphi.data(), tphi.size() * sizeof(Task));
   for (int k = 0; k < Lists::NK; ++k)
     if (!segs[k].empty()) std::memcpy(host.data() + o_sg[k], segs[k].data(), segs[k].size() * sizeof(CztSeg<T>));
   try {
@@ -688,11 +774,20 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
   const ContractDesc<T>* dw = reinterpret_cast<const ContractDesc<T>*>(ls.desc_w);
   const ContractDesc<T>* dp = reinterpret_cast<const ContractDesc<T>*>(ls.desc_phi);
   rec(ev, 0, st);
-  for (auto& t : ls.tiles_w)
-    launch_contract<T>(t.first, 2, false, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
-                       ptrs, st);
-  rec(ev, 1, st);
-  launch_contract<T>(1, 1, false, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    launch_fpack(dw, ls.njobs, ls.nbmax, ls.Lrmax, ptrs, st);
+    for (auto& t : ls.tiles_w)
+      launch_contract_pair(t.first, 2, false, dw, reinterpret_cast<const PairTask*>(t.second.first),
+                           t.second.second, ptrs, st);
+    rec(ev, 1, st);
+    launch_contract_pair(1, 1, false, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+  } else {
+    for (auto& t : ls.tiles_w)
+      launch_contract<T>(t.first, 2, false, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
+                         ptrs, st);
+    rec(ev, 1, st);
+    launch_contract<T>(1, 1, false, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+  }
   rec(ev, 2, st);
   launch_czt<T>(CZT_BETA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[0]), ls.nseg[0], ls.items[0], ls.maxlogM,
                 ptrs, st);
@@ -736,11 +831,19 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
   launch_czt<T>(CZT_BETA_SYN_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[7]), ls.nseg[7], ls.items[7],
                 ls.maxlogM, ptrs, st);
   rec(ev, 3, st);
-  for (auto& t : ls.tiles_w)
-    launch_contract<T>(t.first, 2, true, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
-                       ptrs, st);
-  rec(ev, 4, st);
-  launch_contract<T>(1, 1, true, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    for (auto& t : ls.tiles_w)
+      launch_contract_pair(t.first, 2, true, dw, reinterpret_cast<const PairTask*>(t.second.first), t.second.second,
+                           ptrs, st);
+    rec(ev, 4, st);
+    launch_contract_pair(1, 1, true, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+  } else {
+    for (auto& t : ls.tiles_w)
+      launch_contract<T>(t.first, 2, true, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
+                         ptrs, st);
+    rec(ev, 4, st);
+    launch_contract<T>(1, 1, true, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+  }
   rec(ev, 5, st);
   launch_syn_reduce<T>(rj, njobs, ls.Lmax, st);
   rec(ev, 6, st);
@@ -757,8 +860,17 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     off = align256(off + bytes);
     return o;
   };
-  const size_t o_RS = take((size_t)L * 2 * ((N + 1) / 2) * p->Lp * sizeof(T));
-  const size_t o_RSphi = take((size_t)p->Lphi * p->Lphip * sizeof(T));
+  const bool pairc = sizeof(T) == sizeof(float);  // tile-pair contraction (FP32 plans)
+  const int NH = (N + 1) / 2;
+  p->Lr = L + 2;
+  p->Lrphi = p->Lphi + 2;
+  p->Lrf = L + 2;
+  const int nbw = (L + 31) / 32, nbp = (p->Lphi + 31) / 32;
+  const size_t o_RS = pairc ? take(0) : take((size_t)L * 2 * NH * p->Lp * sizeof(T));
+  const size_t o_RSphi = pairc ? take(0) : take((size_t)p->Lphi * p->Lphip * sizeof(T));
+  const size_t o_RSp = pairc ? take((size_t)nbw * p->Lr * 2 * NH * 32 * sizeof(float)) : take(0);
+  const size_t o_RSphi_p = pairc ? take((size_t)nbp * p->Lrphi * 32 * sizeof(float)) : take(0);
+  const size_t o_fP = pairc ? take((size_t)nbw * p->Lrf * 32 * sizeof(cx<T>)) : take(0);
   std::vector<size_t> o_Y(p->nscale + 1), o_X(p->nscale + 1);
   for (int j = 0; j <= p->nscale; ++j) {
     const int Nj = (j == p->nscale) ? 1 : N;
@@ -813,8 +925,11 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   p->ws_bytes = off;
   amalloc(&p->ws, off, st);
   char* b = reinterpret_cast<char*>(p->ws);
-  p->RS = b + o_RS;
-  p->RSphi = b + o_RSphi;
+  p->RS = pairc ? nullptr : b + o_RS;
+  p->RSphi = pairc ? nullptr : b + o_RSphi;
+  p->RSp = pairc ? b + o_RSp : nullptr;
+  p->RSphi_p = pairc ? b + o_RSphi_p : nullptr;
+  p->fP = pairc ? b + o_fP : nullptr;
   p->Y.resize(p->nscale + 1);
   p->X.resize(p->nscale + 1);
   for (int j = 0; j <= p->nscale; ++j) {
@@ -867,9 +982,16 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   ck(cudaMemcpyAsync(slot_d, slot_w.data(), slot_w.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   ck(cudaMemcpyAsync(slot_d + slot_w.size(), slot_p.data(), slot_p.size() * sizeof(int), cudaMemcpyHostToDevice,
                      st));
-  ck(launch_rtable<T>(reinterpret_cast<T*>(p->RS), p->tab->d64, kap_d, sabs_d, slot_d, L, p->Lp, N, 2, L, st));
-  ck(launch_rtable<T>(reinterpret_cast<T*>(p->RSphi), p->tab->d64, phi_d, nullptr, slot_d + slot_w.size(), p->Lphi,
-                      p->Lphip, 1, 1, L, st));
+  if (pairc) {
+    ck(launch_rtable_pair(reinterpret_cast<float*>(p->RSp), p->tab->d64, kap_d, sabs_d, slot_d, L, p->Lr, N, 2, L,
+                          st));
+    ck(launch_rtable_pair(reinterpret_cast<float*>(p->RSphi_p), p->tab->d64, phi_d, nullptr, slot_d + slot_w.size(),
+                          p->Lphi, p->Lrphi, 1, 1, L, st));
+  } else {
+    ck(launch_rtable<T>(reinterpret_cast<T*>(p->RS), p->tab->d64, kap_d, sabs_d, slot_d, L, p->Lp, N, 2, L, st));
+    ck(launch_rtable<T>(reinterpret_cast<T*>(p->RSphi), p->tab->d64, phi_d, nullptr, slot_d + slot_w.size(),
+                        p->Lphi, p->Lphip, 1, 1, L, st));
+  }
   // ---- chirp tables of every grid (float64, then the working precision) ----
   double2* t64 = nullptr;
   double* qg = nullptr;
@@ -952,16 +1074,25 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   ck(cudaStreamSynchronize(st));  // slot_w / slot_p host vectors are local
 
   // ---- descriptors, tiles, launch lists ----
+  if (pairc) {
+    delta_pair_ensure(p->tab, st);
+    ck(pair_prepare());
+  }
   ContractDesc<T> dw, dp;
   const T* delta = (sizeof(T) == sizeof(double)) ? reinterpret_cast<const T*>(p->tab->d64)
                                                  : reinterpret_cast<const T*>(p->tab->d32);
   fill_desc<T>(p, dw, dp, delta);
   p->desc_w_host.assign(reinterpret_cast<unsigned char*>(&dw), reinterpret_cast<unsigned char*>(&dw) + sizeof(dw));
   p->desc_phi_host.assign(reinterpret_cast<unsigned char*>(&dp), reinterpret_cast<unsigned char*>(&dp) + sizeof(dp));
-  build_tiles(p->L0, p->lend_w, p->TMP, 0, p->tiles_w_host);
-  build_tiles(p->Lphi, p->lphi, p->TMP, 0, p->tiles_phi_host);
-  sort_tiles(p->tiles_w_host);
-  sort_tiles(p->tiles_phi_host);
+  if (pairc) {
+    build_pair_tasks(p->L0, p->lend_w, N, p->tab->Lmax, p->ptasks_w_host);
+    build_pair_tasks(p->Lphi, p->lphi, 1, p->tab->Lmax, p->ptasks_phi_host);
+  } else {
+    build_tiles(p->L0, p->lend_w, p->TMP, 0, p->tiles_w_host);
+    build_tiles(p->Lphi, p->lphi, p->TMP, 0, p->tiles_phi_host);
+    sort_tiles(p->tiles_w_host);
+    sort_tiles(p->tiles_phi_host);
+  }
   Lists* ls = build_lists<T>(std::vector<s2dw_plan_t>{p});
   // move into the plan (the plan frees the list memory at destruction)
   p->own_mem = ls->mem;
@@ -980,6 +1111,9 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   p->own.maxlogM = ls->maxlogM;
   p->own.Lmax = ls->Lmax;
   p->own.odd = ls->odd;
+  p->own.njobs = ls->njobs;
+  p->own.nbmax = ls->nbmax;
+  p->own.Lrmax = ls->Lrmax;
   delete ls;
   // the cap covers every plan size (M <= 8192 for L <= 2048), so plans of
   // different sizes can share a batched launch
@@ -1338,6 +1472,10 @@ int s2dw_wait_timeouts(int* count) {
   if (e != cudaSuccess) return err_of(e);
   e = alpha_tc_timeouts(count);
   if (e != cudaSuccess) return err_of(e);
+  int pc = 0;
+  e = pair_timeouts(&pc);
+  if (e != cudaSuccess) return err_of(e);
+  *count += pc;
   return *count > 0 ? S2DW_ETIMEOUT : S2DW_OK;
 }
 

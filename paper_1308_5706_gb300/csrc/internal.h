@@ -22,6 +22,11 @@ struct LSeg {
 template <typename T>
 struct ContractDesc {
   const T* delta;    // Delta table (padded eighth domain), working precision
+  // FP32 plans (tile-pair contraction, contract_pair.cuh):
+  const float* dpair;  // Delta pair table of the plan's shared table
+  const float* RSp;    // [nb][Lr][nslot][(N+1)/2][32]: R rows per 32-block of m', l outermost
+  const cx<T>* fP;     // [nb][Lrf][32]: f_lm per 32-block of m (zero for m > l), packed per call
+  int Lr, Lrf;         // l rows of RSp and fP (>= L + 1: a stage may read one l past the last)
   const T* RS;       // [L][nslot][(N+1)/2][Lp]: Delta^l_{m',n_k} kappa^j(l) |s_{l,n_k}|, n_k >= 0
   cx<T>* P;          // synthesis partials [nbr][L][Lp32]
   int L, Lp, Lp32, nbr;
@@ -31,6 +36,30 @@ struct ContractDesc {
   cx<T>* Y[MAXS];          // per scale cube [N][Lj][Lj] (analysis out / synthesis in)
   LSeg seg[2 * MAXS + 2];
 };
+
+// One tile pair of the FP32 contraction: blocks p <= q of 32 rows / columns;
+// tile A = (m' block p, m block q), tile B = (q, p).  dbase: entry of the
+// pair table holding l = lstart = 32 q (1024 entries per l follow).
+struct PairTask {
+  int prob;
+  int p, q;
+  int lstart, lend;
+  int half;  // one-tile launches (N > 5): 0 = tile A, 1 = tile B
+  long long dbase;
+};
+
+// Pair table of reach Lmax (a multiple of 32): pairs ordered by q, then p;
+// the run of pair (p, q) holds Lmax - 32 q blocks of 32 x 32 entries.
+// Entry of its first block (l = 32 q):
+//   1024 * (Lmax q (q+1)/2 - 32 (q-1) q (q+1)/3 + p (Lmax - 32 q)).
+__host__ __device__ __forceinline__ long long pair_run_base(int p, int q, int Lmax) {
+  const long long Q = q;
+  return 1024LL * ((long long)Lmax * Q * (Q + 1) / 2 - 32LL * (Q - 1) * Q * (Q + 1) / 3 + (long long)p * (Lmax - 32 * Q));
+}
+// entries of the whole table (+ one stage of read-ahead past the last run)
+__host__ __device__ __forceinline__ long long pair_table_entries(int Lmax) {
+  return pair_run_base(0, Lmax / 32, Lmax) + 2 * 1024;
+}
 
 struct TileTask {
   int prob;    // index into the descriptor array of the launch
@@ -131,6 +160,17 @@ struct ReduceJobs {
 template <typename T>
 void launch_contract(int N, int nslot, bool syn, const ContractDesc<T>* descs, const TileTask* tiles,
                      int ntiles, const CallPtrs& ptrs, cudaStream_t st);
+// FP32 tile-pair contraction and its tables (contract_pair.cu)
+bool pair_two_tiles(int N);  // one CTA computes both tiles of a pair (N <= 5)
+void launch_contract_pair(int N, int nslot, bool syn, const ContractDesc<float>* descs, const PairTask* tasks,
+                          int ntasks, const CallPtrs& ptrs, cudaStream_t st);
+void launch_fpack(const ContractDesc<float>* descs, int njobs, int nbmax, int Lrmax, const CallPtrs& ptrs,
+                  cudaStream_t st);
+cudaError_t launch_pair_table(float* out, const double* d64, int Lmax, cudaStream_t st);
+cudaError_t launch_rtable_pair(float* RSp, const double* d64, const double* kap, const double* sabs,
+                               const int* slotj, int L, int Lr, int N, int nslot, int kapL, cudaStream_t st);
+cudaError_t pair_prepare();
+cudaError_t pair_timeouts(int* count);  // reads and resets the device count
 template <typename T>
 void launch_czt(int kind, const CztSeg<T>* segs, int nseg, int total_items, int maxlogM,
                 const CallPtrs& ptrs, cudaStream_t st);

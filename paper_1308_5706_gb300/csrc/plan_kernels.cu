@@ -4,6 +4,7 @@
 //   * the Wigner table Delta^l_{m'm} = d^l_{m'm}(pi/2) (Sec. 3.2, Eq. (25));
 //   * the per-plan R tables and the chirp-z tables.
 #include "fft16.cuh"
+#include "internal.h"
 #include "plan_kernels.h"
 
 namespace s2dw {
@@ -243,6 +244,78 @@ __global__ void k_rtable(T* RS, const double* d64, const double* kap, const doub
     if (sa != 0.0 && kv != 0.0) v = delta_lookup(d64, l, mp, n) * kv * sa;
   }
   RS[idx] = (T)v;
+}
+
+// Pair table (FP32) of the tile-pair contraction from the FP64 table: block
+// (pair (p, q), l) is [r][c] = Delta^l_{32p+r, 32q+c}, zero where an index
+// exceeds l.  Grid (Lmax, number of pairs); CTAs with l < 32 q exit.  Each
+// thread writes 4 consecutive c (one 16-byte store).
+__global__ void __launch_bounds__(256) k_pair_table(float* __restrict__ out, const double* __restrict__ d64,
+                                                    int Lmax) {
+  const int l = blockIdx.x;
+  const int pi = blockIdx.y;
+  int q = 0;
+  while ((q + 1) * (q + 2) / 2 <= pi) ++q;
+  const int p = pi - q * (q + 1) / 2;
+  if (l < 32 * q) return;
+  const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+  const int mp = 32 * p + r;
+  float v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = 32 * q + c0 + i;
+    v[i] = (mp <= l && m <= l) ? (float)delta_lookup(d64, l, mp, m) : 0.0f;
+  }
+  float* dst = out + pair_run_base(p, q, Lmax) + (long long)(l - 32 * q) * 1024 + r * 32 + c0;
+  *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+cudaError_t launch_pair_table(float* out, const double* d64, int Lmax, cudaStream_t st) {
+  const int B = Lmax / 32;
+  if (B <= 0) return cudaSuccess;
+  dim3 grid(Lmax, B * (B + 1) / 2);
+  k_pair_table<<<grid, 256, 0, st>>>(out, d64, Lmax);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // the read-ahead stage after the last run
+  return cudaMemsetAsync(out + pair_run_base(0, B, Lmax), 0, 2 * 1024 * sizeof(float), st);
+}
+
+// R rows in the layout of the tile-pair contraction:
+// RSp[b][l][s][h][c] = R at (l, m' = 32 b + c, slot s, order n_k, k = N/2 + h),
+// as k_rtable (zero for l >= L, m' > l, inactive slots).
+__global__ void k_rtable_pair(float* RSp, const double* d64, const double* kap, const double* sabs, const int* slotj,
+                              int L, int Lr, int N, int nslot, int kapL, int64_t total) {
+  const int NH = (N + 1) / 2;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int c = (int)(idx & 31);
+  const int h = (int)((idx >> 5) % NH);
+  const int s = (int)((idx / (32 * NH)) % nslot);
+  const int l = (int)((idx / ((int64_t)32 * NH * nslot)) % Lr);
+  const int b = (int)(idx / ((int64_t)32 * NH * nslot * Lr));
+  const int mp = 32 * b + c;
+  const int k = N / 2 + h;
+  const int n = -(N - 1) + 2 * k;
+  double v = 0.0;
+  if (l < L) {
+    const int js = slotj[l * nslot + s];
+    if (js >= 0 && mp <= l && abs(n) <= l) {
+      const double sa = sabs ? sabs[l * N + k] : 1.0;
+      const double kv = kap[(size_t)js * kapL + l];
+      if (sa != 0.0 && kv != 0.0) v = delta_lookup(d64, l, mp, n) * kv * sa;
+    }
+  }
+  RSp[idx] = (float)v;
+}
+
+cudaError_t launch_rtable_pair(float* RSp, const double* d64, const double* kap, const double* sabs,
+                               const int* slotj, int L, int Lr, int N, int nslot, int kapL, cudaStream_t st) {
+  const int nb = (L + 31) / 32;
+  const int64_t total = (int64_t)nb * Lr * nslot * ((N + 1) / 2) * 32;
+  if (total == 0) return cudaSuccess;
+  k_rtable_pair<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(RSp, d64, kap, sabs, slotj, L, Lr, N, nslot, kapL, total);
+  return cudaGetLastError();
 }
 
 // Entry i of the twiddle table of length 2^logM: locate level d, then (k, j)
