@@ -81,9 +81,39 @@ def _oracle_task(b):
     return t1 - t0, t2 - t1
 
 
+def _oracle_full(Ls):
+    """A full oracle round trip (analysis of every beta row, then synthesis)
+    of the workload's parameters at band-limit Ls; returns its seconds."""
+    O = _ORACLE["O"]
+    f = flm_gaussian(Ls, SEED, "cl")
+    kern = O.kernels(Ls, N, LAM, J0)
+    t0 = time.perf_counter()
+    W, Wphi = O.analysis(f, Ls, N, LAM, J0, kern)
+    fr = O.synthesis(W, Wphi, Ls, N, LAM, J0, kern)
+    dt = time.perf_counter() - t0
+    assert np.abs(fr - f).max() < 1e-10
+    return dt
+
+
+def oracle_full_round_trips(pool, workers: int, Ls=(16, 32, 64)):
+    """Full oracle round trips at small band-limits, one per host core at a
+    time: {L: {transforms/s over all cores, seconds per round trip}}."""
+    out = {}
+    for Ls_ in Ls:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_full, [Ls_] * workers, chunksize=1)
+        wall = time.perf_counter() - t0
+        out[str(Ls_)] = {"transforms_per_s": workers / wall, "s_per_round_trip": statistics.mean(res)}
+    return out
+
+
 def oracle_pool(workers: int):
     """Spawned pool (safe after CUDA initialisation), warmed outside timing."""
     import multiprocessing as mp
+    # one thread per worker: the spawned workers import numpy (and its BLAS)
+    # before their initializer runs, so the limits go in their environment
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
     pool = mp.get_context("spawn").Pool(workers, initializer=_init_worker)
     pool.map(_oracle_task, [1] * workers, chunksize=1)
     return pool
@@ -203,103 +233,109 @@ def aggregate_replicas(total_ms: float, steps: int, dist=None, device=None):
 
 
 def contraction_flops(plan) -> float:
-    """Algorithmic flops of one contraction launch (analysis or synthesis):
-    per scale j and l in its support, (l+1)^2 (m', m >= 0) triples, each
-    Delta * f (2 flops) plus one complex-by-real multiply-add (4 flops) per
-    order n_k >= 0: the rows of -n_k equal those of n_k up to the sign
-    (-1)^{l+m'}, so a +-n pair costs one multiply-add per l."""
+    """Algorithmic flops of one contraction launch (analysis or synthesis),
+    counted as the measurement plan states them: per scale j and l in its
+    support, (l+1)^2 (m', m >= 0) triples, each Delta * f (2 flops) plus one
+    complex-by-real multiply-add (4 flops) per order n: 2 + 4N per triple
+    (1.58e10 at L=1024, N=5).  The kernel shares one multiply-add between
+    the orders +-n (the rows of -n equal those of n up to (-1)^{l+m'}), so it
+    executes fewer flops than this count."""
     tot = 0.0
     for j in range(plan.nscale):
         lo, hi = plan.support(j)
         if hi < 0:
             continue
         ls = np.arange(lo, hi + 1, dtype=np.float64)
-        tot += float(((ls + 1.0) ** 2).sum()) * (2 + 4 * ((plan.N + 1) // 2))
+        tot += float(((ls + 1.0) ** 2).sum()) * (2 + 4 * plan.N)
     return tot
 
 
-def alpha_bytes(plan, elem: int, direct: bool, side: str) -> float:
+def delta_eighth_bytes(L_: int) -> float:
+    """FP32 bytes of Delta^l_{m'm}, 0 <= m' <= m <= l < L (the eighth domain the
+    symmetries reduce the table to): read once per contraction."""
+    ls = np.arange(L_, dtype=np.float64)
+    return float(((ls + 1) * (ls + 2) / 2).sum()) * 4
+
+
+def scale_rows(plan, j):
+    """(gamma samples, beta rows per gamma sample, band L_j) of scale j (j = nscale: scaling part)."""
+    lo, hi = plan.support(j)
+    return (1 if j == plan.nscale else N), 2 * L, hi + 1
+
+
+def alpha_bytes(plan, elem: int, method: int, side: str) -> float:
     """Algorithmic bytes of one alpha launch over the scales it handles
-    (direct sums, or chirp-z of either form, as the plan reports): W written
-    (or read) once plus the [N][2L][L_j] complex rows read (or written) once."""
+    (method 0 direct sums, 1 full-band chirp-z, 2 segmented chirp-z, as the
+    plan reports): W written (or read) once plus the [N][2L][L_j] complex
+    rows of X (or V) read (or written) once."""
     n = 2 * L - 1
     tot = 0.0
     for j in range(plan.nscale + 1):
-        phi = j == plan.nscale
-        lo, hi = plan.support(j)
-        Lj = hi + 1
-        if Lj <= 0 or (plan.alpha_method(j, SIDE[side])[0] == 0) != direct:
+        g, rows, Lj = scale_rows(plan, j)
+        if Lj <= 0 or plan.alpha_method(j, SIDE[side])[0] != method:
             continue
-        rows = (1 if phi else N) * 2 * L
-        tot += rows * n * elem + rows * Lj * 2 * elem
+        tot += g * rows * n * elem + g * rows * Lj * 2 * elem
     return tot
 
 
-def fft_len(L_: int) -> int:
-    """The chirp-z / FFT length of a plan: the power of two >= 4L - 2 (at least 32)."""
-    M = 32
-    while M < 4 * L_ - 2:
-        M *= 2
-    return M
-
-
-def fft_flops(M: int) -> float:
-    """Conventional flop count of one complex FFT of power-of-two length M."""
-    return 5.0 * M * math.log2(M)
-
-
-def alpha_czt_flops(plan, side: str) -> float:
-    """Algorithmic flops of the chirp-z alpha launches of one direction: per
-    complex transform (two real rows) two length-M FFTs and the spectrum
-    product (6M); segmented: S + 1 FFTs of length M' and S products."""
+def beta_bytes(plan, elem: int) -> float:
+    """Algorithmic bytes of one beta launch: the cube Y [N][L_j][L_j] and the
+    rows X [N][2L][L_j] (complex) of every scale, each moved once."""
     tot = 0.0
     for j in range(plan.nscale + 1):
-        method, Mf, S, _ = plan.alpha_method(j, SIDE[side])
-        pairs = (1 if j == plan.nscale else N) * L
-        if method == 1:
-            tot += pairs * (2 * fft_flops(Mf) + 6.0 * Mf)
-        elif method == 2:
-            tot += pairs * ((S + 1) * fft_flops(Mf) + S * 6.0 * Mf)
+        g, rows, Lj = scale_rows(plan, j)
+        if Lj > 0:
+            tot += g * (Lj * Lj + rows * Lj) * 2 * elem
     return tot
 
 
-def beta_flops(plan) -> float:
-    """Algorithmic flops of one beta launch: one length-4L FFT per (g, m)
-    column when 4L is a power of two (else a chirp-z convolution)."""
-    M = fft_len(plan.L)
-    cols = sum((1 if j == plan.nscale else N) * (plan.support(j)[1] + 1) for j in range(plan.nscale + 1))
-    per = fft_flops(M) if M == 4 * L else 2 * fft_flops(M) + 6.0 * M
-    return cols * per
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
 
-# DRAM bytes per launch (read + write) of kernels captured with ncu on this
-# workload; None once the kernel has changed since the capture.
-NCU_TRAFFIC = {
-    # the alpha chirp-z stage is two launches (full-band and segmented): their sum
-    "ana_alpha_czt": (0.167998e9 + 0.122535e9 + 0.079100e9 + 0.275988e9, "profiles/k_czt_alpha_L1024_N5.md"),
-    "syn_alpha_czt": (0.167881e9 + 0.119082e9 + 0.335626e9 + 0.076106e9, "profiles/k_czt_alpha_L1024_N5.md"),
-    "ana_contract": (1.218407e9 + 0.070254e9, "profiles/k_contract_L1024_N5.md"),
-    "syn_contract": (1.575094e9 + 0.091380e9, "profiles/k_contract_L1024_N5.md"),
-}
+def source_fingerprint(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
-def roofline(pm, mean_stage):
-    """Roofline of the dominant kernel (largest mean duration) and of every
-    other timed kernel, from the live CUDA-event durations."""
+def recorded_traffic(stage: str):
+    """DRAM bytes per launch of the kernel behind `stage`, from the ncu record,
+    if the kernel's sources are unchanged since that capture (else None)."""
+    try:
+        rec = json.load(open(TRAFFIC_RECORD)).get(stage)
+    except (OSError, ValueError):
+        return None, None
+    if not rec:
+        return None, None
+    if source_fingerprint(rec["files"]) != rec["fingerprint"]:
+        return None, "sources changed since the capture of " + rec["date"]
+    return rec["bytes_per_launch"], f"ncu capture of {rec['date']} ({rec['kernel']})"
+
+
+def roofline(pm, mean_stage, ms_per_step):
+    """Roofline of every timed launch and of the dominant one (largest mean
+    duration), from the live CUDA-event durations; and the round trip against
+    the sum of the stage roofs of the measurement plan: per direction the
+    contraction at max(Delta bytes / HBM, 2+4N flops per triple / FP32 peak)
+    and the FFT passes at (W + f bytes) / HBM."""
     hbm, sm_max, peak_src = peaks()
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at max SM clock
     alu_src = f"derived FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz"
     work = {
         "ana_contract": ("alu", contraction_flops(pm)), "syn_contract": ("alu", contraction_flops(pm)),
-        "ana_alpha_czt": ("alu", alpha_czt_flops(pm, "ana")), "syn_alpha_czt": ("alu", alpha_czt_flops(pm, "syn")),
-        "ana_beta": ("alu", beta_flops(pm)), "syn_beta": ("alu", beta_flops(pm)),
-        "ana_alpha_direct": ("hbm", alpha_bytes(pm, 4, True, "ana")),
-        "syn_alpha_direct": ("hbm", alpha_bytes(pm, 4, True, "syn")),
+        "ana_alpha_czt": ("hbm", alpha_bytes(pm, 4, 1, "ana")), "syn_alpha_czt": ("hbm", alpha_bytes(pm, 4, 1, "syn")),
+        "ana_alpha_seg": ("hbm", alpha_bytes(pm, 4, 2, "ana")), "syn_alpha_seg": ("hbm", alpha_bytes(pm, 4, 2, "syn")),
+        "ana_alpha_direct": ("hbm", alpha_bytes(pm, 4, 0, "ana")),
+        "syn_alpha_direct": ("hbm", alpha_bytes(pm, 4, 0, "syn")),
+        "ana_beta": ("hbm", beta_bytes(pm, 4)), "syn_beta": ("hbm", beta_bytes(pm, 4)),
     }
     per = {}
     for k, (bound, w) in work.items():
         ms = mean_stage.get(k, 0.0)
-        if ms <= 0:
+        if ms <= 0 or w <= 0:
             continue
         if bound == "alu":
             a = w / (ms * 1e-3) / 1e12
@@ -312,13 +348,18 @@ def roofline(pm, mean_stage):
     dom = max(per, key=lambda k: per[k]["ms"])
     r = dict(per[dom])
     r["kernel"] = dom
-    tr = NCU_TRAFFIC.get(dom)
-    r["traffic"] = tr[0] if tr else None
-    r["traffic_source"] = tr[1] if tr else None
-    r["peak_source"] = alu_src if r["bound"] == "alu" else f"{peak_src} hbm_gbs (of {peak_src})"
+    r["traffic"], r["traffic_source"] = recorded_traffic(dom)
+    r["peak_source"] = alu_src if r["bound"] == "alu" else f"hbm_gbs of {peak_src} peaks"
     r["work_per_launch"] = work[dom][1]
     r["kernels"] = {k: {"ms": v["ms"], "frac": round(v["frac"], 4), "bound": v["bound"]} for k, v in per.items()}
     r["stage_ms"] = {k: round(v, 4) for k, v in mean_stage.items()}
+    # round trip against the stage roofs (both directions)
+    t_con = max(delta_eighth_bytes(pm.L) / (hbm * 1e9), contraction_flops(pm) / (fp32_peak * 1e12))
+    w_bytes = 4.0 * (pm.nscale * N * 2 * L * (2 * L - 1) + 2 * L * (2 * L - 1)) + 8.0 * L * L
+    t_fft = w_bytes / (hbm * 1e9)
+    r["round_trip_roof_ms"] = 2e3 * (t_con + t_fft)
+    r["round_trip_ms"] = ms_per_step
+    r["round_trip_frac"] = r["round_trip_roof_ms"] / ms_per_step
     return r
 
 
@@ -398,6 +439,29 @@ def run_batch_workload(args):
     return 0
 
 
+def serve_report(torch, rate: float, seconds: float):
+    """The serving workload (Poisson arrivals, analysis/synthesis 50/50, L =
+    round(exp U[ln 32, ln 2048]), N 1..8, lambda {2, 3}, seed 4) for a few
+    seconds: p50/p99 latency from arrival to completion, transforms/s,
+    admission deferrals.  The server builds the process-wide Wigner tables up
+    to L = 2048 when it starts; plans are made on demand while serving."""
+    from paper_1308_5706_gb300.serve import Server, poisson_workload
+    reqs = poisson_workload(rate=rate, duration=seconds, seed=4, L_range=(32, 2048))
+    srv = Server("mixed", slots=4, max_batch=16, table_L=2048)
+    bank = [torch.from_numpy(flm_gaussian(2048, 100 + k, "cl")).to(torch.complex64).pin_memory() for k in range(4)]
+    torch.cuda.synchronize()
+    rep = srv.run(reqs, payload=lambda r: bank[r.seed % 4][: r.L * r.L])
+    srv.close()
+    torch.cuda.synchronize()
+    return {"transforms_per_s": rep["transforms_per_s"], "latency_ms": rep["latency_ms"],
+            "requests": rep["requests"], "admission_deferrals": rep["admission_deferrals"],
+            "mean_batch": rep["mean_batch"], "plans_created": rep["plans_created"],
+            "plan_create_ms_mean": rep["plan_create_ms_mean"],
+            "distinct_configurations": len({(r.L, r.N, r.lam) for r in reqs}),
+            "workload": (f"Poisson {rate:g} req/s for {seconds:g} s, analysis/synthesis 50/50, L = round(exp "
+                         f"U[ln 32, ln 2048]), N 1..8, lambda {{2,3}}, seed 4, mixed precision")}
+
+
 def run_serve_workload(args):
     """Poisson arrivals of analysis/synthesis requests (50/50, a synthesis
     consumes an earlier analysis' W), L = round(exp U[ln 32, ln 2048]), N
@@ -408,7 +472,7 @@ def run_serve_workload(args):
     import torch
     from paper_1308_5706_gb300.serve import Server, poisson_workload
     reqs = poisson_workload(rate=args.serve_rate, duration=args.serve_seconds, seed=4, L_range=(32, 2048))
-    srv = Server("mixed", slots=4, max_batch=16)
+    srv = Server("mixed", slots=4, max_batch=16, table_L=2048)
     # client payloads: four pinned host signals at L = 2048; a request of
     # band-limit L sends the first L^2 coefficients (l < L) of one of them
     from paper_1308_5706_gb300.inputs import flm_gaussian
@@ -464,6 +528,46 @@ def run_multires_workload(args):
     print(json.dumps(out))
     pm.close()
     p64.close()
+    return 0
+
+
+def run_precision_workload(args):
+    """Error of the mixed path against the FP64 path as the band-limit grows
+    (N=5, lambda=2, J0=0, C_l spectrum): the largest normwise error over the
+    scales of W (max|W_mixed - W_fp64| / max|W_fp64| per scale), of W^Phi, and
+    of the round trip f (max|f_rec - f| / max|f|), at L = 256, 512, 1024, 2048."""
+    import torch
+    from paper_1308_5706_gb300 import binding as B
+    rows = []
+    for Ls in (256, 512, 1024, 2048):
+        f64 = flm_gaussian(Ls, SEED, "cl")
+        res = {}
+        for prec in ("mixed", "fp64"):
+            p = B.Plan(Ls, N, LAM, J0, prec)
+            cd, _ = p.torch_dtypes()
+            f = torch.from_numpy(f64).to(cd).cuda()
+            W, Wp = p.alloc_w()
+            p.analysis(f, W, Wp)
+            fr = p.alloc_flm()
+            p.synthesis(W, Wp, fr)
+            torch.cuda.synchronize()
+            res[prec] = (W, fr.to(torch.complex128), p.nscale)
+            p.close()
+        Wm, frm, ns = res["mixed"]
+        W64, fr64, _ = res["fp64"]
+        per_scale = []
+        for j in range(ns):
+            ref = W64[j].abs().max()
+            if float(ref) > 0:
+                per_scale.append(float((Wm[j].double() - W64[j]).abs().max() / ref))
+        f0 = torch.from_numpy(f64).cuda()
+        rows.append({"L": Ls, "W_max_rel_over_scales": max(per_scale), "W_rel_per_scale": per_scale,
+                     "round_trip_mixed": float((frm - f0).abs().max() / f0.abs().max()),
+                     "round_trip_fp64": float((fr64 - f0).abs().max() / f0.abs().max())})
+        del res, Wm, W64
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "mixed-precision error against the FP64 path vs band-limit (N=5, lambda=2)",
+                      "rows": rows}))
     return 0
 
 
@@ -589,9 +693,11 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="roundtrip",
-                    choices=["roundtrip", "batch", "serve", "steer", "multires", "sht", "mw"])
+                    choices=["roundtrip", "batch", "serve", "steer", "multires", "sht", "mw", "precision"])
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-line-seconds", type=float, default=10.0,
+                    help="seconds of the served mixed-L Poisson run reported in the roundtrip line (0: none)")
     ap.add_argument("--L", type=int, default=1024,
                     help="band-limit of the roundtrip workload; values other than 1024 are for profiling "
                          "captures at a smaller size and give no bench line of the metric")
@@ -615,6 +721,8 @@ def main():
         return run_sht_workload(args)
     if args.workload == "mw":
         return run_mw_workload(args)
+    if args.workload == "precision":
+        return run_precision_workload(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -626,13 +734,17 @@ def main():
         workers = max(1, os.cpu_count() or 1)
         pool = oracle_pool(workers)
         v, wall, ana, syn = oracle_run(pool, workers)
+        full = oracle_full_round_trips(pool, workers)
         pool.close()
         pool.join()
         cpu = {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
                "sample": (f"{workers} sample units (1 analysis beta-row + 1 synthesis beta-row each) of the "
-                          f"L=1024 workload on {workers} spawn workers in {wall:.1f} s (row: analysis "
+                          f"L={L} workload on {workers} spawn workers in {wall:.1f} s (row: analysis "
                           f"{ana:.2f} s, synthesis {syn:.2f} s); a round trip is 2L = {2 * L} rows of each, "
-                          f"extrapolated")}
+                          f"extrapolated"),
+               "full_round_trips": full,
+               "full_round_trips_note": (f"complete oracle round trips (N={N}, lambda={LAM:g}, J0={J0}, same "
+                                         f"spectrum and seed), {workers} at a time on the {workers} workers")}
 
     import torch
     from paper_1308_5706_gb300 import binding as B
@@ -715,10 +827,15 @@ def main():
                                          + [0.0])
         err["oracle_spot"] = "beta row b=700, all scales, gamma and alpha samples"
 
+    # served latency: a short run of the mixed-L Poisson serving workload
+    serve = None
+    if rank == 0 and args.serve_line_seconds > 0 and L == 1024:
+        serve = serve_report(torch, args.serve_rate, args.serve_line_seconds)
+
     # roofline of the dominant kernel, from the stage events of the timed region
     stage_ms, nana, nsyn = prof
     mean_stage = {k: (v / (nana if k.startswith("ana") else nsyn)) for k, v in stage_ms.items()}
-    roof = roofline(pm, mean_stage)
+    roof = roofline(pm, mean_stage, total / args.steps)
 
     per_sorted = sorted(per)
     out = {
@@ -738,6 +855,7 @@ def main():
         "max_rel_err": err,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "serve": serve,
         "e2e": e2e,
         "gpu_launches": args.steps * sum(pm.launch_counts()),
         "clocks": clk.summary(),

@@ -272,12 +272,14 @@ int s2dw_stage(s2dw_plan_t plan, int stage, int j, void* host_out, int64_t* nbyt
  *   s2dw_analysis / s2dw_synthesis calls on this plan record CUDA events
  *   around each of their launches, on the call's stream; 0 stops recording.
  *   s2dw_profile_read(plan, ms, ncalls) waits for the recorded calls and
- *   fills ms[11] with per-stage durations (ms) summed over them:
+ *   fills ms[13] with per-launch durations (ms) summed over them:
  *   [0] analysis contraction + gamma step, [1] scaling contraction,
- *   [2] beta step, [3] alpha step (chirp-z part), [4] alpha step (direct
- *   sums of the small-band scales); [5] synthesis alpha step (direct sums),
- *   [6] alpha step (chirp-z part), [7] beta step, [8] contraction,
- *   [9] scaling contraction, [10] final reduction;
+ *   [2] beta step, [3] alpha step, chirp-z of the full-band scales,
+ *   [4] alpha step, segmented chirp-z of the mid-band scales, [5] alpha
+ *   step, direct sums of the small-band scales; [6] synthesis alpha step
+ *   (direct sums), [7] alpha step (full-band chirp-z), [8] alpha step
+ *   (segmented chirp-z), [9] beta step, [10] contraction, [11] scaling
+ *   contraction, [12] final reduction (an empty launch reads 0);
  *   ncalls[2] (may be NULL) gets the numbers of analysis and synthesis calls.
  */
 int s2dw_profile(s2dw_plan_t plan, int enable);

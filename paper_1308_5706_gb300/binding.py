@@ -54,8 +54,9 @@ _SIGNATURES = {
     "s2dw_wait_probe": (_c_i, [ctypes.c_longlong, _c_p]),
 }
 
-STAGES = ["ana_contract", "ana_contract_phi", "ana_beta", "ana_alpha_czt", "ana_alpha_direct",
-          "syn_alpha_direct", "syn_alpha_czt", "syn_beta", "syn_contract", "syn_contract_phi", "syn_reduce"]
+STAGES = ["ana_contract", "ana_contract_phi", "ana_beta", "ana_alpha_czt", "ana_alpha_seg", "ana_alpha_direct",
+          "syn_alpha_direct", "syn_alpha_czt", "syn_alpha_seg", "syn_beta", "syn_contract", "syn_contract_phi",
+          "syn_reduce"]
 
 
 class S2dwError(RuntimeError):

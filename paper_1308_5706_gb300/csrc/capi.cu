@@ -325,7 +325,7 @@ struct s2dw_plan_s {
   // stage timing (s2dw_profile): one set of events per call, up to kProfCalls
   static constexpr int kProfCalls = 256;
   bool prof = false;
-  static constexpr int kEvAna = 6, kEvSyn = 7;  // events per call (stages + 1)
+  static constexpr int kEvAna = 7, kEvSyn = 8;  // events per call (stages + 1)
   std::vector<cudaEvent_t> ev_ana, ev_syn;      // kProfCalls x kEvAna, kProfCalls x kEvSyn
   int nana = 0, nsyn = 0;
   ~s2dw_plan_s() {
@@ -768,7 +768,8 @@ inline void mark_use(s2dw_plan_t p, cudaStream_t st) {
   if (!capturing(st)) cudaEventRecord(p->last_use, st);
 }
 
-// Analysis stages: [contraction + gamma | scaling contraction | beta | alpha chirp-z | alpha direct].
+// Analysis stages: [contraction + gamma | scaling contraction | beta | alpha chirp-z full-band | segmented
+// | alpha direct].
 template <typename T>
 void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   const ContractDesc<T>* dw = reinterpret_cast<const ContractDesc<T>*>(ls.desc_w);
@@ -796,15 +797,17 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
   rec(ev, 3, st);
   launch_czt<T>(CZT_ALPHA_ANA | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1],
                 ls.maxlogM, ptrs, st);
+  rec(ev, 4, st);
   launch_czt<T>(CZT_ALPHA_ANA_SEG | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[8]), ls.nseg[8], ls.items[8],
                 ls.maxlogM, ptrs, st);
-  rec(ev, 4, st);
+  rec(ev, 5, st);
   launch_czt<T>(CZT_ALPHA_ANA_DIRECT, reinterpret_cast<const CztSeg<T>*>(ls.segs[4]), ls.nseg[4], ls.items[4],
                 ls.maxlogM, ptrs, st);
-  rec(ev, 5, st);
+  rec(ev, 6, st);
 }
 
-// Synthesis stages: [alpha direct | alpha chirp-z | beta | contraction | scaling contraction | reduction].
+// Synthesis stages: [alpha direct | alpha chirp-z full-band | segmented | beta | contraction | scaling
+// contraction | reduction].
 template <typename T>
 void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, int njobs, cudaStream_t st,
                    cudaEvent_t* ev = nullptr) {
@@ -816,9 +819,10 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
   rec(ev, 1, st);
   launch_czt<T>(CZT_ALPHA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[2]), ls.nseg[2], ls.items[2], ls.maxlogM,
                 ptrs, st);
+  rec(ev, 2, st);
   launch_czt<T>(CZT_ALPHA_SYN_SEG | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[9]), ls.nseg[9], ls.items[9],
                 ls.maxlogM, ptrs, st);
-  rec(ev, 2, st);
+  rec(ev, 3, st);
   // MW grid: V from its L beta samples to the DH grid (torus coefficients, then the DH samples)
   launch_czt<T>(CZT_BETA_MW_DFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[10]), ls.nseg[10], ls.items[10],
                 ls.maxlogM, ptrs, st);
@@ -830,23 +834,23 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
                 ptrs, st);
   launch_czt<T>(CZT_BETA_SYN_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[7]), ls.nseg[7], ls.items[7],
                 ls.maxlogM, ptrs, st);
-  rec(ev, 3, st);
+  rec(ev, 4, st);
   if constexpr (sizeof(T) == sizeof(float)) {
     for (auto& t : ls.tiles_w)
       launch_contract_pair(t.first, 2, true, dw, reinterpret_cast<const PairTask*>(t.second.first), t.second.second,
                            ptrs, st);
-    rec(ev, 4, st);
+    rec(ev, 5, st);
     launch_contract_pair(1, 1, true, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
   } else {
     for (auto& t : ls.tiles_w)
       launch_contract<T>(t.first, 2, true, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
                          ptrs, st);
-    rec(ev, 4, st);
+    rec(ev, 5, st);
     launch_contract<T>(1, 1, true, dp, reinterpret_cast<const TileTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
   }
-  rec(ev, 5, st);
-  launch_syn_reduce<T>(rj, njobs, ls.Lmax, st);
   rec(ev, 6, st);
+  launch_syn_reduce<T>(rj, njobs, ls.Lmax, st);
+  rec(ev, 7, st);
 }
 
 template <typename T>
@@ -1490,7 +1494,8 @@ int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {
   int contract = ls.ntiles_phi > 0 ? 1 : 0;
   for (auto& t : ls.tiles_w) contract += t.second.second > 0 ? 1 : 0;
   auto has = [&](int k) { return ls.items[k] > 0 ? 1 : 0; };
-  if (analysis) *analysis = contract + has(0) + has(1) + has(4) + has(6) + has(8);
+  const int fpack = (!p->fp64 && ls.njobs > 0 && ls.nbmax > 0) ? 1 : 0;  // f packing of the FP32 contraction
+  if (analysis) *analysis = fpack + contract + has(0) + has(1) + has(4) + has(6) + has(8);
   if (synthesis) *synthesis = contract + has(2) + has(3) + has(5) + has(7) + has(9) + has(10) + has(11) + has(12) + 1;
   return S2DW_OK;
 }

@@ -468,7 +468,9 @@ cudaError_t launch_dh_weights(double* q, int L, cudaStream_t st) {
 
 cudaError_t launch_delta_build(double* d64, float* d32, double* em, int* ee, int Lmax, int l_first,
                                cudaStream_t st) {
-  k_delta_edge<<<nblk(Lmax, 128), 128, 0, st>>>(em, ee, Lmax);
+  // one thread per diagonal, each a serial FP64 chain: 32 threads per CTA
+  // spread the chains over as many SMs as possible
+  k_delta_edge<<<nblk(Lmax, 32), 32, 0, st>>>(em, ee, Lmax);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   // slabs l_first .. Lmax-1 in chunks of l so that a single launch stays short

@@ -89,10 +89,14 @@ def poisson_workload(rate: float, duration: float, seed: int, L_range=(32, 2048)
 class Server:
     def __init__(self, precision: str = "mixed", slots: int = 4, max_batch: int = 16,
                  hbm_budget: Optional[int] = None, max_pool_bytes: Optional[int] = None,
-                 plan_workers: int = 2):
+                 plan_workers: int = 2, table_L: int = 0):
+        """table_L > 0: build the process-wide Wigner tables for band-limits up
+        to table_L at start-up (a plan of that size is kept for the server's
+        lifetime), so that no request pays for growing them."""
         import torch
         self.torch = torch
         self.precision = precision
+        self.anchor = B.Plan(table_L, 1, 2.0, 0, precision) if table_L > 0 else None
         self.max_batch = min(max_batch, 64)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         free, total = torch.cuda.mem_get_info()
@@ -195,15 +199,22 @@ class Server:
                         r.t_done = tdone
                         self._give_plan(p)
                         done_count += 1
+                        # buffers leave the server's account once consumed (kept
+                        # outputs are handed to the caller and stop counting too)
                         if r.kind == "synthesis":
                             par = by_id[r.parent]
                             consumers[par.rid] -= 1
-                            if consumers[par.rid] == 0 and not keep_outputs:
+                            if consumers[par.rid] == 0:
                                 self.in_use -= _nbytes(par.W) + _nbytes(par.Wphi)
-                                par.W = par.Wphi = None
+                                if not keep_outputs:
+                                    par.W = par.Wphi = None
+                            self.in_use -= _nbytes(r.f)
                             if not keep_outputs:
-                                self.in_use -= _nbytes(r.f)
                                 r.f = None
+                        elif consumers[r.rid] == 0:  # an analysis no synthesis consumes
+                            self.in_use -= _nbytes(r.W) + _nbytes(r.Wphi)
+                            if not keep_outputs:
+                                r.W = r.Wphi = None
                     busy[s] = None
             self._collect_plans()
             # arrivals -> ready (synthesis waits for its analysis)
@@ -250,9 +261,9 @@ class Server:
                             self.in_use += _nbytes(r.f) + _nbytes(r.W) + _nbytes(r.Wphi)
                         B.s2dw_analysis_batch([p.handle for p in plans], [r.f for r in batch],
                                               [r.W for r in batch], [r.Wphi for r in batch], stream)
-                        if not keep_outputs:
-                            for r in batch:
-                                self.in_use -= _nbytes(r.f)
+                        for r in batch:  # the input f is read by the launch set on this stream
+                            self.in_use -= _nbytes(r.f)
+                            if not keep_outputs:
                                 r.f = None
                     else:
                         for r in batch:
@@ -285,7 +296,8 @@ class Server:
                 "admission_deferrals": self.rejected, "batches": self.stats["batches"],
                 "mean_batch": self.stats["batched_jobs"] / max(1, self.stats["batches"]),
                 "plans_created": self.stats["plan_create"], "plans_taken_from_pool": self.stats["plan_take"],
-                "plan_create_s": round(self.stats["plan_create_s"], 3)}
+                "plan_create_s": round(self.stats["plan_create_s"], 3),
+                "plan_create_ms_mean": round(1e3 * self.stats["plan_create_s"] / max(1, self.stats["plan_create"]), 3)}
 
     def close(self):
         self.workers.shutdown(wait=True)
@@ -294,6 +306,9 @@ class Server:
             for p in lst:
                 p.close()
         self.pool.clear()
+        if self.anchor is not None:
+            self.anchor.close()
+            self.anchor = None
 
 
 def _nbytes(t) -> int:

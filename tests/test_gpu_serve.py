@@ -10,15 +10,9 @@ from paper_1308_5706_gb300.serve import Server, poisson_workload
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_alone():
+def _check_alone(reqs):
+    """Every served result equals the same job run alone on a fresh plan."""
     import torch
-    reqs = poisson_workload(rate=600.0, duration=0.1, seed=4, L_range=(16, 96), N_range=(1, 6))
-    assert len(reqs) >= 20 and any(r.kind == "synthesis" for r in reqs)
-    srv = Server("mixed", slots=3, max_batch=8)
-    rep = srv.run(reqs, keep_outputs=True)
-    assert rep["requests"] == len(reqs)
-    assert rep["latency_ms"]["p99"] >= rep["latency_ms"]["p50"] > 0
-    assert rep["mean_batch"] >= 1.0
     by_id = {r.rid: r for r in reqs}
     for r in reqs:
         p = B.Plan(r.L, r.N, r.lam, r.J0, "mixed")
@@ -38,4 +32,35 @@ def test_served_results_equal_alone():
             ref = flm_gaussian(r.L, par.seed, "cl")
             assert np.abs(f.to(torch.complex128).cpu().numpy() - ref).max() < 1e-5
         p.close()
+
+
+def test_served_results_equal_alone():
+    reqs = poisson_workload(rate=600.0, duration=0.1, seed=4, L_range=(16, 96), N_range=(1, 6))
+    assert len(reqs) >= 20 and any(r.kind == "synthesis" for r in reqs)
+    srv = Server("mixed", slots=3, max_batch=8)
+    rep = srv.run(reqs, keep_outputs=True)
+    assert rep["requests"] == len(reqs)
+    assert rep["latency_ms"]["p99"] >= rep["latency_ms"]["p50"] > 0
+    assert rep["mean_batch"] >= 1.0
+    _check_alone(reqs)
+    srv.close()
+
+
+@pytest.mark.timeout(300)
+def test_admission_by_hbm_footprint_defers_and_results_stay_equal():
+    """A budget of a few requests' footprint: requests wait for memory (the
+    server counts each deferral), every request still completes, and each
+    result is still bit-identical to the job run alone."""
+    reqs = poisson_workload(rate=800.0, duration=0.06, seed=9, L_range=(32, 96), N_range=(2, 6))
+    assert len(reqs) >= 20
+    srv = Server("mixed", slots=3, max_batch=8, hbm_budget=12 << 20)
+    rep = srv.run(reqs, keep_outputs=False)
+    assert rep["requests"] == len(reqs)
+    assert rep["admission_deferrals"] > 0
+    srv.close()
+    reqs = poisson_workload(rate=800.0, duration=0.06, seed=9, L_range=(32, 96), N_range=(2, 6))
+    srv = Server("mixed", slots=3, max_batch=8, hbm_budget=12 << 20)
+    rep = srv.run(reqs, keep_outputs=True)
+    assert rep["admission_deferrals"] > 0
+    _check_alone(reqs)
     srv.close()
