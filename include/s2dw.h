@@ -286,6 +286,35 @@ int s2dw_profile(s2dw_plan_t plan, int enable);
 int s2dw_profile_read(s2dw_plan_t plan, double* ms, int* ncalls);
 
 /*
+ * Launch methods and the autotuner (the paper has no counterpart: these pick
+ * among exact evaluations of the same sums, so results agree to rounding).
+ *   Choices of a plan, int[2 + 2 (J+2)]:
+ *   [0] beta sums of the analysis, [1] beta sums of the synthesis:
+ *       0 = one FFT of length 4L per column, 1 = one complex DCT/DST of length
+ *       2L per column (both where L is a power of two; a grid with other L,
+ *       or L < 16, keeps its default);
+ *   [2 + 2j] alpha sums of the analysis of scale j (j = J+1: scaling part),
+ *   [3 + 2j] of the synthesis: 0 = direct sums (L_j <= 32), 1 = chirp-z of
+ *       the grid's length, 2 = segmented chirp-z (where the plan built its
+ *       tables, s2dw_alpha_method).
+ *   s2dw_plan_choices(plan, choices, n): *n in = capacity, out = entries;
+ *     choices == NULL only queries *n; S2DW_EINVAL if the capacity is short.
+ *   s2dw_plan_set_choices(plan, choices, n): n must be the plan's count and
+ *     every value available (else S2DW_EINVAL); waits for the plan's previous
+ *     calls, then rebuilds its launch lists (batched launch lists holding the
+ *     plan are dropped).
+ *   s2dw_plan_tune(plan, reps, choices, n): times the candidates on the
+ *     plan's private stream with scratch buffers it allocates and frees
+ *     (coordinate descent: each direction's beta method, then each scale's
+ *     alpha method, largest band first, the minimum of `reps` round trips
+ *     per trial, a candidate kept when it is 2% faster), applies the best and
+ *     writes it to choices (may be NULL).  Synchronous; 1 <= reps <= 64.
+ */
+int s2dw_plan_choices(s2dw_plan_t plan, int* choices, int* n);
+int s2dw_plan_set_choices(s2dw_plan_t plan, const int* choices, int n);
+int s2dw_plan_tune(s2dw_plan_t plan, int reps, int* choices, int* n);
+
+/*
  * s2dw_delta_table_noalloc: build the Wigner Delta table without allocating.
  *   The paper has no counterpart to this entry point.  It serves callers
  *   that cannot let this library call cudaMalloc: code whose device memory

@@ -51,6 +51,9 @@ _SIGNATURES = {
     "s2dw_profile_read": (_c_i, [_c_p, _c_dp, _c_ip]),
     "s2dw_delta_table_noalloc": (_c_i, [_c_i, _c_p, _c_p, _c_i64p, _c_p]),
     "s2dw_wait_timeouts": (_c_i, [_c_ip]),
+    "s2dw_plan_choices": (_c_i, [_c_p, _c_ip, _c_ip]),
+    "s2dw_plan_set_choices": (_c_i, [_c_p, _c_ip, _c_i]),
+    "s2dw_plan_tune": (_c_i, [_c_p, _c_i, _c_ip, _c_ip]),
     "s2dw_wait_probe": (_c_i, [ctypes.c_longlong, _c_p]),
 }
 
@@ -286,6 +289,36 @@ def s2dw_delta_table_noalloc(Lmax: int, table64=None, table32=None, stream=None)
     return n.value
 
 
+def s2dw_plan_choices(plan: int):
+    """The plan's launch methods (layout in include/s2dw.h)."""
+    n = ctypes.c_int(0)
+    _check(lib().s2dw_plan_choices(plan, None, ctypes.byref(n)), "s2dw_plan_choices")
+    arr = (ctypes.c_int * n.value)()
+    _check(lib().s2dw_plan_choices(plan, arr, ctypes.byref(n)), "s2dw_plan_choices")
+    return list(arr)
+
+
+def s2dw_plan_set_choices(plan: int, choices):
+    arr = (ctypes.c_int * len(choices))(*[int(c) for c in choices])
+    _check(lib().s2dw_plan_set_choices(plan, arr, len(choices)), "s2dw_plan_set_choices")
+
+
+def s2dw_plan_tune(plan: int, reps: int = 5):
+    """Times the candidate launch methods and applies the fastest; returns them."""
+    n = ctypes.c_int(0)
+    _check(lib().s2dw_plan_choices(plan, None, ctypes.byref(n)), "s2dw_plan_choices")
+    arr = (ctypes.c_int * n.value)()
+    _check(lib().s2dw_plan_tune(plan, reps, arr, ctypes.byref(n)), "s2dw_plan_tune")
+    return list(arr)
+
+
+def autotune_cache_path() -> str:
+    """JSON file of tuned launch methods: $S2DW_AUTOTUNE_CACHE, else a file in
+    the temporary directory."""
+    import tempfile
+    return os.environ.get("S2DW_AUTOTUNE_CACHE") or os.path.join(tempfile.gettempdir(), "s2dw_autotune.json")
+
+
 # ---- thin object wrapper ----------------------------------------------------
 
 class Plan:
@@ -296,7 +329,7 @@ class Plan:
     """
 
     def __init__(self, L: int, N: int, lam: float = 2.0, J0: int = 0, precision: str = "mixed",
-                 multires: bool = False, mw: bool = False):
+                 multires: bool = False, mw: bool = False, autotune: bool = False):
         flags = (S2DW_FP64 if precision == "fp64" else S2DW_MIXED) | S2DW_REAL_SIGNAL
         if multires:
             flags |= S2DW_MULTIRES
@@ -315,6 +348,45 @@ class Plan:
         self.info = q
         # (band-limit, offset, elements) of every scale's grid; last: scaling part
         self.grids = [s2dw_scale_grid(self.handle, j) for j in range(self.nscale + 1)]
+        self.tuned = None
+        if autotune:
+            self.tuned = self.autotune()
+
+    def tune_key(self) -> str:
+        import torch
+        return (f"{torch.cuda.get_device_name()}|L={self.L}|N={self.N}|lam={self.lam!r}|J0={self.J0}|"
+                f"{self.precision}|multires={int(self.multires)}|mw={int(self.mw)}")
+
+    def autotune(self, reps: int = 5):
+        """Launch methods from the tuning cache, or tuned now (and cached);
+        returns (choices, "cache" | "tuned")."""
+        import json
+        path = autotune_cache_path()
+        key = self.tune_key()
+        try:
+            with open(path) as fh:
+                cache = json.load(fh)
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            try:
+                s2dw_plan_set_choices(self.handle, cache[key])
+                return cache[key], "cache"
+            except S2dwError:
+                pass  # stale entry (another build): tune again
+        ch = s2dw_plan_tune(self.handle, reps)
+        cache[key] = ch
+        tmp = f"{path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=0)
+        os.replace(tmp, path)
+        return ch, "tuned"
+
+    def choices(self):
+        return s2dw_plan_choices(self.handle)
+
+    def set_choices(self, choices):
+        s2dw_plan_set_choices(self.handle, choices)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -235,8 +235,8 @@ struct Lists {
   std::vector<std::pair<int, std::pair<void*, int>>> tiles_w;  // (N, (tiles, count))
   void* tiles_phi = nullptr;
   int ntiles_phi = 0;
-  static constexpr int NK = 13;  // chirp-z 0..3, direct alpha 4..5, single-FFT beta 6..7, segmented alpha 8..9,
-                                 // MW-grid synthesis beta 10..12
+  static constexpr int NK = 16;  // chirp-z 0..3, direct alpha 4..5, single-FFT beta 6..7, segmented alpha 8..9,
+                                 // MW-grid synthesis beta 10..12, half-length beta 13..15
   void* segs[NK] = {};
   int nseg[NK] = {};
   int items[NK] = {};
@@ -295,6 +295,7 @@ struct s2dw_plan_s {
     void* root_a = nullptr;  // e^{2 pi i t/(2Lg-1)}
     void* pre_mw = nullptr;  // MW beta chirp e^{i pi (m'^2 + m')/(2Lg-1)}, |m'| < Lg
     void* bfft = nullptr;    // e^{i pi m'/(4Lg)} (|m'| < Lg), then q_b (b < 2Lg): single-FFT beta
+    void* tw2 = nullptr;     // FFT twiddles of length 2Lg (half-length beta)
     void* Hs = nullptr;      // 4 x M spectra
   };
   bool multires = false;       // every scale on the grid of its own band-limit
@@ -310,6 +311,12 @@ struct s2dw_plan_s {
     void* Hs = nullptr;  // S synthesis spectra
   };
   std::vector<SegTables> seg;  // [nscale + 1]
+  // launch methods (s2dw_plan_choices / s2dw_plan_tune): beta_mode[dir] 0 = one
+  // FFT of length 4L, 1 = half-length transforms (power-of-two L >= 16 only);
+  // alpha_mode[dir][j] 0 = direct sums (L_j <= 32), 1 = chirp-z of the grid's
+  // length, 2 = segmented chirp-z (where its tables exist); dir 0 = analysis
+  int beta_mode[2] = {1, 0};
+  std::vector<int> alpha_mode[2];
   // [nscale + 1]: tensor-core basis images of the direct alpha sums (FP32 plans)
   std::vector<void*> tc_ana, tc_syn;
   // FP32 plans: R rows and packed f of the tile-pair contraction
@@ -517,14 +524,18 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
   // kinds 10..12 (MW grid only) the synthesis-side resampling of V from the L
   // MW beta samples to the DH beta grid (torus coefficients, then their
   // evaluation on the DH grid by the analysis beta kernels)
-  if ((kind == CZT_BETA_MW_DFT || kind == CZT_BETA_RS_FFT || kind == CZT_BETA_RS) && !p->mw) return;
+  if ((kind == CZT_BETA_MW_DFT || kind == CZT_BETA_RS_FFT || kind == CZT_BETA_RS || kind == CZT_BETA_RS_DCT) &&
+      !p->mw)
+    return;
   const int base_kind = (kind == CZT_ALPHA_ANA_DIRECT || kind == CZT_ALPHA_ANA_SEG) ? CZT_ALPHA_ANA
                         : (kind == CZT_ALPHA_SYN_DIRECT || kind == CZT_ALPHA_SYN_SEG) ? CZT_ALPHA_SYN
                         : (kind == CZT_BETA_ANA_FFT || kind == CZT_BETA_RS_FFT || kind == CZT_BETA_RS ||
-                           kind == CZT_BETA_MW_DFT) ? CZT_BETA_ANA
-                        : (kind == CZT_BETA_SYN_FFT)     ? CZT_BETA_SYN
-                                                         : kind;
-  const bool rs_list = kind == CZT_BETA_RS_FFT || kind == CZT_BETA_RS;
+                           kind == CZT_BETA_MW_DFT || kind == CZT_BETA_ANA_DCT || kind == CZT_BETA_RS_DCT)
+                            ? CZT_BETA_ANA
+                        : (kind == CZT_BETA_SYN_FFT || kind == CZT_BETA_SYN_DCT) ? CZT_BETA_SYN
+                                                                                  : kind;
+  const bool rs_list = kind == CZT_BETA_RS_FFT || kind == CZT_BETA_RS || kind == CZT_BETA_RS_DCT;
+  const bool dct_list = kind == CZT_BETA_ANA_DCT || kind == CZT_BETA_SYN_DCT || kind == CZT_BETA_RS_DCT;
   const bool direct_list = kind == CZT_ALPHA_ANA_DIRECT || kind == CZT_ALPHA_SYN_DIRECT;
   const bool seg_list = kind == CZT_ALPHA_ANA_SEG || kind == CZT_ALPHA_SYN_SEG;
   const bool fft_list = kind == CZT_BETA_ANA_FFT || kind == CZT_BETA_SYN_FFT || kind == CZT_BETA_RS_FFT;
@@ -537,8 +548,13 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     // the analysis beta step of an MW plan evaluates at the MW samples (chirp-z only);
     // the DH-grid beta kernels (FFT for power-of-two L) serve DH plans and the MW resampling
     const bool mw_ana_beta = p->mw && base_kind == CZT_BETA_ANA && !rs_list && kind != CZT_BETA_MW_DFT;
-    const bool beta_fft = (4 * L == G.M) && !mw_ana_beta;
-    if ((base_kind == CZT_BETA_ANA || base_kind == CZT_BETA_SYN) && kind != CZT_BETA_MW_DFT && beta_fft != fft_list)
+    // power-of-two L: half-length transforms (L >= 16) or one FFT of length 4L (L = 8); else chirp-z
+    const bool beta_pow2 = (4 * L == G.M) && !mw_ana_beta;
+    const int bdir = base_kind == CZT_BETA_SYN ? 1 : 0;
+    const bool beta_dct = beta_pow2 && L >= 16 && p->beta_mode[bdir] == 1;
+    const bool beta_fft = beta_pow2 && !beta_dct;
+    if ((base_kind == CZT_BETA_ANA || base_kind == CZT_BETA_SYN) && kind != CZT_BETA_MW_DFT &&
+        (beta_fft != fft_list || beta_dct != dct_list))
       continue;
     const cx<T>* Hs = reinterpret_cast<const cx<T>*>(G.Hs);
     CztSeg<T> s;
@@ -554,9 +570,10 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     s.scale = (T)(2.0 * 3.14159265358979323846 / n);
     s.nb = G.nb;
     const bool is_alpha = base_kind == CZT_ALPHA_ANA || base_kind == CZT_ALPHA_SYN;
-    const bool direct = is_alpha && Lj <= (base_kind == CZT_ALPHA_ANA ? kDirectMaxLjAna : kDirectMaxLj);
+    const int amode = is_alpha ? p->alpha_mode[base_kind == CZT_ALPHA_SYN ? 1 : 0][j] : -1;
+    const bool direct = is_alpha && amode == 0;
     if (direct != direct_list) continue;
-    if (is_alpha && !direct && (p->seg[j].S > 0) != seg_list) continue;
+    if (is_alpha && !direct && (amode == 2) != seg_list) continue;
     switch (base_kind) {
       case CZT_BETA_ANA:
         s.items = Nj * Lj;
@@ -606,6 +623,13 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     if (fft_list) {
       const int ntb = beta_fft_nt(sizeof(T) == 8);
       s.items = Nj * ((Lj + ntb - 1) / ntb);
+      s.pre = reinterpret_cast<const cx<T>*>(G.bfft);
+      s.post = reinterpret_cast<const cx<T>*>(G.bfft) + (2 * L - 1);
+    }
+    if (dct_list) {
+      const int cols = 4096 / (2 * L);  // transforms of length 2L per CTA
+      s.items = Nj * ((Lj + cols - 1) / cols);
+      s.tw = reinterpret_cast<const cx<T>*>(G.tw2);
       s.pre = reinterpret_cast<const cx<T>*>(G.bfft);
       s.post = reinterpret_cast<const cx<T>*>(G.bfft) + (2 * L - 1);
     }
@@ -794,6 +818,8 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
                 ptrs, st);
   launch_czt<T>(CZT_BETA_ANA_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[6]), ls.nseg[6], ls.items[6],
                 ls.maxlogM, ptrs, st);
+  launch_czt<T>(CZT_BETA_ANA_DCT, reinterpret_cast<const CztSeg<T>*>(ls.segs[13]), ls.nseg[13], ls.items[13],
+                ls.maxlogM, ptrs, st);
   rec(ev, 3, st);
   launch_czt<T>(CZT_ALPHA_ANA | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1],
                 ls.maxlogM, ptrs, st);
@@ -828,11 +854,15 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
                 ls.maxlogM, ptrs, st);
   launch_czt<T>(CZT_BETA_RS_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[11]), ls.nseg[11], ls.items[11],
                 ls.maxlogM, ptrs, st);
+  launch_czt<T>(CZT_BETA_RS_DCT, reinterpret_cast<const CztSeg<T>*>(ls.segs[15]), ls.nseg[15], ls.items[15],
+                ls.maxlogM, ptrs, st);
   launch_czt<T>(CZT_BETA_RS, reinterpret_cast<const CztSeg<T>*>(ls.segs[12]), ls.nseg[12], ls.items[12],
                 ls.maxlogM, ptrs, st);
   launch_czt<T>(CZT_BETA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[3]), ls.nseg[3], ls.items[3], ls.maxlogM,
                 ptrs, st);
   launch_czt<T>(CZT_BETA_SYN_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[7]), ls.nseg[7], ls.items[7],
+                ls.maxlogM, ptrs, st);
+  launch_czt<T>(CZT_BETA_SYN_DCT, reinterpret_cast<const CztSeg<T>*>(ls.segs[14]), ls.nseg[14], ls.items[14],
                 ls.maxlogM, ptrs, st);
   rec(ev, 4, st);
   if constexpr (sizeof(T) == sizeof(float)) {
@@ -851,6 +881,35 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
   rec(ev, 6, st);
   launch_syn_reduce<T>(rj, njobs, ls.Lmax, st);
   rec(ev, 7, st);
+}
+
+// (Re)builds the plan's own launch lists from its current methods; the
+// previous lists are freed once the plan's private stream is idle.
+template <typename T>
+void own_lists_build(s2dw_plan_s* p) {
+  Lists* ls = build_lists<T>(std::vector<s2dw_plan_t>{p});
+  if (p->own_mem) cudaFreeAsync(p->own_mem, p->pst);
+  // move into the plan (the plan frees the list memory at destruction)
+  p->own_mem = ls->mem;
+  p->own.mem = nullptr;
+  ls->mem = nullptr;
+  p->own.desc_w = ls->desc_w;
+  p->own.desc_phi = ls->desc_phi;
+  p->own.tiles_w = ls->tiles_w;
+  p->own.tiles_phi = ls->tiles_phi;
+  p->own.ntiles_phi = ls->ntiles_phi;
+  for (int k = 0; k < Lists::NK; ++k) {
+    p->own.segs[k] = ls->segs[k];
+    p->own.nseg[k] = ls->nseg[k];
+    p->own.items[k] = ls->items[k];
+  }
+  p->own.maxlogM = ls->maxlogM;
+  p->own.Lmax = ls->Lmax;
+  p->own.odd = ls->odd;
+  p->own.njobs = ls->njobs;
+  p->own.nbmax = ls->nbmax;
+  p->own.Lrmax = ls->Lrmax;
+  delete ls;
 }
 
 template <typename T>
@@ -885,7 +944,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   const size_t o_P = take((size_t)p->nbr * L * p->Lp32 * sizeof(cx<T>));
   const size_t o_Pphi = take((size_t)p->nbr_phi * p->Lphi * p->Lphip32 * sizeof(cx<T>));
   // per grid: twiddles, chirps, roots, beta phases and weights, spectra
-  struct GridOff { size_t tw, ca, pb, qb, pS, qS, root, bf, H, pm; };
+  struct GridOff { size_t tw, ca, pb, qb, pS, qS, root, bf, H, pm, tw2; };
   std::vector<GridOff> go(p->gt.size());
   for (size_t g = 0; g < p->gt.size(); ++g) {
     const int Lg = p->gt[g].L, ng = 2 * Lg - 1, Mg = p->gt[g].M;
@@ -899,6 +958,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     go[g].bf = take((size_t)(4 * Lg - 1) * sizeof(cx<T>));
     go[g].H = take((size_t)4 * Mg * sizeof(cx<T>));
     go[g].pm = take((size_t)ng * sizeof(cx<T>));
+    go[g].tw2 = take((size_t)twiddle_entries(p->gt[g].logM - 1) * sizeof(cx<T>));
   }
   // segmented chirp-z tables of the scales that use it (chirp-z bands only)
   p->seg.assign(p->nscale + 1, s2dw_plan_s::SegTables());
@@ -915,6 +975,16 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     so[j].tw = take((size_t)twiddle_entries(sgt.logM) * sizeof(cx<T>));
     so[j].Ha = take((size_t)sgt.S * Ms * sizeof(cx<T>));
     so[j].Hs = take((size_t)sgt.S * Ms * sizeof(cx<T>));
+  }
+  // default launch methods: direct sums for L_j <= 32, segmented chirp-z where it
+  // was chosen above, else the grid's chirp-z
+  for (int d = 0; d < 2; ++d) {
+    p->alpha_mode[d].assign(p->nscale + 1, 1);
+    for (int j = 0; j <= p->nscale; ++j) {
+      const int Lj = p->Ycols[j];
+      if (Lj <= (d == 0 ? kDirectMaxLjAna : kDirectMaxLj)) p->alpha_mode[d][j] = 0;
+      else if (p->seg[j].S > 0) p->alpha_mode[d][j] = 2;
+    }
   }
   // tensor-core basis images of the direct alpha sums (FP32 plans)
   std::vector<size_t> o_ta(p->nscale + 1, SIZE_MAX), o_ts(p->nscale + 1, SIZE_MAX);
@@ -954,6 +1024,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     G.bfft = b + go[g].bf;
     G.Hs = b + go[g].H;
     G.pre_mw = b + go[g].pm;
+    G.tw2 = b + go[g].tw2;
   }
   for (int j = 0; j <= p->nscale; ++j) {
     auto& sgt = p->seg[j];
@@ -1043,6 +1114,8 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     put(G.Hs, H64, (int64_t)4 * Mg);
     ck(launch_mw_pre64(tw64, Lg, st));  // reuse the scratch: the grid's tables are converted above
     put(G.pre_mw, tw64, ng);
+    ck(launch_twiddles64(tw64, G.logM - 1, st));  // length 2Lg (half-length beta transforms)
+    put(G.tw2, tw64, twiddle_entries(G.logM - 1));
   }
   {
     size_t need = 0;
@@ -1097,28 +1170,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
     sort_tiles(p->tiles_w_host);
     sort_tiles(p->tiles_phi_host);
   }
-  Lists* ls = build_lists<T>(std::vector<s2dw_plan_t>{p});
-  // move into the plan (the plan frees the list memory at destruction)
-  p->own_mem = ls->mem;
-  p->own.mem = nullptr;
-  ls->mem = nullptr;
-  p->own.desc_w = ls->desc_w;
-  p->own.desc_phi = ls->desc_phi;
-  p->own.tiles_w = ls->tiles_w;
-  p->own.tiles_phi = ls->tiles_phi;
-  p->own.ntiles_phi = ls->ntiles_phi;
-  for (int k = 0; k < Lists::NK; ++k) {
-    p->own.segs[k] = ls->segs[k];
-    p->own.nseg[k] = ls->nseg[k];
-    p->own.items[k] = ls->items[k];
-  }
-  p->own.maxlogM = ls->maxlogM;
-  p->own.Lmax = ls->Lmax;
-  p->own.odd = ls->odd;
-  p->own.njobs = ls->njobs;
-  p->own.nbmax = ls->nbmax;
-  p->own.Lrmax = ls->Lrmax;
-  delete ls;
+  own_lists_build<T>(p);
   // the cap covers every plan size (M <= 8192 for L <= 2048), so plans of
   // different sizes can share a batched launch
   ck(sizeof(T) == sizeof(double) ? czt_prepare_f64(13) : czt_prepare_f32(13));
@@ -1454,10 +1506,11 @@ int s2dw_alpha_method(s2dw_plan_t p, int j, int dir, int* method, int* fft_len, 
   const auto& G = p->gt[p->grid_of[j]];
   const auto& sgt = p->seg[j];
   int m = 1, len = G.M, ns = 1, sl = 2 * G.L - 1;
-  if (Lj <= (dir == 0 ? kDirectMaxLjAna : kDirectMaxLj)) {
+  (void)Lj;
+  if (p->alpha_mode[dir][j] == 0) {
     m = 0;
     len = ns = sl = 0;
-  } else if (sgt.S > 0) {
+  } else if (p->alpha_mode[dir][j] == 2) {
     m = 2;
     len = 1 << sgt.logM;
     ns = sgt.S;
@@ -1467,6 +1520,205 @@ int s2dw_alpha_method(s2dw_plan_t p, int j, int dir, int* method, int* fft_len, 
   if (fft_len) *fft_len = len;
   if (segments) *segments = ns;
   if (seg_len) *seg_len = sl;
+  return S2DW_OK;
+}
+
+// ---- launch methods and the autotuner -------------------------------------
+static int choices_count(s2dw_plan_t p) { return 2 + 2 * (p->nscale + 1); }
+
+// Whether method v is available for choice idx of the plan (layout of s2dw_plan_choices).
+static bool choice_valid(s2dw_plan_t p, int idx, int v) {
+  if (idx < 2) return v == 0 || v == 1;  // grids without half-length transforms keep the FFT
+  const int j = (idx - 2) / 2, d = (idx - 2) % 2;
+  const int Lj = p->Ycols[j];
+  if (v == 0) return Lj <= (d == 0 ? kDirectMaxLjAna : kDirectMaxLj);  // direct kernels sized for L_j <= 32
+  if (v == 1) return true;
+  if (v == 2) return p->seg[j].S > 0;  // segment tables built at plan creation
+  return false;
+}
+
+static void choices_get(s2dw_plan_t p, int* c) {
+  c[0] = p->beta_mode[0];
+  c[1] = p->beta_mode[1];
+  for (int j = 0; j <= p->nscale; ++j) {
+    c[2 + 2 * j] = p->alpha_mode[0][j];
+    c[3 + 2 * j] = p->alpha_mode[1][j];
+  }
+}
+
+static void choices_put(s2dw_plan_t p, const int* c) {
+  p->beta_mode[0] = c[0];
+  p->beta_mode[1] = c[1];
+  for (int j = 0; j <= p->nscale; ++j) {
+    p->alpha_mode[0][j] = c[2 + 2 * j];
+    p->alpha_mode[1][j] = c[3 + 2 * j];
+  }
+  drop_batches_with(p);
+  if (p->fp64) own_lists_build<double>(p);
+  else own_lists_build<float>(p);
+}
+
+int s2dw_plan_choices(s2dw_plan_t p, int* choices, int* n) {
+  if (!p || !n) return S2DW_EINVAL;
+  const int need = choices_count(p);
+  if (!choices) {
+    *n = need;
+    return S2DW_OK;
+  }
+  if (*n < need) {
+    *n = need;
+    return S2DW_EINVAL;
+  }
+  choices_get(p, choices);
+  *n = need;
+  return S2DW_OK;
+}
+
+int s2dw_plan_set_choices(s2dw_plan_t p, const int* choices, int n) {
+  if (!p || !choices || n != choices_count(p)) return S2DW_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!choice_valid(p, i, choices[i])) return S2DW_EINVAL;
+  try {
+    ck(cudaEventSynchronize(p->last_use));  // this plan's calls so far (the lists are replaced)
+    choices_put(p, choices);
+    ck(cudaStreamSynchronize(p->pst));
+  } catch (const CudaFail& e) {
+    return err_of(e.err);
+  } catch (...) {
+    return S2DW_ECUDA;
+  }
+  return S2DW_OK;
+}
+
+int s2dw_plan_tune(s2dw_plan_t p, int reps, int* choices, int* n) {
+  if (!p || reps < 1 || reps > 64 || (choices && !n)) return S2DW_EINVAL;
+  const int nc = choices_count(p);
+  if (choices && *n < nc) {
+    *n = nc;
+    return S2DW_EINVAL;
+  }
+  cudaStream_t st = p->pst;
+  const size_t el = p->fp64 ? 8 : 4;
+  int64_t wphi = 0;
+  s2dw_query(p, nullptr, nullptr, &wphi, nullptr, nullptr);
+  const size_t fbytes = (size_t)p->L * p->L * 2 * el;
+  const size_t wbytes = ((size_t)p->woff[p->nscale] + (size_t)wphi) * el;
+  void *f = nullptr, *fr = nullptr, *W = nullptr;
+  constexpr int A = s2dw_plan_s::kEvAna, S = s2dw_plan_s::kEvSyn;
+  cudaEvent_t ev[A + S] = {};
+  std::vector<int> cur(nc), best(nc);
+  try {
+    ck(cudaEventSynchronize(p->last_use));
+    amalloc(&f, fbytes, st);
+    amalloc(&fr, fbytes, st);
+    amalloc(&W, wbytes, st);
+    ck(cudaMemsetAsync(f, 0, fbytes, st));
+    ck(cudaMemsetAsync(W, 0, wbytes, st));
+    for (auto& e : ev) ck(cudaEventCreate(&e));
+    CallPtrs ptrs;
+    std::memset(&ptrs, 0, sizeof(ptrs));
+    ptrs.f[0] = f;
+    ptrs.out[0] = fr;
+    ptrs.W[0] = W;
+    ptrs.Wphi[0] = reinterpret_cast<char*>(W) + (size_t)p->woff[p->nscale] * el;
+    // milliseconds of the beta launch and of the alpha launches of each
+    // direction, the minimum over `reps` round trips
+    auto measure = [&](double (&ms)[4]) {
+      for (double& v : ms) v = 1e30;
+      for (int r = 0; r < reps; ++r) {
+        ReduceJobs rj;
+        std::memset(&rj, 0, sizeof(rj));
+        rj.dw[0] = p->own.desc_w;
+        rj.dp[0] = p->own.desc_phi;
+        rj.out[0] = fr;
+        rj.L[0] = p->L;
+        rj.lend[0] = p->lend_w;
+        rj.Lphi[0] = p->Lphi;
+        if (p->fp64) {
+          run_analysis<double>(p->own, ptrs, st, ev);
+          run_synthesis<double>(p->own, ptrs, rj, 1, st, ev + A);
+        } else {
+          run_analysis<float>(p->own, ptrs, st, ev);
+          run_synthesis<float>(p->own, ptrs, rj, 1, st, ev + A);
+        }
+        ck(cudaGetLastError());
+        ck(cudaEventSynchronize(ev[A + S - 1]));
+        float t[4] = {};
+        ck(cudaEventElapsedTime(&t[0], ev[2], ev[3]));          // analysis beta
+        ck(cudaEventElapsedTime(&t[1], ev[A + 3], ev[A + 4]));  // synthesis beta
+        ck(cudaEventElapsedTime(&t[2], ev[3], ev[6]));          // analysis alpha (all launches)
+        ck(cudaEventElapsedTime(&t[3], ev[A + 0], ev[A + 3]));  // synthesis alpha
+        for (int i = 0; i < 4; ++i) ms[i] = std::min(ms[i], (double)t[i]);
+      }
+    };
+    choices_get(p, cur.data());
+    double base[4];
+    choices_put(p, cur.data());
+    measure(base);  // warms up as well
+    measure(base);
+    // coordinate descent: the beta method of each direction, then each
+    // scale's alpha method (largest band first) against its direction's total
+    for (int d = 0; d < 2; ++d) {
+      for (int v = 0; v < 2; ++v) {
+        if (v == cur[d] || !choice_valid(p, d, v)) continue;
+        std::vector<int> trial(cur);
+        trial[d] = v;
+        choices_put(p, trial.data());
+        double ms[4];
+        measure(ms);
+        if (ms[d] < 0.98 * base[d]) {
+          cur = trial;
+          base[d] = ms[d];
+        }
+      }
+    }
+    choices_put(p, cur.data());
+    measure(base);
+    std::vector<int> order(p->nscale + 1);
+    for (int j = 0; j <= p->nscale; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p->Ycols[a] > p->Ycols[b]; });
+    for (int d = 0; d < 2; ++d)
+      for (int j : order) {
+        const int idx = 2 + 2 * j + d;
+        for (int v = 0; v < 3; ++v) {
+          if (v == cur[idx] || !choice_valid(p, idx, v) || p->Ycols[j] <= 0) continue;
+          std::vector<int> trial(cur);
+          trial[idx] = v;
+          choices_put(p, trial.data());
+          double ms[4];
+          measure(ms);
+          if (ms[2 + d] < 0.98 * base[2 + d]) {
+            cur = trial;
+            base[2 + d] = ms[2 + d];
+          }
+        }
+      }
+    choices_put(p, cur.data());
+    ck(cudaStreamSynchronize(st));
+  } catch (const CudaFail& e) {
+    cudaStreamSynchronize(st);
+    for (auto& e2 : ev) if (e2) cudaEventDestroy(e2);
+    afree(f, st);
+    afree(fr, st);
+    afree(W, st);
+    return err_of(e.err);
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    for (auto& e2 : ev) if (e2) cudaEventDestroy(e2);
+    afree(f, st);
+    afree(fr, st);
+    afree(W, st);
+    return S2DW_ECUDA;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  afree(f, st);
+  afree(fr, st);
+  afree(W, st);
+  cudaStreamSynchronize(st);
+  if (choices) {
+    choices_get(p, choices);
+    *n = nc;
+  }
   return S2DW_OK;
 }
 
@@ -1495,8 +1747,10 @@ int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {
   for (auto& t : ls.tiles_w) contract += t.second.second > 0 ? 1 : 0;
   auto has = [&](int k) { return ls.items[k] > 0 ? 1 : 0; };
   const int fpack = (!p->fp64 && ls.njobs > 0 && ls.nbmax > 0) ? 1 : 0;  // f packing of the FP32 contraction
-  if (analysis) *analysis = fpack + contract + has(0) + has(1) + has(4) + has(6) + has(8);
-  if (synthesis) *synthesis = contract + has(2) + has(3) + has(5) + has(7) + has(9) + has(10) + has(11) + has(12) + 1;
+  if (analysis) *analysis = fpack + contract + has(0) + has(1) + has(4) + has(6) + has(8) + has(13);
+  if (synthesis)
+    *synthesis = contract + has(2) + has(3) + has(5) + has(7) + has(9) + has(10) + has(11) + has(12) + has(14) +
+                 has(15) + 1;
   return S2DW_OK;
 }
 

@@ -585,6 +585,232 @@ size_t beta_syn_fft_smem(int maxlogM) {
 }
 
 // ---------------------------------------------------------------------------
+// Beta sums as half-length transforms (L a power of two, L >= 16).  With the
+// fold Yhat_{-m'} = sigma Yhat_{m'} every beta sum is a cosine or sine
+// series in m' evaluated at beta_b = pi (2b+1) / (2N), N = 2L, i.e. a complex
+// DCT-III / DST-III (analysis) or DCT-II / DST-II (synthesis quadrature) of
+// length N, each computed with one complex FFT of length N (the length-4L
+// FFT of k_beta_*_fft computes the same samples with half its output unused):
+//   analysis:  Z_k = (Yhat_k - sigma i Yhat_{N-k}) e^{i pi k/(2N)},
+//              u_n = sum_k Z_k e^{2 pi i k n/N},
+//              X_b(n) = s_b u_n with b(n) = 2n (n < N/2), 2N-1-2n (n >= N/2),
+//              s_b = (-1)^b if sigma = -1, else 1;
+//   synthesis: y_v = sgn_v q_b(v) V_b(v) (sgn_v = -1 for sigma = -1, v >= N/2),
+//              Y = sum_v y_v e^{-2 pi i k v/N},
+//              Vhat_k = e^{-i pi k/(2N)} Y_k + sigma e^{i pi k/(2N)} Y_{N-k} (k >= 1),
+//              Vhat_0 = Y_0 (sigma = +1; for sigma = -1 the m' = 0 entry meets
+//              Delta^l_{0m} Delta^l_{0n} = 0 in the contraction and is set to 0).
+// A CTA runs G = 4096/N transforms side by side, one per group of N/16
+// threads (adjacent columns m of one gamma sample), with the thread-group
+// stages of fft16.cuh.  All shared-memory reads after the FFT are in natural
+// position order (position p holds frequency fft_rev(p); its negation
+// partner N - fft_rev(p) sits in a descending run of positions), and each
+// output row gets the G columns in one contiguous store.  Persistent: the next
+// item's input is staged by cp.async while the current one is transformed.
+// pre: e^{i pi m'/(4L)} at index m' + L - 1 (|m'| < L); post: q_b (real part), b < 2L.
+// ---------------------------------------------------------------------------
+
+// Frequency held at position p after the forward stages (inverse of fft_pos).
+__device__ __forceinline__ int fft_rev(int p, int logM) {
+  const int a = logM >> 2, b = logM & 3;
+  int f = 0;
+  for (int i = 0; i < a; ++i) f |= ((p >> (logM - 4 * (i + 1))) & 15) << (4 * i);
+  if (b) f |= (p & ((1 << b) - 1)) << (4 * a);
+  return f;
+}
+
+// e^{i pi k/(2N)}, k in [0, N), from the table of e^{i pi m'/(4L)}, |m'| < L = N/2
+// (k > L: i e^{i pi (k - 2L)/(4L)}; k = L never multiplies a nonzero value).
+template <typename T>
+__device__ __forceinline__ cx<T> dct_twiddle(const cx<T>* __restrict__ tb, int k, int L) {
+  if (k < L) return __ldg(tb + k);
+  if (k == L) return mkc<T>(0, 0);
+  const cx<T> t = __ldg(tb + (k - 2 * L));
+  return mkc<T>(-t.y, t.x);
+}
+
+constexpr int kDctSpan = 4096;  // G * N: transforms per CTA times their length
+
+template <typename T>
+size_t beta_dct_smem(bool syn) {
+  // FFT buffers (G transforms) + staged input: analysis G rows of at most N/2,
+  // synthesis G columns of N samples
+  return ((size_t)fft_smem_elems(kDctSpan) + (syn ? kDctSpan : kDctSpan / 2)) * sizeof(cx<T>);
+}
+
+template <typename T>
+__device__ __forceinline__ bool beta_dct_ana_staged(int Lj) {
+  return sizeof(T) == 8 || Lj % 2 == 0;  // 16-byte chunks of the contiguous rows
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_beta_ana_dct(const CztSeg<T>* __restrict__ segs, int nseg, int total) {
+  constexpr int EPC = 16 / (int)sizeof(cx<T>);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* stg = A + fft_smem_elems(kDctSpan);  // [gi][Lj] rows of the next item
+  const int tid = threadIdx.x;
+  auto geom = [&](const CztSeg<T>& sp, int it, int& logN, int& G, int& g, int& m0, int& nt) {
+    logN = sp.logM - 1;
+    G = kDctSpan >> logN;
+    const int item = it - sp.start, per_g = (sp.Lj + G - 1) / G;
+    g = item / per_g;
+    m0 = (item % per_g) * G;
+    nt = min(G, sp.Lj - m0);
+  };
+  auto prefetch = [&](int it) {
+    if (it < total) {
+      const CztSeg<T> sp = segs[czt_find_seg<T>(segs, nseg, it)];
+      int logN, G, g, m0, nt;
+      geom(sp, it, logN, G, g, m0, nt);
+      if (beta_dct_ana_staged<T>(sp.Lj)) {
+        const cx<T>* Y = sp.buf_in + ((size_t)g * sp.Lj + m0) * sp.Lj;  // nt consecutive rows
+        const int nchunk = nt * sp.Lj / EPC;
+        for (int i = tid; i < nchunk; i += blockDim.x) cp_async16(stg + i * EPC, Y + i * EPC, 16);
+      }
+    }
+    cp_async_commit();
+  };
+  prefetch(blockIdx.x);
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg, it)];
+    int logN, G, g, m0, nt;
+    geom(sg, it, logN, G, g, m0, nt);
+    const int Nn = 1 << logN, nthr = Nn >> 4, gi = tid / nthr, tg = tid % nthr, ST = fft_smem_elems(Nn);
+    const int Lj = sg.Lj, L = sg.L;
+    const bool staged = beta_dct_ana_staged<T>(Lj);
+    const cx<T>* __restrict__ tb = sg.pre + (L - 1);
+    const int m = m0 + gi;
+    const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
+    const cx<T>* __restrict__ Yg = sg.buf_in + ((size_t)g * Lj + m) * Lj;
+    cx<T>* Ag = A + gi * ST;
+    cp_async_wait<0>();
+    __syncthreads();  // staged rows visible; A free
+    int Rl, nmid;
+    fft_schedule(logN, Rl, nmid);
+    auto yhat = [&](int u) -> cx<T> {
+      if (u >= Lj || gi >= nt) return mkc<T>(0, 0);
+      return staged ? stg[gi * Lj + u] : Yg[u];
+    };
+    // conj(Z_v): the forward stages then give the conjugate of the inverse transform
+    fftg_first_fwd<T>(Ag, Nn, tg, sg.tw, [&](int v) -> cx<T> {
+      const cx<T> a = yhat(v), b = yhat(Nn - v);
+      const cx<T> z = mkc<T>(a.x + sigma * b.y, a.y - sigma * b.x);  // a - sigma i b
+      return cconj<T>(cmul<T>(z, dct_twiddle<T>(tb, v, L)));
+    });
+    __syncthreads();
+    prefetch(it + gridDim.x);  // every staged value has been read
+    int S = Nn >> 4;
+    for (int s = 0; s < nmid; ++s) {
+      fftg_stage16<T, false>(Ag, Nn, S, tg, nthr, sg.tw + fft_twiddle_level_offset(logN, s + 1));
+      __syncthreads();
+      S >>= 4;
+    }
+    fftg_inner<T, 0>(Ag, Ag, Nn, Rl, tg, nthr, nullptr);
+    __syncthreads();
+    // X_b(n) = s_b conj(A[pos]) for the position p holding n; G columns per row
+    cx<T>* __restrict__ X = sg.buf_out + (size_t)g * sg.nb * Lj + m0;
+    for (int p = tid; p < Nn; p += blockDim.x) {
+      const int n = fft_rev(p, logN);
+      const int b = n < (Nn >> 1) ? 2 * n : 2 * Nn - 1 - 2 * n;
+      if (b >= sg.nb) continue;
+      cx<T>* xr = X + (size_t)b * Lj;
+      for (int t = 0; t < nt; ++t) {
+        const T sg_t = (((m0 + t + sg.N - 1) & 1) && (b & 1)) ? T(-1) : T(1);
+        const cx<T> u = A[t * ST + fpad(p)];
+        xr[t] = mkc<T>(sg_t * u.x, -sg_t * u.y);
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restrict__ segs, int nseg, int total) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* stg = A + fft_smem_elems(kDctSpan);  // [gi][v]: column gi in FFT input order
+  const int tid = threadIdx.x;
+  auto geom = [&](const CztSeg<T>& sp, int it, int& logN, int& G, int& g, int& m0, int& nt) {
+    logN = sp.logM - 1;
+    G = kDctSpan >> logN;
+    const int item = it - sp.start, per_g = (sp.Lj + G - 1) / G;
+    g = item / per_g;
+    m0 = (item % per_g) * G;
+    nt = min(G, sp.Lj - m0);
+  };
+  // column t of V_g[b][m0 + t], b < N, staged at v(b) = b/2 (b even), N - 1 - (b-1)/2 (b odd)
+  auto prefetch = [&](int it) {
+    if (it < total) {
+      const CztSeg<T> sp = segs[czt_find_seg<T>(segs, nseg, it)];
+      int logN, G, g, m0, nt;
+      geom(sp, it, logN, G, g, m0, nt);
+      const int Nn = 1 << logN;
+      const cx<T>* V = sp.buf_in + (size_t)g * sp.nb * sp.Lj + m0;
+      for (int i = tid; i < nt * Nn; i += blockDim.x) {
+        const int t = i / Nn, b = i - t * Nn;
+        const int v = (b & 1) ? Nn - 1 - (b >> 1) : (b >> 1);
+        cp_async_ca<sizeof(cx<T>)>(stg + t * Nn + v, V + (size_t)b * sp.Lj + t);
+      }
+    }
+    cp_async_commit();
+  };
+  prefetch(blockIdx.x);
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg, it)];
+    int logN, G, g, m0, nt;
+    geom(sg, it, logN, G, g, m0, nt);
+    const int Nn = 1 << logN, nthr = Nn >> 4, gi = tid / nthr, tg = tid % nthr, ST = fft_smem_elems(Nn);
+    const int Lj = sg.Lj, L = sg.L;
+    const T sigma = ((m0 + gi + sg.N - 1) & 1) ? T(-1) : T(1);
+    const cx<T>* __restrict__ q = sg.post;
+    cx<T>* Ag = A + gi * ST;
+    cp_async_wait<0>();
+    __syncthreads();
+    int Rl, nmid;
+    fft_schedule(logN, Rl, nmid);
+    fftg_first_fwd<T>(Ag, Nn, tg, sg.tw, [&](int v) -> cx<T> {
+      if (gi >= nt) return mkc<T>(0, 0);
+      const int b = v < (Nn >> 1) ? 2 * v : 2 * (Nn - 1 - v) + 1;
+      const T w = __ldg(q + b).x * ((sigma < T(0) && v >= (Nn >> 1)) ? T(-1) : T(1));
+      return cscale<T>(stg[gi * Nn + v], w);
+    });
+    __syncthreads();
+    prefetch(it + gridDim.x);
+    int S = Nn >> 4;
+    for (int s = 0; s < nmid; ++s) {
+      fftg_stage16<T, false>(Ag, Nn, S, tg, nthr, sg.tw + fft_twiddle_level_offset(logN, s + 1));
+      __syncthreads();
+      S >>= 4;
+    }
+    fftg_inner<T, 0>(Ag, Ag, Nn, Rl, tg, nthr, nullptr);
+    __syncthreads();
+    const cx<T>* __restrict__ tb = sg.pre + (L - 1);
+    cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m0;  // row k of Vhat_g[m'][m]
+    for (int p = tid; p < Nn; p += blockDim.x) {
+      const int k = fft_rev(p, logN);
+      if (k >= Lj) continue;
+      const int pp = fft_pos((Nn - k) & (Nn - 1), logN);
+      const cx<T> w = cconj<T>(__ldg(tb + k));  // e^{-i pi k/(2N)}
+      cx<T>* vr = Vh + (size_t)k * Lj;
+      for (int t = 0; t < nt; ++t) {
+        const T sg_t = ((m0 + t + sg.N - 1) & 1) ? T(-1) : T(1);
+        const cx<T> yk = A[t * ST + fpad(p)], ynk = A[t * ST + fpad(pp)];
+        cx<T> o;
+        if (k == 0) {
+          o = sg_t > T(0) ? yk : mkc<T>(0, 0);
+        } else {
+          const cx<T> a = cmul<T>(w, yk), c = cmul<T>(cconj<T>(w), ynk);
+          o = mkc<T>(a.x + sg_t * c.x, a.y + sg_t * c.y);
+        }
+        vr[t] = o;
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // Direct evaluation of the alpha sums for scales with a small band-limit
 // L_j <= kDirectMax: the chirp-z cost does not shrink with L_j (the output
 // grid has 2L-1 points for every scale) while a direct sum costs ~L_j per
@@ -878,6 +1104,19 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
         k_alpha_ana_direct<T><<<grid, block, alpha_ana_direct_smem<T>(), st>>>(segs, nseg, ptrs);
       break;
 
+    case CZT_BETA_ANA_DCT:
+    case CZT_BETA_RS_DCT: {  // persistent
+      const size_t sm = beta_dct_smem<T>(false);
+      const int g = std::min(total_items, alpha_czt_grid<T>(k_beta_ana_dct<T>, sm));
+      k_beta_ana_dct<T><<<g, block, sm, st>>>(segs, nseg, total_items);
+      break;
+    }
+    case CZT_BETA_SYN_DCT: {  // persistent
+      const size_t sm = beta_dct_smem<T>(true);
+      const int g = std::min(total_items, alpha_czt_grid<T>(k_beta_syn_dct<T>, sm));
+      k_beta_syn_dct<T><<<g, block, sm, st>>>(segs, nseg, total_items);
+      break;
+    }
     case CZT_BETA_SYN_FFT: {  // persistent
       const size_t sm = beta_syn_fft_smem<T>(maxlogM);
       const int g = std::min(total_items, alpha_czt_grid<T>(k_beta_syn_fft<T>, sm));
@@ -914,6 +1153,10 @@ cudaError_t czt_set_smem(int maxlogM) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)beta_syn_fft_smem<T>(maxlogM));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_beta_ana_dct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_dct_smem<T>(false));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_beta_syn_dct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_dct_smem<T>(true));
   if (e != cudaSuccess) return e;
   for (auto k : {k_czt_alpha_ana_seg<T, false>, k_czt_alpha_ana_seg<T, true>, k_czt_alpha_syn_seg<T, false>,
                  k_czt_alpha_syn_seg<T, true>}) {

@@ -90,7 +90,10 @@ enum CztKind {
   CZT_ALPHA_SYN_SEG = 9,
   CZT_BETA_MW_DFT = 10,      // MW grid, synthesis: torus coefficients from the L beta samples
   CZT_BETA_RS_FFT = 11,      // MW grid, synthesis: those coefficients evaluated on the DH beta grid
-  CZT_BETA_RS = 12           //   (single FFT, or chirp-z for non-power-of-two L)
+  CZT_BETA_RS = 12,          //   (single FFT, or chirp-z for non-power-of-two L)
+  CZT_BETA_ANA_DCT = 13,     // beta sums as half-length transforms (L a power of two, L >= 16)
+  CZT_BETA_SYN_DCT = 14,
+  CZT_BETA_RS_DCT = 15       //   (MW grid, synthesis: evaluation on the DH beta grid)
 };
 // Or-ed into an alpha chirp-z kind: the list may hold segments with an odd row
 // count N nb (MW grid), whose last row pair has one row.

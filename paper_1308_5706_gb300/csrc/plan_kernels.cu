@@ -514,6 +514,13 @@ cudaError_t launch_chirp_build64(double2* tw, double2* chirp_a, double2* pre_b, 
 
 int twiddle_entries(int logM) { return fft_twiddle_entries(logM); }
 
+cudaError_t launch_twiddles64(double2* tw, int logM, cudaStream_t st) {
+  const int n = fft_twiddle_entries(logM);
+  if (n <= 0) return cudaSuccess;
+  k_twiddles<<<nblk(n, 256), 256, 0, st>>>(tw, logM);
+  return cudaGetLastError();
+}
+
 // MW beta chirp: pre_mw[m' + L - 1] = e^{i pi (m'^2 + m')/n}, |m'| < L, n = 2L-1
 // (the linear term is the grid's offset beta_b = (2b+1) pi / n).
 __global__ void k_mw_pre(double2* pre, int L) {

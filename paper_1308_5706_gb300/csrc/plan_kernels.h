@@ -9,6 +9,7 @@ cudaError_t launch_kernel_values(double* kap, double* phi, double* sabs, double2
                                  int J, double lam, const double* glx, const double* glw, int Q, int P,
                                  double* I0, cudaStream_t st);
 int twiddle_entries(int logM);  // entries of the FFT twiddle table of length 2^logM
+cudaError_t launch_twiddles64(double2* tw, int logM, cudaStream_t st);  // that table (float64)
 cudaError_t launch_mw_pre64(double2* pre, int L, cudaStream_t st);  // MW beta chirp, 2L-1 entries
 // Segmented chirp-z tables (float64): twiddles of length 2^logM and the S
 // analysis / synthesis kernel spectra (S x 2^logM each) of a band Lj.

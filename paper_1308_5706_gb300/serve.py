@@ -10,7 +10,9 @@ Scheduling (host thread, non-blocking):
   * admission: a request becomes ready when it has arrived and, for a
     synthesis, its analysis has completed; it is admitted while the HBM
     footprint of everything in flight or resident (plan workspaces, f and W
-    buffers) stays under the budget, and a stream slot is free;
+    buffers) stays under the budget, and a stream slot is free; a request
+    over the budget waits (a counted deferral) while other batches run, and
+    goes ahead once nothing is on the GPU, so the queue always progresses;
   * continuous batching: each free slot takes the ready requests of one
     direction (up to `max_batch`) and runs them as ONE batched launch set
     (s2dw_analysis_batch / s2dw_synthesis_batch) on its own CUDA stream, so
@@ -234,7 +236,12 @@ class Server:
                     if (kind is not None and r.kind != kind) or len(batch) >= self.max_batch:
                         continue
                     fp = self._footprint(r)
-                    if fp > budget_left and (batch or self.in_use > 0):
+                    # over the budget: wait while other work runs (it frees memory);
+                    # with nothing on the GPU the request goes ahead, so the queue
+                    # always progresses (resident W that waits for its synthesis is
+                    # not work in flight)
+                    running = any(b is not None for b in busy)
+                    if fp > budget_left and (batch or running):
                         self.rejected += 1
                         continue
                     p = self._take_plan(r)

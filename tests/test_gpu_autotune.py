@@ -1,0 +1,130 @@
+"""Launch methods and the autotuner: every available method of the beta and
+alpha sums gives the oracle's coefficients (FP64 within 1e-11, mixed within
+1e-5), invalid choices are refused, and a tuned plan agrees with the default
+plan and is not slower than it."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1308_5706_gb300 import binding as B
+from paper_1308_5706_gb300.inputs import flm_gaussian
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(p, f):
+    import torch
+    W, Wp = p.alloc_w()
+    p.analysis(f, W, Wp)
+    fr = p.alloc_flm()
+    p.synthesis(W, Wp, fr)
+    torch.cuda.synchronize()
+    return W, Wp, fr
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 1e-5)])
+def test_every_method_matches_the_oracle(prec, tol):
+    import torch
+    L, N, lam, J0 = 64, 3, 2.0, 1
+    f = flm_gaussian(L, 21, "cl")
+    Wo, Wpo = O.analysis(f, L, N, lam, J0)
+    p = B.Plan(L, N, lam, J0, prec)
+    cd, _ = p.torch_dtypes()
+    fd = torch.from_numpy(f).to(cd).cuda()
+    base = p.choices()
+    nsc = (len(base) - 2) // 2
+    # every alternative of each choice, one at a time
+    trials = []
+    for i in range(2):
+        trials.append((i, 1 - base[i]))
+    for j in range(nsc):
+        for d in range(2):
+            for v in (0, 1, 2):
+                if v != base[2 + 2 * j + d]:
+                    trials.append((2 + 2 * j + d, v))
+    tried = 0
+    for idx, v in trials:
+        ch = list(base)
+        ch[idx] = v
+        try:
+            p.set_choices(ch)
+        except B.S2dwError as e:
+            assert e.status == B.S2DW_EINVAL   # method not available for that scale
+            continue
+        tried += 1
+        W, Wp, fr = _run(p, fd)
+        assert p.choices() == ch
+        Wn = W.double().cpu().numpy()
+        assert _rel(Wn, Wo) < tol, (idx, v)
+        assert _rel(Wp.double().cpu().numpy(), Wpo) < tol or np.abs(Wpo).max() == 0
+        assert _rel(fr.to(torch.complex128).cpu().numpy(), f) < tol, (idx, v)
+    assert tried >= 4
+    p.close()
+
+
+def test_invalid_choices_are_refused():
+    p = B.Plan(64, 3, 2.0, 0, "mixed")
+    ch = p.choices()
+    with pytest.raises(B.S2dwError) as ei:
+        p.set_choices(ch[:-1])
+    assert ei.value.status == B.S2DW_EINVAL
+    bad = list(ch)
+    bad[0] = 7
+    with pytest.raises(B.S2dwError):
+        p.set_choices(bad)
+    # direct sums are sized for bands up to 32: not available for the largest scale
+    bad = list(ch)
+    bad[2] = 0
+    with pytest.raises(B.S2dwError):
+        p.set_choices(bad)
+    assert p.choices() == ch
+    p.close()
+
+
+def test_tuned_plan_agrees_with_default_and_is_not_slower(tmp_path, monkeypatch):
+    import torch
+    monkeypatch.setenv("S2DW_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    L, N = 512, 5
+    f = torch.from_numpy(flm_gaussian(L, 2, "cl")).to(torch.complex64).cuda()
+    pd = B.Plan(L, N, 2.0, 0, "mixed")
+    pt = B.Plan(L, N, 2.0, 0, "mixed", autotune=True)
+    assert pt.tuned[1] == "tuned"
+    Wd, Wpd, frd = _run(pd, f)
+    Wt, Wpt, frt = _run(pt, f)
+    for j in range(pd.nscale):
+        ref = Wd[j].abs().max()
+        if float(ref) > 0:
+            assert float((Wt[j] - Wd[j]).abs().max() / ref) < 1e-5
+    f0 = f.to(torch.complex128)
+    assert float((frt.to(torch.complex128) - f0).abs().max() / f0.abs().max()) < 1e-5
+
+    def timed(p):
+        W, Wp = p.alloc_w()
+        fr = p.alloc_flm()
+        for _ in range(3):
+            p.analysis(f, W, Wp)
+            p.synthesis(W, Wp, fr)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                p.analysis(f, W, Wp)
+                p.synthesis(W, Wp, fr)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    td, tt = timed(pd), timed(pt)
+    assert tt <= 1.05 * td, (tt, td)
+    # a second plan of the configuration takes the cached choices
+    pc = B.Plan(L, N, 2.0, 0, "mixed", autotune=True)
+    assert pc.tuned == (pt.choices(), "cache")
+    for p in (pd, pt, pc):
+        p.close()
