@@ -240,6 +240,7 @@ struct Lists {
   void* segs[NK] = {};
   int nseg[NK] = {};
   int items[NK] = {};
+  int ulogM[NK] = {};  // the segments' common transform length log2 (0: lengths differ)
   int maxlogM = 0;
   int Lmax = 0;
   int odd = 0;  // CZT_ODD_ROWS when a plan of the list samples the MW grid
@@ -704,6 +705,12 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
     ls->Lrmax = std::max(ls->Lrmax, p->Lrf);
     if (p->mw) ls->odd = CZT_ODD_ROWS;
   }
+  for (int k = 0; k < Lists::NK; ++k) {
+    int u = segs[k].empty() ? 0 : segs[k][0].logM;
+    for (const CztSeg<T>& sg : segs[k])
+      if (sg.logM != u) u = 0;
+    ls->ulogM[k] = u;
+  }
   // longest tasks first (a CTA computing both tiles of a pair counts double)
   auto by_work = [](std::vector<Task>& v, int N) {
     if constexpr (sizeof(T) == sizeof(float)) {
@@ -815,20 +822,20 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
   }
   rec(ev, 2, st);
   launch_czt<T>(CZT_BETA_ANA, reinterpret_cast<const CztSeg<T>*>(ls.segs[0]), ls.nseg[0], ls.items[0], ls.maxlogM,
-                ptrs, st);
+                ptrs, st, ls.ulogM[0]);
   launch_czt<T>(CZT_BETA_ANA_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[6]), ls.nseg[6], ls.items[6],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[6]);
   launch_czt<T>(CZT_BETA_ANA_DCT, reinterpret_cast<const CztSeg<T>*>(ls.segs[13]), ls.nseg[13], ls.items[13],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[13]);
   rec(ev, 3, st);
   launch_czt<T>(CZT_ALPHA_ANA | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[1]);
   rec(ev, 4, st);
   launch_czt<T>(CZT_ALPHA_ANA_SEG | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[8]), ls.nseg[8], ls.items[8],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[8]);
   rec(ev, 5, st);
   launch_czt<T>(CZT_ALPHA_ANA_DIRECT, reinterpret_cast<const CztSeg<T>*>(ls.segs[4]), ls.nseg[4], ls.items[4],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[4]);
   rec(ev, 6, st);
 }
 
@@ -841,29 +848,29 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
   const ContractDesc<T>* dp = reinterpret_cast<const ContractDesc<T>*>(ls.desc_phi);
   rec(ev, 0, st);
   launch_czt<T>(CZT_ALPHA_SYN_DIRECT, reinterpret_cast<const CztSeg<T>*>(ls.segs[5]), ls.nseg[5], ls.items[5],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[5]);
   rec(ev, 1, st);
   launch_czt<T>(CZT_ALPHA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[2]), ls.nseg[2], ls.items[2], ls.maxlogM,
-                ptrs, st);
+                ptrs, st, ls.ulogM[2]);
   rec(ev, 2, st);
   launch_czt<T>(CZT_ALPHA_SYN_SEG | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[9]), ls.nseg[9], ls.items[9],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[9]);
   rec(ev, 3, st);
   // MW grid: V from its L beta samples to the DH grid (torus coefficients, then the DH samples)
   launch_czt<T>(CZT_BETA_MW_DFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[10]), ls.nseg[10], ls.items[10],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[10]);
   launch_czt<T>(CZT_BETA_RS_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[11]), ls.nseg[11], ls.items[11],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[11]);
   launch_czt<T>(CZT_BETA_RS_DCT, reinterpret_cast<const CztSeg<T>*>(ls.segs[15]), ls.nseg[15], ls.items[15],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[15]);
   launch_czt<T>(CZT_BETA_RS, reinterpret_cast<const CztSeg<T>*>(ls.segs[12]), ls.nseg[12], ls.items[12],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[12]);
   launch_czt<T>(CZT_BETA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[3]), ls.nseg[3], ls.items[3], ls.maxlogM,
-                ptrs, st);
+                ptrs, st, ls.ulogM[3]);
   launch_czt<T>(CZT_BETA_SYN_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[7]), ls.nseg[7], ls.items[7],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[7]);
   launch_czt<T>(CZT_BETA_SYN_DCT, reinterpret_cast<const CztSeg<T>*>(ls.segs[14]), ls.nseg[14], ls.items[14],
-                ls.maxlogM, ptrs, st);
+                ls.maxlogM, ptrs, st, ls.ulogM[14]);
   rec(ev, 4, st);
   if constexpr (sizeof(T) == sizeof(float)) {
     for (auto& t : ls.tiles_w)
@@ -902,6 +909,7 @@ void own_lists_build(s2dw_plan_s* p) {
     p->own.segs[k] = ls->segs[k];
     p->own.nseg[k] = ls->nseg[k];
     p->own.items[k] = ls->items[k];
+    p->own.ulogM[k] = ls->ulogM[k];
   }
   p->own.maxlogM = ls->maxlogM;
   p->own.Lmax = ls->Lmax;

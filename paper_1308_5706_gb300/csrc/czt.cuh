@@ -643,7 +643,9 @@ __device__ __forceinline__ bool beta_dct_ana_staged(int Lj) {
   return sizeof(T) == 8 || Lj % 2 == 0;  // 16-byte chunks of the contiguous rows
 }
 
-template <typename T>
+// LOGN > 0: every segment of the launch has transforms of length 2^LOGN (a
+// compile-time length lets the stage loops and index maps fold); 0: any.
+template <typename T, int LOGN>
 __global__ void __launch_bounds__(256) k_beta_ana_dct(const CztSeg<T>* __restrict__ segs, int nseg, int total) {
   constexpr int EPC = 16 / (int)sizeof(cx<T>);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(256) k_beta_ana_dct(const CztSeg<T>* __restric
   cx<T>* stg = A + fft_smem_elems(kDctSpan);  // [gi][Lj] rows of the next item
   const int tid = threadIdx.x;
   auto geom = [&](const CztSeg<T>& sp, int it, int& logN, int& G, int& g, int& m0, int& nt) {
-    logN = sp.logM - 1;
+    logN = LOGN ? LOGN : sp.logM - 1;
     G = kDctSpan >> logN;
     const int item = it - sp.start, per_g = (sp.Lj + G - 1) / G;
     g = item / per_g;
@@ -725,14 +727,14 @@ __global__ void __launch_bounds__(256) k_beta_ana_dct(const CztSeg<T>* __restric
   cp_async_wait<0>();
 }
 
-template <typename T>
+template <typename T, int LOGN>
 __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restrict__ segs, int nseg, int total) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* stg = A + fft_smem_elems(kDctSpan);  // [gi][v]: column gi in FFT input order
   const int tid = threadIdx.x;
   auto geom = [&](const CztSeg<T>& sp, int it, int& logN, int& G, int& g, int& m0, int& nt) {
-    logN = sp.logM - 1;
+    logN = LOGN ? LOGN : sp.logM - 1;
     G = kDctSpan >> logN;
     const int item = it - sp.start, per_g = (sp.Lj + G - 1) / G;
     g = item / per_g;
@@ -1058,7 +1060,7 @@ int alpha_czt_grid(K kernel, size_t smem) {
 
 template <typename T>
 void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items, int maxlogM,
-                     const CallPtrs& ptrs, cudaStream_t st) {
+                     const CallPtrs& ptrs, cudaStream_t st, int uniform_logM = 0) {
   if (total_items <= 0) return;
   const bool odd = (kind & CZT_ODD_ROWS) != 0;
   kind &= ~CZT_ODD_ROWS;
@@ -1105,16 +1107,27 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
       break;
 
     case CZT_BETA_ANA_DCT:
-    case CZT_BETA_RS_DCT: {  // persistent
-      const size_t sm = beta_dct_smem<T>(false);
-      const int g = std::min(total_items, alpha_czt_grid<T>(k_beta_ana_dct<T>, sm));
-      k_beta_ana_dct<T><<<g, block, sm, st>>>(segs, nseg, total_items);
-      break;
-    }
-    case CZT_BETA_SYN_DCT: {  // persistent
-      const size_t sm = beta_dct_smem<T>(true);
-      const int g = std::min(total_items, alpha_czt_grid<T>(k_beta_syn_dct<T>, sm));
-      k_beta_syn_dct<T><<<g, block, sm, st>>>(segs, nseg, total_items);
+    case CZT_BETA_RS_DCT:
+    case CZT_BETA_SYN_DCT: {  // persistent; uniform transform length: the specialised kernel
+      const bool syn = kind == CZT_BETA_SYN_DCT;
+      const size_t sm = beta_dct_smem<T>(syn);
+      const int logN = (uniform_logM > 0) ? uniform_logM - 1 : 0;
+      auto pick = [&](auto ana_k, auto syn_k) {
+        if (syn) {
+          const int g = std::min(total_items, alpha_czt_grid<T>(syn_k, sm));
+          syn_k<<<g, block, sm, st>>>(segs, nseg, total_items);
+        } else {
+          const int g = std::min(total_items, alpha_czt_grid<T>(ana_k, sm));
+          ana_k<<<g, block, sm, st>>>(segs, nseg, total_items);
+        }
+      };
+      switch (logN) {
+        case 11: pick(k_beta_ana_dct<T, 11>, k_beta_syn_dct<T, 11>); break;
+        case 10: pick(k_beta_ana_dct<T, 10>, k_beta_syn_dct<T, 10>); break;
+        case 9: pick(k_beta_ana_dct<T, 9>, k_beta_syn_dct<T, 9>); break;
+        case 8: pick(k_beta_ana_dct<T, 8>, k_beta_syn_dct<T, 8>); break;
+        default: pick(k_beta_ana_dct<T, 0>, k_beta_syn_dct<T, 0>); break;
+      }
       break;
     }
     case CZT_BETA_SYN_FFT: {  // persistent
@@ -1154,10 +1167,16 @@ cudaError_t czt_set_smem(int maxlogM) {
   e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)beta_syn_fft_smem<T>(maxlogM));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_beta_ana_dct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_dct_smem<T>(false));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_beta_syn_dct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_dct_smem<T>(true));
-  if (e != cudaSuccess) return e;
+  for (auto k : {k_beta_ana_dct<T, 0>, k_beta_ana_dct<T, 8>, k_beta_ana_dct<T, 9>, k_beta_ana_dct<T, 10>,
+                 k_beta_ana_dct<T, 11>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_dct_smem<T>(false));
+    if (e != cudaSuccess) return e;
+  }
+  for (auto k : {k_beta_syn_dct<T, 0>, k_beta_syn_dct<T, 8>, k_beta_syn_dct<T, 9>, k_beta_syn_dct<T, 10>,
+                 k_beta_syn_dct<T, 11>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_dct_smem<T>(true));
+    if (e != cudaSuccess) return e;
+  }
   for (auto k : {k_czt_alpha_ana_seg<T, false>, k_czt_alpha_ana_seg<T, true>, k_czt_alpha_syn_seg<T, false>,
                  k_czt_alpha_syn_seg<T, true>}) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)alpha_seg_smem<T>());

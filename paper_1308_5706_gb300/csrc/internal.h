@@ -176,7 +176,7 @@ cudaError_t pair_prepare();
 cudaError_t pair_timeouts(int* count);  // reads and resets the device count
 template <typename T>
 void launch_czt(int kind, const CztSeg<T>* segs, int nseg, int total_items, int maxlogM,
-                const CallPtrs& ptrs, cudaStream_t st);
+                const CallPtrs& ptrs, cudaStream_t st, int uniform_logM);
 template <typename T>
 void launch_syn_reduce(const ReduceJobs& jobs, int njobs, int Lmax, cudaStream_t st);
 
@@ -184,8 +184,8 @@ template <> void launch_contract<float>(int, int, bool, const ContractDesc<float
                                         const CallPtrs&, cudaStream_t);
 template <> void launch_contract<double>(int, int, bool, const ContractDesc<double>*, const TileTask*, int,
                                          const CallPtrs&, cudaStream_t);
-template <> void launch_czt<float>(int, const CztSeg<float>*, int, int, int, const CallPtrs&, cudaStream_t);
-template <> void launch_czt<double>(int, const CztSeg<double>*, int, int, int, const CallPtrs&, cudaStream_t);
+template <> void launch_czt<float>(int, const CztSeg<float>*, int, int, int, const CallPtrs&, cudaStream_t, int);
+template <> void launch_czt<double>(int, const CztSeg<double>*, int, int, int, const CallPtrs&, cudaStream_t, int);
 template <> void launch_syn_reduce<float>(const ReduceJobs&, int, int, cudaStream_t);
 template <> void launch_syn_reduce<double>(const ReduceJobs&, int, int, cudaStream_t);
 cudaError_t czt_prepare_f32(int maxlogM);
