@@ -304,11 +304,13 @@ int s2dw_profile_read(s2dw_plan_t plan, double* ms, int* ncalls);
  *     calls, then rebuilds its launch lists (batched launch lists holding the
  *     plan are dropped).
  *   s2dw_plan_tune(plan, reps, choices, n): times the candidates on the
- *     plan's private stream with scratch buffers it allocates and frees
- *     (coordinate descent: each direction's beta method, then each scale's
- *     alpha method, largest band first, the minimum of `reps` round trips
- *     per trial, a candidate kept when it is 2% faster), applies the best and
- *     writes it to choices (may be NULL).  Synchronous; 1 <= reps <= 64.
+ *     plan's private stream with scratch buffers it allocates and frees (a
+ *     pseudo-random f_lm and the W its analysis writes; coordinate descent:
+ *     each direction's beta method, then each scale's alpha method, largest
+ *     band first, the minimum of `reps` round trips per trial, a candidate
+ *     kept when it is 3% faster in two measurements with the incumbent
+ *     re-timed between them), applies the best and writes it to choices (may
+ *     be NULL).  Synchronous; 1 <= reps <= 64.
  */
 int s2dw_plan_choices(s2dw_plan_t plan, int* choices, int* n);
 int s2dw_plan_set_choices(s2dw_plan_t plan, const int* choices, int n);

@@ -1620,7 +1620,9 @@ int s2dw_plan_tune(s2dw_plan_t p, int reps, int* choices, int* n) {
     amalloc(&f, fbytes, st);
     amalloc(&fr, fbytes, st);
     amalloc(&W, wbytes, st);
-    ck(cudaMemsetAsync(f, 0, fbytes, st));
+    // nonzero inputs: the analysis then writes W of the same kind for the synthesis
+    if (p->fp64) ck(launch_fill_noise<double>(reinterpret_cast<double*>(f), (int64_t)(fbytes / 8), 0x5eedu, st));
+    else ck(launch_fill_noise<float>(reinterpret_cast<float*>(f), (int64_t)(fbytes / 4), 0x5eedu, st));
     ck(cudaMemsetAsync(W, 0, wbytes, st));
     for (auto& e : ev) ck(cudaEventCreate(&e));
     CallPtrs ptrs;
@@ -1659,6 +1661,24 @@ int s2dw_plan_tune(s2dw_plan_t p, int reps, int* choices, int* n) {
         for (int i = 0; i < 4; ++i) ms[i] = std::min(ms[i], (double)t[i]);
       }
     };
+    // the choices now in place beat the incumbent's time base[i] on stage i:
+    // 3 % faster in a first measurement and again in a second one (the
+    // incumbent re-measured between them), so that noise does not switch methods
+    auto better = [&](double (&ms)[4], int i, double (&base)[4]) {
+      measure(ms);
+      if (!(ms[i] < 0.97 * base[i])) return false;
+      std::vector<int> trial(nc);
+      choices_get(p, trial.data());
+      choices_put(p, cur.data());
+      double again[4];
+      measure(again);
+      base[i] = std::min(base[i], again[i]);
+      choices_put(p, trial.data());
+      double ms2[4];
+      measure(ms2);
+      for (int k = 0; k < 4; ++k) ms[k] = std::min(ms[k], ms2[k]);
+      return ms[i] < 0.97 * base[i];
+    };
     choices_get(p, cur.data());
     double base[4];
     choices_put(p, cur.data());
@@ -1673,8 +1693,7 @@ int s2dw_plan_tune(s2dw_plan_t p, int reps, int* choices, int* n) {
         trial[d] = v;
         choices_put(p, trial.data());
         double ms[4];
-        measure(ms);
-        if (ms[d] < 0.98 * base[d]) {
+        if (better(ms, d, base)) {
           cur = trial;
           base[d] = ms[d];
         }
@@ -1694,8 +1713,7 @@ int s2dw_plan_tune(s2dw_plan_t p, int reps, int* choices, int* n) {
           trial[idx] = v;
           choices_put(p, trial.data());
           double ms[4];
-          measure(ms);
-          if (ms[2 + d] < 0.98 * base[2 + d]) {
+          if (better(ms, 2 + d, base)) {
             cur = trial;
             base[2 + d] = ms[2 + d];
           }

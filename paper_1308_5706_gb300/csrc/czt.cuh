@@ -130,7 +130,9 @@ __host__ __device__ constexpr size_t alpha_czt_smem(int maxlogM, bool staging) {
 // direct loads measured faster than staging them ahead.
 // ODD: some segment may have an odd row count (MW grid); the DH grid's even
 // counts compile without the guards.
-template <typename T, bool ODD>
+// LOGM > 0 (here and in the kernels below): every segment of the launch has
+// transforms of length 2^LOGM, a compile-time length; 0: any.
+template <typename T, bool ODD, int LOGM>
 __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __restrict__ segs, int nseg, int maxlogM,
                                                           CallPtrs ptrs) {
   constexpr int NT = alpha_czt_nt(sizeof(T) == 8);
@@ -138,7 +140,8 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __res
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
   const int ST = fft_smem_elems(1 << maxlogM);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
-  const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM, n = 2 * L - 1;
+  const int logM = LOGM ? LOGM : sg.logM;
+  const int Lj = sg.Lj, L = sg.L, M = 1 << logM, n = 2 * L - 1;
   const int p0 = (blockIdx.x - sg.start) * NT;
   const int rows = sg.N * sg.nb;           // rows (g, b); row pair p = rows 2p, 2p+1
   const int nt = min(NT, (ODD ? rows + 1 : rows) / 2 - p0);  // transforms present in this CTA
@@ -154,13 +157,14 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __res
   auto two = [&](int t) { return !ODD || 2 * (p0 + t) + 1 < rows; };
   auto in = [&](int v, int t, cx<T> c) -> cx<T> {
     if (t >= nt) return mkc<T>(0, 0);
+    // X is read once: streaming loads keep L1 for the tables
     if (v < Lj) {
-      const cx<T> x1 = X[(size_t)(2 * t) * Lj + v], x2 = X[(size_t)(2 * t + 1) * Lj + v];
+      const cx<T> x1 = __ldcs(X + (size_t)(2 * t) * Lj + v), x2 = __ldcs(X + (size_t)(2 * t + 1) * Lj + v);
       return cmul<T>(mkc<T>(x1.x - x2.y, x1.y + x2.x), c);  // X1 + i X2
     }
     if (v > M - Lj) {
       const int mm = M - v;
-      const cx<T> x1 = X[(size_t)(2 * t) * Lj + mm], x2 = X[(size_t)(2 * t + 1) * Lj + mm];
+      const cx<T> x1 = __ldcs(X + (size_t)(2 * t) * Lj + mm), x2 = __ldcs(X + (size_t)(2 * t + 1) * Lj + mm);
       return cmul<T>(mkc<T>(x1.x + x2.y, x2.x - x1.y), c);  // conj(X1) + i conj(X2)
     }
     return mkc<T>(0, 0);
@@ -171,14 +175,14 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __res
   auto out = [&](int v, int t, cx<T> y, cx<T> c) {
     if (v < n && t < nt) {
       const cx<T> w = cmul<T>(y, c);
-      Wb[(size_t)(2 * t) * n + v] = w.x;
-      if (two(t)) Wb[(size_t)(2 * t + 1) * n + v] = w.y;
+      __stcs(Wb + (size_t)(2 * t) * n + v, w.x);
+      if (two(t)) __stcs(Wb + (size_t)(2 * t + 1) * n + v, w.y);
     }
   };
-  fft_convolve_n<T, NT, false>(A, ST, sg.logM, sg.H, sg.tw, pre, in, post, out, []() {});
+  fft_convolve_n<T, NT, false>(A, ST, logM, sg.H, sg.tw, pre, in, post, out, []() {});
 }
 
-template <typename T>
+template <typename T, int LOGM>
 __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __restrict__ segs, int nseg, int total,
                                                           int maxlogM, CallPtrs ptrs) {
   constexpr int NT = alpha_czt_nt(sizeof(T) == 8);
@@ -206,7 +210,8 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
   prefetch(it);
   for (; it < total; it += gridDim.x) {
     const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg, it)];
-    const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM, n = 2 * L - 1;
+    const int logM = LOGM ? LOGM : sg.logM;
+    const int Lj = sg.Lj, L = sg.L, M = 1 << logM, n = 2 * L - 1;
     const int p0 = (it - sg.start) * NT;
     const int rows = sg.N * sg.nb;
     const int nt = min(NT, (rows + 1) / 2 - p0);
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
     auto nopost = [](int) -> cx<T> { return mkc<T>(0, 0); };
     auto none = [](int, int, cx<T>, cx<T>) {};
     const int next = it + gridDim.x;
-    fft_convolve_n<T, NT, true>(A, ST, sg.logM, sg.H, sg.tw, pre, in, nopost, none, [&]() { prefetch(next); });
+    fft_convolve_n<T, NT, true>(A, ST, logM, sg.H, sg.tw, pre, in, nopost, none, [&]() { prefetch(next); });
     const T h = sg.scale * T(0.5);
     for (int mm = threadIdx.x; mm < Lj; mm += blockDim.x) {
       const cx<T> ch = __ldg(sg.post + mm);
@@ -254,12 +259,12 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
 // domain, then one inverse FFT.  S + 1 FFTs of M' replace two of M.  A CTA
 // runs G = 4096 / M' row pairs side by side, one per group of M'/16 threads.
 // ---------------------------------------------------------------------------
-template <typename T, bool ODD>
-__global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
-  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
-  const int logM = sg.logM, M = 1 << logM, nthr = M / 16, G = 256 / nthr;
+// The analysis kernel branches once per CTA (its segment's length M') to a
+// body compiled for that length (FP32 DH plans: M' = 2^9 .. 2^11; others,
+// and the FP64 and MW-grid instantiations, take the runtime-length body).
+template <typename T, bool ODD, int LOGM>
+__device__ __forceinline__ void alpha_ana_seg_body(const CztSeg<T>& sg, const CallPtrs& ptrs, cx<T>* sm) {
+  const int logM = LOGM ? LOGM : sg.logM, M = 1 << logM, nthr = M / 16, G = 256 / nthr;
   const int g = threadIdx.x / nthr, tid = threadIdx.x % nthr, ST = fft_smem_elems(M);
   cx<T>* Y = sm + g * ST;
   cx<T>* Z = sm + (G + g) * ST;
@@ -274,13 +279,13 @@ __global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __re
   // y_m = (X1 + i X2)_m e^{i pi m^2/n} at position m mod M
   fftg_first_fwd<T>(Y, M, tid, sg.tw, [&](int v) -> cx<T> {
     if (!valid) return mkc<T>(0, 0);
-    if (v < Lj) {
-      const cx<T> x1 = X[v], x2 = X[Lj + v];  // a missing partner: the zero row after the last
+    if (v < Lj) {  // X read once: streaming loads
+      const cx<T> x1 = __ldcs(X + v), x2 = __ldcs(X + Lj + v);  // a missing partner: the zero row after the last
       return cmul<T>(mkc<T>(x1.x - x2.y, x1.y + x2.x), __ldg(sg.pre + v));
     }
     if (v > M - Lj) {
       const int mm = M - v;
-      const cx<T> x1 = X[mm], x2 = X[Lj + mm];
+      const cx<T> x1 = __ldcs(X + mm), x2 = __ldcs(X + Lj + mm);
       return cmul<T>(mkc<T>(x1.x + x2.y, x2.x - x1.y), __ldg(sg.pre + mm));  // conj(X1) + i conj(X2)
     }
     return mkc<T>(0, 0);
@@ -302,8 +307,8 @@ __global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __re
       const int a = as + v;
       if (valid && v < P && a < n) {
         const cx<T> w = cmul<T>(y, __ldg(sg.post + a));
-        Wb[a] = w.x;
-        if (two) Wb[n + a] = w.y;
+        __stcs(Wb + a, w.x);
+        if (two) __stcs(Wb + n + a, w.y);
       }
     });
     __syncthreads();  // Z is rewritten by the next segment
@@ -311,11 +316,24 @@ __global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __re
 }
 
 template <typename T, bool ODD>
-__global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+__global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
-  const int logM = sg.logM, M = 1 << logM, nthr = M / 16, G = 256 / nthr;
+  if constexpr (sizeof(T) == sizeof(float) && !ODD) {
+    switch (sg.logM) {
+      case 9: alpha_ana_seg_body<T, ODD, 9>(sg, ptrs, sm); return;
+      case 10: alpha_ana_seg_body<T, ODD, 10>(sg, ptrs, sm); return;
+      case 11: alpha_ana_seg_body<T, ODD, 11>(sg, ptrs, sm); return;
+      default: break;
+    }
+  }
+  alpha_ana_seg_body<T, ODD, 0>(sg, ptrs, sm);
+}
+
+template <typename T, bool ODD, int LOGM>
+__device__ __forceinline__ void alpha_syn_seg_body(const CztSeg<T>& sg, const CallPtrs& ptrs, cx<T>* sm) {
+  const int logM = LOGM ? LOGM : sg.logM, M = 1 << logM, nthr = M / 16, G = 256 / nthr;
   const int g = threadIdx.x / nthr, tid = threadIdx.x % nthr, ST = fft_smem_elems(M);
   cx<T>* ACC = sm + g * ST;
   cx<T>* B = sm + (G + g) * ST;
@@ -339,7 +357,7 @@ __global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __re
     fftg_first_fwd<T>(B, M, tid, sg.tw, [&](int v) -> cx<T> {
       const int a = as + v;
       if (!valid || v >= P || a >= n) return mkc<T>(0, 0);
-      return cmulc<T>(mkc<T>(Wr[a], Wr[o2 + a]), __ldg(sg.pre + a));
+      return cmulc<T>(mkc<T>(__ldcs(Wr + a), __ldcs(Wr + o2 + a)), __ldg(sg.pre + a));
     });
     __syncthreads();
     fftg_stage16<T, false>(B, M, M / 16, tid, nthr, tw1);
@@ -364,6 +382,15 @@ __global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __re
     V1[mm] = mkc<T>((zp.x + zm.x) * h, (zp.y - zm.y) * h);
     if (two) V1[Lj + mm] = mkc<T>((zp.y + zm.y) * h, (zm.x - zp.x) * h);
   }
+}
+
+template <typename T, bool ODD>
+__global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
+  // (the bodies compiled per length measured slower here than this one)
+  alpha_syn_seg_body<T, ODD, 0>(sg, ptrs, sm);
 }
 
 template <typename T>
@@ -414,7 +441,7 @@ __device__ __forceinline__ bool beta_ana_staged(int Lj) {
   return sizeof(T) == 8 || Lj % 2 == 0;
 }
 
-template <typename T>
+template <typename T, int LOGM>
 __global__ void __launch_bounds__(256, 2) k_beta_ana_fft(const CztSeg<T>* __restrict__ segs, int nseg, int total,
                                                          int maxlogM) {
   constexpr int NT = beta_fft_nt(sizeof(T) == 8);
@@ -440,7 +467,7 @@ __global__ void __launch_bounds__(256, 2) k_beta_ana_fft(const CztSeg<T>* __rest
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg, it)];
     const int item = it - sg.start;
-    const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM, ST = fft_smem_elems(M);
+    const int Lj = sg.Lj, L = sg.L, logM = LOGM ? LOGM : sg.logM, M = 1 << logM, ST = fft_smem_elems(M);
     const int per_g = (Lj + NT - 1) / NT;
     const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
     const bool staged = beta_ana_staged<T>(Lj);
@@ -497,7 +524,7 @@ __device__ __forceinline__ bool beta_syn_staged(int Lj, int nt) {
   return NT * sizeof(cx<T>) == 16 && nt == NT && (sizeof(T) == 8 || Lj % 2 == 0);
 }
 
-template <typename T>
+template <typename T, int LOGM>
 __global__ void __launch_bounds__(256, 2) k_beta_syn_fft(const CztSeg<T>* __restrict__ segs, int nseg, int total,
                                                          int maxlogM) {
   constexpr int NT = beta_fft_nt(sizeof(T) == 8);
@@ -521,7 +548,7 @@ __global__ void __launch_bounds__(256, 2) k_beta_syn_fft(const CztSeg<T>* __rest
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg, it)];
     const int item = it - sg.start;
-    const int Lj = sg.Lj, L = sg.L, logM = sg.logM, M = 1 << logM, ST = fft_smem_elems(M);
+    const int Lj = sg.Lj, L = sg.L, logM = LOGM ? LOGM : sg.logM, M = 1 << logM, ST = fft_smem_elems(M);
     const int per_g = (Lj + NT - 1) / NT;
     const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
     const bool staged = beta_syn_staged<T>(Lj, nt);
@@ -1064,8 +1091,16 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
   if (total_items <= 0) return;
   const bool odd = (kind & CZT_ODD_ROWS) != 0;
   kind &= ~CZT_ODD_ROWS;
+  // FP32 launches whose segments share one transform length of 2^11 .. 2^13
+  // take the kernels compiled for that length
+  const int ulog = (sizeof(T) == sizeof(float) && uniform_logM >= 11 && uniform_logM <= 13) ? uniform_logM : 0;
   if (kind == CZT_ALPHA_ANA) {
-    auto k = odd ? k_czt_alpha_ana<T, true> : k_czt_alpha_ana<T, false>;
+    auto k = odd ? k_czt_alpha_ana<T, true, 0> : k_czt_alpha_ana<T, false, 0>;
+    if constexpr (sizeof(T) == sizeof(float)) {
+      if (!odd && ulog == 11) k = k_czt_alpha_ana<T, false, 11>;
+      if (!odd && ulog == 12) k = k_czt_alpha_ana<T, false, 12>;
+      if (!odd && ulog == 13) k = k_czt_alpha_ana<T, false, 13>;
+    }
     k<<<total_items, 256, alpha_czt_smem<T>(maxlogM, false), st>>>(segs, nseg, maxlogM, ptrs);
     return;
   }
@@ -1081,8 +1116,14 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
   }
   if (kind == CZT_ALPHA_SYN) {
     const size_t sm = alpha_czt_smem<T>(maxlogM, true);
-    const int g = std::min(total_items, alpha_czt_grid<T>(k_czt_alpha_syn<T>, sm));
-    k_czt_alpha_syn<T><<<g, 256, sm, st>>>(segs, nseg, total_items, maxlogM, ptrs);
+    auto k = k_czt_alpha_syn<T, 0>;
+    if constexpr (sizeof(T) == sizeof(float)) {
+      if (ulog == 11) k = k_czt_alpha_syn<T, 11>;
+      if (ulog == 12) k = k_czt_alpha_syn<T, 12>;
+      if (ulog == 13) k = k_czt_alpha_syn<T, 13>;
+    }
+    const int g = std::min(total_items, alpha_czt_grid<T>(k, sm));
+    k<<<g, 256, sm, st>>>(segs, nseg, total_items, maxlogM, ptrs);
     return;
   }
   const size_t smem = sizeof(cx<T>) * (size_t)fft_smem_elems(1 << maxlogM);
@@ -1095,8 +1136,14 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
     case CZT_BETA_RS_FFT:
     case CZT_BETA_ANA_FFT: {  // persistent
       const size_t sm = beta_ana_fft_smem<T>(maxlogM);
-      const int g = std::min(total_items, alpha_czt_grid<T>(k_beta_ana_fft<T>, sm));
-      k_beta_ana_fft<T><<<g, block, sm, st>>>(segs, nseg, total_items, maxlogM);
+      auto k = k_beta_ana_fft<T, 0>;
+      if constexpr (sizeof(T) == sizeof(float)) {
+        if (ulog == 11) k = k_beta_ana_fft<T, 11>;
+        if (ulog == 12) k = k_beta_ana_fft<T, 12>;
+        if (ulog == 13) k = k_beta_ana_fft<T, 13>;
+      }
+      const int g = std::min(total_items, alpha_czt_grid<T>(k, sm));
+      k<<<g, block, sm, st>>>(segs, nseg, total_items, maxlogM);
       break;
     }
     case CZT_ALPHA_ANA_DIRECT:
@@ -1132,8 +1179,14 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
     }
     case CZT_BETA_SYN_FFT: {  // persistent
       const size_t sm = beta_syn_fft_smem<T>(maxlogM);
-      const int g = std::min(total_items, alpha_czt_grid<T>(k_beta_syn_fft<T>, sm));
-      k_beta_syn_fft<T><<<g, block, sm, st>>>(segs, nseg, total_items, maxlogM);
+      auto k = k_beta_syn_fft<T, 0>;
+      if constexpr (sizeof(T) == sizeof(float)) {
+        if (ulog == 11) k = k_beta_syn_fft<T, 11>;
+        if (ulog == 12) k = k_beta_syn_fft<T, 12>;
+        if (ulog == 13) k = k_beta_syn_fft<T, 13>;
+      }
+      const int g = std::min(total_items, alpha_czt_grid<T>(k, sm));
+      k<<<g, block, sm, st>>>(segs, nseg, total_items, maxlogM);
       break;
     }
     case CZT_ALPHA_SYN_DIRECT:
@@ -1154,19 +1207,37 @@ cudaError_t czt_set_smem(int maxlogM) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_czt_beta_ana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  for (auto k : {k_czt_alpha_ana<T, false>, k_czt_alpha_ana<T, true>}) {
+  for (auto k : {k_czt_alpha_ana<T, false, 0>, k_czt_alpha_ana<T, true, 0>}) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)alpha_czt_smem<T>(maxlogM, false));
     if (e != cudaSuccess) return e;
   }
-  e = cudaFuncSetAttribute(k_czt_alpha_syn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_czt_alpha_syn<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)alpha_czt_smem<T>(maxlogM, true));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_beta_ana_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_beta_ana_fft<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)beta_ana_fft_smem<T>(maxlogM));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_beta_syn_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_beta_syn_fft<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)beta_syn_fft_smem<T>(maxlogM));
   if (e != cudaSuccess) return e;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    for (auto k : {k_czt_alpha_ana<T, false, 11>, k_czt_alpha_ana<T, false, 12>, k_czt_alpha_ana<T, false, 13>}) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)alpha_czt_smem<T>(maxlogM, false));
+      if (e != cudaSuccess) return e;
+    }
+    for (auto k : {k_czt_alpha_syn<T, 11>, k_czt_alpha_syn<T, 12>, k_czt_alpha_syn<T, 13>}) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)alpha_czt_smem<T>(maxlogM, true));
+      if (e != cudaSuccess) return e;
+    }
+    for (auto k : {k_beta_ana_fft<T, 11>, k_beta_ana_fft<T, 12>, k_beta_ana_fft<T, 13>}) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_ana_fft_smem<T>(maxlogM));
+      if (e != cudaSuccess) return e;
+    }
+    for (auto k : {k_beta_syn_fft<T, 11>, k_beta_syn_fft<T, 12>, k_beta_syn_fft<T, 13>}) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_syn_fft_smem<T>(maxlogM));
+      if (e != cudaSuccess) return e;
+    }
+  }
   for (auto k : {k_beta_ana_dct<T, 0>, k_beta_ana_dct<T, 8>, k_beta_ana_dct<T, 9>, k_beta_ana_dct<T, 10>,
                  k_beta_ana_dct<T, 11>}) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_dct_smem<T>(false));

@@ -568,4 +568,30 @@ template cudaError_t launch_rtable<double>(double*, const double*, const double*
                                            int, int, int, int, cudaStream_t);
 template cudaError_t launch_to_prec<float>(float2*, const double2*, int64_t, cudaStream_t);
 
+// Timing inputs: a 32-bit integer hash (multiply-xorshift rounds) of the
+// index, scaled to [-1/2, 1/2).  Only the run time of the transforms that read
+// these values matters, not their distribution.
+template <typename T>
+__global__ void k_fill_noise(T* __restrict__ dst, int64_t n, uint32_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 0x9E3779B1u ^ seed ^ (uint32_t)(i >> 32) * 0x85EBCA77u;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    dst[i] = (T)((double)h * (1.0 / 4294967296.0) - 0.5);
+  }
+}
+
+template <typename T>
+cudaError_t launch_fill_noise(T* dst, int64_t n, uint32_t seed, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  k_fill_noise<T><<<(unsigned)blocks, 256, 0, st>>>(dst, n, seed);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fill_noise<float>(float*, int64_t, uint32_t, cudaStream_t);
+template cudaError_t launch_fill_noise<double>(double*, int64_t, uint32_t, cudaStream_t);
+
 }  // namespace s2dw

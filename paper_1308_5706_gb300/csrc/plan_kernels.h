@@ -28,5 +28,8 @@ cudaError_t launch_chirp_build64(double2* tw, double2* chirp_a, double2* pre_b, 
                                  cudaStream_t st);
 template <typename T>
 cudaError_t launch_to_prec(cx<T>* dst, const double2* src, int64_t n, cudaStream_t st);
+// n values of T in [-1/2, 1/2) from a hash of (seed, index): inputs for timing runs
+template <typename T>
+cudaError_t launch_fill_noise(T* dst, int64_t n, uint32_t seed, cudaStream_t st);
 
 }  // namespace s2dw
