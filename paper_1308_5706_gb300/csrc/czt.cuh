@@ -64,11 +64,11 @@ __global__ void __launch_bounds__(256) k_czt_beta_ana(const CztSeg<T>* __restric
     else return mkc<T>(0, 0);
     cx<T> y = Y[mp < 0 ? -mp : mp];
     if (mp < 0) y = cscale<T>(y, sigma);
-    return cmul<T>(y, __ldg(pre + mp));
+    return cmul<T>(y, ldk(pre + mp));
   };
   cx<T>* __restrict__ X = sg.buf_out + (size_t)g * sg.nb * Lj + m;
   auto out = [&](int v, cx<T> val) {
-    if (v < sg.nb) X[(size_t)v * Lj] = cmul<T>(val, __ldg(sg.post + v));
+    if (v < sg.nb) X[(size_t)v * Lj] = cmul<T>(val, ldk(sg.post + v));
   };
   // An odd row count N nb (MW grid) pairs the last row with row N nb of the
   // buffer (which holds 2L rows per gamma sample) in the alpha analysis: zero it.
@@ -101,12 +101,12 @@ __global__ void __launch_bounds__(256) k_beta_mw_dft(const CztSeg<T>* __restrict
     // beta = pi (v = L - 1) is its own reflection: a sigma = -1 column vanishes there
     const cx<T> x = v < L ? cscale<T>(V[(size_t)v * Lj], (v == L - 1 && sigma < T(0)) ? T(0) : T(1))
                           : cscale<T>(V[(size_t)(n - 1 - v) * Lj], sigma);
-    return cmulc<T>(x, __ldg(sg.pre + v));  // sg.pre: e^{i pi b^2/n}
+    return cmulc<T>(x, ldk(sg.pre + v));  // sg.pre: e^{i pi b^2/n}
   };
   cx<T>* __restrict__ C = sg.buf_out + ((size_t)g * Lj + m) * Lj;  // c_p, p < Lj
   const T inv_n = T(1) / T(n);
   auto out = [&](int v, cx<T> val) {
-    if (v < Lj) C[v] = cscale<T>(cmulc<T>(val, __ldg(sg.post + (L - 1) + v)), inv_n);  // sg.post: MW chirp
+    if (v < Lj) C[v] = cscale<T>(cmulc<T>(val, ldk(sg.post + (L - 1) + v)), inv_n);  // sg.post: MW chirp
   };
   fft_convolve<T, false>(A, sg.logM, sg.H, sg.tw, in, out);
 }
@@ -148,8 +148,8 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __res
   const cx<T>* __restrict__ X = sg.buf_in + (size_t)(2 * p0) * Lj;
   // input position v holds m = v (v < Lj) or m = v - M (v > M - Lj)
   auto pre = [&](int v) -> cx<T> {
-    if (v < Lj) return __ldg(sg.pre + v);
-    if (v > M - Lj) return __ldg(sg.pre + (M - v));
+    if (v < Lj) return ldk(sg.pre + v);
+    if (v > M - Lj) return ldk(sg.pre + (M - v));
     return mkc<T>(0, 0);
   };
   // an odd row count (MW grid) leaves the last pair one row; its partner is
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __res
   };
   T* __restrict__ Wb = reinterpret_cast<T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff +
                        (size_t)(2 * p0) * n;
-  auto post = [&](int v) -> cx<T> { return v < n ? __ldg(sg.post + v) : mkc<T>(0, 0); };
+  auto post = [&](int v) -> cx<T> { return v < n ? ldk(sg.post + v) : mkc<T>(0, 0); };
   auto out = [&](int v, int t, cx<T> y, cx<T> c) {
     if (v < n && t < nt) {
       const cx<T> w = cmul<T>(y, c);
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
     const int nt = min(NT, (rows + 1) / 2 - p0);
     cp_async_wait<0>();
     __syncthreads();
-    auto pre = [&](int v) -> cx<T> { return v < n ? __ldg(sg.pre + v) : mkc<T>(0, 0); };
+    auto pre = [&](int v) -> cx<T> { return v < n ? ldk(sg.pre + v) : mkc<T>(0, 0); };
     auto in = [&](int v, int t, cx<T> c) -> cx<T> {
       if (v >= n || t >= nt) return mkc<T>(0, 0);
       return cmulc<T>(mkc<T>(stg[(2 * t) * P + v], stg[(2 * t + 1) * P + v]), c);
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
     fft_convolve_n<T, NT, true>(A, ST, logM, sg.H, sg.tw, pre, in, nopost, none, [&]() { prefetch(next); });
     const T h = sg.scale * T(0.5);
     for (int mm = threadIdx.x; mm < Lj; mm += blockDim.x) {
-      const cx<T> ch = __ldg(sg.post + mm);
+      const cx<T> ch = ldk(sg.post + mm);
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         if (t >= nt) break;
@@ -281,12 +281,12 @@ __device__ __forceinline__ void alpha_ana_seg_body(const CztSeg<T>& sg, const Ca
     if (!valid) return mkc<T>(0, 0);
     if (v < Lj) {  // X read once: streaming loads
       const cx<T> x1 = __ldcs(X + v), x2 = __ldcs(X + Lj + v);  // a missing partner: the zero row after the last
-      return cmul<T>(mkc<T>(x1.x - x2.y, x1.y + x2.x), __ldg(sg.pre + v));
+      return cmul<T>(mkc<T>(x1.x - x2.y, x1.y + x2.x), ldk(sg.pre + v));
     }
     if (v > M - Lj) {
       const int mm = M - v;
       const cx<T> x1 = __ldcs(X + mm), x2 = __ldcs(X + Lj + mm);
-      return cmul<T>(mkc<T>(x1.x + x2.y, x2.x - x1.y), __ldg(sg.pre + mm));  // conj(X1) + i conj(X2)
+      return cmul<T>(mkc<T>(x1.x + x2.y, x2.x - x1.y), ldk(sg.pre + mm));  // conj(X1) + i conj(X2)
     }
     return mkc<T>(0, 0);
   });
@@ -306,7 +306,7 @@ __device__ __forceinline__ void alpha_ana_seg_body(const CztSeg<T>& sg, const Ca
     fftg_last_inv<T>(Z, M, tid, sg.tw, [&](int v, cx<T> y) {
       const int a = as + v;
       if (valid && v < P && a < n) {
-        const cx<T> w = cmul<T>(y, __ldg(sg.post + a));
+        const cx<T> w = cmul<T>(y, ldk(sg.post + a));
         __stcs(Wb + a, w.x);
         if (two) __stcs(Wb + n + a, w.y);
       }
@@ -357,7 +357,7 @@ __device__ __forceinline__ void alpha_syn_seg_body(const CztSeg<T>& sg, const Ca
     fftg_first_fwd<T>(B, M, tid, sg.tw, [&](int v) -> cx<T> {
       const int a = as + v;
       if (!valid || v >= P || a >= n) return mkc<T>(0, 0);
-      return cmulc<T>(mkc<T>(__ldcs(Wr + a), __ldcs(Wr + o2 + a)), __ldg(sg.pre + a));
+      return cmulc<T>(mkc<T>(__ldcs(Wr + a), __ldcs(Wr + o2 + a)), ldk(sg.pre + a));
     });
     __syncthreads();
     fftg_stage16<T, false>(B, M, M / 16, tid, nthr, tw1);
@@ -375,7 +375,7 @@ __device__ __forceinline__ void alpha_syn_seg_body(const CztSeg<T>& sg, const Ca
   const T h = sg.scale * T(0.5);
   cx<T>* __restrict__ V1 = sg.buf_out + (size_t)(2 * pidx) * Lj;  // V_g[b][m] rows, m fastest
   for (int mm = tid; mm < Lj; mm += nthr) {
-    const cx<T> ch = __ldg(sg.post + mm);
+    const cx<T> ch = ldk(sg.post + mm);
     const cx<T> zp = cmulc<T>(ACC[fpad(mm)], ch);
     const cx<T> zm = cmulc<T>(ACC[fpad((M - mm) & (M - 1))], ch);
     // V1 = (Zp + conj(Zm))/2, V2 = (Zp - conj(Zm))/(2i)
@@ -405,16 +405,16 @@ __global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restric
   const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * sg.nb * Lj + m;  // column m of V_g[b][m]
   auto in = [&](int v) -> cx<T> {
     if (v >= sg.nb) return mkc<T>(0, 0);
-    return cmul<T>(V[(size_t)v * Lj], __ldg(sg.pre + v));
+    return cmul<T>(V[(size_t)v * Lj], ldk(sg.pre + v));
   };
   auto none = [](int, cx<T>) {};
   fft_convolve<T, true>(A, sg.logM, sg.H, sg.tw, in, none);
   cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m;  // column m of Vhat_g[m'][m]
   for (int mp = threadIdx.x; mp < Lj; mp += blockDim.x) {
-    const cx<T> tp = cmul<T>(A[fpad(mp)], __ldg(sg.post + L - 1 + mp));
+    const cx<T> tp = cmul<T>(A[fpad(mp)], ldk(sg.post + L - 1 + mp));
     cx<T> o = tp;
     if (mp > 0) {
-      const cx<T> tm = cmul<T>(A[fpad(M - mp)], __ldg(sg.post + L - 1 - mp));
+      const cx<T> tm = cmul<T>(A[fpad(M - mp)], ldk(sg.post + L - 1 - mp));
       o = mkc<T>(tp.x + sigma * tm.x, tp.y + sigma * tm.y);
     }
     Vh[(size_t)mp * Lj] = o;
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(256, 2) k_beta_ana_fft(const CztSeg<T>* __rest
         const int am = mp < 0 ? -mp : mp;
         cx<T> y = staged ? stg[t * Lj + am] : Y[am];
         if (mp < 0) y = cscale<T>(y, sigma);
-        A[t * ST + fpad(fft_pos(mp & (M - 1), logM))] = cmul<T>(y, __ldg(tb + mp));
+        A[t * ST + fpad(fft_pos(mp & (M - 1), logM))] = cmul<T>(y, ldk(tb + mp));
       }
     }
     __syncthreads();
@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(256, 2) k_beta_syn_fft(const CztSeg<T>* __rest
             for (int t = 0; t < NT; ++t) x[t] = mkc<T>(0, 0);
             return;
           }
-          const T qv = __ldg(q + v).x;
+          const T qv = ldk(q + v).x;
           if (staged) {
 #pragma unroll
             for (int t = 0; t < NT; ++t) x[t] = cscale<T>(stg[v * NT + t], qv);
@@ -587,9 +587,9 @@ __global__ void __launch_bounds__(256, 2) k_beta_syn_fft(const CztSeg<T>* __rest
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         const T sigma = ((m0 + t + sg.N - 1) & 1) ? T(-1) : T(1);
-        o[t] = cmulc<T>(A[t * ST + fpad(fft_pos(mp, logM))], __ldg(tb + mp));
+        o[t] = cmulc<T>(A[t * ST + fpad(fft_pos(mp, logM))], ldk(tb + mp));
         if (mp > 0) {
-          const cx<T> tm = cmulc<T>(A[t * ST + fpad(fft_pos(M - mp, logM))], __ldg(tb - mp));
+          const cx<T> tm = cmulc<T>(A[t * ST + fpad(fft_pos(M - mp, logM))], ldk(tb - mp));
           o[t] = mkc<T>(o[t].x + sigma * tm.x, o[t].y + sigma * tm.y);
         }
       }
@@ -650,9 +650,9 @@ __device__ __forceinline__ int fft_rev(int p, int logM) {
 // (k > L: i e^{i pi (k - 2L)/(4L)}; k = L never multiplies a nonzero value).
 template <typename T>
 __device__ __forceinline__ cx<T> dct_twiddle(const cx<T>* __restrict__ tb, int k, int L) {
-  if (k < L) return __ldg(tb + k);
+  if (k < L) return ldk(tb + k);
   if (k == L) return mkc<T>(0, 0);
-  const cx<T> t = __ldg(tb + (k - 2 * L));
+  const cx<T> t = ldk(tb + (k - 2 * L));
   return mkc<T>(-t.y, t.x);
 }
 
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restric
     fftg_first_fwd<T>(Ag, Nn, tg, sg.tw, [&](int v) -> cx<T> {
       if (gi >= nt) return mkc<T>(0, 0);
       const int b = v < (Nn >> 1) ? 2 * v : 2 * (Nn - 1 - v) + 1;
-      const T w = __ldg(q + b).x * ((sigma < T(0) && v >= (Nn >> 1)) ? T(-1) : T(1));
+      const T w = ldk(q + b).x * ((sigma < T(0) && v >= (Nn >> 1)) ? T(-1) : T(1));
       return cscale<T>(stg[gi * Nn + v], w);
     });
     __syncthreads();
@@ -820,7 +820,7 @@ __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restric
       const int k = fft_rev(p, logN);
       if (k >= Lj) continue;
       const int pp = fft_pos((Nn - k) & (Nn - 1), logN);
-      const cx<T> w = cconj<T>(__ldg(tb + k));  // e^{-i pi k/(2N)}
+      const cx<T> w = cconj<T>(ldk(tb + k));  // e^{-i pi k/(2N)}
       cx<T>* vr = Vh + (size_t)k * Lj;
       for (int t = 0; t < nt; ++t) {
         const T sg_t = ((m0 + t + sg.N - 1) & 1) ? T(-1) : T(1);
@@ -894,7 +894,7 @@ __global__ void __launch_bounds__(256) k_alpha_ana_direct(const CztSeg<T>* __res
     const int du = ok ? (int)(((long long)MS * a) % n) : 0;
 #pragma unroll 8
     for (; m < Lj; m += MS) {  // unrolled: the root loads of 8 steps are in flight together
-      const cx<T> e = ok ? __ldg(root + u) : mkc<T>(0, 0);
+      const cx<T> e = ok ? ldk(root + u) : mkc<T>(0, 0);
       Bs[(2 * m - 1) * kAgCols + pos] = T(2) * e.x;
       Bs[(2 * m) * kAgCols + pos] = T(-2) * e.y;
       u += du;
@@ -1013,10 +1013,10 @@ __global__ void __launch_bounds__(256) k_alpha_syn_direct(const CztSeg<T>* __res
     const int c_lo = (int)(((long long)n * warp) / 8), c_hi = (int)(((long long)n * (warp + 1)) / 8);
     const int a_lo = c_lo + (int)(((long long)(c_hi - c_lo) * sub) / P);
     const int a_hi = c_lo + (int)(((long long)(c_hi - c_lo) * (sub + 1)) / P);
-    const cx<T> st = cconj<T>(__ldg(root + m));
+    const cx<T> st = cconj<T>(ldk(root + m));
     cx<T> w = mkc<T>(1, 0);
     for (int a = a_lo; a < a_hi; ++a) {
-      if (((a - a_lo) & 15) == 0) w = cconj<T>(__ldg(root + (m * a) % n));
+      if (((a - a_lo) & 15) == 0) w = cconj<T>(ldk(root + (m * a) % n));
       T x[R];
       syn_direct_line<T>(Ws + (size_t)a * R, x);
 #pragma unroll

@@ -179,7 +179,7 @@ __device__ __forceinline__ void fft_fwd_stage(cx<T>* A, int M, int S, const cx<T
       DftR<T, R, false>::run(v);
 #pragma unroll
       for (int k = 1; k < R; ++k) {
-        if (t == 0) w[k] = __ldg(tw + (k - 1) * Q + j);
+        if (t == 0) w[k] = ldk(tw + (k - 1) * Q + j);
         v[k] = cmul<T>(v[k], w[k]);
       }
 #pragma unroll
@@ -202,7 +202,7 @@ __device__ __forceinline__ void fft_inv_stage(cx<T>* A, int M, int S, const cx<T
       for (int k = 0; k < R; ++k) v[k] = A[t * ST + fpad(base + Q * k)];
 #pragma unroll
       for (int k = 1; k < R; ++k) {
-        if (t == 0) w[k] = __ldg(tw + (k - 1) * Q + j);
+        if (t == 0) w[k] = ldk(tw + (k - 1) * Q + j);
         v[k] = cmulc<T>(v[k], w[k]);
       }
       DftR<T, R, true>::run(v);
@@ -229,7 +229,7 @@ __device__ __forceinline__ void fft_mid_stage(cx<T>* A, int M, const cx<T>* __re
         DftR<T, R, false>::run(v);
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-          if (t == 0) h[k] = __ldg(H + k * (M / R) + u);
+          if (t == 0) h[k] = ldk(H + k * (M / R) + u);
           v[k] = cmul<T>(v[k], h[k]);
         }
         DftR<T, R, true>::run(v);
@@ -296,7 +296,7 @@ __device__ __forceinline__ void fft_convolve(cx<T>* A, int logM, const cx<T>* __
       DftR<T, 16, false>::run(v);
       if (j) {
 #pragma unroll
-        for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+        for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], ldk(tw + (k - 1) * Q + j));
       }
 #pragma unroll
       for (int k = 0; k < 16; ++k) A[fpad(j + Q * k)] = v[k];
@@ -325,7 +325,7 @@ __device__ __forceinline__ void fft_convolve(cx<T>* A, int logM, const cx<T>* __
       for (int k = 0; k < 16; ++k) v[k] = A[fpad(j + Q * k)];
       if (j) {
 #pragma unroll
-        for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+        for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], ldk(tw + (k - 1) * Q + j));
       }
       DftR<T, 16, true>::run(v);
       if (WRITE_SMEM) {
@@ -391,7 +391,7 @@ __device__ __forceinline__ void fft_forward_from(cx<T>* A, int logM, const cx<T>
       DftR<T, 16, false>::run(v);
       if (j) {
 #pragma unroll
-        for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+        for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], ldk(tw + (k - 1) * Q + j));
       }
 #pragma unroll
       for (int k = 0; k < 16; ++k) A[fpad(j + Q * k)] = v[k];
@@ -431,7 +431,7 @@ __device__ __forceinline__ void fft_inverse_to(cx<T>* A, int logM, const cx<T>* 
     for (int k = 0; k < 16; ++k) v[k] = A[fpad(j + Q * k)];
     if (j) {
 #pragma unroll
-      for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+      for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], ldk(tw + (k - 1) * Q + j));
     }
     DftR<T, 16, true>::run(v);
 #pragma unroll
@@ -463,7 +463,7 @@ __device__ __forceinline__ void fft_convolve_n(cx<T>* A, int ST, int logM, const
         DftR<T, 16, false>::run(v);
 #pragma unroll
         for (int k = 1; k < 16; ++k) {
-          if (t == 0) w[k] = __ldg(tw + (k - 1) * Q + j);
+          if (t == 0) w[k] = ldk(tw + (k - 1) * Q + j);
           v[k] = cmul<T>(v[k], w[k]);
         }
 #pragma unroll
@@ -497,7 +497,7 @@ __device__ __forceinline__ void fft_convolve_n(cx<T>* A, int ST, int logM, const
         for (int k = 0; k < 16; ++k) v[k] = A[t * ST + fpad(j + Q * k)];
 #pragma unroll
         for (int k = 1; k < 16; ++k) {
-          if (t == 0) w[k] = __ldg(tw + (k - 1) * Q + j);
+          if (t == 0) w[k] = ldk(tw + (k - 1) * Q + j);
           v[k] = cmulc<T>(v[k], w[k]);
         }
         DftR<T, 16, true>::run(v);
@@ -565,7 +565,7 @@ __device__ __forceinline__ void fft_forward_from_n(cx<T>* A, int ST, int logM, c
       for (int t = 0; t < NT; ++t) {
         DftR<T, 16, false>::run(v[t]);
 #pragma unroll
-        for (int k = 1; k < 16; ++k) v[t][k] = cmul<T>(v[t][k], __ldg(tw + (k - 1) * Q + j));
+        for (int k = 1; k < 16; ++k) v[t][k] = cmul<T>(v[t][k], ldk(tw + (k - 1) * Q + j));
 #pragma unroll
         for (int k = 0; k < 16; ++k) A[t * ST + fpad(j + Q * k)] = v[t][k];
       }
@@ -607,7 +607,7 @@ __device__ __forceinline__ void fft_inverse_to_n(cx<T>* A, int ST, int logM, con
 #pragma unroll
       for (int k = 0; k < 16; ++k) v[t][k] = A[t * ST + fpad(j + Q * k)];
 #pragma unroll
-      for (int k = 1; k < 16; ++k) v[t][k] = cmulc<T>(v[t][k], __ldg(tw + (k - 1) * Q + j));
+      for (int k = 1; k < 16; ++k) v[t][k] = cmulc<T>(v[t][k], ldk(tw + (k - 1) * Q + j));
       DftR<T, 16, true>::run(v[t]);
     }
 #pragma unroll
@@ -638,7 +638,7 @@ __device__ __forceinline__ void fftg_first_fwd(cx<T>* A, int M, int tid, const c
   for (int r = 0; r < 16; ++r) v[r] = in(j + Q * r);
   DftR<T, 16, false>::run(v);
 #pragma unroll
-  for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+  for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], ldk(tw + (k - 1) * Q + j));
 #pragma unroll
   for (int k = 0; k < 16; ++k) A[fpad(j + Q * k)] = v[k];
 }
@@ -655,10 +655,10 @@ __device__ __forceinline__ void fftg_stage16(cx<T>* A, int M, int S, int tid, in
     if (!INV) {
       DftR<T, 16, false>::run(v);
 #pragma unroll
-      for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+      for (int k = 1; k < 16; ++k) v[k] = cmul<T>(v[k], ldk(tw + (k - 1) * Q + j));
     } else {
 #pragma unroll
-      for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+      for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], ldk(tw + (k - 1) * Q + j));
       DftR<T, 16, true>::run(v);
     }
 #pragma unroll
@@ -682,7 +682,7 @@ __device__ __forceinline__ void fftg_inner_r(const cx<T>* Src, cx<T>* Dst, int M
     if (MODE == 1 || MODE == 3) {
       if (MODE == 1) {
 #pragma unroll
-        for (int k = 0; k < R; ++k) v[k] = cmul<T>(v[k], __ldg(H + k * (M / R) + u));
+        for (int k = 0; k < R; ++k) v[k] = cmul<T>(v[k], ldk(H + k * (M / R) + u));
       }
       DftR<T, R, true>::run(v);
 #pragma unroll
@@ -695,7 +695,7 @@ __device__ __forceinline__ void fftg_inner_r(const cx<T>* Src, cx<T>* Dst, int M
       } else {
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-          const cx<T> p = cmul<T>(v[k], __ldg(H + k * (M / R) + u));
+          const cx<T> p = cmul<T>(v[k], ldk(H + k * (M / R) + u));
           Dst[fpad(base + k)] = first ? p : cadd<T>(Dst[fpad(base + k)], p);
         }
       }
@@ -721,7 +721,7 @@ __device__ __forceinline__ void fftg_last_inv(const cx<T>* A, int M, int tid, co
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = A[fpad(j + Q * k)];
 #pragma unroll
-  for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], __ldg(tw + (k - 1) * Q + j));
+  for (int k = 1; k < 16; ++k) v[k] = cmulc<T>(v[k], ldk(tw + (k - 1) * Q + j));
   DftR<T, 16, true>::run(v);
 #pragma unroll
   for (int r = 0; r < 16; ++r) out(j + Q * r, v[r]);
