@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __res
       if (two(t)) __stcs(Wb + (size_t)(2 * t + 1) * n + v, w.y);
     }
   };
-  fft_convolve_n<T, NT, false>(A, ST, logM, sg.H, sg.tw, pre, in, post, out, []() {});
+  // M >= 4L: the inputs (|m| < L_j <= M/4) sit in the first and last
+  // quarter of the period, the n = 2L-1 outputs in the first half
+  fft_convolve_n<T, NT, false, 0xF00Fu, 0x00FFu>(A, ST, logM, sg.H, sg.tw, pre, in, post, out, []() {});
 }
 
 template <typename T, int LOGM>
@@ -225,7 +227,10 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __res
     auto nopost = [](int) -> cx<T> { return mkc<T>(0, 0); };
     auto none = [](int, int, cx<T>, cx<T>) {};
     const int next = it + gridDim.x;
-    fft_convolve_n<T, NT, true>(A, ST, logM, sg.H, sg.tw, pre, in, nopost, none, [&]() { prefetch(next); });
+    // M >= 4L: the n = 2L-1 inputs sit in the first half of the period, the
+    // outputs m (and M - m), m < L_j <= M/4, in the first and last quarter
+    fft_convolve_n<T, NT, true, 0x00FFu, 0xF00Fu>(A, ST, logM, sg.H, sg.tw, pre, in, nopost, none,
+                                                   [&]() { prefetch(next); });
     const T h = sg.scale * T(0.5);
     for (int mm = threadIdx.x; mm < Lj; mm += blockDim.x) {
       const cx<T> ch = ldk(sg.post + mm);
@@ -491,7 +496,7 @@ __global__ void __launch_bounds__(256, 2) k_beta_ana_fft(const CztSeg<T>* __rest
     prefetch(it + gridDim.x);  // stg has been read by every thread
     cx<T>* __restrict__ X = sg.buf_out + (size_t)g * sg.nb * Lj + m0;
     const bool pair = (NT == 2) && (nt == 2) && (Lj % 2 == 0);  // 16-byte aligned column pairs
-    fft_inverse_to_n<T, NT>(A, ST, logM, sg.tw, [&](int v, const cx<T>* y) {
+    fft_inverse_to_n<T, NT, 0x00FFu>(A, ST, logM, sg.tw, [&](int v, const cx<T>* y) {  // v < 2L = M/2
       if (v < sg.nb) {
         if (pair) {
           *reinterpret_cast<float4*>(X + (size_t)v * Lj) = *reinterpret_cast<const float4*>(y);
@@ -557,7 +562,7 @@ __global__ void __launch_bounds__(256, 2) k_beta_syn_fft(const CztSeg<T>* __rest
     const cx<T>* __restrict__ q = sg.post;
     cp_async_wait<0>();
     __syncthreads();  // staged rows visible; A free
-    fft_forward_from_n<T, NT>(
+    fft_forward_from_n<T, NT, 0x00FFu>(  // inputs b < 2L = M/2
         A, ST, logM, sg.tw,
         [&](int v, cx<T>* x) {
           if (v >= sg.nb) {

@@ -443,8 +443,12 @@ __device__ __forceinline__ void fft_inverse_to(cx<T>* A, int logM, const cx<T>* 
 //   input(v, t, pre(v)) -> element v of transform t;
 //   output(v, t, value, post(v)) consumes element v of transform t;
 //   after_first() runs once all inputs have been read (after the first stage).
-template <typename T, int NT, bool WRITE_SMEM, typename Pre, typename In, typename Post, typename Out,
-          typename AfterFirst>
+// IN_MASK / OUT_MASK: bit r clear means that the inputs v = j + r M/16 are
+// zero (not read) / the outputs there are not needed (neither computed to
+// the end nor passed on or stored): the chirp-z sums have inputs only in the
+// first and last quarter and need outputs in one half of the period.
+template <typename T, int NT, bool WRITE_SMEM, unsigned IN_MASK = 0xFFFFu, unsigned OUT_MASK = 0xFFFFu,
+          typename Pre, typename In, typename Post, typename Out, typename AfterFirst>
 __device__ __forceinline__ void fft_convolve_n(cx<T>* A, int ST, int logM, const cx<T>* __restrict__ H,
                                                const cx<T>* __restrict__ tw, Pre pre, In input, Post post,
                                                Out output, AfterFirst after_first) {
@@ -459,7 +463,7 @@ __device__ __forceinline__ void fft_convolve_n(cx<T>* A, int ST, int logM, const
       for (int t = 0; t < NT; ++t) {
         cx<T> v[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = input(j + Q * r, t, pre(j + Q * r));
+        for (int r = 0; r < 16; ++r) v[r] = ((IN_MASK >> r) & 1u) ? input(j + Q * r, t, pre(j + Q * r)) : mkc<T>(0, 0);
         DftR<T, 16, false>::run(v);
 #pragma unroll
         for (int k = 1; k < 16; ++k) {
@@ -503,10 +507,12 @@ __device__ __forceinline__ void fft_convolve_n(cx<T>* A, int ST, int logM, const
         DftR<T, 16, true>::run(v);
         if (WRITE_SMEM) {
 #pragma unroll
-          for (int r = 0; r < 16; ++r) A[t * ST + fpad(j + Q * r)] = v[r];
+          for (int r = 0; r < 16; ++r)
+            if ((OUT_MASK >> r) & 1u) A[t * ST + fpad(j + Q * r)] = v[r];
         } else {
 #pragma unroll
-          for (int r = 0; r < 16; ++r) output(j + Q * r, t, v[r], post(j + Q * r));
+          for (int r = 0; r < 16; ++r)
+            if ((OUT_MASK >> r) & 1u) output(j + Q * r, t, v[r], post(j + Q * r));
         }
       }
     }
@@ -544,7 +550,8 @@ __device__ __forceinline__ void fft_inner_dispatch_n(cx<T>* A, int M, int Rl, in
 // fft_forward_from on NT transforms: input(v, x) fills x[t], t < NT, with
 // element v of transform t.  after_input() runs once every input has been
 // read (after the first stage's barrier).  Ends with __syncthreads().
-template <typename T, int NT, typename In, typename AfterInput>
+// IN_MASK: bit r clear means that the inputs v = j + r M/16 are zero (not read).
+template <typename T, int NT, unsigned IN_MASK = 0xFFFFu, typename In, typename AfterInput>
 __device__ __forceinline__ void fft_forward_from_n(cx<T>* A, int ST, int logM, const cx<T>* __restrict__ tw,
                                                    In input, AfterInput after_input) {
   const int M = 1 << logM;
@@ -557,7 +564,12 @@ __device__ __forceinline__ void fft_forward_from_n(cx<T>* A, int ST, int logM, c
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         cx<T> x[NT];
-        input(j + Q * r, x);
+        if ((IN_MASK >> r) & 1u) {
+          input(j + Q * r, x);
+        } else {
+#pragma unroll
+          for (int t = 0; t < NT; ++t) x[t] = mkc<T>(0, 0);
+        }
 #pragma unroll
         for (int t = 0; t < NT; ++t) v[t][r] = x[t];
       }
@@ -585,7 +597,8 @@ __device__ __forceinline__ void fft_forward_from_n(cx<T>* A, int ST, int logM, c
 
 // fft_inverse_to on NT transforms: output(v, y) receives element v of every
 // transform (y[t]).  Expects A complete (call after a __syncthreads()).
-template <typename T, int NT, typename Out>
+// OUT_MASK: bit r clear means that the outputs v = j + r M/16 are not needed.
+template <typename T, int NT, unsigned OUT_MASK = 0xFFFFu, typename Out>
 __device__ __forceinline__ void fft_inverse_to_n(cx<T>* A, int ST, int logM, const cx<T>* __restrict__ tw,
                                                  Out output) {
   const int M = 1 << logM;
@@ -612,6 +625,7 @@ __device__ __forceinline__ void fft_inverse_to_n(cx<T>* A, int ST, int logM, con
     }
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
+      if (!((OUT_MASK >> r) & 1u)) continue;
       cx<T> y[NT];
 #pragma unroll
       for (int t = 0; t < NT; ++t) y[t] = v[t][r];
