@@ -312,6 +312,20 @@ def s2dw_plan_tune(plan: int, reps: int = 5):
     return list(arr)
 
 
+_lib_fp = None
+
+
+def lib_fingerprint() -> str:
+    """Short hash of the loaded library file: tuned choices are cached per
+    build, so that a rebuilt library is tuned again."""
+    global _lib_fp
+    if _lib_fp is None:
+        import hashlib
+        with open(LIB_PATH, "rb") as fh:
+            _lib_fp = hashlib.sha1(fh.read()).hexdigest()[:12]
+    return _lib_fp
+
+
 def autotune_cache_path() -> str:
     """JSON file of tuned launch methods: $S2DW_AUTOTUNE_CACHE, else a file in
     the temporary directory."""
@@ -355,7 +369,7 @@ class Plan:
     def tune_key(self) -> str:
         import torch
         return (f"{torch.cuda.get_device_name()}|L={self.L}|N={self.N}|lam={self.lam!r}|J0={self.J0}|"
-                f"{self.precision}|multires={int(self.multires)}|mw={int(self.mw)}")
+                f"{self.precision}|multires={int(self.multires)}|mw={int(self.mw)}|lib={lib_fingerprint()}")
 
     def autotune(self, reps: int = 5):
         """Launch methods from the tuning cache, or tuned now (and cached);
