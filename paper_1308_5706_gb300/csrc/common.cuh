@@ -84,6 +84,13 @@ __device__ __forceinline__ void cp_async_ca(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
 }
+// Asks L2 to fetch the 16-byte aligned part of [p, p + bytes) ahead of use
+// (the bytes must lie inside one allocation; the hint never faults on them).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15, e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  if (e > a) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
+}
+
 // Read-only table loads (twiddles, chirps, kernel spectra) marked to be
 // evicted last from L1, so that the single-use rows streaming past them do
 // not push them out.

@@ -28,6 +28,8 @@
 #pragma once
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "fft16.cuh"
 #include "internal.h"
@@ -132,13 +134,20 @@ __host__ __device__ constexpr size_t alpha_czt_smem(int maxlogM, bool staging) {
 // counts compile without the guards.
 // LOGM > 0 (here and in the kernels below): every segment of the launch has
 // transforms of length 2^LOGM, a compile-time length; 0: any.
+// ahead: CTAs resident at once; a CTA asks L2 for the X rows of the CTA
+// `ahead` places later, which runs about one wave later.
 template <typename T, bool ODD, int LOGM>
 __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __restrict__ segs, int nseg, int maxlogM,
-                                                          CallPtrs ptrs) {
+                                                          CallPtrs ptrs, int ahead) {
   constexpr int NT = alpha_czt_nt(sizeof(T) == 8);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
   const int ST = fft_smem_elems(1 << maxlogM);
+  if (threadIdx.x == 0 && blockIdx.x + ahead < gridDim.x) {
+    const CztSeg<T>& s2 = segs[czt_find_seg<T>(segs, nseg, blockIdx.x + ahead)];
+    const int q0 = (blockIdx.x + ahead - s2.start) * NT, nr = min(2 * NT, s2.N * s2.nb - 2 * q0);
+    if (nr > 0) prefetch_l2(s2.buf_in + (size_t)(2 * q0) * s2.Lj, (size_t)nr * s2.Lj * sizeof(cx<T>));
+  }
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
   const int logM = LOGM ? LOGM : sg.logM;
   const int Lj = sg.Lj, L = sg.L, M = 1 << logM, n = 2 * L - 1;
@@ -320,10 +329,33 @@ __device__ __forceinline__ void alpha_ana_seg_body(const CztSeg<T>& sg, const Ca
   }
 }
 
+// CTA `ahead` places later (about one wave): its rows of the layout its
+// segment uses (G = 4096 / M' row pairs per CTA, rows 2 p0 .. of `base`
+// with `pitch` elements of E per row), asked of L2 ahead of use.
+template <typename T, typename E>
+__device__ __forceinline__ void seg_prefetch_rows(const CztSeg<T>* __restrict__ segs, int nseg, int ahead,
+                                                  const E* base_of_seg_dummy, bool w_rows, const CallPtrs& ptrs) {
+  if (threadIdx.x != 0 || blockIdx.x + ahead >= gridDim.x) return;
+  const int b2 = blockIdx.x + ahead;
+  const CztSeg<T>& s2 = segs[czt_find_seg<T>(segs, nseg, b2)];
+  const int G2 = 4096 >> s2.logM, p0 = (b2 - s2.start) * G2, nr = min(2 * G2, s2.N * s2.nb - 2 * p0);
+  if (nr <= 0) return;
+  (void)base_of_seg_dummy;
+  if (!w_rows) {
+    prefetch_l2(s2.buf_in + (size_t)(2 * p0) * s2.Lj, (size_t)nr * s2.Lj * sizeof(cx<T>));
+  } else {
+    const int n = 2 * s2.L - 1;
+    const T* W = reinterpret_cast<const T*>(s2.is_phi ? ptrs.Wphi[s2.job] : ptrs.W[s2.job]) + s2.woff;
+    prefetch_l2(W + (size_t)(2 * p0) * n, (size_t)nr * n * sizeof(T));
+  }
+}
+
 template <typename T, bool ODD>
-__global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+__global__ void __launch_bounds__(256) k_czt_alpha_ana_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs,
+                                                           int ahead) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  seg_prefetch_rows<T, T>(segs, nseg, ahead, nullptr, false, ptrs);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
   if constexpr (sizeof(T) == sizeof(float) && !ODD) {
     switch (sg.logM) {
@@ -390,9 +422,11 @@ __device__ __forceinline__ void alpha_syn_seg_body(const CztSeg<T>& sg, const Ca
 }
 
 template <typename T, bool ODD>
-__global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs) {
+__global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __restrict__ segs, int nseg, CallPtrs ptrs,
+                                                           int ahead) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  seg_prefetch_rows<T, T>(segs, nseg, ahead, nullptr, true, ptrs);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
   // (the bodies compiled per length measured slower here than this one)
   alpha_syn_seg_body<T, ODD, 0>(sg, ptrs, sm);
@@ -1070,23 +1104,33 @@ size_t alpha_syn_direct_smem(int L) {
   return rows > parts ? rows : parts;
 }
 
-// Resident CTAs of a persistent alpha kernel on this device (cached per
-// device, precision and shared-memory size): 2 per SM when they fit.
+// CTAs of a kernel resident at once on this device (the grid of a
+// persistent kernel; the look-ahead of the L2 prefetches).
 template <typename T, typename K>
 int alpha_czt_grid(K kernel, size_t smem) {
-  static int cache_dev[64][2] = {};
-  static size_t cache_smem[64][2] = {};
+  // cached per (device, kernel, shared-memory size)
+  struct Entry {
+    int dev;
+    const void* fn;
+    size_t smem;
+    int grid;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
   int dev = 0;
   cudaGetDevice(&dev);
-  const int slot = (dev >= 0 && dev < 64) ? dev : 0;
-  const int pi = sizeof(T) == 8 ? 1 : 0;
-  if (cache_dev[slot][pi] > 0 && cache_smem[slot][pi] == smem) return cache_dev[slot][pi];
+  const void* fn = reinterpret_cast<const void*>(kernel);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry& e : cache)
+      if (e.dev == dev && e.fn == fn && e.smem == smem) return e.grid;
+  }
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, smem);
   const int g = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
-  cache_dev[slot][pi] = g;
-  cache_smem[slot][pi] = smem;
+  std::lock_guard<std::mutex> lk(mu);
+  cache.push_back({dev, fn, smem, g});
   return g;
 }
 
@@ -1106,17 +1150,18 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
       if (!odd && ulog == 12) k = k_czt_alpha_ana<T, false, 12>;
       if (!odd && ulog == 13) k = k_czt_alpha_ana<T, false, 13>;
     }
-    k<<<total_items, 256, alpha_czt_smem<T>(maxlogM, false), st>>>(segs, nseg, maxlogM, ptrs);
+    const size_t sm = alpha_czt_smem<T>(maxlogM, false);
+    k<<<total_items, 256, sm, st>>>(segs, nseg, maxlogM, ptrs, alpha_czt_grid<T>(k, sm));
     return;
   }
   if (kind == CZT_ALPHA_ANA_SEG) {
     auto k = odd ? k_czt_alpha_ana_seg<T, true> : k_czt_alpha_ana_seg<T, false>;
-    k<<<total_items, 256, alpha_seg_smem<T>(), st>>>(segs, nseg, ptrs);
+    k<<<total_items, 256, alpha_seg_smem<T>(), st>>>(segs, nseg, ptrs, alpha_czt_grid<T>(k, alpha_seg_smem<T>()));
     return;
   }
   if (kind == CZT_ALPHA_SYN_SEG) {
     auto k = odd ? k_czt_alpha_syn_seg<T, true> : k_czt_alpha_syn_seg<T, false>;
-    k<<<total_items, 256, alpha_seg_smem<T>(), st>>>(segs, nseg, ptrs);
+    k<<<total_items, 256, alpha_seg_smem<T>(), st>>>(segs, nseg, ptrs, alpha_czt_grid<T>(k, alpha_seg_smem<T>()));
     return;
   }
   if (kind == CZT_ALPHA_SYN) {
