@@ -97,6 +97,28 @@ void gauss_legendre(int Q, std::vector<double>& x, std::vector<double>& w) {
 // of a serving process).
 std::mutex g_setup_mu;
 cudaStream_t g_setup_stream[64] = {};
+
+// Kernel attributes (shared-memory limits sized for every plan, L <= 2048)
+// are set once per device and precision under a lock, so that creating a plan
+// in one host thread never changes an attribute of a kernel that another
+// thread is launching.
+std::mutex g_prep_mu;
+void kernels_prepare(bool fp64, bool pair) {
+  int dev = 0;
+  ck(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw CudaFail{cudaErrorInvalidDevice};
+  static unsigned long long done_czt[2] = {0, 0}, done_pair = 0;
+  const unsigned long long bit = 1ull << dev;
+  std::lock_guard<std::mutex> lk(g_prep_mu);
+  if (!(done_czt[fp64 ? 1 : 0] & bit)) {
+    ck(fp64 ? czt_prepare_f64(13) : czt_prepare_f32(13));
+    done_czt[fp64 ? 1 : 0] |= bit;
+  }
+  if (pair && !(done_pair & bit)) {
+    ck(pair_prepare());
+    done_pair |= bit;
+  }
+}
 cudaStream_t setup_stream() {
   int dev = 0;
   ck(cudaGetDevice(&dev));
@@ -1161,7 +1183,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   // ---- descriptors, tiles, launch lists ----
   if (pairc) {
     delta_pair_ensure(p->tab, st);
-    ck(pair_prepare());
+    kernels_prepare(false, true);
   }
   ContractDesc<T> dw, dp;
   const T* delta = (sizeof(T) == sizeof(double)) ? reinterpret_cast<const T*>(p->tab->d64)
@@ -1181,7 +1203,7 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   own_lists_build<T>(p);
   // the cap covers every plan size (M <= 8192 for L <= 2048), so plans of
   // different sizes can share a batched launch
-  ck(sizeof(T) == sizeof(double) ? czt_prepare_f64(13) : czt_prepare_f32(13));
+  kernels_prepare(sizeof(T) == sizeof(double), false);
 }
 
 // sht_mode: the companion plan of s2dw_sht_*: no wavelet scales, N = 1 and

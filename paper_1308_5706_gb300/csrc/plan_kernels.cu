@@ -494,6 +494,15 @@ cudaError_t launch_rtable(T* RS, const double* d64, const double* kap, const dou
   return cudaGetLastError();
 }
 
+// The shared-memory limit of k_chirp_spectra, set to that of the longest
+// transform (M = 2^13, L <= 2048) whatever the call's length: plans built
+// concurrently in several host threads then never lower the limit between
+// another thread's setting and its launch.
+cudaError_t chirp_spectra_prepare() {
+  return cudaFuncSetAttribute(k_chirp_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(double2) * fft_smem_elems(1 << 13));
+}
+
 cudaError_t launch_chirp_build64(double2* tw, double2* chirp_a, double2* pre_b, double2* post_b, double2* preS_b,
                                  double2* postS_b, double2* root_a, double2* bfft, double2* H, const double* q, int L,
                                  int logM,
@@ -506,7 +515,7 @@ cudaError_t launch_chirp_build64(double2* tw, double2* chirp_a, double2* pre_b, 
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int smem = (int)sizeof(double2) * fft_smem_elems(M);
-  err = cudaFuncSetAttribute(k_chirp_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  err = chirp_spectra_prepare();
   if (err != cudaSuccess) return err;
   k_chirp_spectra<<<4, 256, smem, st>>>(H, tw, logM);
   return cudaGetLastError();
@@ -548,7 +557,7 @@ cudaError_t launch_seg_build64(double2* tw, double2* Ha, double2* Hs, int L, int
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int smem = (int)sizeof(double2) * fft_smem_elems(M);
-  err = cudaFuncSetAttribute(k_chirp_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  err = chirp_spectra_prepare();
   if (err != cudaSuccess) return err;
   k_chirp_spectra<<<S, 256, smem, st>>>(Ha, tw, logM);
   k_chirp_spectra<<<S, 256, smem, st>>>(Hs, tw, logM);
