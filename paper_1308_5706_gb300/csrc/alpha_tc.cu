@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
       if (a < n) {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (r0 + j < rend) pw[(size_t)j * n] = v[j];
+          if (r0 + j < rend) __stcs(pw + (size_t)j * n, v[j]);  // written once: streaming
       }
     }
     tc::fence_before();
