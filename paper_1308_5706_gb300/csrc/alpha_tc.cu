@@ -181,10 +181,24 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
     {
       float v[32];
       tc::tmem_ld32(te, v);
-      if (a < n) {
+      // row j at pw + j n: the pointer advances by one row per store, and a
+      // full group of 32 rows (all but the last tile) needs no row test
+      const int jn = rend - r0;
+      if (a < n && jn > 0) {
+        float* q = pw;
+        if (jn >= 32) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (r0 + j < rend) __stcs(pw + (size_t)j * n, v[j]);  // written once: streaming
+          for (int j = 0; j < 32; ++j) {
+            __stcs(q, v[j]);  // written once: streaming
+            q += n;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (j < jn) __stcs(q, v[j]);
+            q += n;
+          }
+        }
       }
     }
     tc::fence_before();
