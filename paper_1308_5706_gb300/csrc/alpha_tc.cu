@@ -279,12 +279,17 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_alpha_syn_tc(const CztSeg<fl
   if (w < kSynProd) {
     // ---- producers: rows w + 8 q (q < 16), samples 32 c + lane ----
     const float* __restrict__ basis = reinterpret_cast<const float*>(sg.H);  // [chunk][B hi, B lo]
+    // row w + 8 q at wrow + 8 q n; rows w + 8 q < nr exist (q < nq)
+    const float* __restrict__ wrow = Wb + (size_t)w * n + lane;
+    const size_t n8 = (size_t)8 * n;
+    const int nq = (nr - w + 7) >> 3;
     auto load = [&](int c, float (&x)[16]) {
-      const int a = kTcKc * c + lane;
+      const bool ain = kTcKc * c + lane < n;
+      const float* __restrict__ p = wrow + kTcKc * c;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const int r = w + 8 * q;
-        x[q] = (r < nr && a < n) ? __ldcs(Wb + (size_t)r * n + a) : 0.f;  // read once: streaming
+        x[q] = (ain && q < nq) ? __ldcs(p) : 0.f;  // read once: streaming
+        p += n8;
       }
     };
     auto fetch_basis = [&](int c) {  // basis chunk c into the B images of stage c % S
