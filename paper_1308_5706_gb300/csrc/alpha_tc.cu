@@ -99,12 +99,16 @@ __global__ void __launch_bounds__(kTcAnaThreads, 1) k_alpha_ana_tc(const CztSeg<
   const bool kin = k < K, kst = k < K8;
   const int o0 = kst ? tc::img_off(rl0, k, K8) : 0, oq = (RS / 8) * (K8 / 4) * tc::kLboF;
   const float* __restrict__ X = reinterpret_cast<const float*>(sg.buf_in);
+  const size_t rsk = (size_t)RS * K;  // elements between the rows q and q + 1 of a thread
   auto load = [&](int i, float (&xr)[16]) {  // NQ <= 16
     const int r = rbeg + i * kTcRows + rl0;
     const float* src = X + (size_t)r * K + k;
+    const int qn = kin ? (rend - r + RS - 1) / RS : 0;  // rows r + q RS < rend exist
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (q < NQ) xr[q] = (kin && r + q * RS < rend) ? __ldg(src + (size_t)q * RS * K) : 0.f;
+    for (int q = 0; q < 16; ++q) {
+      if (q < NQ) xr[q] = q < qn ? __ldg(src) : 0.f;
+      src += rsk;
+    }
   };
   auto store = [&](int stg, const float (&xr)[16]) {
     float* hi = Bimg + (size_t)stg * 2 * img + o0;
