@@ -848,7 +848,7 @@ def main():
                    "grid": "full-resolution DH SO(3) grid per scale: 5 x 2048 x 2047",
                    "parallelism": f"replicas x{world}",
                    "launch_methods": {"choices": pm.tuned[0], "source": pm.tuned[1],
-                                      "layout": "beta ana, beta syn, then alpha ana / syn per scale (s2dw.h)"},
+                                      "layout": "beta ana, beta syn, alpha ana / syn per scale, then the contraction CTA shape (s2dw.h)"},
                    "l2": "inputs larger than L2 (W 0.92 GB, Delta table 0.72 GB per step)"},
         "latency_ms": {"p50": per_sorted[len(per) // 2],
                        "p99": per_sorted[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]},

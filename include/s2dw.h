@@ -288,7 +288,7 @@ int s2dw_profile_read(s2dw_plan_t plan, double* ms, int* ncalls);
 /*
  * Launch methods and the autotuner (the paper has no counterpart: these pick
  * among exact evaluations of the same sums, so results agree to rounding).
- *   Choices of a plan, int[2 + 2 (J+2)]:
+ *   Choices of a plan, int[3 + 2 (J+2)]:
  *   [0] beta sums of the analysis, [1] beta sums of the synthesis:
  *       0 = one FFT of length 4L per column, 1 = one complex DCT/DST of length
  *       2L per column (both where L is a power of two; a grid with other L,
@@ -296,7 +296,10 @@ int s2dw_profile_read(s2dw_plan_t plan, double* ms, int* ncalls);
  *   [2 + 2j] alpha sums of the analysis of scale j (j = J+1: scaling part),
  *   [3 + 2j] of the synthesis: 0 = direct sums (L_j <= 32), 1 = chirp-z of
  *       the grid's length, 2 = segmented chirp-z (where the plan built its
- *       tables, s2dw_alpha_method).
+ *       tables, s2dw_alpha_method);
+ *   [last] the contraction's CTA shape (FP32 plans): 0 = both tiles of a
+ *       pair of 32-wide blocks per CTA (N <= 5), 1 = one tile per CTA (the
+ *       only shape for N > 5); FP64 plans: 0.
  *   s2dw_plan_choices(plan, choices, n): *n in = capacity, out = entries;
  *     choices == NULL only queries *n; S2DW_EINVAL if the capacity is short.
  *   s2dw_plan_set_choices(plan, choices, n): n must be the plan's count and
@@ -307,7 +310,8 @@ int s2dw_profile_read(s2dw_plan_t plan, double* ms, int* ncalls);
  *     plan's private stream with scratch buffers it allocates and frees (a
  *     pseudo-random f_lm and the W its analysis writes; coordinate descent:
  *     each direction's beta method, then each scale's alpha method, largest
- *     band first, the minimum of `reps` round trips per trial, a candidate
+ *     band first, then the contraction's CTA shape (both directions' times),
+ *     the minimum of `reps` round trips per trial, a candidate
  *     kept when it is 3% faster in two measurements with the incumbent
  *     re-timed between them), applies the best and writes it to choices (may
  *     be NULL).  Synchronous; 1 <= reps <= 64.

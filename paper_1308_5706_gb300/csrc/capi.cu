@@ -249,12 +249,15 @@ void delta_release(DeltaTab* t) {
   }
 }
 
+constexpr int kOneTile = 0x100;  // launch-list key flag: FP32 contraction tasks of one tile each
+
 // Device-resident launch lists for a set of jobs (one plan = one job).
 struct Lists {
   void* mem = nullptr;
   void* desc_w = nullptr;     // ContractDesc<T>[njobs]
   void* desc_phi = nullptr;   // ContractDesc<T>[njobs]
-  std::vector<std::pair<int, std::pair<void*, int>>> tiles_w;  // (N, (tiles, count))
+  // (N, or N | kOneTile for FP32 tile-per-CTA tasks, (tiles, count))
+  std::vector<std::pair<int, std::pair<void*, int>>> tiles_w;
   void* tiles_phi = nullptr;
   int ntiles_phi = 0;
   static constexpr int NK = 16;  // chirp-z 0..3, direct alpha 4..5, single-FFT beta 6..7, segmented alpha 8..9,
@@ -351,6 +354,7 @@ struct s2dw_plan_s {
   std::vector<unsigned char> desc_w_host, desc_phi_host;
   std::vector<TileTask> tiles_w_host, tiles_phi_host;  // FP64 plans
   std::vector<PairTask> ptasks_w_host, ptasks_phi_host;  // FP32 plans
+  bool pair_one = false;  // FP32, N <= 5: one tile per CTA instead of a pair (a launch method)
   Lists own;
   // stage timing (s2dw_profile): one set of events per call, up to kProfCalls
   static constexpr int kProfCalls = 256;
@@ -512,10 +516,12 @@ void build_tiles(int Lband, int lend, int TMP, int prob, std::vector<TileTask>& 
 // Tile pairs (p <= q) of a band Lband with l in [32 q, lend]; a pair whose
 // tiles run on separate CTAs (N > 5) becomes two tasks.  Sorted by decreasing
 // work (two tiles count double) so that the long ones start first.
-void build_pair_tasks(int Lband, int lend, int N, int table_Lmax, std::vector<PairTask>& out) {
+// two: one task per pair of tiles (both computed by one CTA, N <= 5), else
+// one task per tile
+void build_pair_tasks(int Lband, int lend, bool two, int table_Lmax, std::vector<PairTask>& out) {
+  out.clear();
   if (Lband <= 0 || lend < 0) return;
   const int nb = (Lband + 31) / 32;
-  const bool two = pair_two_tiles(N);
   for (int q = 0; q < nb; ++q)
     for (int p = 0; p <= q; ++p) {
       const int ls = 32 * q;
@@ -712,9 +718,10 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
       tws = &p->tiles_w_host;
       tps = &p->tiles_phi_host;
     }
+    const int key = p->N | ((sizeof(T) == sizeof(float) && (p->pair_one || !pair_two_tiles(p->N))) ? kOneTile : 0);
     for (Task t : *tws) {
       t.prob = i;
-      tw_byN[p->N].push_back(t);
+      tw_byN[key].push_back(t);
     }
     for (Task t : *tps) {
       t.prob = i;
@@ -734,15 +741,15 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
     ls->ulogM[k] = u;
   }
   // longest tasks first (a CTA computing both tiles of a pair counts double)
-  auto by_work = [](std::vector<Task>& v, int N) {
+  auto by_work = [](std::vector<Task>& v, int key) {
     if constexpr (sizeof(T) == sizeof(float)) {
-      const bool two = pair_two_tiles(N);
+      const bool two = !(key & kOneTile);
       auto work = [two](const PairTask& t) {
         return (long long)(t.lend - t.lstart + 1) * (two && t.p != t.q ? 2 : 1);
       };
       std::stable_sort(v.begin(), v.end(), [&](const PairTask& a, const PairTask& b) { return work(a) > work(b); });
     } else {
-      (void)N;
+      (void)key;
       sort_tiles(v);
     }
   };
@@ -831,10 +838,11 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
   if constexpr (sizeof(T) == sizeof(float)) {
     launch_fpack(dw, ls.njobs, ls.nbmax, ls.Lrmax, ptrs, st);
     for (auto& t : ls.tiles_w)
-      launch_contract_pair(t.first, 2, false, dw, reinterpret_cast<const PairTask*>(t.second.first),
-                           t.second.second, ptrs, st);
+      launch_contract_pair(t.first & ~kOneTile, 2, false, !(t.first & kOneTile), dw,
+                           reinterpret_cast<const PairTask*>(t.second.first), t.second.second, ptrs, st);
     rec(ev, 1, st);
-    launch_contract_pair(1, 1, false, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+    launch_contract_pair(1, 1, false, true, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs,
+                         st);
   } else {
     for (auto& t : ls.tiles_w)
       launch_contract<T>(t.first, 2, false, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
@@ -896,10 +904,11 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
   rec(ev, 4, st);
   if constexpr (sizeof(T) == sizeof(float)) {
     for (auto& t : ls.tiles_w)
-      launch_contract_pair(t.first, 2, true, dw, reinterpret_cast<const PairTask*>(t.second.first), t.second.second,
-                           ptrs, st);
+      launch_contract_pair(t.first & ~kOneTile, 2, true, !(t.first & kOneTile), dw,
+                           reinterpret_cast<const PairTask*>(t.second.first), t.second.second, ptrs, st);
     rec(ev, 5, st);
-    launch_contract_pair(1, 1, true, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs, st);
+    launch_contract_pair(1, 1, true, true, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs,
+                         st);
   } else {
     for (auto& t : ls.tiles_w)
       launch_contract<T>(t.first, 2, true, dw, reinterpret_cast<const TileTask*>(t.second.first), t.second.second,
@@ -1192,8 +1201,18 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   p->desc_w_host.assign(reinterpret_cast<unsigned char*>(&dw), reinterpret_cast<unsigned char*>(&dw) + sizeof(dw));
   p->desc_phi_host.assign(reinterpret_cast<unsigned char*>(&dp), reinterpret_cast<unsigned char*>(&dp) + sizeof(dp));
   if (pairc) {
-    build_pair_tasks(p->L0, p->lend_w, N, p->tab->Lmax, p->ptasks_w_host);
-    build_pair_tasks(p->Lphi, p->lphi, 1, p->tab->Lmax, p->ptasks_phi_host);
+    // default CTA shape: a pair of tiles per CTA reads each Delta block once
+    // but gives half the CTAs; measured on GB300, pairs win only with N >= 2
+    // and at least 3 pairs per SM (L >= 1024), one tile per CTA below
+    {
+      int dev = 0, sms = 0;
+      ck(cudaGetDevice(&dev));
+      ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      const long long nbk = (p->L0 + 31) / 32, npairs = nbk * (nbk + 1) / 2;
+      p->pair_one = pair_two_tiles(N) && !(N >= 2 && npairs >= 3LL * sms);
+    }
+    build_pair_tasks(p->L0, p->lend_w, pair_two_tiles(N) && !p->pair_one, p->tab->Lmax, p->ptasks_w_host);
+    build_pair_tasks(p->Lphi, p->lphi, true, p->tab->Lmax, p->ptasks_phi_host);
   } else {
     build_tiles(p->L0, p->lend_w, p->TMP, 0, p->tiles_w_host);
     build_tiles(p->Lphi, p->lphi, p->TMP, 0, p->tiles_phi_host);
@@ -1554,11 +1573,15 @@ int s2dw_alpha_method(s2dw_plan_t p, int j, int dir, int* method, int* fft_len, 
 }
 
 // ---- launch methods and the autotuner -------------------------------------
-static int choices_count(s2dw_plan_t p) { return 2 + 2 * (p->nscale + 1); }
+static int choices_count(s2dw_plan_t p) { return 3 + 2 * (p->nscale + 1); }
 
 // Whether method v is available for choice idx of the plan (layout of s2dw_plan_choices).
 static bool choice_valid(s2dw_plan_t p, int idx, int v) {
   if (idx < 2) return v == 0 || v == 1;  // grids without half-length transforms keep the FFT
+  if (idx == choices_count(p) - 1) {  // contraction CTA shape (FP32 plans with N <= 5 have two)
+    if (p->fp64) return v == 0;
+    return pair_two_tiles(p->N) ? (v == 0 || v == 1) : v == 1;
+  }
   const int j = (idx - 2) / 2, d = (idx - 2) % 2;
   const int Lj = p->Ycols[j];
   if (v == 0) return Lj <= (d == 0 ? kDirectMaxLjAna : kDirectMaxLj);  // direct kernels sized for L_j <= 32
@@ -1574,6 +1597,7 @@ static void choices_get(s2dw_plan_t p, int* c) {
     c[2 + 2 * j] = p->alpha_mode[0][j];
     c[3 + 2 * j] = p->alpha_mode[1][j];
   }
+  c[choices_count(p) - 1] = p->fp64 ? 0 : ((p->pair_one || !pair_two_tiles(p->N)) ? 1 : 0);
 }
 
 static void choices_put(s2dw_plan_t p, const int* c) {
@@ -1582,6 +1606,13 @@ static void choices_put(s2dw_plan_t p, const int* c) {
   for (int j = 0; j <= p->nscale; ++j) {
     p->alpha_mode[0][j] = c[2 + 2 * j];
     p->alpha_mode[1][j] = c[3 + 2 * j];
+  }
+  if (!p->fp64) {
+    const bool one = c[choices_count(p) - 1] == 1 && pair_two_tiles(p->N);
+    if (one != p->pair_one) {
+      p->pair_one = one;
+      build_pair_tasks(p->L0, p->lend_w, pair_two_tiles(p->N) && !one, p->tab->Lmax, p->ptasks_w_host);
+    }
   }
   drop_batches_with(p);
   if (p->fp64) own_lists_build<double>(p);
@@ -1655,7 +1686,7 @@ int s2dw_plan_tune(s2dw_plan_t p, int reps, int* choices, int* n) {
     ptrs.Wphi[0] = reinterpret_cast<char*>(W) + (size_t)p->woff[p->nscale] * el;
     // milliseconds of the beta launch and of the alpha launches of each
     // direction, the minimum over `reps` round trips
-    auto measure = [&](double (&ms)[4]) {
+    auto measure = [&](double (&ms)[5]) {
       for (double& v : ms) v = 1e30;
       for (int r = 0; r < reps; ++r) {
         ReduceJobs rj;
@@ -1675,34 +1706,37 @@ int s2dw_plan_tune(s2dw_plan_t p, int reps, int* choices, int* n) {
         }
         ck(cudaGetLastError());
         ck(cudaEventSynchronize(ev[A + S - 1]));
-        float t[4] = {};
+        float t[6] = {};
         ck(cudaEventElapsedTime(&t[0], ev[2], ev[3]));          // analysis beta
         ck(cudaEventElapsedTime(&t[1], ev[A + 3], ev[A + 4]));  // synthesis beta
         ck(cudaEventElapsedTime(&t[2], ev[3], ev[6]));          // analysis alpha (all launches)
         ck(cudaEventElapsedTime(&t[3], ev[A + 0], ev[A + 3]));  // synthesis alpha
-        for (int i = 0; i < 4; ++i) ms[i] = std::min(ms[i], (double)t[i]);
+        ck(cudaEventElapsedTime(&t[4], ev[0], ev[2]));          // analysis contractions
+        ck(cudaEventElapsedTime(&t[5], ev[A + 4], ev[A + 6]));  // synthesis contractions
+        t[4] += t[5];
+        for (int i = 0; i < 5; ++i) ms[i] = std::min(ms[i], (double)t[i]);
       }
     };
     // the choices now in place beat the incumbent's time base[i] on stage i:
     // 3 % faster in a first measurement and again in a second one (the
     // incumbent re-measured between them), so that noise does not switch methods
-    auto better = [&](double (&ms)[4], int i, double (&base)[4]) {
+    auto better = [&](double (&ms)[5], int i, double (&base)[5]) {
       measure(ms);
       if (!(ms[i] < 0.97 * base[i])) return false;
       std::vector<int> trial(nc);
       choices_get(p, trial.data());
       choices_put(p, cur.data());
-      double again[4];
+      double again[5];
       measure(again);
       base[i] = std::min(base[i], again[i]);
       choices_put(p, trial.data());
-      double ms2[4];
+      double ms2[5];
       measure(ms2);
-      for (int k = 0; k < 4; ++k) ms[k] = std::min(ms[k], ms2[k]);
+      for (int k = 0; k < 5; ++k) ms[k] = std::min(ms[k], ms2[k]);
       return ms[i] < 0.97 * base[i];
     };
     choices_get(p, cur.data());
-    double base[4];
+    double base[5];
     choices_put(p, cur.data());
     measure(base);  // warms up as well
     measure(base);
@@ -1714,7 +1748,7 @@ int s2dw_plan_tune(s2dw_plan_t p, int reps, int* choices, int* n) {
         std::vector<int> trial(cur);
         trial[d] = v;
         choices_put(p, trial.data());
-        double ms[4];
+        double ms[5];
         if (better(ms, d, base)) {
           cur = trial;
           base[d] = ms[d];
@@ -1734,13 +1768,28 @@ int s2dw_plan_tune(s2dw_plan_t p, int reps, int* choices, int* n) {
           std::vector<int> trial(cur);
           trial[idx] = v;
           choices_put(p, trial.data());
-          double ms[4];
+          double ms[5];
           if (better(ms, 2 + d, base)) {
             cur = trial;
             base[2 + d] = ms[2 + d];
           }
         }
       }
+    // the contraction's CTA shape (both directions)
+    {
+      const int idx = nc - 1;
+      for (int v = 0; v < 2; ++v) {
+        if (v == cur[idx] || !choice_valid(p, idx, v)) continue;
+        std::vector<int> trial(cur);
+        trial[idx] = v;
+        choices_put(p, trial.data());
+        double ms[5];
+        if (better(ms, 4, base)) {
+          cur = trial;
+          base[4] = ms[4];
+        }
+      }
+    }
     choices_put(p, cur.data());
     ck(cudaStreamSynchronize(st));
   } catch (const CudaFail& e) {

@@ -36,42 +36,55 @@ static void pair_one(int ntasks, const ContractDesc<float>* descs, const PairTas
 }
 
 template <int N, int NSLOT>
-static void pair_dir(bool syn, int ntasks, const ContractDesc<float>* descs, const PairTask* tasks,
+static void pair_dir(bool syn, bool two, int ntasks, const ContractDesc<float>* descs, const PairTask* tasks,
                      const CallPtrs& ptrs, cudaStream_t st) {
-  constexpr int H = N <= 5 ? 2 : 1;
-  if (syn) pair_one<N, NSLOT, true, H>(ntasks, descs, tasks, ptrs, st);
-  else pair_one<N, NSLOT, false, H>(ntasks, descs, tasks, ptrs, st);
+  if constexpr (N <= 5) {
+    if (two) {
+      if (syn) pair_one<N, NSLOT, true, 2>(ntasks, descs, tasks, ptrs, st);
+      else pair_one<N, NSLOT, false, 2>(ntasks, descs, tasks, ptrs, st);
+      return;
+    }
+  }
+  if (syn) pair_one<N, NSLOT, true, 1>(ntasks, descs, tasks, ptrs, st);
+  else pair_one<N, NSLOT, false, 1>(ntasks, descs, tasks, ptrs, st);
 }
 
-void launch_contract_pair(int N, int nslot, bool syn, const ContractDesc<float>* descs, const PairTask* tasks,
-                          int ntasks, const CallPtrs& ptrs, cudaStream_t st) {
+void launch_contract_pair(int N, int nslot, bool syn, bool two, const ContractDesc<float>* descs,
+                          const PairTask* tasks, int ntasks, const CallPtrs& ptrs, cudaStream_t st) {
   if (ntasks <= 0) return;
   if (N == 1 && nslot == 1) {
-    pair_dir<1, 1>(syn, ntasks, descs, tasks, ptrs, st);
+    pair_dir<1, 1>(syn, two, ntasks, descs, tasks, ptrs, st);
     return;
   }
   switch (N) {
-    case 1: pair_dir<1, 2>(syn, ntasks, descs, tasks, ptrs, st); break;
-    case 2: pair_dir<2, 2>(syn, ntasks, descs, tasks, ptrs, st); break;
-    case 3: pair_dir<3, 2>(syn, ntasks, descs, tasks, ptrs, st); break;
-    case 4: pair_dir<4, 2>(syn, ntasks, descs, tasks, ptrs, st); break;
-    case 5: pair_dir<5, 2>(syn, ntasks, descs, tasks, ptrs, st); break;
-    case 6: pair_dir<6, 2>(syn, ntasks, descs, tasks, ptrs, st); break;
-    case 7: pair_dir<7, 2>(syn, ntasks, descs, tasks, ptrs, st); break;
-    case 8: pair_dir<8, 2>(syn, ntasks, descs, tasks, ptrs, st); break;
+    case 1: pair_dir<1, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
+    case 2: pair_dir<2, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
+    case 3: pair_dir<3, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
+    case 4: pair_dir<4, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
+    case 5: pair_dir<5, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
+    case 6: pair_dir<6, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
+    case 7: pair_dir<7, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
+    case 8: pair_dir<8, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
     default: break;
   }
 }
 
-template <int N, int NSLOT>
-static cudaError_t pair_attr() {
-  constexpr int H = N <= 5 ? 2 : 1;
+template <int N, int NSLOT, int H>
+static cudaError_t pair_attr_h() {
   cudaError_t e = cudaFuncSetAttribute(k_contract_pair<N, NSLOT, false, H>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)PairGeom<N, NSLOT, false, H>::SMEM);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_contract_pair<N, NSLOT, true, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PairGeom<N, NSLOT, true, H>::SMEM);
+}
+// both CTA shapes for N <= 5 (a pair of tiles or one tile per CTA), one tile above
+template <int N, int NSLOT>
+static cudaError_t pair_attr() {
+  cudaError_t e = pair_attr_h<N, NSLOT, 1>();
+  if (e != cudaSuccess) return e;
+  if constexpr (N <= 5) e = pair_attr_h<N, NSLOT, 2>();
+  return e;
 }
 
 // Shared-memory caps of every instantiation, once per device.

@@ -164,9 +164,11 @@ template <typename T>
 void launch_contract(int N, int nslot, bool syn, const ContractDesc<T>* descs, const TileTask* tiles,
                      int ntiles, const CallPtrs& ptrs, cudaStream_t st);
 // FP32 tile-pair contraction and its tables (contract_pair.cu)
-bool pair_two_tiles(int N);  // one CTA computes both tiles of a pair (N <= 5)
-void launch_contract_pair(int N, int nslot, bool syn, const ContractDesc<float>* descs, const PairTask* tasks,
-                          int ntasks, const CallPtrs& ptrs, cudaStream_t st);
+bool pair_two_tiles(int N);  // a CTA may compute both tiles of a pair (N <= 5)
+// two: the tasks name pairs, each CTA computes both tiles (N <= 5 only);
+// else each task names one tile (its half)
+void launch_contract_pair(int N, int nslot, bool syn, bool two, const ContractDesc<float>* descs,
+                          const PairTask* tasks, int ntasks, const CallPtrs& ptrs, cudaStream_t st);
 void launch_fpack(const ContractDesc<float>* descs, int njobs, int nbmax, int Lrmax, const CallPtrs& ptrs,
                   cudaStream_t st);
 cudaError_t launch_pair_table(float* out, const double* d64, int Lmax, cudaStream_t st);

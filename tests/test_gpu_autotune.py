@@ -36,7 +36,7 @@ def test_every_method_matches_the_oracle(prec, tol):
     cd, _ = p.torch_dtypes()
     fd = torch.from_numpy(f).to(cd).cuda()
     base = p.choices()
-    nsc = (len(base) - 2) // 2
+    nsc = (len(base) - 3) // 2
     # every alternative of each choice, one at a time
     trials = []
     for i in range(2):
@@ -46,6 +46,7 @@ def test_every_method_matches_the_oracle(prec, tol):
             for v in (0, 1, 2):
                 if v != base[2 + 2 * j + d]:
                     trials.append((2 + 2 * j + d, v))
+    trials.append((len(base) - 1, 1 - base[-1]))  # the contraction's CTA shape
     tried = 0
     for idx, v in trials:
         ch = list(base)
@@ -69,6 +70,33 @@ def test_every_method_matches_the_oracle(prec, tol):
 def test_invalid_choices_are_refused():
     p = B.Plan(64, 3, 2.0, 0, "mixed")
     ch = p.choices()
+    assert ch[-1] == 1  # L = 64: one tile per CTA by default (too few pairs for the SMs)
+    big = B.Plan(1024, 3, 2.0, 0, "mixed")  # 528 pairs: both tiles of a pair per CTA
+    assert big.choices()[-1] == 0
+    big.close()
+    bad = list(ch)
+    bad[-1] = 2
+    with pytest.raises(B.S2dwError):
+        p.set_choices(bad)
+    ok = list(ch)
+    ok[-1] = 0  # N <= 5: both shapes available
+    p.set_choices(ok)
+    assert p.choices()[-1] == 0
+    p.set_choices(ch)
+    q = B.Plan(64, 7, 2.0, 0, "mixed")  # N > 5: one tile per CTA only
+    chq = q.choices()
+    assert chq[-1] == 1
+    chq[-1] = 0
+    with pytest.raises(B.S2dwError):
+        q.set_choices(chq)
+    q.close()
+    r = B.Plan(64, 3, 2.0, 0, "fp64")  # the FP64 contraction has one shape
+    chr_ = r.choices()
+    assert chr_[-1] == 0
+    chr_[-1] = 1
+    with pytest.raises(B.S2dwError):
+        r.set_choices(chr_)
+    r.close()
     with pytest.raises(B.S2dwError) as ei:
         p.set_choices(ch[:-1])
     assert ei.value.status == B.S2DW_EINVAL
