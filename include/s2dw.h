@@ -299,7 +299,8 @@ int s2dw_profile_read(s2dw_plan_t plan, double* ms, int* ncalls);
  *       tables, s2dw_alpha_method);
  *   [last] the contraction's CTA shape (FP32 plans): 0 = both tiles of a
  *       pair of 32-wide blocks per CTA (N <= 5), 1 = one tile per CTA (the
- *       only shape for N > 5); FP64 plans: 0.
+ *       only shape for N > 5), 2 = one tile per CTA at two CTAs per SM
+ *       (N <= 5); FP64 plans: 0.
  *   s2dw_plan_choices(plan, choices, n): *n in = capacity, out = entries;
  *     choices == NULL only queries *n; S2DW_EINVAL if the capacity is short.
  *   s2dw_plan_set_choices(plan, choices, n): n must be the plan's count and

@@ -249,14 +249,15 @@ void delta_release(DeltaTab* t) {
   }
 }
 
-constexpr int kOneTile = 0x100;  // launch-list key flag: FP32 contraction tasks of one tile each
+// launch-list keys of the FP32 contraction tasks: N | (CTA shape << 8)
+constexpr int kShapeShift = 8;
 
 // Device-resident launch lists for a set of jobs (one plan = one job).
 struct Lists {
   void* mem = nullptr;
   void* desc_w = nullptr;     // ContractDesc<T>[njobs]
   void* desc_phi = nullptr;   // ContractDesc<T>[njobs]
-  // (N, or N | kOneTile for FP32 tile-per-CTA tasks, (tiles, count))
+  // (N, or N | shape << kShapeShift for the FP32 contraction, (tiles, count))
   std::vector<std::pair<int, std::pair<void*, int>>> tiles_w;
   void* tiles_phi = nullptr;
   int ntiles_phi = 0;
@@ -354,7 +355,7 @@ struct s2dw_plan_s {
   std::vector<unsigned char> desc_w_host, desc_phi_host;
   std::vector<TileTask> tiles_w_host, tiles_phi_host;  // FP64 plans
   std::vector<PairTask> ptasks_w_host, ptasks_phi_host;  // FP32 plans
-  bool pair_one = false;  // FP32, N <= 5: one tile per CTA instead of a pair (a launch method)
+  int pair_shape = kPairShapePair;  // FP32: the contraction's CTA shape (a launch method; N > 5: one tile)
   Lists own;
   // stage timing (s2dw_profile): one set of events per call, up to kProfCalls
   static constexpr int kProfCalls = 256;
@@ -718,7 +719,7 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
       tws = &p->tiles_w_host;
       tps = &p->tiles_phi_host;
     }
-    const int key = p->N | ((sizeof(T) == sizeof(float) && (p->pair_one || !pair_two_tiles(p->N))) ? kOneTile : 0);
+    const int key = p->N | ((sizeof(T) == sizeof(float)) ? (p->pair_shape << kShapeShift) : 0);
     for (Task t : *tws) {
       t.prob = i;
       tw_byN[key].push_back(t);
@@ -743,7 +744,7 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
   // longest tasks first (a CTA computing both tiles of a pair counts double)
   auto by_work = [](std::vector<Task>& v, int key) {
     if constexpr (sizeof(T) == sizeof(float)) {
-      const bool two = !(key & kOneTile);
+      const bool two = (key >> kShapeShift) == kPairShapePair;
       auto work = [two](const PairTask& t) {
         return (long long)(t.lend - t.lstart + 1) * (two && t.p != t.q ? 2 : 1);
       };
@@ -838,10 +839,10 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
   if constexpr (sizeof(T) == sizeof(float)) {
     launch_fpack(dw, ls.njobs, ls.nbmax, ls.Lrmax, ptrs, st);
     for (auto& t : ls.tiles_w)
-      launch_contract_pair(t.first & ~kOneTile, 2, false, !(t.first & kOneTile), dw,
+      launch_contract_pair(t.first & 0xff, 2, false, t.first >> kShapeShift, dw,
                            reinterpret_cast<const PairTask*>(t.second.first), t.second.second, ptrs, st);
     rec(ev, 1, st);
-    launch_contract_pair(1, 1, false, true, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs,
+    launch_contract_pair(1, 1, false, kPairShapePair, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs,
                          st);
   } else {
     for (auto& t : ls.tiles_w)
@@ -904,10 +905,10 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
   rec(ev, 4, st);
   if constexpr (sizeof(T) == sizeof(float)) {
     for (auto& t : ls.tiles_w)
-      launch_contract_pair(t.first & ~kOneTile, 2, true, !(t.first & kOneTile), dw,
+      launch_contract_pair(t.first & 0xff, 2, true, t.first >> kShapeShift, dw,
                            reinterpret_cast<const PairTask*>(t.second.first), t.second.second, ptrs, st);
     rec(ev, 5, st);
-    launch_contract_pair(1, 1, true, true, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs,
+    launch_contract_pair(1, 1, true, kPairShapePair, dp, reinterpret_cast<const PairTask*>(ls.tiles_phi), ls.ntiles_phi, ptrs,
                          st);
   } else {
     for (auto& t : ls.tiles_w)
@@ -1201,17 +1202,19 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   p->desc_w_host.assign(reinterpret_cast<unsigned char*>(&dw), reinterpret_cast<unsigned char*>(&dw) + sizeof(dw));
   p->desc_phi_host.assign(reinterpret_cast<unsigned char*>(&dp), reinterpret_cast<unsigned char*>(&dp) + sizeof(dp));
   if (pairc) {
-    // default CTA shape: a pair of tiles per CTA reads each Delta block once
-    // but gives half the CTAs; measured on GB300, pairs win only with N >= 2
-    // and at least 3 pairs per SM (L >= 1024), one tile per CTA below
+    // default CTA shape (measured on GB300): below about 3 pairs per SM one
+    // tile per CTA with every value in registers; above it both tiles of a
+    // pair (each Delta block read once) for N >= 4, one tile at two CTAs per
+    // SM for N <= 3
     {
       int dev = 0, sms = 0;
       ck(cudaGetDevice(&dev));
       ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       const long long nbk = (p->L0 + 31) / 32, npairs = nbk * (nbk + 1) / 2;
-      p->pair_one = pair_two_tiles(N) && !(N >= 2 && npairs >= 3LL * sms);
+      if (!pair_two_tiles(N) || npairs < 3LL * sms) p->pair_shape = kPairShapeTile;
+      else p->pair_shape = N >= 4 ? kPairShapePair : kPairShapeTile2;
     }
-    build_pair_tasks(p->L0, p->lend_w, pair_two_tiles(N) && !p->pair_one, p->tab->Lmax, p->ptasks_w_host);
+    build_pair_tasks(p->L0, p->lend_w, p->pair_shape == kPairShapePair, p->tab->Lmax, p->ptasks_w_host);
     build_pair_tasks(p->Lphi, p->lphi, true, p->tab->Lmax, p->ptasks_phi_host);
   } else {
     build_tiles(p->L0, p->lend_w, p->TMP, 0, p->tiles_w_host);
@@ -1578,9 +1581,9 @@ static int choices_count(s2dw_plan_t p) { return 3 + 2 * (p->nscale + 1); }
 // Whether method v is available for choice idx of the plan (layout of s2dw_plan_choices).
 static bool choice_valid(s2dw_plan_t p, int idx, int v) {
   if (idx < 2) return v == 0 || v == 1;  // grids without half-length transforms keep the FFT
-  if (idx == choices_count(p) - 1) {  // contraction CTA shape (FP32 plans with N <= 5 have two)
+  if (idx == choices_count(p) - 1) {  // contraction CTA shape (FP32 plans with N <= 5 have three)
     if (p->fp64) return v == 0;
-    return pair_two_tiles(p->N) ? (v == 0 || v == 1) : v == 1;
+    return pair_two_tiles(p->N) ? (v >= kPairShapePair && v <= kPairShapeTile2) : v == kPairShapeTile;
   }
   const int j = (idx - 2) / 2, d = (idx - 2) % 2;
   const int Lj = p->Ycols[j];
@@ -1597,7 +1600,7 @@ static void choices_get(s2dw_plan_t p, int* c) {
     c[2 + 2 * j] = p->alpha_mode[0][j];
     c[3 + 2 * j] = p->alpha_mode[1][j];
   }
-  c[choices_count(p) - 1] = p->fp64 ? 0 : ((p->pair_one || !pair_two_tiles(p->N)) ? 1 : 0);
+  c[choices_count(p) - 1] = p->fp64 ? 0 : p->pair_shape;
 }
 
 static void choices_put(s2dw_plan_t p, const int* c) {
@@ -1608,10 +1611,10 @@ static void choices_put(s2dw_plan_t p, const int* c) {
     p->alpha_mode[1][j] = c[3 + 2 * j];
   }
   if (!p->fp64) {
-    const bool one = c[choices_count(p) - 1] == 1 && pair_two_tiles(p->N);
-    if (one != p->pair_one) {
-      p->pair_one = one;
-      build_pair_tasks(p->L0, p->lend_w, pair_two_tiles(p->N) && !one, p->tab->Lmax, p->ptasks_w_host);
+    const int shape = c[choices_count(p) - 1];
+    if (shape != p->pair_shape) {
+      p->pair_shape = shape;
+      build_pair_tasks(p->L0, p->lend_w, shape == kPairShapePair, p->tab->Lmax, p->ptasks_w_host);
     }
   }
   drop_batches_with(p);
@@ -1778,7 +1781,7 @@ int s2dw_plan_tune(s2dw_plan_t p, int reps, int* choices, int* n) {
     // the contraction's CTA shape (both directions)
     {
       const int idx = nc - 1;
-      for (int v = 0; v < 2; ++v) {
+      for (int v = 0; v < 3; ++v) {
         if (v == cur[idx] || !choice_valid(p, idx, v)) continue;
         std::vector<int> trial(cur);
         trial[idx] = v;

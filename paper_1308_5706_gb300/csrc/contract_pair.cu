@@ -28,20 +28,25 @@ void launch_fpack(const ContractDesc<float>* descs, int njobs, int nbmax, int Lr
 
 bool pair_two_tiles(int N) { return N <= 5; }
 
-template <int N, int NSLOT, bool SYN, int HALVES>
+template <int N, int NSLOT, bool SYN, int HALVES, int MINB = 1>
 static void pair_one(int ntasks, const ContractDesc<float>* descs, const PairTask* tasks, const CallPtrs& ptrs,
                      cudaStream_t st) {
   using G = PairGeom<N, NSLOT, SYN, HALVES>;
-  k_contract_pair<N, NSLOT, SYN, HALVES><<<ntasks, 256 * HALVES, G::SMEM, st>>>(descs, tasks, ptrs);
+  k_contract_pair<N, NSLOT, SYN, HALVES, MINB><<<ntasks, 256 * HALVES, G::SMEM, st>>>(descs, tasks, ptrs);
 }
 
 template <int N, int NSLOT>
-static void pair_dir(bool syn, bool two, int ntasks, const ContractDesc<float>* descs, const PairTask* tasks,
+static void pair_dir(bool syn, int shape, int ntasks, const ContractDesc<float>* descs, const PairTask* tasks,
                      const CallPtrs& ptrs, cudaStream_t st) {
   if constexpr (N <= 5) {
-    if (two) {
+    if (shape == kPairShapePair) {
       if (syn) pair_one<N, NSLOT, true, 2>(ntasks, descs, tasks, ptrs, st);
       else pair_one<N, NSLOT, false, 2>(ntasks, descs, tasks, ptrs, st);
+      return;
+    }
+    if (shape == kPairShapeTile2) {
+      if (syn) pair_one<N, NSLOT, true, 1, 2>(ntasks, descs, tasks, ptrs, st);
+      else pair_one<N, NSLOT, false, 1, 2>(ntasks, descs, tasks, ptrs, st);
       return;
     }
   }
@@ -49,41 +54,46 @@ static void pair_dir(bool syn, bool two, int ntasks, const ContractDesc<float>* 
   else pair_one<N, NSLOT, false, 1>(ntasks, descs, tasks, ptrs, st);
 }
 
-void launch_contract_pair(int N, int nslot, bool syn, bool two, const ContractDesc<float>* descs,
+void launch_contract_pair(int N, int nslot, bool syn, int shape, const ContractDesc<float>* descs,
                           const PairTask* tasks, int ntasks, const CallPtrs& ptrs, cudaStream_t st) {
   if (ntasks <= 0) return;
   if (N == 1 && nslot == 1) {
-    pair_dir<1, 1>(syn, two, ntasks, descs, tasks, ptrs, st);
+    pair_dir<1, 1>(syn, shape, ntasks, descs, tasks, ptrs, st);
     return;
   }
   switch (N) {
-    case 1: pair_dir<1, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
-    case 2: pair_dir<2, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
-    case 3: pair_dir<3, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
-    case 4: pair_dir<4, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
-    case 5: pair_dir<5, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
-    case 6: pair_dir<6, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
-    case 7: pair_dir<7, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
-    case 8: pair_dir<8, 2>(syn, two, ntasks, descs, tasks, ptrs, st); break;
+    case 1: pair_dir<1, 2>(syn, shape, ntasks, descs, tasks, ptrs, st); break;
+    case 2: pair_dir<2, 2>(syn, shape, ntasks, descs, tasks, ptrs, st); break;
+    case 3: pair_dir<3, 2>(syn, shape, ntasks, descs, tasks, ptrs, st); break;
+    case 4: pair_dir<4, 2>(syn, shape, ntasks, descs, tasks, ptrs, st); break;
+    case 5: pair_dir<5, 2>(syn, shape, ntasks, descs, tasks, ptrs, st); break;
+    case 6: pair_dir<6, 2>(syn, shape, ntasks, descs, tasks, ptrs, st); break;
+    case 7: pair_dir<7, 2>(syn, shape, ntasks, descs, tasks, ptrs, st); break;
+    case 8: pair_dir<8, 2>(syn, shape, ntasks, descs, tasks, ptrs, st); break;
     default: break;
   }
 }
 
-template <int N, int NSLOT, int H>
+template <int N, int NSLOT, int H, int MINB = 1>
 static cudaError_t pair_attr_h() {
-  cudaError_t e = cudaFuncSetAttribute(k_contract_pair<N, NSLOT, false, H>,
+  cudaError_t e = cudaFuncSetAttribute(k_contract_pair<N, NSLOT, false, H, MINB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)PairGeom<N, NSLOT, false, H>::SMEM);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_contract_pair<N, NSLOT, true, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_contract_pair<N, NSLOT, true, H, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PairGeom<N, NSLOT, true, H>::SMEM);
 }
-// both CTA shapes for N <= 5 (a pair of tiles or one tile per CTA), one tile above
+// every CTA shape: N <= 5 a pair of tiles, one tile, or one tile at two CTAs
+// per SM; one tile above
 template <int N, int NSLOT>
 static cudaError_t pair_attr() {
   cudaError_t e = pair_attr_h<N, NSLOT, 1>();
   if (e != cudaSuccess) return e;
-  if constexpr (N <= 5) e = pair_attr_h<N, NSLOT, 2>();
+  if constexpr (N <= 5) {
+    e = pair_attr_h<N, NSLOT, 2>();
+    if (e != cudaSuccess) return e;
+    e = pair_attr_h<N, NSLOT, 1, 2>();
+  }
   return e;
 }
 

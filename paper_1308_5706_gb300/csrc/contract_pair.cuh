@@ -111,8 +111,11 @@ __device__ __forceinline__ void cp_async_arrive(uint32_t mbar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-template <int N, int NSLOT, bool SYN, int HALVES>
-__global__ void __launch_bounds__(256 * HALVES, 1)
+// MINB: CTAs per SM the register allocation must allow (2 caps a one-tile
+// CTA at 128 registers per thread; 1 lets N <= 5 keep every accumulator and
+// address in registers)
+template <int N, int NSLOT, bool SYN, int HALVES, int MINB = 1>
+__global__ void __launch_bounds__(256 * HALVES, MINB)
 k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* __restrict__ tasks, CallPtrs ptrs) {
   using G = PairGeom<N, NSLOT, SYN, HALVES>;
   using T = float;

@@ -165,9 +165,12 @@ void launch_contract(int N, int nslot, bool syn, const ContractDesc<T>* descs, c
                      int ntiles, const CallPtrs& ptrs, cudaStream_t st);
 // FP32 tile-pair contraction and its tables (contract_pair.cu)
 bool pair_two_tiles(int N);  // a CTA may compute both tiles of a pair (N <= 5)
-// two: the tasks name pairs, each CTA computes both tiles (N <= 5 only);
-// else each task names one tile (its half)
-void launch_contract_pair(int N, int nslot, bool syn, bool two, const ContractDesc<float>* descs,
+// CTA shapes of the FP32 contraction: the tasks name pairs and each CTA
+// computes both tiles (N <= 5 only), or each task names one tile (its half),
+// at one CTA per SM (the only shape for N > 5) or at two (N <= 5, 128
+// registers per thread)
+constexpr int kPairShapePair = 0, kPairShapeTile = 1, kPairShapeTile2 = 2;
+void launch_contract_pair(int N, int nslot, bool syn, int shape, const ContractDesc<float>* descs,
                           const PairTask* tasks, int ntasks, const CallPtrs& ptrs, cudaStream_t st);
 void launch_fpack(const ContractDesc<float>* descs, int njobs, int nbmax, int Lrmax, const CallPtrs& ptrs,
                   cudaStream_t st);

@@ -46,7 +46,9 @@ def test_every_method_matches_the_oracle(prec, tol):
             for v in (0, 1, 2):
                 if v != base[2 + 2 * j + d]:
                     trials.append((2 + 2 * j + d, v))
-    trials.append((len(base) - 1, 1 - base[-1]))  # the contraction's CTA shape
+    for v in (0, 1, 2):  # the contraction's CTA shapes
+        if v != base[-1]:
+            trials.append((len(base) - 1, v))
     tried = 0
     for idx, v in trials:
         ch = list(base)
@@ -71,24 +73,29 @@ def test_invalid_choices_are_refused():
     p = B.Plan(64, 3, 2.0, 0, "mixed")
     ch = p.choices()
     assert ch[-1] == 1  # L = 64: one tile per CTA by default (too few pairs for the SMs)
-    big = B.Plan(1024, 3, 2.0, 0, "mixed")  # 528 pairs: both tiles of a pair per CTA
+    big = B.Plan(1024, 5, 2.0, 0, "mixed")  # 528 pairs, N >= 4: both tiles of a pair per CTA
     assert big.choices()[-1] == 0
     big.close()
+    big = B.Plan(1024, 3, 2.0, 0, "mixed")  # N <= 3: one tile at two CTAs per SM
+    assert big.choices()[-1] == 2
+    big.close()
     bad = list(ch)
-    bad[-1] = 2
+    bad[-1] = 3
     with pytest.raises(B.S2dwError):
         p.set_choices(bad)
-    ok = list(ch)
-    ok[-1] = 0  # N <= 5: both shapes available
-    p.set_choices(ok)
-    assert p.choices()[-1] == 0
+    for v in (0, 2):  # N <= 5: all three shapes available
+        ok = list(ch)
+        ok[-1] = v
+        p.set_choices(ok)
+        assert p.choices()[-1] == v
     p.set_choices(ch)
     q = B.Plan(64, 7, 2.0, 0, "mixed")  # N > 5: one tile per CTA only
     chq = q.choices()
     assert chq[-1] == 1
-    chq[-1] = 0
-    with pytest.raises(B.S2dwError):
-        q.set_choices(chq)
+    for v in (0, 2):
+        chq[-1] = v
+        with pytest.raises(B.S2dwError):
+            q.set_choices(chq)
     q.close()
     r = B.Plan(64, 3, 2.0, 0, "fp64")  # the FP64 contraction has one shape
     chr_ = r.choices()
