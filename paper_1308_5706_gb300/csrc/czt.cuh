@@ -137,7 +137,7 @@ __host__ __device__ constexpr size_t alpha_czt_smem(int maxlogM, bool staging) {
 // ahead: CTAs resident at once; a CTA asks L2 for the X rows of the CTA
 // `ahead` places later, which runs about one wave later.
 template <typename T, bool ODD, int LOGM>
-__global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __restrict__ segs, int nseg, int maxlogM,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_czt_alpha_ana(const CztSeg<T>* __restrict__ segs, int nseg, int maxlogM,
                                                           CallPtrs ptrs, int ahead) {
   constexpr int NT = alpha_czt_nt(sizeof(T) == 8);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256, 2) k_czt_alpha_ana(const CztSeg<T>* __res
 }
 
 template <typename T, int LOGM>
-__global__ void __launch_bounds__(256, 2) k_czt_alpha_syn(const CztSeg<T>* __restrict__ segs, int nseg, int total,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_czt_alpha_syn(const CztSeg<T>* __restrict__ segs, int nseg, int total,
                                                           int maxlogM, CallPtrs ptrs) {
   constexpr int NT = alpha_czt_nt(sizeof(T) == 8);
   extern __shared__ __align__(16) unsigned char smem_raw[];
