@@ -273,6 +273,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_czt_alpha_syn(c
 // domain, then one inverse FFT.  S + 1 FFTs of M' replace two of M.  A CTA
 // runs G = 4096 / M' row pairs side by side, one per group of M'/16 threads.
 // ---------------------------------------------------------------------------
+// Barrier of thread group g (nthr = M'/16 threads, G = 256 / nthr groups per
+// CTA): a warp's own sync for one warp, a named barrier (id 1 + g) for a
+// part of the CTA, the CTA barrier for the whole.
+__device__ __forceinline__ void seg_group_sync(int nthr, int g) {
+  if (nthr >= 256) __syncthreads();
+  else if (nthr == 32) __syncwarp();
+  else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(nthr) : "memory");
+}
+
 // The analysis kernel branches once per CTA (its segment's length M') to a
 // body compiled for that length (FP32 DH plans: M' = 2^9 .. 2^11; others,
 // and the FP64 and MW-grid instantiations, take the runtime-length body).
@@ -280,6 +289,8 @@ template <typename T, bool ODD, int LOGM>
 __device__ __forceinline__ void alpha_ana_seg_body(const CztSeg<T>& sg, const CallPtrs& ptrs, cx<T>* sm) {
   const int logM = LOGM ? LOGM : sg.logM, M = 1 << logM, nthr = M / 16, G = 256 / nthr;
   const int g = threadIdx.x / nthr, tid = threadIdx.x % nthr, ST = fft_smem_elems(M);
+  // the groups share no shared memory: each waits for its own threads only
+  auto gsync = [&]() { seg_group_sync(nthr, g); };
   cx<T>* Y = sm + g * ST;
   cx<T>* Z = sm + (G + g) * ST;
   const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1, P = sg.P, S = sg.nsegs;
@@ -304,18 +315,18 @@ __device__ __forceinline__ void alpha_ana_seg_body(const CztSeg<T>& sg, const Ca
     }
     return mkc<T>(0, 0);
   });
-  __syncthreads();
+  gsync();
   fftg_stage16<T, false>(Y, M, M / 16, tid, nthr, tw1);
-  __syncthreads();
+  gsync();
   fftg_inner<T, 0>(Y, Y, M, Rl, tid, nthr, nullptr);
-  __syncthreads();
+  gsync();
   T* __restrict__ Wb = reinterpret_cast<T*>(sg.is_phi ? ptrs.Wphi[sg.job] : ptrs.W[sg.job]) + sg.woff +
                        (size_t)(2 * (valid ? pidx : 0)) * n;
   for (int s = 0; s < S; ++s) {
     fftg_inner<T, 1>(Y, Z, M, Rl, tid, nthr, sg.H + (size_t)s * M);
-    __syncthreads();
+    gsync();
     fftg_stage16<T, true>(Z, M, M / 16, tid, nthr, tw1);
-    __syncthreads();
+    gsync();
     const int as = s * P;
     fftg_last_inv<T>(Z, M, tid, sg.tw, [&](int v, cx<T> y) {
       const int a = as + v;
@@ -325,7 +336,7 @@ __device__ __forceinline__ void alpha_ana_seg_body(const CztSeg<T>& sg, const Ca
         if (two) __stcs(Wb + n + a, w.y);
       }
     });
-    __syncthreads();  // Z is rewritten by the next segment
+    gsync();  // Z is rewritten by the next segment
   }
 }
 
@@ -372,6 +383,7 @@ template <typename T, bool ODD, int LOGM>
 __device__ __forceinline__ void alpha_syn_seg_body(const CztSeg<T>& sg, const CallPtrs& ptrs, cx<T>* sm) {
   const int logM = LOGM ? LOGM : sg.logM, M = 1 << logM, nthr = M / 16, G = 256 / nthr;
   const int g = threadIdx.x / nthr, tid = threadIdx.x % nthr, ST = fft_smem_elems(M);
+  auto gsync = [&]() { seg_group_sync(nthr, g); };
   cx<T>* ACC = sm + g * ST;
   cx<T>* B = sm + (G + g) * ST;
   const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1, P = sg.P, S = sg.nsegs;
@@ -396,18 +408,18 @@ __device__ __forceinline__ void alpha_syn_seg_body(const CztSeg<T>& sg, const Ca
       if (!valid || v >= P || a >= n) return mkc<T>(0, 0);
       return cmulc<T>(mkc<T>(__ldcs(Wr + a), __ldcs(Wr + o2 + a)), ldk(sg.pre + a));
     });
-    __syncthreads();
+    gsync();
     fftg_stage16<T, false>(B, M, M / 16, tid, nthr, tw1);
-    __syncthreads();
+    gsync();
     fftg_inner<T, 2>(B, ACC, M, Rl, tid, nthr, sg.H + (size_t)s * M, s == 0);
-    __syncthreads();
+    gsync();
   }
   fftg_inner<T, 3>(ACC, ACC, M, Rl, tid, nthr, nullptr);
-  __syncthreads();
+  gsync();
   fftg_stage16<T, true>(ACC, M, M / 16, tid, nthr, tw1);
-  __syncthreads();
+  gsync();
   fftg_last_inv<T>(ACC, M, tid, sg.tw, [&](int v, cx<T> y) { ACC[fpad(v)] = y; });
-  __syncthreads();
+  gsync();
   if (!valid) return;
   const T h = sg.scale * T(0.5);
   cx<T>* __restrict__ V1 = sg.buf_out + (size_t)(2 * pidx) * Lj;  // V_g[b][m] rows, m fastest
