@@ -163,3 +163,25 @@ def test_tuned_plan_agrees_with_default_and_is_not_slower(tmp_path, monkeypatch)
     assert pc.tuned == (pt.choices(), "cache")
     for p in (pd, pt, pc):
         p.close()
+
+
+@pytest.mark.parametrize("L,N", [(300, 5), (300, 3), (1030, 2)])
+def test_contraction_shapes_give_identical_results(L, N):
+    """The three CTA shapes of the FP32 contraction sum the same terms in the
+    same l order per output: W and the synthesis are bit-identical."""
+    import torch
+    p = B.Plan(L, N, 2.0, 0, "mixed")
+    f = torch.from_numpy(flm_gaussian(L, 13, "cl")).to(torch.complex64).cuda()
+    ch = p.choices()
+    outs = []
+    for shape in (0, 1, 2):
+        c = list(ch)
+        c[-1] = shape
+        p.set_choices(c)
+        W, Wp, fr = _run(p, f)
+        outs.append((W.clone(), Wp.clone(), fr.clone()))
+    for W, Wp, fr in outs[1:]:
+        assert torch.equal(W, outs[0][0]) and torch.equal(Wp, outs[0][1]) and torch.equal(fr, outs[0][2])
+    f0 = f.to(torch.complex128)
+    assert float((outs[0][2].to(torch.complex128) - f0).abs().max() / f0.abs().max()) < 1e-5
+    p.close()
