@@ -790,11 +790,27 @@ __global__ void __launch_bounds__(256) k_beta_ana_dct(const CztSeg<T>* __restric
     __syncthreads();
     // X_b(n) = s_b conj(A[pos]) for the position p holding n; G columns per row
     cx<T>* __restrict__ X = sg.buf_out + (size_t)g * sg.nb * Lj + m0;
+    // FP32, a compile-time length, all G columns present and 16-byte aligned
+    // rows: the G columns of a row leave as G/2 16-byte stores (8-byte
+    // stores scattered over rows fill a quarter of each sector)
+    constexpr int GC = LOGN > 0 ? (kDctSpan >> LOGN) : 0;
+    constexpr bool PAIRS = sizeof(T) == sizeof(float) && GC >= 2;
+    const bool pair_st = PAIRS && nt == GC && (Lj & 1) == 0;
     for (int p = tid; p < Nn; p += blockDim.x) {
       const int n = fft_rev(p, logN);
       const int b = n < (Nn >> 1) ? 2 * n : 2 * Nn - 1 - 2 * n;
       if (b >= sg.nb) continue;
       cx<T>* xr = X + (size_t)b * Lj;
+      if (pair_st) {
+        const T s0 = (((m0 + sg.N - 1) & 1) && (b & 1)) ? T(-1) : T(1);
+        const T s1 = (b & 1) ? -s0 : s0;  // odd columns m0 + 2k + 1 have the other parity
+#pragma unroll
+        for (int k = 0; k < GC / 2; ++k) {
+          const cx<T> u0 = A[(2 * k) * ST + fpad(p)], u1 = A[(2 * k + 1) * ST + fpad(p)];
+          reinterpret_cast<float4*>(xr)[k] = make_float4(s0 * u0.x, -s0 * u0.y, s1 * u1.x, -s1 * u1.y);
+        }
+        continue;
+      }
       for (int t = 0; t < nt; ++t) {
         const T sg_t = (((m0 + t + sg.N - 1) & 1) && (b & 1)) ? T(-1) : T(1);
         const cx<T> u = A[t * ST + fpad(p)];
@@ -819,7 +835,10 @@ __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restric
     m0 = (item % per_g) * G;
     nt = min(G, sp.Lj - m0);
   };
-  // column t of V_g[b][m0 + t], b < N, staged at v(b) = b/2 (b even), N - 1 - (b-1)/2 (b odd)
+  // column t of V_g[b][m0 + t], b < N, staged at v(b) = b/2 (b even), N - 1 - (b-1)/2 (b odd):
+  // at stg[t N + v], or, for two FP32 columns per CTA (N = 2^11), interleaved
+  // at stg[2 v + t] so that one 16-byte copy moves both columns of a row
+  constexpr bool PAIRS = sizeof(T) == sizeof(float) && LOGN > 0 && (kDctSpan >> LOGN) == 2;
   auto prefetch = [&](int it) {
     if (it < total) {
       const CztSeg<T> sp = segs[czt_find_seg<T>(segs, nseg, it)];
@@ -827,10 +846,17 @@ __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restric
       geom(sp, it, logN, G, g, m0, nt);
       const int Nn = 1 << logN;
       const cx<T>* V = sp.buf_in + (size_t)g * sp.nb * sp.Lj + m0;
-      for (int i = tid; i < nt * Nn; i += blockDim.x) {
-        const int t = i / Nn, b = i - t * Nn;
-        const int v = (b & 1) ? Nn - 1 - (b >> 1) : (b >> 1);
-        cp_async_ca<sizeof(cx<T>)>(stg + t * Nn + v, V + (size_t)b * sp.Lj + t);
+      if (PAIRS && nt == 2 && (sp.Lj & 1) == 0) {  // 16-byte aligned column pairs
+        for (int b = tid; b < Nn; b += blockDim.x) {
+          const int v = (b & 1) ? Nn - 1 - (b >> 1) : (b >> 1);
+          cp_async16(stg + 2 * v, V + (size_t)b * sp.Lj, 16);
+        }
+      } else {
+        for (int i = tid; i < nt * Nn; i += blockDim.x) {
+          const int t = i / Nn, b = i - t * Nn;
+          const int v = (b & 1) ? Nn - 1 - (b >> 1) : (b >> 1);
+          cp_async_ca<sizeof(cx<T>)>(stg + (PAIRS ? 2 * v + t : t * Nn + v), V + (size_t)b * sp.Lj + t);
+        }
       }
     }
     cp_async_commit();
@@ -853,7 +879,7 @@ __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restric
       if (gi >= nt) return mkc<T>(0, 0);
       const int b = v < (Nn >> 1) ? 2 * v : 2 * (Nn - 1 - v) + 1;
       const T w = ldk(q + b).x * ((sigma < T(0) && v >= (Nn >> 1)) ? T(-1) : T(1));
-      return cscale<T>(stg[gi * Nn + v], w);
+      return cscale<T>(stg[PAIRS ? 2 * v + gi : gi * Nn + v], w);
     });
     __syncthreads();
     prefetch(it + gridDim.x);
@@ -867,23 +893,29 @@ __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restric
     __syncthreads();
     const cx<T>* __restrict__ tb = sg.pre + (L - 1);
     cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m0;  // row k of Vhat_g[m'][m]
+    constexpr int GC = LOGN > 0 ? (kDctSpan >> LOGN) : 0;
+    const bool pair_st = sizeof(T) == sizeof(float) && GC >= 2 && nt == GC && (Lj & 1) == 0;
     for (int p = tid; p < Nn; p += blockDim.x) {
       const int k = fft_rev(p, logN);
       if (k >= Lj) continue;
       const int pp = fft_pos((Nn - k) & (Nn - 1), logN);
       const cx<T> w = cconj<T>(ldk(tb + k));  // e^{-i pi k/(2N)}
       cx<T>* vr = Vh + (size_t)k * Lj;
-      for (int t = 0; t < nt; ++t) {
+      auto value = [&](int t) -> cx<T> {
         const T sg_t = ((m0 + t + sg.N - 1) & 1) ? T(-1) : T(1);
         const cx<T> yk = A[t * ST + fpad(p)], ynk = A[t * ST + fpad(pp)];
-        cx<T> o;
-        if (k == 0) {
-          o = sg_t > T(0) ? yk : mkc<T>(0, 0);
-        } else {
-          const cx<T> a = cmul<T>(w, yk), c = cmul<T>(cconj<T>(w), ynk);
-          o = mkc<T>(a.x + sg_t * c.x, a.y + sg_t * c.y);
+        if (k == 0) return sg_t > T(0) ? yk : mkc<T>(0, 0);
+        const cx<T> a = cmul<T>(w, yk), c = cmul<T>(cconj<T>(w), ynk);
+        return mkc<T>(a.x + sg_t * c.x, a.y + sg_t * c.y);
+      };
+      if (pair_st) {  // the G columns of a row as G/2 16-byte stores
+#pragma unroll
+        for (int q2 = 0; q2 < GC / 2; ++q2) {
+          const cx<T> o0 = value(2 * q2), o1 = value(2 * q2 + 1);
+          reinterpret_cast<float4*>(vr)[q2] = make_float4(o0.x, o0.y, o1.x, o1.y);
         }
-        vr[t] = o;
+      } else {
+        for (int t = 0; t < nt; ++t) vr[t] = value(t);
       }
     }
   }
