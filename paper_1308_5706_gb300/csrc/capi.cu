@@ -606,7 +606,8 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     if (is_alpha && !direct && (amode == 2) != seg_list) continue;
     switch (base_kind) {
       case CZT_BETA_ANA:
-        s.items = Nj * Lj;
+        s.P = beta_czt_cols(G.logM, sizeof(T) == 8);  // columns per CTA of the chirp-z beta kernels
+        s.items = Nj * ((Lj + s.P - 1) / s.P);
         s.buf_in = reinterpret_cast<cx<T>*>(p->Y[j]);
         s.buf_out = reinterpret_cast<cx<T>*>(p->X[j]);
         s.H = Hs + 0 * (size_t)G.M;
@@ -641,7 +642,8 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
         s.post = reinterpret_cast<const cx<T>*>(G.chirp_a);
         break;
       case CZT_BETA_SYN:
-        s.items = Nj * Lj;
+        s.P = beta_czt_cols(G.logM, sizeof(T) == 8);  // columns per CTA of the chirp-z beta kernels
+        s.items = Nj * ((Lj + s.P - 1) / s.P);
         s.nb = 2 * L;  // DH quadrature (an MW plan resamples V to the DH grid first)
         s.buf_in = reinterpret_cast<cx<T>*>(p->X[j]);
         s.buf_out = reinterpret_cast<cx<T>*>(p->Y[j]);

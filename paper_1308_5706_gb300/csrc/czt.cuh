@@ -48,34 +48,69 @@ __device__ __forceinline__ int czt_find_seg(const CztSeg<T>* segs, int nseg, int
   return lo;
 }
 
+// NT adjacent columns m0.. per CTA (the segment's P: FP32 two up to M = 2^12,
+// so that each output row b gets both columns in one 16-byte store, one at
+// M = 2^13 so that a CTA's buffers stay at 69.6 KB).  M >= 4L: the inputs
+// (|m'| < L_j <= M/4) sit in the first and last quarter of the period, the
+// outputs b < nb <= 2L in the first half.
+// buffer elements of the chirp-z beta kernels for segments up to length 2^maxlogM
+inline size_t beta_czt_smem_elems(int maxlogM, bool fp64) {
+  size_t e = 0;
+  for (int lm = 5; lm <= maxlogM; ++lm)
+    e = std::max(e, (size_t)beta_czt_cols(lm, fp64) * (size_t)fft_smem_elems(1 << lm));
+  return e;
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void czt_beta_ana_body(const CztSeg<T>& sg, cx<T>* A) {
+  const int item = blockIdx.x - sg.start;
+  const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM, ST = fft_smem_elems(M);
+  const int per_g = (Lj + NT - 1) / NT;
+  const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
+  const cx<T>* __restrict__ pre = sg.pre + (L - 1);
+  const cx<T>* __restrict__ Y0 = sg.buf_in + ((size_t)g * Lj + m0) * Lj;  // Y_g[m0 + t][.], m' fastest
+  auto pref = [&](int v) -> cx<T> {
+    if (v < Lj) return ldk(pre + v);
+    if (v > M - Lj) return ldk(pre + (v - M));
+    return mkc<T>(0, 0);
+  };
+  auto in = [&](int v, int t, cx<T> c) -> cx<T> {
+    if (t >= nt) return mkc<T>(0, 0);
+    const cx<T>* __restrict__ Y = Y0 + (size_t)t * Lj;
+    if (v < Lj) return cmul<T>(Y[v], c);
+    if (v > M - Lj) {
+      const T sigma = ((m0 + t + sg.N - 1) & 1) ? T(-1) : T(1);
+      return cmul<T>(cscale<T>(Y[M - v], sigma), c);
+    }
+    return mkc<T>(0, 0);
+  };
+  auto nopost = [](int) -> cx<T> { return mkc<T>(0, 0); };
+  auto none = [](int, int, cx<T>, cx<T>) {};
+  cx<T>* __restrict__ X = sg.buf_out + (size_t)g * sg.nb * Lj + m0;
+  // An odd row count N nb (MW grid) pairs the last row with row N nb of the
+  // buffer (which holds 2L rows per gamma sample) in the alpha analysis: zero it.
+  if (g == sg.N - 1 && ((sg.N * sg.nb) & 1) && threadIdx.x < nt) X[(size_t)sg.nb * Lj + threadIdx.x] = mkc<T>(0, 0);
+  fft_convolve_n<T, NT, true, 0xF00Fu, 0x00FFu>(A, ST, sg.logM, sg.H, sg.tw, pref, in, nopost, none, []() {});
+  const bool pair = NT == 2 && nt == 2 && (Lj & 1) == 0;  // 16-byte aligned column pairs
+  for (int b = threadIdx.x; b < sg.nb; b += blockDim.x) {
+    const cx<T> c = ldk(sg.post + b);
+    cx<T>* __restrict__ xr = X + (size_t)b * Lj;
+    if (pair) {
+      const cx<T> y0 = cmul<T>(A[fpad(b)], c), y1 = cmul<T>(A[ST + fpad(b)], c);
+      *reinterpret_cast<float4*>(xr) = make_float4(y0.x, y0.y, y1.x, y1.y);
+    } else {
+      for (int t = 0; t < nt; ++t) xr[t] = cmul<T>(A[t * ST + fpad(b)], c);
+    }
+  }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_czt_beta_ana(const CztSeg<T>* __restrict__ segs, int nseg) {
+__global__ void __launch_bounds__(256, 2) k_czt_beta_ana(const CztSeg<T>* __restrict__ segs, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
-  const int item = blockIdx.x - sg.start;
-  const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM;
-  const int g = item / Lj, m = item % Lj;
-  const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
-  const cx<T>* __restrict__ Y = sg.buf_in + ((size_t)g * Lj + m) * Lj;  // Y_g[m][.], m' fastest
-  const cx<T>* __restrict__ pre = sg.pre + (L - 1);
-  auto in = [&](int v) -> cx<T> {
-    int mp;
-    if (v < Lj) mp = v;
-    else if (v > M - Lj) mp = v - M;
-    else return mkc<T>(0, 0);
-    cx<T> y = Y[mp < 0 ? -mp : mp];
-    if (mp < 0) y = cscale<T>(y, sigma);
-    return cmul<T>(y, ldk(pre + mp));
-  };
-  cx<T>* __restrict__ X = sg.buf_out + (size_t)g * sg.nb * Lj + m;
-  auto out = [&](int v, cx<T> val) {
-    if (v < sg.nb) X[(size_t)v * Lj] = cmul<T>(val, ldk(sg.post + v));
-  };
-  // An odd row count N nb (MW grid) pairs the last row with row N nb of the
-  // buffer (which holds 2L rows per gamma sample) in the alpha analysis: zero it.
-  if (g == sg.N - 1 && ((sg.N * sg.nb) & 1) && threadIdx.x == 0) X[(size_t)sg.nb * Lj] = mkc<T>(0, 0);
-  fft_convolve<T, false>(A, sg.logM, sg.H, sg.tw, in, out);
+  if (sizeof(T) == sizeof(float) && sg.P == 2) czt_beta_ana_body<T, 2>(sg, A);
+  else czt_beta_ana_body<T, 1>(sg, A);
 }
 
 // MW grid, synthesis: the beta dependence of a (g, m) column of V is a
@@ -88,29 +123,41 @@ __global__ void __launch_bounds__(256) k_czt_beta_ana(const CztSeg<T>* __restric
 // length M: c_p = (1/n) e^{-i pi (p^2 + p)/n} sum_b [V_b e^{-i pi b^2/n}]
 // e^{+i pi (p - b)^2/n}.  Output in the Y layout [g][m][p] that the beta
 // evaluation kernels read, which then give the column on the DH grid.
+template <typename T, int NT>  // NT adjacent columns per CTA (the segment's P)
+__device__ __forceinline__ void beta_mw_dft_body(const CztSeg<T>& sg, cx<T>* A) {
+  const int item = blockIdx.x - sg.start;
+  const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1, M = 1 << sg.logM, ST = fft_smem_elems(M);
+  const int per_g = (Lj + NT - 1) / NT;
+  const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
+  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * sg.nb * Lj + m0;  // columns m0.. of V_g[b][m], b < L
+  auto pref = [&](int v) -> cx<T> { return v < n ? ldk(sg.pre + v) : mkc<T>(0, 0); };  // e^{i pi b^2/n}
+  auto in = [&](int v, int t, cx<T> c) -> cx<T> {
+    if (v >= n || t >= nt) return mkc<T>(0, 0);
+    const T sigma = ((m0 + t + sg.N - 1) & 1) ? T(-1) : T(1);
+    // beta = pi (v = L - 1) is its own reflection: a sigma = -1 column vanishes there
+    const cx<T> x = v < L ? cscale<T>(V[(size_t)v * Lj + t], (v == L - 1 && sigma < T(0)) ? T(0) : T(1))
+                          : cscale<T>(V[(size_t)(n - 1 - v) * Lj + t], sigma);
+    return cmulc<T>(x, c);
+  };
+  auto nopost = [](int) -> cx<T> { return mkc<T>(0, 0); };
+  auto none = [](int, int, cx<T>, cx<T>) {};
+  // inputs v < n <= M/2; outputs p < L_j <= M/4
+  fft_convolve_n<T, NT, true, 0x00FFu, 0x000Fu>(A, ST, sg.logM, sg.H, sg.tw, pref, in, nopost, none, []() {});
+  const T inv_n = T(1) / T(n);
+  for (int t = 0; t < nt; ++t) {
+    cx<T>* __restrict__ C = sg.buf_out + ((size_t)g * Lj + m0 + t) * Lj;  // c_p, p < Lj
+    for (int v = threadIdx.x; v < Lj; v += blockDim.x)
+      C[v] = cscale<T>(cmulc<T>(A[t * ST + fpad(v)], ldk(sg.post + (L - 1) + v)), inv_n);  // sg.post: MW chirp
+  }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_beta_mw_dft(const CztSeg<T>* __restrict__ segs, int nseg) {
+__global__ void __launch_bounds__(256, 2) k_beta_mw_dft(const CztSeg<T>* __restrict__ segs, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
-  const int item = blockIdx.x - sg.start;
-  const int Lj = sg.Lj, L = sg.L, n = 2 * L - 1;
-  const int g = item / Lj, m = item % Lj;
-  const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
-  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * sg.nb * Lj + m;  // column m of V_g[b][m], b < L
-  auto in = [&](int v) -> cx<T> {
-    if (v >= n) return mkc<T>(0, 0);
-    // beta = pi (v = L - 1) is its own reflection: a sigma = -1 column vanishes there
-    const cx<T> x = v < L ? cscale<T>(V[(size_t)v * Lj], (v == L - 1 && sigma < T(0)) ? T(0) : T(1))
-                          : cscale<T>(V[(size_t)(n - 1 - v) * Lj], sigma);
-    return cmulc<T>(x, ldk(sg.pre + v));  // sg.pre: e^{i pi b^2/n}
-  };
-  cx<T>* __restrict__ C = sg.buf_out + ((size_t)g * Lj + m) * Lj;  // c_p, p < Lj
-  const T inv_n = T(1) / T(n);
-  auto out = [&](int v, cx<T> val) {
-    if (v < Lj) C[v] = cscale<T>(cmulc<T>(val, ldk(sg.post + (L - 1) + v)), inv_n);  // sg.post: MW chirp
-  };
-  fft_convolve<T, false>(A, sg.logM, sg.H, sg.tw, in, out);
+  if (sizeof(T) == sizeof(float) && sg.P == 2) beta_mw_dft_body<T, 2>(sg, A);
+  else beta_mw_dft_body<T, 1>(sg, A);
 }
 
 // alpha sums: item `it` is NT row pairs (rows 2(it' NT + t), +1, t < NT, it'
@@ -444,32 +491,52 @@ __global__ void __launch_bounds__(256) k_czt_alpha_syn_seg(const CztSeg<T>* __re
   alpha_syn_seg_body<T, ODD, 0>(sg, ptrs, sm);
 }
 
+template <typename T, int NT>  // NT adjacent columns per CTA (the segment's P)
+__device__ __forceinline__ void czt_beta_syn_body(const CztSeg<T>& sg, cx<T>* A) {
+  const int item = blockIdx.x - sg.start;
+  const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM, ST = fft_smem_elems(M);
+  const int per_g = (Lj + NT - 1) / NT;
+  const int g = item / per_g, m0 = (item % per_g) * NT, nt = min(NT, Lj - m0);
+  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * sg.nb * Lj + m0;  // columns m0.. of V_g[b][m]
+  auto pref = [&](int v) -> cx<T> { return v < sg.nb ? ldk(sg.pre + v) : mkc<T>(0, 0); };
+  auto in = [&](int v, int t, cx<T> c) -> cx<T> {
+    if (v >= sg.nb || t >= nt) return mkc<T>(0, 0);
+    return cmul<T>(V[(size_t)v * Lj + t], c);
+  };
+  auto nopost = [](int) -> cx<T> { return mkc<T>(0, 0); };
+  auto none = [](int, int, cx<T>, cx<T>) {};
+  // inputs b < nb <= 2L <= M/2; outputs m' < L_j and M - m', L_j <= M/4
+  fft_convolve_n<T, NT, true, 0x00FFu, 0xF00Fu>(A, ST, sg.logM, sg.H, sg.tw, pref, in, nopost, none, []() {});
+  cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m0;  // columns m0.. of Vhat_g[m'][m]
+  const bool pair = NT == 2 && nt == 2 && (Lj & 1) == 0;  // 16-byte aligned column pairs
+  for (int mp = threadIdx.x; mp < Lj; mp += blockDim.x) {
+    const cx<T> cp = ldk(sg.post + L - 1 + mp), cm = mp > 0 ? ldk(sg.post + L - 1 - mp) : mkc<T>(0, 0);
+    cx<T> o[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const T sigma = ((m0 + t + sg.N - 1) & 1) ? T(-1) : T(1);
+      o[t] = cmul<T>(A[t * ST + fpad(mp)], cp);
+      if (mp > 0) {
+        const cx<T> tm = cmul<T>(A[t * ST + fpad(M - mp)], cm);
+        o[t] = mkc<T>(o[t].x + sigma * tm.x, o[t].y + sigma * tm.y);
+      }
+    }
+    cx<T>* __restrict__ vr = Vh + (size_t)mp * Lj;
+    if (pair) {
+      *reinterpret_cast<float4*>(vr) = make_float4(o[0].x, o[0].y, o[NT - 1].x, o[NT - 1].y);
+    } else {
+      for (int t = 0; t < nt; ++t) vr[t] = o[t];
+    }
+  }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_czt_beta_syn(const CztSeg<T>* __restrict__ segs, int nseg) {
+__global__ void __launch_bounds__(256, 2) k_czt_beta_syn(const CztSeg<T>* __restrict__ segs, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);
   const CztSeg<T> sg = segs[czt_find_seg<T>(segs, nseg)];
-  const int item = blockIdx.x - sg.start;
-  const int Lj = sg.Lj, L = sg.L, M = 1 << sg.logM;
-  const int g = item / Lj, m = item % Lj;
-  const T sigma = ((m + sg.N - 1) & 1) ? T(-1) : T(1);
-  const cx<T>* __restrict__ V = sg.buf_in + (size_t)g * sg.nb * Lj + m;  // column m of V_g[b][m]
-  auto in = [&](int v) -> cx<T> {
-    if (v >= sg.nb) return mkc<T>(0, 0);
-    return cmul<T>(V[(size_t)v * Lj], ldk(sg.pre + v));
-  };
-  auto none = [](int, cx<T>) {};
-  fft_convolve<T, true>(A, sg.logM, sg.H, sg.tw, in, none);
-  cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m;  // column m of Vhat_g[m'][m]
-  for (int mp = threadIdx.x; mp < Lj; mp += blockDim.x) {
-    const cx<T> tp = cmul<T>(A[fpad(mp)], ldk(sg.post + L - 1 + mp));
-    cx<T> o = tp;
-    if (mp > 0) {
-      const cx<T> tm = cmul<T>(A[fpad(M - mp)], ldk(sg.post + L - 1 - mp));
-      o = mkc<T>(tp.x + sigma * tm.x, tp.y + sigma * tm.y);
-    }
-    Vh[(size_t)mp * Lj] = o;
-  }
+  if (sizeof(T) == sizeof(float) && sg.P == 2) czt_beta_syn_body<T, 2>(sg, A);
+  else czt_beta_syn_body<T, 1>(sg, A);
 }
 
 // ---------------------------------------------------------------------------
@@ -1220,7 +1287,7 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
     k<<<g, 256, sm, st>>>(segs, nseg, total_items, maxlogM, ptrs);
     return;
   }
-  const size_t smem = sizeof(cx<T>) * (size_t)fft_smem_elems(1 << maxlogM);
+  const size_t smem = sizeof(cx<T>) * beta_czt_smem_elems(maxlogM, sizeof(T) == 8);
   dim3 grid(total_items), block(256);
   switch (kind) {
     case CZT_BETA_ANA: k_czt_beta_ana<T><<<grid, block, smem, st>>>(segs, nseg); break;
@@ -1295,7 +1362,8 @@ void launch_czt_impl(int kind, const CztSeg<T>* segs, int nseg, int total_items,
 
 template <typename T>
 cudaError_t czt_set_smem(int maxlogM) {
-  const int smem = (int)(sizeof(cx<T>) * (size_t)fft_smem_elems(1 << maxlogM));
+  // the chirp-z beta kernels (beta_czt_cols columns per CTA)
+  const int smem = (int)(sizeof(cx<T>) * beta_czt_smem_elems(maxlogM, sizeof(T) == 8));
   cudaError_t e = cudaSuccess;
   e = cudaFuncSetAttribute(k_beta_mw_dft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

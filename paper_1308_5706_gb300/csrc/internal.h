@@ -116,6 +116,10 @@ constexpr size_t alpha_ana_direct_smem() {
 __host__ __device__ constexpr int alpha_czt_nt(bool fp64) { return (void)fp64, 1; }
 // adjacent columns per CTA of the single-FFT beta kernels (FP32: a 16-byte pair)
 __host__ __device__ constexpr int beta_fft_nt(bool fp64) { return fp64 ? 1 : 2; }
+// adjacent columns per CTA of the chirp-z beta kernels for transforms of
+// length 2^logM: FP32 a 16-byte pair up to 2^12, one at 2^13 (so that a CTA's
+// buffers stay at 2 x 4352 complex); FP64 one
+__host__ __device__ constexpr int beta_czt_cols(int logM, bool fp64) { return (fp64 || logM >= 13) ? 1 : 2; }
 inline int direct_rows_syn(bool fp64) { return fp64 ? 4 : 8; }  // 32-byte line per alpha sample
 
 // One segment of a chirp-z launch: all columns / row pairs of one scale of
