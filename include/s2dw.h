@@ -291,8 +291,11 @@ int s2dw_profile_read(s2dw_plan_t plan, double* ms, int* ncalls);
  *   Choices of a plan, int[3 + 2 (J+2)]:
  *   [0] beta sums of the analysis, [1] beta sums of the synthesis:
  *       0 = one FFT of length 4L per column, 1 = one complex DCT/DST of length
- *       2L per column (both where L is a power of two; a grid with other L,
- *       or L < 16, keeps its default);
+ *       2L per column on the grids where it measured faster (L >= 128 in the
+ *       analysis, 128 <= L <= 1024 in the synthesis), the FFT on the others
+ *       (both where L is a power of two; a grid with other L keeps its
+ *       chirp-z; the DCT/DST is launched once per transform length);
+ *       default 1;
  *   [2 + 2j] alpha sums of the analysis of scale j (j = J+1: scaling part),
  *   [3 + 2j] of the synthesis: 0 = direct sums (L_j <= 32), 1 = chirp-z of
  *       the grid's length, 2 = segmented chirp-z (where the plan built its

@@ -1,5 +1,6 @@
 // C ABI: plans, the shared Delta table, launch lists, analysis and synthesis.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -267,6 +268,10 @@ struct Lists {
   int nseg[NK] = {};
   int items[NK] = {};
   int ulogM[NK] = {};  // the segments' common transform length log2 (0: lengths differ)
+  // half-length beta kinds (13..15): the segments ordered by transform length,
+  // one launch per length {first segment, segments, items, log2 length}, so
+  // that each launch runs the kernel compiled for its length
+  std::vector<std::array<int, 4>> dct_parts[3];
   int maxlogM = 0;
   int Lmax = 0;
   int odd = 0;  // CZT_ODD_ROWS when a plan of the list samples the MW grid
@@ -339,10 +344,11 @@ struct s2dw_plan_s {
   };
   std::vector<SegTables> seg;  // [nscale + 1]
   // launch methods (s2dw_plan_choices / s2dw_plan_tune): beta_mode[dir] 0 = one
-  // FFT of length 4L, 1 = half-length transforms (power-of-two L >= 16 only);
+  // FFT of length 4L, 1 = half-length transforms on the grids where they are
+  // faster (power-of-two L >= 128; synthesis up to 1024);
   // alpha_mode[dir][j] 0 = direct sums (L_j <= 32), 1 = chirp-z of the grid's
   // length, 2 = segmented chirp-z (where its tables exist); dir 0 = analysis
-  int beta_mode[2] = {1, 0};
+  int beta_mode[2] = {1, 1};
   std::vector<int> alpha_mode[2];
   // [nscale + 1]: tensor-core basis images of the direct alpha sums (FP32 plans)
   std::vector<void*> tc_ana, tc_syn;
@@ -581,7 +587,11 @@ void build_segs(s2dw_plan_s* p, int job, int kind, std::vector<CztSeg<T>>& out, 
     // power-of-two L: half-length transforms (L >= 16) or one FFT of length 4L (L = 8); else chirp-z
     const bool beta_pow2 = (4 * L == G.M) && !mw_ana_beta;
     const int bdir = base_kind == CZT_BETA_SYN ? 1 : 0;
-    const bool beta_dct = beta_pow2 && L >= 16 && p->beta_mode[bdir] == 1;
+    // mode 1: the half-length transforms on the grids where they measured
+    // faster than the length-4L FFT (GB300, N = 3): L >= 128 in the analysis,
+    // 128 <= L <= 1024 in the synthesis
+    const bool dct_faster = bdir == 0 ? L >= 128 : (L >= 128 && L <= 1024);
+    const bool beta_dct = beta_pow2 && L >= 16 && p->beta_mode[bdir] == 1 && dct_faster;
     const bool beta_fft = beta_pow2 && !beta_dct;
     if ((base_kind == CZT_BETA_ANA || base_kind == CZT_BETA_SYN) && kind != CZT_BETA_MW_DFT &&
         (beta_fft != fft_list || beta_dct != dct_list))
@@ -737,6 +747,22 @@ Lists* build_lists(const std::vector<s2dw_plan_t>& plans) {
     ls->Lrmax = std::max(ls->Lrmax, p->Lrf);
     if (p->mw) ls->odd = CZT_ODD_ROWS;
   }
+  for (int k = CZT_BETA_ANA_DCT; k <= CZT_BETA_RS_DCT; ++k) {
+    std::stable_sort(segs[k].begin(), segs[k].end(),
+                     [](const CztSeg<T>& a, const CztSeg<T>& b) { return a.logM < b.logM; });
+    auto& parts = ls->dct_parts[k - CZT_BETA_ANA_DCT];
+    int first = 0, st = 0;
+    for (int i = 0; i <= (int)segs[k].size(); ++i) {
+      if (i == (int)segs[k].size() || (i > first && segs[k][i].logM != segs[k][first].logM)) {
+        if (i > first) parts.push_back({first, i - first, st, segs[k][first].logM});
+        if (i == (int)segs[k].size()) break;
+        first = i;
+        st = 0;
+      }
+      segs[k][i].start = st;  // CTA indices restart in every part
+      st += segs[k][i].items;
+    }
+  }
   for (int k = 0; k < Lists::NK; ++k) {
     int u = segs[k].empty() ? 0 : segs[k][0].logM;
     for (const CztSeg<T>& sg : segs[k])
@@ -833,6 +859,14 @@ inline void mark_use(s2dw_plan_t p, cudaStream_t st) {
 
 // Analysis stages: [contraction + gamma | scaling contraction | beta | alpha chirp-z full-band | segmented
 // | alpha direct].
+// the half-length beta launches of a kind, one per transform length
+template <typename T>
+void launch_dct_parts(const Lists& ls, int kind, const CallPtrs& ptrs, cudaStream_t st) {
+  const CztSeg<T>* segs = reinterpret_cast<const CztSeg<T>*>(ls.segs[kind]);
+  for (const auto& pt : ls.dct_parts[kind - CZT_BETA_ANA_DCT])
+    launch_czt<T>(kind, segs + pt[0], pt[1], pt[2], ls.maxlogM, ptrs, st, pt[3]);
+}
+
 template <typename T>
 void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   const ContractDesc<T>* dw = reinterpret_cast<const ContractDesc<T>*>(ls.desc_w);
@@ -858,8 +892,7 @@ void run_analysis(const Lists& ls, const CallPtrs& ptrs, cudaStream_t st, cudaEv
                 ptrs, st, ls.ulogM[0]);
   launch_czt<T>(CZT_BETA_ANA_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[6]), ls.nseg[6], ls.items[6],
                 ls.maxlogM, ptrs, st, ls.ulogM[6]);
-  launch_czt<T>(CZT_BETA_ANA_DCT, reinterpret_cast<const CztSeg<T>*>(ls.segs[13]), ls.nseg[13], ls.items[13],
-                ls.maxlogM, ptrs, st, ls.ulogM[13]);
+  launch_dct_parts<T>(ls, CZT_BETA_ANA_DCT, ptrs, st);
   rec(ev, 3, st);
   launch_czt<T>(CZT_ALPHA_ANA | ls.odd, reinterpret_cast<const CztSeg<T>*>(ls.segs[1]), ls.nseg[1], ls.items[1],
                 ls.maxlogM, ptrs, st, ls.ulogM[1]);
@@ -894,16 +927,14 @@ void run_synthesis(const Lists& ls, const CallPtrs& ptrs, const ReduceJobs& rj, 
                 ls.maxlogM, ptrs, st, ls.ulogM[10]);
   launch_czt<T>(CZT_BETA_RS_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[11]), ls.nseg[11], ls.items[11],
                 ls.maxlogM, ptrs, st, ls.ulogM[11]);
-  launch_czt<T>(CZT_BETA_RS_DCT, reinterpret_cast<const CztSeg<T>*>(ls.segs[15]), ls.nseg[15], ls.items[15],
-                ls.maxlogM, ptrs, st, ls.ulogM[15]);
+  launch_dct_parts<T>(ls, CZT_BETA_RS_DCT, ptrs, st);
   launch_czt<T>(CZT_BETA_RS, reinterpret_cast<const CztSeg<T>*>(ls.segs[12]), ls.nseg[12], ls.items[12],
                 ls.maxlogM, ptrs, st, ls.ulogM[12]);
   launch_czt<T>(CZT_BETA_SYN, reinterpret_cast<const CztSeg<T>*>(ls.segs[3]), ls.nseg[3], ls.items[3], ls.maxlogM,
                 ptrs, st, ls.ulogM[3]);
   launch_czt<T>(CZT_BETA_SYN_FFT, reinterpret_cast<const CztSeg<T>*>(ls.segs[7]), ls.nseg[7], ls.items[7],
                 ls.maxlogM, ptrs, st, ls.ulogM[7]);
-  launch_czt<T>(CZT_BETA_SYN_DCT, reinterpret_cast<const CztSeg<T>*>(ls.segs[14]), ls.nseg[14], ls.items[14],
-                ls.maxlogM, ptrs, st, ls.ulogM[14]);
+  launch_dct_parts<T>(ls, CZT_BETA_SYN_DCT, ptrs, st);
   rec(ev, 4, st);
   if constexpr (sizeof(T) == sizeof(float)) {
     for (auto& t : ls.tiles_w)
@@ -945,6 +976,7 @@ void own_lists_build(s2dw_plan_s* p) {
     p->own.items[k] = ls->items[k];
     p->own.ulogM[k] = ls->ulogM[k];
   }
+  for (int k = 0; k < 3; ++k) p->own.dct_parts[k] = ls->dct_parts[k];
   p->own.maxlogM = ls->maxlogM;
   p->own.Lmax = ls->Lmax;
   p->own.odd = ls->odd;
@@ -1847,7 +1879,10 @@ int s2dw_launch_counts(s2dw_plan_t p, int* analysis, int* synthesis) {
   const Lists& ls = p->own;
   int contract = ls.ntiles_phi > 0 ? 1 : 0;
   for (auto& t : ls.tiles_w) contract += t.second.second > 0 ? 1 : 0;
-  auto has = [&](int k) { return ls.items[k] > 0 ? 1 : 0; };
+  auto has = [&](int k) {
+    if (k >= CZT_BETA_ANA_DCT && k <= CZT_BETA_RS_DCT) return (int)ls.dct_parts[k - CZT_BETA_ANA_DCT].size();
+    return ls.items[k] > 0 ? 1 : 0;
+  };
   const int fpack = (!p->fp64 && ls.njobs > 0 && ls.nbmax > 0) ? 1 : 0;  // f packing of the FP32 contraction
   if (analysis) *analysis = fpack + contract + has(0) + has(1) + has(4) + has(6) + has(8) + has(13);
   if (synthesis)

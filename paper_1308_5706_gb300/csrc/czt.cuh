@@ -903,9 +903,12 @@ __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restric
     nt = min(G, sp.Lj - m0);
   };
   // column t of V_g[b][m0 + t], b < N, staged at v(b) = b/2 (b even), N - 1 - (b-1)/2 (b odd):
-  // at stg[t N + v], or, for two FP32 columns per CTA (N = 2^11), interleaved
-  // at stg[2 v + t] so that one 16-byte copy moves both columns of a row
-  constexpr bool PAIRS = sizeof(T) == sizeof(float) && LOGN > 0 && (kDctSpan >> LOGN) == 2;
+  // at stg[t N + v], or, for an even number G of FP32 columns per CTA (a
+  // compile-time length), in column pairs at stg[(t/2) 2N + 2 v + t%2] so
+  // that one 16-byte copy moves a pair of columns of a row
+  constexpr int GC = LOGN > 0 ? (kDctSpan >> LOGN) : 0;
+  constexpr bool PAIRS = sizeof(T) == sizeof(float) && GC >= 2;
+  auto sidx = [&](int t, int v, int Nn) { return PAIRS ? (t >> 1) * 2 * Nn + 2 * v + (t & 1) : t * Nn + v; };
   auto prefetch = [&](int it) {
     if (it < total) {
       const CztSeg<T> sp = segs[czt_find_seg<T>(segs, nseg, it)];
@@ -913,16 +916,17 @@ __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restric
       geom(sp, it, logN, G, g, m0, nt);
       const int Nn = 1 << logN;
       const cx<T>* V = sp.buf_in + (size_t)g * sp.nb * sp.Lj + m0;
-      if (PAIRS && nt == 2 && (sp.Lj & 1) == 0) {  // 16-byte aligned column pairs
-        for (int b = tid; b < Nn; b += blockDim.x) {
+      if (PAIRS && nt == GC && (sp.Lj & 1) == 0) {  // 16-byte aligned column pairs
+        for (int i = tid; i < Nn * (GC / 2); i += blockDim.x) {
+          const int k = i / Nn, b = i - k * Nn;
           const int v = (b & 1) ? Nn - 1 - (b >> 1) : (b >> 1);
-          cp_async16(stg + 2 * v, V + (size_t)b * sp.Lj, 16);
+          cp_async16(stg + k * 2 * Nn + 2 * v, V + (size_t)b * sp.Lj + 2 * k, 16);
         }
       } else {
         for (int i = tid; i < nt * Nn; i += blockDim.x) {
           const int t = i / Nn, b = i - t * Nn;
           const int v = (b & 1) ? Nn - 1 - (b >> 1) : (b >> 1);
-          cp_async_ca<sizeof(cx<T>)>(stg + (PAIRS ? 2 * v + t : t * Nn + v), V + (size_t)b * sp.Lj + t);
+          cp_async_ca<sizeof(cx<T>)>(stg + sidx(t, v, Nn), V + (size_t)b * sp.Lj + t);
         }
       }
     }
@@ -946,7 +950,7 @@ __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restric
       if (gi >= nt) return mkc<T>(0, 0);
       const int b = v < (Nn >> 1) ? 2 * v : 2 * (Nn - 1 - v) + 1;
       const T w = ldk(q + b).x * ((sigma < T(0) && v >= (Nn >> 1)) ? T(-1) : T(1));
-      return cscale<T>(stg[PAIRS ? 2 * v + gi : gi * Nn + v], w);
+      return cscale<T>(stg[sidx(gi, v, Nn)], w);
     });
     __syncthreads();
     prefetch(it + gridDim.x);
@@ -960,7 +964,6 @@ __global__ void __launch_bounds__(256) k_beta_syn_dct(const CztSeg<T>* __restric
     __syncthreads();
     const cx<T>* __restrict__ tb = sg.pre + (L - 1);
     cx<T>* __restrict__ Vh = sg.buf_out + (size_t)g * Lj * Lj + m0;  // row k of Vhat_g[m'][m]
-    constexpr int GC = LOGN > 0 ? (kDctSpan >> LOGN) : 0;
     const bool pair_st = sizeof(T) == sizeof(float) && GC >= 2 && nt == GC && (Lj & 1) == 0;
     for (int p = tid; p < Nn; p += blockDim.x) {
       const int k = fft_rev(p, logN);
