@@ -25,7 +25,7 @@
 // than one thread issuing 1-D bulk copies), which signal the stage's `full`
 // mbarrier through cp.async.mbarrier.arrive; every warp arrives on the
 // stage's `empty` mbarrier once it has read it, and the threads refill the
-// slot three stages later.  Stages that lie inside one l-segment (constant
+// slot four stages later.  Stages that lie inside one l-segment (constant
 // scales in both accumulator slots) take a path without any checks; segment
 // changes and the last stage take a slower one.  Every wait is bounded
 // (about a second): a CTA that gives up stops computing, waits for its own
@@ -48,7 +48,7 @@ namespace s2dw {
 constexpr int kPairKL = 2;       // l per pipeline stage
 constexpr int kPairStages = 8;   // ring depth (a power of two)
 constexpr int kPairLogStages = 3;
-constexpr int kPairLag = 3;      // a slot is refilled three stages after it was read (measured: 2 is 1% slower)
+constexpr int kPairLag = 4;      // a slot is refilled four stages after it was read (measured: 2, 3 and 5 slower by 1-3%)
 
 __device__ int g_pair_timeouts;  // bounded waits that gave up (read and reset by the host)
 
@@ -438,7 +438,7 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
     if (lane == 0) tc::mbar_arrive(empty_s + 8u * slot);
     // refill the slot read kPairLag stages ago (every warp has normally left it)
     const int r = i - kPairLag;
-    if (r >= 0 && r + STAGES < nst && !*abort) {
+    if (r >= 0 && r + STAGES < nst) {  // (after a timeout the wait returns false at once)
       if (pair_wait(empty_s + 8u * ((uint32_t)r & (STAGES - 1)), (uint32_t)(r >> kPairLogStages) & 1u, abort))
         issue(r + STAGES);
     }
