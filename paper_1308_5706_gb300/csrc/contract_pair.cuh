@@ -18,14 +18,14 @@
 //   analysis epilogue and to H in the synthesis prologue.  Each Delta block is
 //   read from HBM once per transform instead of twice.
 // * R rows and f values are stored per 32-block with l outermost
-//   (RSp[b][l][slot][n_k >= 0][32], fP[b][l][32]), so they too arrive as one
-//   bulk copy per stage and half.
-// The ring of kPairStages stages (two l each) is filled with cp.async by all
+//   (RSp[b][l][slot][n_k >= 0][32], fP[b][l][32]), so they too are one
+//   contiguous run per stage and half.
+// The ring of kPairStages stages (kPairKL l each) is filled with cp.async by all
 // threads (each owns fixed 16-byte chunks of a stage; measured faster here
 // than one thread issuing 1-D bulk copies), which signal the stage's `full`
 // mbarrier through cp.async.mbarrier.arrive; every warp arrives on the
 // stage's `empty` mbarrier once it has read it, and the threads refill the
-// slot four stages later.  Stages that lie inside one l-segment (constant
+// slot kPairLag stages later.  Stages that lie inside one l-segment (constant
 // scales in both accumulator slots) take a path without any checks; segment
 // changes and the last stage take a slower one.  Every wait is bounded
 // (about a second): a CTA that gives up stops computing, waits for its own
@@ -45,10 +45,14 @@
 
 namespace s2dw {
 
-constexpr int kPairKL = 2;       // l per pipeline stage
-constexpr int kPairStages = 8;   // ring depth (a power of two)
-constexpr int kPairLogStages = 3;
-constexpr int kPairLag = 4;      // a slot is refilled four stages after it was read (measured: 2, 3 and 5 slower by 1-3%)
+// Four l per stage (measured against two: 0.46 vs 0.55 ms per launch at
+// L = 1024, N = 5: the waits, arrivals and refills of a stage are paid once
+// per four l); refilled two stages (8 l) after the read (1: 0.50 ms in the
+// analysis, 3: 0.79 ms).
+constexpr int kPairKL = 4;       // l per pipeline stage (even: the l parity is the stage position's)
+constexpr int kPairStages = 4;   // ring depth (a power of two)
+constexpr int kPairLogStages = 2;
+constexpr int kPairLag = 2;
 
 __device__ int g_pair_timeouts;  // bounded waits that gave up (read and reset by the host)
 
@@ -70,6 +74,15 @@ struct PairGeom {
   static constexpr size_t RED_BYTES = SYN ? (size_t)2 * LCH * HALVES * RED_SLAB * sizeof(float2) : 0;
   static constexpr size_t SMEM = kPairStages * BYTES + RED_BYTES;
 };
+
+// f(integral_constant<0>) .. f(integral_constant<K - 1>), unrolled
+template <int K, typename F>
+__device__ __forceinline__ void pair_unroll(F&& f) {
+  if constexpr (K > 0) {
+    pair_unroll<K - 1>(f);
+    f(std::integral_constant<int, K - 1>());
+  }
+}
 
 // Non-blocking test of the phase of parity `par`.
 __device__ __forceinline__ bool mbar_ready(uint32_t mbar, uint32_t par) {
@@ -121,7 +134,7 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
   using T = float;
   constexpr int NH = G::NH, ZH = N & 1, NP = N / 2;
   constexpr int STAGES = kPairStages, KL = kPairKL;
-  static_assert(KL == 2, "banks 0 / 1 are the two l of a stage");
+  static_assert(KL % 2 == 0, "the l parity (accumulator bank) is the position's parity in a stage");
   extern __shared__ __align__(128) unsigned char pair_smem[];
   float* ring = reinterpret_cast<float*>(pair_smem);
   float2* red = reinterpret_cast<float2*>(pair_smem + STAGES * G::BYTES);  // [2][LCH][HALVES][RED_SLAB]
@@ -176,16 +189,21 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
   volatile int* abort = &s_abort;
 
   // ---- producer: every thread copies fixed 16-byte chunks of each stage ----
-  // chunk u of thread tid is chunk tid + u NTH of the stage; the Delta
-  // blocks come first (16-byte chunk k of the stage is Delta floats 4k..),
-  // then the R rows of each half, then (analysis) the f values of each half.
-  // Source pointers advance by one stage per issue.
+  // The Delta blocks of a stage (16-byte chunk k is Delta floats 4k..) are
+  // chunks tid + u NTH, u < DPT, of thread tid: one source pointer and one
+  // destination, the others at fixed offsets.  The R rows of each half and
+  // (analysis) the f values of each half follow as chunks tid + u NTH of
+  // their own numbering.  Source pointers advance by one stage per issue.
   constexpr int NTH = 256 * HALVES;
   constexpr int NCH_D = KL * 256;              // 16-byte chunks of Delta per stage
+  static_assert(NCH_D % NTH == 0, "whole Delta chunks per thread");
+  constexpr int DPT = NCH_D / NTH;
   constexpr int NCH_R = HALVES * G::R_F / 4;   // of R rows
   constexpr int NCH_F = HALVES * G::F_F / 4;   // of f values
-  constexpr int NCH = NCH_D + NCH_R + NCH_F;
-  constexpr int CPT = (NCH + NTH - 1) / NTH;
+  constexpr int NRF = NCH_R + NCH_F;
+  constexpr int CPT = (NRF + NTH - 1) / NTH;
+  const float* dsrc = D->dpair + tk.dbase + (size_t)tid * 4;
+  const uint32_t ddst = (uint32_t)((tid >> 8) * G::DL + ((tid >> 3) & 31) * G::DP + (tid & 7) * 4) * 4;
   const float* csrc[CPT];
   int cadv[CPT];
   uint32_t cdst[CPT];
@@ -193,26 +211,20 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
 #pragma unroll
   for (int u = 0; u < CPT; ++u) {
     const int ch = tid + u * NTH;
-    cok[u] = ch < NCH;
+    cok[u] = ch < NRF;
     csrc[u] = D->dpair;
     cadv[u] = 0;
     cdst[u] = 0;
     if (!cok[u]) continue;
-    if (ch < NCH_D) {
-      // Delta chunk (l, row, 4-column group) of the stage, into its padded row
-      const int lk = ch >> 8, row = (ch >> 3) & 31, c4 = ch & 7;
-      csrc[u] = D->dpair + tk.dbase + (size_t)ch * 4;
-      cdst[u] = (uint32_t)(lk * G::DL + row * G::DP + c4 * 4) * 4;
-      cadv[u] = KL * 1024;
-    } else if (ch < NCH_D + NCH_R) {
-      const int fo = (ch - NCH_D) * 4, h = fo / G::R_F, o = fo % G::R_F;
+    if (ch < NCH_R) {
+      const int fo = ch * 4, h = fo / G::R_F, o = fo % G::R_F;
       const bool hb = HALVES == 2 ? (h == 1) : is_b;
       csrc[u] = D->RSp + ((size_t)(hb ? tk.q : tk.p) * D->Lr + l_start) * G::RROW + o;
       cdst[u] = (uint32_t)(G::R_OFF + fo) * 4;
       cadv[u] = KL * G::RROW;
     } else {
       constexpr int FF = G::F_F > 0 ? G::F_F : 1;
-      const int fo = (ch - NCH_D - NCH_R) * 4, h = fo / FF, o = fo % FF;
+      const int fo = (ch - NCH_R) * 4, h = fo / FF, o = fo % FF;
       const bool hb = HALVES == 2 ? (h == 1) : is_b;
       csrc[u] = reinterpret_cast<const float*>(D->fP + ((size_t)(hb ? tk.p : tk.q) * D->Lrf + l_start) * 32) + o;
       cdst[u] = (uint32_t)(G::F_OFF + fo) * 4;
@@ -222,6 +234,10 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
   const uint32_t full_s = tc::smem_u32(&full[0]), empty_s = tc::smem_u32(&empty[0]);
   auto issue = [&](int i) {  // called for i = 0, 1, 2, ... in order
     const uint32_t so = ring_s + (uint32_t)(i & (STAGES - 1)) * (uint32_t)G::BYTES;
+#pragma unroll
+    for (int u = 0; u < DPT; ++u)
+      cp_async16_s(so + ddst + (uint32_t)(u * (NTH / 256) * G::DL * 4), dsrc + u * NTH * 4);
+    dsrc += KL * 1024;
 #pragma unroll
     for (int u = 0; u < CPT; ++u) {
       if (cok[u]) cp_async16_s(so + cdst[u], csrc[u]);
@@ -349,7 +365,7 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
 
   // the arithmetic of one l (no checks); bank = parity of l - l_start
   auto compute = [&](const int l, const float* S, auto bank) {
-    constexpr int BQ = decltype(bank)::value * NP;
+    constexpr int BQ = (decltype(bank)::value & 1) * NP;
     constexpr int DB = decltype(bank)::value * G::DL;
     float dv[4];
     if (!is_b) {
@@ -417,11 +433,8 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
     const uint32_t slot = (uint32_t)i & (STAGES - 1);
     if (pair_wait(full_s + 8u * slot, (uint32_t)(i >> kPairLogStages) & 1u, abort)) {
       const float* S = ring + slot * G::SIZE;
-      if (l0 + 1 < next_b && l0 + 1 <= l_end) {  // both l inside the current segment
-        if (!idle) {
-          compute(l0, S, std::integral_constant<int, 0>());
-          compute(l0 + 1, S, std::integral_constant<int, 1>());
-        }
+      if (l0 + KL - 1 < next_b && l0 + KL - 1 <= l_end) {  // every l inside the current segment
+        if (!idle) pair_unroll<KL>([&](auto kk) { compute(l0 + decltype(kk)::value, S, kk); });
       } else {
 #pragma unroll 1
         for (int kk = 0; kk < KL; ++kk) {
@@ -429,8 +442,9 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
           if (l > l_end) break;
           if (l >= next_b) enter(l);
           if (idle) continue;
-          if (kk == 0) compute(l, S, std::integral_constant<int, 0>());
-          else compute(l, S, std::integral_constant<int, 1>());
+          pair_unroll<KL>([&](auto kc) {
+            if (kk == decltype(kc)::value) compute(l, S, kc);
+          });
         }
       }
     }
