@@ -20,7 +20,7 @@
 // * R rows and f values are stored per 32-block with l outermost
 //   (RSp[b][l][slot][n_k >= 0][32], fP[b][l][32]), so they too are one
 //   contiguous run per stage and half.
-// The ring of kPairStages stages (kPairKL l each) is filled with cp.async by all
+// The ring of kPairStages stages (4 or 8 l each) is filled with cp.async by all
 // threads (each owns fixed 16-byte chunks of a stage; measured faster here
 // than one thread issuing 1-D bulk copies), which signal the stage's `full`
 // mbarrier through cp.async.mbarrier.arrive; every warp arrives on the
@@ -45,11 +45,14 @@
 
 namespace s2dw {
 
-// Four l per stage (measured against two: 0.46 vs 0.55 ms per launch at
-// L = 1024, N = 5: the waits, arrivals and refills of a stage are paid once
-// per four l); refilled two stages (8 l) after the read (1: 0.50 ms in the
-// analysis, 3: 0.79 ms).
-constexpr int kPairKL = 4;       // l per pipeline stage (even: the l parity is the stage position's)
+// Four l per stage, eight in the analysis on tile pairs (measured against
+// two: 0.46 and 0.45 vs 0.55 ms per launch at L = 1024, N = 5: the waits,
+// arrivals and refills of a stage are paid once per stage); refilled two
+// stages after the read (1: 0.50 ms in the analysis, 3: 0.79 ms).  Eight l
+// per stage are only taken where four stages of them fit beside nothing
+// else: the synthesis keeps shared memory for its partial sums, the one-tile
+// CTAs for a second CTA per SM.
+constexpr int kPairKLMax = 8;    // l per pipeline stage, at most (tables are padded for it)
 constexpr int kPairStages = 4;   // ring depth (a power of two)
 constexpr int kPairLogStages = 2;
 constexpr int kPairLag = 2;
@@ -62,9 +65,10 @@ struct PairGeom {
   static constexpr int RROW = NSLOT * NH * 32;   // floats of one l of one R block
   static constexpr int DP = 36;                  // shared-memory pitch of a Delta row (32 + 4)
   static constexpr int DL = 32 * DP;             // floats of one l of Delta in shared memory
-  static constexpr int D_F = kPairKL * DL;       // Delta floats per stage
-  static constexpr int R_F = kPairKL * RROW;     // R floats per stage and half
-  static constexpr int F_F = SYN ? 0 : kPairKL * 64;  // f floats per stage and half
+  static constexpr int KL = (SYN || HALVES == 1) ? 4 : 8;  // l per stage (even: a position's parity is its l's)
+  static constexpr int D_F = KL * DL;            // Delta floats per stage
+  static constexpr int R_F = KL * RROW;          // R floats per stage and half
+  static constexpr int F_F = SYN ? 0 : KL * 64;  // f floats per stage and half
   static constexpr int R_OFF = D_F;
   static constexpr int F_OFF = R_OFF + HALVES * R_F;
   static constexpr int SIZE = F_OFF + HALVES * F_F;
@@ -133,7 +137,8 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
   using G = PairGeom<N, NSLOT, SYN, HALVES>;
   using T = float;
   constexpr int NH = G::NH, ZH = N & 1, NP = N / 2;
-  constexpr int STAGES = kPairStages, KL = kPairKL;
+  constexpr int STAGES = kPairStages, KL = G::KL;
+  static_assert(KL <= kPairKLMax, "tables are padded for kPairKLMax l per stage");
   static_assert(KL % 2 == 0, "the l parity (accumulator bank) is the position's parity in a stage");
   extern __shared__ __align__(128) unsigned char pair_smem[];
   float* ring = reinterpret_cast<float*>(pair_smem);

@@ -26,7 +26,7 @@ struct ContractDesc {
   const float* dpair;  // Delta pair table of the plan's shared table
   const float* RSp;    // [nb][Lr][nslot][(N+1)/2][32]: R rows per 32-block of m', l outermost
   const cx<T>* fP;     // [nb][Lrf][32]: f_lm per 32-block of m (zero for m > l), packed per call
-  int Lr, Lrf;         // l rows of RSp and fP (>= L + 3: a stage may read three l past the last)
+  int Lr, Lrf;         // l rows of RSp and fP (>= L + 7: a stage may read seven l past the last)
   const T* RS;       // [L][nslot][(N+1)/2][Lp]: Delta^l_{m',n_k} kappa^j(l) |s_{l,n_k}|, n_k >= 0
   cx<T>* P;          // synthesis partials [nbr][L][Lp32]
   int L, Lp, Lp32, nbr;
@@ -58,7 +58,7 @@ __host__ __device__ __forceinline__ long long pair_run_base(int p, int q, int Lm
 }
 // entries of the whole table (+ one stage of read-ahead past the last run)
 __host__ __device__ __forceinline__ long long pair_table_entries(int Lmax) {
-  return pair_run_base(0, Lmax / 32, Lmax) + 4 * 1024;  // a stage may read three l past a run's end
+  return pair_run_base(0, Lmax / 32, Lmax) + 8 * 1024;  // a stage may read seven l past a run's end
 }
 
 struct TileTask {
