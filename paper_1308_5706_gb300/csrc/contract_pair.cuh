@@ -40,6 +40,8 @@
 // registers) launches one CTA per tile; a task then names its half.
 #pragma once
 
+#include <type_traits>
+
 #include "contract.cuh"
 #include "tc.cuh"
 
@@ -77,6 +79,28 @@ struct PairGeom {
   static constexpr int RED_SLAB = 8 * 32;
   static constexpr size_t RED_BYTES = SYN ? (size_t)2 * LCH * HALVES * RED_SLAB * sizeof(float2) : 0;
   static constexpr size_t SMEM = kPairStages * BYTES + RED_BYTES;
+};
+
+// Accumulators of rows (2i, 2i+1) as float2 pairs for the packed FP32
+// builtins (__ffma2_rn); the tile-pair CTAs use these (measured: analysis
+// 0.451 -> 0.399 ms at L = 1024, N = 5), the one-tile CTAs the inline-PTX
+// f32x2 forms of Acc<float, ..., true>, with which they do not spill
+template <int E, int NSLOT, int N>
+struct AccF2 {
+  float2 x[E / 2][NSLOT][N], y[E / 2][NSLOT][N];
+  __device__ __forceinline__ cx<float> get(int e, int s, int k) const {
+    const float2 a = x[e >> 1][s][k], b = y[e >> 1][s][k];
+    return (e & 1) ? mkc<float>(a.y, b.y) : mkc<float>(a.x, b.x);
+  }
+  __device__ __forceinline__ void set(int e, int s, int k, cx<float> v) {
+    if (e & 1) {
+      x[e >> 1][s][k].y = v.x;
+      y[e >> 1][s][k].y = v.y;
+    } else {
+      x[e >> 1][s][k].x = v.x;
+      y[e >> 1][s][k].x = v.y;
+    }
+  }
 };
 
 // f(integral_constant<0>) .. f(integral_constant<K - 1>), unrolled
@@ -255,7 +279,8 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
     for (int i = 0; i < npre; ++i) issue(i);
   }
 
-  using AccT = Acc<T, 4, NSLOT, N, true>;
+  constexpr bool BUILTIN = HALVES == 2;  // packed FP32 builtins, else inline PTX
+  using AccT = std::conditional_t<BUILTIN, AccF2<4, NSLOT, N>, Acc<T, 4, NSLOT, N, true>>;
   AccT acc;
 #pragma unroll
   for (int e = 0; e < 4; ++e)
@@ -331,9 +356,10 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
     }
   };
   // sum of the 8 row groups of each column for `count` l of buffer `buf`
+  // (with two halves, each half sums its own tile's partials)
   auto reduce_chunk = [&](int buf, int lfirst, int count) {
     constexpr int SH = HALVES == 2 ? 6 : 5;
-    const int lc2 = tid >> SH, h2 = HALVES == 2 ? ((tid >> 5) & 1) : 0, c2 = tid & 31;
+    const int lc2 = HALVES == 2 ? ((tid >> 5) & 7) : (tid >> SH), h2 = HALVES == 2 ? (tid >> 8) : 0, c2 = tid & 31;
     if (lc2 < count) {
       const bool b2 = HALVES == 2 ? (h2 == 1) : is_b;
       if (HALVES == 2 && b2 && diag) return;
@@ -386,41 +412,80 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
     const float* Rr = S + G::R_OFF + hh * G::R_F + decltype(bank)::value * G::RROW + 4 * rg;
     if (!SYN) {
       const float2 fv = reinterpret_cast<const float2*>(S + G::F_OFF + hh * G::F_F + decltype(bank)::value * 64)[c];
-      const f2p fx = pk2(fv.x, fv.x), fy = pk2(fv.y, fv.y);
-      const f2p d01 = pk2(dv[0], dv[1]), d23 = pk2(dv[2], dv[3]);
-      const f2p tx0 = mul2(d01, fx), tx1 = mul2(d23, fx), ty0 = mul2(d01, fy), ty1 = mul2(d23, fy);
+      if constexpr (BUILTIN) {
+        const float2 fx = make_float2(fv.x, fv.x), fy = make_float2(fv.y, fv.y);
+        const float2 d01 = make_float2(dv[0], dv[1]), d23 = make_float2(dv[2], dv[3]);
+        const float2 tx0 = __fmul2_rn(d01, fx), tx1 = __fmul2_rn(d23, fx), ty0 = __fmul2_rn(d01, fy),
+                     ty1 = __fmul2_rn(d23, fy);
 #pragma unroll
-      for (int s = 0; s < NSLOT; ++s)
+        for (int s = 0; s < NSLOT; ++s)
 #pragma unroll
-        for (int h = 0; h < NH; ++h) {
-          const int q = (ZH && h == 0) ? 2 * NP : BQ + h - ZH;
-          const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(Rr + (s * NH + h) * 32);
-          acc.x[0][s][q] = fma2(tx0, r.x, acc.x[0][s][q]);
-          acc.y[0][s][q] = fma2(ty0, r.x, acc.y[0][s][q]);
-          acc.x[1][s][q] = fma2(tx1, r.y, acc.x[1][s][q]);
-          acc.y[1][s][q] = fma2(ty1, r.y, acc.y[1][s][q]);
-        }
+          for (int h = 0; h < NH; ++h) {
+            const int q = (ZH && h == 0) ? 2 * NP : BQ + h - ZH;
+            const float4 r4 = *reinterpret_cast<const float4*>(Rr + (s * NH + h) * 32);
+            const float2 rx = make_float2(r4.x, r4.y), ry = make_float2(r4.z, r4.w);
+            acc.x[0][s][q] = __ffma2_rn(tx0, rx, acc.x[0][s][q]);
+            acc.y[0][s][q] = __ffma2_rn(ty0, rx, acc.y[0][s][q]);
+            acc.x[1][s][q] = __ffma2_rn(tx1, ry, acc.x[1][s][q]);
+            acc.y[1][s][q] = __ffma2_rn(ty1, ry, acc.y[1][s][q]);
+          }
+      } else {
+        const f2p fx = pk2(fv.x, fv.x), fy = pk2(fv.y, fv.y);
+        const f2p d01 = pk2(dv[0], dv[1]), d23 = pk2(dv[2], dv[3]);
+        const f2p tx0 = mul2(d01, fx), tx1 = mul2(d23, fx), ty0 = mul2(d01, fy), ty1 = mul2(d23, fy);
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s)
+#pragma unroll
+          for (int h = 0; h < NH; ++h) {
+            const int q = (ZH && h == 0) ? 2 * NP : BQ + h - ZH;
+            const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(Rr + (s * NH + h) * 32);
+            acc.x[0][s][q] = fma2(tx0, r.x, acc.x[0][s][q]);
+            acc.y[0][s][q] = fma2(ty0, r.x, acc.y[0][s][q]);
+            acc.x[1][s][q] = fma2(tx1, r.y, acc.x[1][s][q]);
+            acc.y[1][s][q] = fma2(ty1, r.y, acc.y[1][s][q]);
+          }
+      }
     } else {
-      f2p px0 = 0, py0 = 0, px1 = 0, py1 = 0;
-#pragma unroll
-      for (int s = 0; s < NSLOT; ++s)
-#pragma unroll
-        for (int h = 0; h < NH; ++h) {
-          const int q = (ZH && h == 0) ? 2 * NP : BQ + h - ZH;
-          const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(Rr + (s * NH + h) * 32);
-          px0 = fma2(acc.x[0][s][q], r.x, px0);
-          py0 = fma2(acc.y[0][s][q], r.x, py0);
-          px1 = fma2(acc.x[1][s][q], r.y, px1);
-          py1 = fma2(acc.y[1][s][q], r.y, py1);
-        }
-      const f2p d01 = pk2(dv[0], dv[1]), d23 = pk2(dv[2], dv[3]);
-      const f2p sx = fma2(d23, px1, mul2(d01, px0)), sy = fma2(d23, py1, mul2(d01, py0));
-      float a, b2;
       cx<T> part;
-      upk2(sx, a, b2);
-      part.x = a + b2;
-      upk2(sy, a, b2);
-      part.y = a + b2;
+      if constexpr (BUILTIN) {
+        float2 px0 = make_float2(0.f, 0.f), py0 = px0, px1 = px0, py1 = px0;
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s)
+#pragma unroll
+          for (int h = 0; h < NH; ++h) {
+            const int q = (ZH && h == 0) ? 2 * NP : BQ + h - ZH;
+            const float4 r4 = *reinterpret_cast<const float4*>(Rr + (s * NH + h) * 32);
+            const float2 rx = make_float2(r4.x, r4.y), ry = make_float2(r4.z, r4.w);
+            px0 = __ffma2_rn(acc.x[0][s][q], rx, px0);
+            py0 = __ffma2_rn(acc.y[0][s][q], rx, py0);
+            px1 = __ffma2_rn(acc.x[1][s][q], ry, px1);
+            py1 = __ffma2_rn(acc.y[1][s][q], ry, py1);
+          }
+        const float2 d01 = make_float2(dv[0], dv[1]), d23 = make_float2(dv[2], dv[3]);
+        const float2 sx = __ffma2_rn(d23, px1, __fmul2_rn(d01, px0)), sy = __ffma2_rn(d23, py1, __fmul2_rn(d01, py0));
+        part.x = sx.x + sx.y;
+        part.y = sy.x + sy.y;
+      } else {
+        f2p px0 = 0, py0 = 0, px1 = 0, py1 = 0;
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s)
+#pragma unroll
+          for (int h = 0; h < NH; ++h) {
+            const int q = (ZH && h == 0) ? 2 * NP : BQ + h - ZH;
+            const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(Rr + (s * NH + h) * 32);
+            px0 = fma2(acc.x[0][s][q], r.x, px0);
+            py0 = fma2(acc.y[0][s][q], r.x, py0);
+            px1 = fma2(acc.x[1][s][q], r.y, px1);
+            py1 = fma2(acc.y[1][s][q], r.y, py1);
+          }
+        const f2p d01 = pk2(dv[0], dv[1]), d23 = pk2(dv[2], dv[3]);
+        const f2p sx = fma2(d23, px1, mul2(d01, px0)), sy = fma2(d23, py1, mul2(d01, py0));
+        float a, b2;
+        upk2(sx, a, b2);
+        part.x = a + b2;
+        upk2(sy, a, b2);
+        part.y = a + b2;
+      }
       const int lc = (l - l_start) & (LCH - 1);
       red[(((size_t)rbuf * LCH + lc) * HALVES + hh) * G::RED_SLAB + rg * 32 + c] = part;
     }
@@ -431,7 +496,10 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
   for (int i = 0; i < nst; ++i) {
     const int l0 = l_start + KL * i;
     if (SYN && i > 0 && ((KL * i) & (LCH - 1)) == 0) {
-      __syncthreads();  // the chunk's partials are in red
+      // the chunk's partials are in red: with two halves, each half waits
+      // for its own warps only (named barrier 1 + half, 256 threads)
+      if (HALVES == 2) asm volatile("bar.sync %0, 256;" ::"r"(1 + hh) : "memory");
+      else __syncthreads();
       rbuf ^= 1;
       reduce_chunk(rbuf ^ 1, l0 - LCH, LCH);
     }
