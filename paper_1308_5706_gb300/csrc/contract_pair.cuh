@@ -20,12 +20,12 @@
 // * R rows and f values are stored per 32-block with l outermost
 //   (RSp[b][l][slot][n_k >= 0][32], fP[b][l][32]), so they too are one
 //   contiguous run per stage and half.
-// The ring of kPairStages stages (4 or 8 l each) is filled with cp.async by all
+// The ring of three or four stages (4 or 8 l each) is filled with cp.async by all
 // threads (each owns fixed 16-byte chunks of a stage; measured faster here
 // than one thread issuing 1-D bulk copies), which signal the stage's `full`
 // mbarrier through cp.async.mbarrier.arrive; every warp arrives on the
 // stage's `empty` mbarrier once it has read it, and the threads refill the
-// slot kPairLag stages later.  Stages that lie inside one l-segment (constant
+// slot one or two stages later.  Stages that lie inside one l-segment (constant
 // scales in both accumulator slots) take a path without any checks; segment
 // changes and the last stage take a slower one.  Every wait is bounded
 // (about a second): a CTA that gives up stops computing, waits for its own
@@ -47,17 +47,17 @@
 
 namespace s2dw {
 
-// Four l per stage, eight in the analysis on tile pairs (measured against
-// two: 0.46 and 0.45 vs 0.55 ms per launch at L = 1024, N = 5: the waits,
-// arrivals and refills of a stage are paid once per stage); refilled two
-// stages after the read (1: 0.50 ms in the analysis, 3: 0.79 ms).  Eight l
-// per stage are only taken where four stages of them fit beside nothing
-// else: the synthesis keeps shared memory for its partial sums, the one-tile
-// CTAs for a second CTA per SM.
+// Ring geometry (PairGeom): eight l per stage in the tile-pair CTAs, four
+// in the one-tile CTAs; four stages, three in the tile-pair synthesis, whose
+// partial sums take the rest of the shared memory; a slot is refilled two
+// stages after it was read (one in that synthesis).  Measured at L = 1024,
+// N = 5 (analysis / synthesis, ms per launch): two l per stage 0.55 / 0.56;
+// four 0.46 / 0.46; eight in the analysis 0.45; with the packed builtins
+// 0.40 / 0.45; eight in the synthesis (three stages) 0.40 / 0.39.  Refills
+// one or three stages after the read were slower (0.50 and 0.79 ms in the
+// four-l analysis, 0.49 ms in the three-stage synthesis at two).  The
+// waits, arrivals and refills of a stage are paid once per stage.
 constexpr int kPairKLMax = 8;    // l per pipeline stage, at most (tables are padded for it)
-constexpr int kPairStages = 4;   // ring depth (a power of two)
-constexpr int kPairLogStages = 2;
-constexpr int kPairLag = 2;
 
 __device__ int g_pair_timeouts;  // bounded waits that gave up (read and reset by the host)
 
@@ -67,7 +67,9 @@ struct PairGeom {
   static constexpr int RROW = NSLOT * NH * 32;   // floats of one l of one R block
   static constexpr int DP = 36;                  // shared-memory pitch of a Delta row (32 + 4)
   static constexpr int DL = 32 * DP;             // floats of one l of Delta in shared memory
-  static constexpr int KL = (SYN || HALVES == 1) ? 4 : 8;  // l per stage (even: a position's parity is its l's)
+  static constexpr int KL = HALVES == 1 ? 4 : 8;  // l per stage (even: a position's parity is its l's)
+  static constexpr int STAGES = (SYN && HALVES == 2) ? 3 : 4;  // ring depth
+  static constexpr int LAG = (SYN && HALVES == 2) ? 1 : 2;     // refill this many stages after the read
   static constexpr int D_F = KL * DL;            // Delta floats per stage
   static constexpr int R_F = KL * RROW;          // R floats per stage and half
   static constexpr int F_F = SYN ? 0 : KL * 64;  // f floats per stage and half
@@ -78,7 +80,7 @@ struct PairGeom {
   // synthesis partials per (buffer, l, half): [row group][32 columns]
   static constexpr int RED_SLAB = 8 * 32;
   static constexpr size_t RED_BYTES = SYN ? (size_t)2 * LCH * HALVES * RED_SLAB * sizeof(float2) : 0;
-  static constexpr size_t SMEM = kPairStages * BYTES + RED_BYTES;
+  static constexpr size_t SMEM = STAGES * BYTES + RED_BYTES;
 };
 
 // Accumulators of rows (2i, 2i+1) as float2 pairs for the packed FP32
@@ -161,7 +163,7 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
   using G = PairGeom<N, NSLOT, SYN, HALVES>;
   using T = float;
   constexpr int NH = G::NH, ZH = N & 1, NP = N / 2;
-  constexpr int STAGES = kPairStages, KL = G::KL;
+  constexpr int STAGES = G::STAGES, KL = G::KL;
   static_assert(KL <= kPairKLMax, "tables are padded for kPairKLMax l per stage");
   static_assert(KL % 2 == 0, "the l parity (accumulator bank) is the position's parity in a stage");
   extern __shared__ __align__(128) unsigned char pair_smem[];
@@ -261,8 +263,8 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
     }
   }
   const uint32_t full_s = tc::smem_u32(&full[0]), empty_s = tc::smem_u32(&empty[0]);
-  auto issue = [&](int i) {  // called for i = 0, 1, 2, ... in order
-    const uint32_t so = ring_s + (uint32_t)(i & (STAGES - 1)) * (uint32_t)G::BYTES;
+  auto issue = [&](uint32_t slot) {  // stages in order, each into its slot
+    const uint32_t so = ring_s + slot * (uint32_t)G::BYTES;
 #pragma unroll
     for (int u = 0; u < DPT; ++u)
       cp_async16_s(so + ddst + (uint32_t)(u * (NTH / 256) * G::DL * 4), dsrc + u * NTH * 4);
@@ -272,11 +274,11 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
       if (cok[u]) cp_async16_s(so + cdst[u], csrc[u]);
       csrc[u] += cadv[u];
     }
-    cp_async_arrive(full_s + 8u * (uint32_t)(i & (STAGES - 1)));
+    cp_async_arrive(full_s + 8u * slot);
   };
   {
     const int npre = nst < STAGES ? nst : STAGES;
-    for (int i = 0; i < npre; ++i) issue(i);
+    for (int i = 0; i < npre; ++i) issue((uint32_t)i);
   }
 
   constexpr bool BUILTIN = HALVES == 2;  // packed FP32 builtins, else inline PTX
@@ -503,8 +505,9 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
       rbuf ^= 1;
       reduce_chunk(rbuf ^ 1, l0 - LCH, LCH);
     }
-    const uint32_t slot = (uint32_t)i & (STAGES - 1);
-    if (pair_wait(full_s + 8u * slot, (uint32_t)(i >> kPairLogStages) & 1u, abort)) {
+    // ring slot and phase parity of stage i (shifts for a power-of-two depth)
+    const uint32_t slot = (uint32_t)i % STAGES, par = ((uint32_t)i / STAGES) & 1u;
+    if (pair_wait(full_s + 8u * slot, par, abort)) {
       const float* S = ring + slot * G::SIZE;
       if (l0 + KL - 1 < next_b && l0 + KL - 1 <= l_end) {  // every l inside the current segment
         if (!idle) pair_unroll<KL>([&](auto kk) { compute(l0 + decltype(kk)::value, S, kk); });
@@ -523,11 +526,12 @@ k_contract_pair(const ContractDesc<float>* __restrict__ descs, const PairTask* _
     }
     __syncwarp();
     if (lane == 0) tc::mbar_arrive(empty_s + 8u * slot);
-    // refill the slot read kPairLag stages ago (every warp has normally left it)
-    const int r = i - kPairLag;
-    if (r >= 0 && r + STAGES < nst) {  // (after a timeout the wait returns false at once)
-      if (pair_wait(empty_s + 8u * ((uint32_t)r & (STAGES - 1)), (uint32_t)(r >> kPairLogStages) & 1u, abort))
-        issue(r + STAGES);
+    // refill the slot read LAG stages ago (every warp has normally left it)
+    // with stage r + STAGES; after a timeout the wait returns false at once
+    const int r = i - G::LAG;
+    if (r >= 0 && r + STAGES < nst) {
+      const uint32_t rslot = (uint32_t)r % STAGES, rpar = ((uint32_t)r / STAGES) & 1u;
+      if (pair_wait(empty_s + 8u * rslot, rpar, abort)) issue(rslot);
     }
   }
   cp_async_wait<0>();  // this thread's copies (all consumed, unless a wait gave up)
