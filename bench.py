@@ -233,9 +233,8 @@ def aggregate_replicas(total_ms: float, steps: int, dist=None, device=None):
 
 
 def contraction_flops(plan) -> float:
-    """Algorithmic flops of one contraction launch (analysis or synthesis),
-    counted as the measurement plan states them: per scale j and l in its
-    support, (l+1)^2 (m', m >= 0) triples, each Delta * f (2 flops) plus one
+    """Algorithmic flops of one contraction launch (analysis or synthesis):
+    per scale j and l in its support, (l+1)^2 (m', m >= 0) triples, each Delta * f (2 flops) plus one
     complex-by-real multiply-add (4 flops) per order n: 2 + 4N per triple
     (1.58e10 at L=1024, N=5).  The kernel shares one multiply-add between
     the orders +-n (the rows of -n equal those of n up to (-1)^{l+m'}), so it
@@ -318,7 +317,7 @@ def recorded_traffic(stage: str):
 def roofline(pm, mean_stage, ms_per_step):
     """Roofline of every timed launch and of the dominant one (largest mean
     duration), from the live CUDA-event durations; and the round trip against
-    the sum of the stage roofs of the measurement plan: per direction the
+    the sum of the stage roofs: per direction the
     contraction at max(Delta bytes / HBM, 2+4N flops per triple / FP32 peak)
     and the FFT passes at (W + f bytes) / HBM."""
     hbm, sm_max, peak_src = peaks()

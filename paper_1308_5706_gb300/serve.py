@@ -62,7 +62,7 @@ class Request:
 def poisson_workload(rate: float, duration: float, seed: int, L_range=(32, 2048), N_range=(1, 8),
                      lams=(2.0, 3.0), p_synthesis=0.5, Ls=None) -> List[Request]:
     """Poisson arrivals; L uniform over the set `Ls` when given (e.g. the
-    powers of two a survey pipeline uses), else log-uniform in `L_range`;
+    powers of two an observation pipeline uses), else log-uniform in `L_range`;
     N uniform, lambda uniform in `lams`; each synthesis request consumes the
     oldest not yet consumed analysis."""
     rng = np.random.Generator(np.random.PCG64(seed))
