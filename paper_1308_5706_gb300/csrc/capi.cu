@@ -999,9 +999,9 @@ void plan_build_typed(s2dw_plan_s* p, const double* kap_d, const double* phi_d, 
   };
   const bool pairc = sizeof(T) == sizeof(float);  // tile-pair contraction (FP32 plans)
   const int NH = (N + 1) / 2;
-  p->Lr = L + 8;  // a contraction stage (up to eight l) may read seven l past the last
-  p->Lrphi = p->Lphi + 8;
-  p->Lrf = L + 8;
+  p->Lr = L + kPairPadL;  // read-ahead rows of the tile-pair contraction
+  p->Lrphi = p->Lphi + kPairPadL;
+  p->Lrf = L + kPairPadL;
   const int nbw = (L + 31) / 32, nbp = (p->Lphi + 31) / 32;
   const size_t o_RS = pairc ? take(0) : take((size_t)L * 2 * NH * p->Lp * sizeof(T));
   const size_t o_RSphi = pairc ? take(0) : take((size_t)p->Lphi * p->Lphip * sizeof(T));

@@ -48,6 +48,12 @@ struct PairTask {
   long long dbase;
 };
 
+// l rows of padding after the tables the tile-pair contraction streams (the
+// pair table's last run, the R rows and f values of each block): a pipeline
+// stage of up to eight l may read seven l past a tile's last l; the values
+// read there never enter the sums.
+constexpr int kPairPadL = 8;
+
 // Pair table of reach Lmax (a multiple of 32): pairs ordered by q, then p;
 // the run of pair (p, q) holds Lmax - 32 q blocks of 32 x 32 entries.
 // Entry of its first block (l = 32 q):
@@ -58,7 +64,7 @@ __host__ __device__ __forceinline__ long long pair_run_base(int p, int q, int Lm
 }
 // entries of the whole table (+ one stage of read-ahead past the last run)
 __host__ __device__ __forceinline__ long long pair_table_entries(int Lmax) {
-  return pair_run_base(0, Lmax / 32, Lmax) + 8 * 1024;  // a stage may read seven l past a run's end
+  return pair_run_base(0, Lmax / 32, Lmax) + kPairPadL * 1024;
 }
 
 struct TileTask {

@@ -277,8 +277,8 @@ cudaError_t launch_pair_table(float* out, const double* d64, int Lmax, cudaStrea
   k_pair_table<<<grid, 256, 0, st>>>(out, d64, Lmax);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // the read-ahead stage after the last run
-  return cudaMemsetAsync(out + pair_run_base(0, B, Lmax), 0, 2 * 1024 * sizeof(float), st);
+  // the read-ahead padding after the last run
+  return cudaMemsetAsync(out + pair_run_base(0, B, Lmax), 0, (size_t)kPairPadL * 1024 * sizeof(float), st);
 }
 
 // R rows in the layout of the tile-pair contraction:
